@@ -1,0 +1,52 @@
+"""End-to-end checks of the oracle (CPU): the whole path is the composition
+of its steps, and strong planted bursts come back as boxes that overlap
+their ground truth (informational accuracy, as the paper itself reports a
+mean IoU near 63%, Sec. VI-A)."""
+import numpy as np
+
+import oracle
+from paper_2603_20481_gb300 import synth
+
+
+def _iou(a, b):
+    t0, t1 = max(a[0], b[0]), min(a[1], b[1])
+    f0, f1 = max(a[2], b[2]), min(a[3], b[3])
+    if t1 < t0 or f1 < f0:
+        return 0.0
+    inter = (t1 - t0 + 1) * (f1 - f0 + 1)
+    ua = (a[1] - a[0] + 1) * (a[3] - a[2] + 1)
+    ub = (b[1] - b[0] + 1) * (b[3] - b[2] + 1)
+    return inter / (ua + ub - inter)
+
+
+def test_detect_is_the_composition_of_its_steps():
+    cap = synth.make_capture(1 << 16, 20e6, 4, 77, fft_size=256, hop=128,
+                             bw_hz=(1e6, 3e6), dur_s=(0.2e-3, 1e-3), snr_db=(10, 20),
+                             tone_fraction=0.0)
+    boxes, img, mx = oracle.detect(cap.iq, 256, 128)
+    P = oracle.stft_power(cap.iq, 256, 128)
+    assert mx == P.max()
+    q = oracle.quantize(P, oracle.hi_db_of(mx))
+    assert np.array_equal(q, img)
+    assert np.array_equal(oracle.detect_image(q), boxes)
+    # anchoring on hi_db equal to the capture max gives the same image
+    b2, img2, _ = oracle.detect(cap.iq, 256, 128, oracle.params(range_mode=1, hi_db=oracle.hi_db_of(mx)))
+    assert np.array_equal(img2, img) and np.array_equal(b2, boxes)
+
+
+def test_strong_planted_bursts_are_found():
+    hits, total = 0, 0
+    for seed in (11, 12, 13):
+        cap = synth.make_capture(1 << 18, 20e6, 5, seed, fft_size=512, hop=256,
+                                 bw_hz=(1e6, 3e6), dur_s=(1e-3, 3e-3), snr_db=(12, 20),
+                                 tone_fraction=0.0)
+        gt = synth.gt_boxes(cap)
+        boxes, _, _ = oracle.detect(cap.iq, 512, 256)
+        for i, g in enumerate(gt):
+            if any(_iou(g, h) > 0 for j, h in enumerate(gt) if j != i):
+                continue            # overlapping emitters merge; skip them
+            total += 1
+            best = max((_iou(g, b[:4]) for b in boxes), default=0.0)
+            hits += best >= 0.5
+    assert total >= 8
+    assert hits >= 0.8 * total
