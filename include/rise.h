@@ -1,0 +1,206 @@
+/*
+ * rise.h -- C ABI of the GB300 RISE library: complex IQ captures in,
+ * detected time-frequency boxes out.
+ *
+ * The calls follow the paper's statement of the problem (RISE, arXiv
+ * 2603.20481, Sec. III-A-1): a capture of I/Q samples becomes a T x F
+ * time-frequency plot by N_FFT-point FFTs over consecutive segments
+ * (F = N_FFT), and every detected energy block is reported as a bounding box
+ * B = (f0, f1, t0, t1) (Eq. 1).  The image pipeline between the two is the
+ * one of Sec. IV-B: PSD-based column pruning around the noise floor N0,
+ * per-column Otsu binarisation (Eq. 4), one 2D closing, one 2D opening and
+ * one horizontal 1D opening with 3x3 / 1x3 all-ones elements (Eq. 5), and
+ * 4-connected component labelling with min/max boxes.
+ *
+ * Conventions for every call:
+ *  - Return value: RISE_OK (0) or a negative RISE_E* code; rise_strerror()
+ *    names it.  Arguments are validated on the host before any launch; a
+ *    rejected call changes nothing.
+ *  - Pointers named *_dev are device pointers on the context's device; all
+ *    other pointers are host pointers.  The caller owns every buffer it
+ *    passes; the context owns its device scratch (grown on demand, up to
+ *    rise_config.mem_budget) and frees it in rise_destroy().
+ *  - Work is issued on the context's stream.  Every call that returns boxes
+ *    is synchronous: on return the boxes are in host memory.
+ *  - A context is used by one host thread at a time.
+ *  - Image layout: row-major [T][F] uint8, row t = frame t (time), column f
+ *    = frequency cell; column f holds FFT bin (f + F/2) mod F, so DC sits in
+ *    column F/2 and column 0 is the most negative frequency.
+ */
+#ifndef RISE_H
+#define RISE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define RISE_OK 0
+#define RISE_EINVAL (-1)    /* bad argument (sizes, pointers, thresholds)      */
+#define RISE_ENOMEM (-2)    /* device scratch would exceed mem_budget / OOM     */
+#define RISE_ETRUNC (-3)    /* more boxes than `cap`; first `cap` returned      */
+#define RISE_ECUDA (-4)     /* a CUDA runtime call failed                       */
+#define RISE_ETIMEOUT (-5)  /* a bounded device-side wait gave up               */
+#define RISE_EINTERNAL (-6) /* a kernel's own consistency check failed          */
+
+/* ---- limits ------------------------------------------------------------ */
+#define RISE_MIN_FFT 256
+#define RISE_MAX_FFT 8192
+#define RISE_MAX_ROWS 524288 /* T <= 2^19 keeps the exact Otsu compare in 128 bits */
+
+/* ---- 8-bit range anchoring --------------------------------------------- */
+#define RISE_RANGE_AUTO_MAX 0 /* top level = the capture's largest |X|^2      */
+#define RISE_RANGE_FIXED 1    /* top level = hi_db (10 log10 |X|^2 units)     */
+
+typedef struct rise_ctx rise_ctx;
+
+/* Context configuration.  Zero fields take the defaults noted. */
+typedef struct {
+  int device;          /* CUDA device ordinal                                  */
+  void *cuda_stream;   /* cudaStream_t for all work; NULL = a stream the ctx   *
+                        * creates and owns                                     */
+  int64_t max_samples; /* samples to pre-size scratch for (0: grow on demand)  */
+  int max_fft;         /* largest FFT to pre-size for (0: grow on demand)      */
+  int64_t max_boxes;   /* device box buffer to pre-size (0: grow on demand)    */
+  size_t mem_budget;   /* cap on device scratch bytes (0: no cap)              */
+} rise_config;
+
+/* Detection parameters.  The paper leaves theta_PSD, theta_Power, the
+ * Savitzky-Golay window and the 8-bit image unspecified (Sec. IV-B);
+ * rise_thresholds_default() gives the library's reading:
+ *   range_mode = RISE_RANGE_AUTO_MAX, level_db = 0.25 (256 levels span
+ *   63.75 dB below the top), psd_offset_db = 0.5, power_offset_db = 10,
+ *   sg_half_window = 5 (11-point quadratic), morph_order = 0.
+ * Column f is kept when D*S_f >= N0 + round(psd_offset_db/level_db*D*T),
+ * with S_f the column sum of levels, N0 the lowest local minimum of the
+ * D-scaled Savitzky-Golay smoothing of S, D the smoother's integer norm.
+ * A kept column's foreground is q > theta_Otsu and q >= P_q, where P_q =
+ * ceil((N0 + round(power_offset_db/level_db*D*T)) / (D*T)).
+ * -INFINITY for an offset switches that threshold off. */
+typedef struct {
+  int range_mode;         /* RISE_RANGE_AUTO_MAX | RISE_RANGE_FIXED            */
+  double hi_db;           /* top of the 8-bit range for RISE_RANGE_FIXED       */
+  double level_db;        /* dB per 8-bit level, > 0                           */
+  double psd_offset_db;   /* theta_PSD above N0; -INFINITY: keep every column  */
+  double power_offset_db; /* theta_Power above N0; -INFINITY: no power floor   */
+  int sg_half_window;     /* Savitzky-Golay half window m, 1..16               */
+  int morph_order;        /* 0: close3x3, open3x3, open1x3 (the paper's order) *
+                           * 1: open1x3, close3x3, open3x3                     */
+} rise_thresholds;
+
+/* One detected energy block (Eq. 1 box plus per-block statistics).
+ * t0..t1 are inclusive frame (row) indices, f0..f1 inclusive frequency
+ * columns; anchor = t*F + f of the block's first pixel in raster order;
+ * area = pixels; sum_q = sum of 8-bit levels; energy_fx = sum over pixels
+ * of round(2^32 * 10^((q-255)*level_db/10)), i.e. linear power relative to
+ * the top level in 2^-32 units.  Boxes are returned in ascending anchor. */
+typedef struct {
+  int32_t t0, t1, f0, f1;
+  int64_t anchor;
+  int64_t area;
+  uint64_t sum_q;
+  uint64_t energy_fx;
+} rise_box;
+
+/* Fills *thr with the defaults listed above. */
+void rise_thresholds_default(rise_thresholds *thr);
+
+/* Creates a context on cfg->device.  *out receives the handle.
+ * Errors: RISE_EINVAL (NULL out/cfg, bad device), RISE_ECUDA. */
+int rise_create(rise_ctx **out, const rise_config *cfg);
+
+/* Frees the context and its device scratch (NULL is a no-op). */
+void rise_destroy(rise_ctx *ctx);
+
+/* Static description of a status code. */
+const char *rise_strerror(int code);
+
+/* Detects energy blocks in one capture (Sec. III-A-1 formulation).
+ *  iq_dev    device pointer to n complex64 samples, interleaved (re, im),
+ *            8-byte aligned.
+ *  n         samples; T = (n - fft_size) / hop + 1 frames; need T >= 1 and
+ *            T <= RISE_MAX_ROWS.
+ *  fft_size  F = N_FFT, a power of two in [RISE_MIN_FFT, RISE_MAX_FFT].
+ *  hop       samples between frame starts, 1..fft_size (hop = fft_size is
+ *            the paper's non-overlapping segmentation).
+ *  thr       NULL for the defaults.
+ *  out       host array of `cap` boxes (may be NULL when cap = 0).
+ *  n_boxes   receives the number of boxes found (always, also on ETRUNC).
+ * Frame t is samples [t*hop, t*hop + F) times a periodic Hann window; its
+ * |X|^2 row is quantised to 8-bit levels of level_db below the anchor
+ * (round half up, clamped to 0..255).
+ * Errors: RISE_EINVAL, RISE_ENOMEM, RISE_ETRUNC, RISE_ECUDA, RISE_EINTERNAL. */
+int rise_detect(rise_ctx *ctx, const void *iq_dev, int64_t n, int fft_size, int hop,
+                const rise_thresholds *thr, rise_box *out, int64_t cap, int64_t *n_boxes);
+
+/* As rise_detect, but iq_host is a host pointer (pinned memory gives the
+ * fastest copy): the call copies the capture into context-owned device
+ * memory on the context's stream, then runs the same path. */
+int rise_detect_host(rise_ctx *ctx, const void *iq_host, int64_t n, int fft_size, int hop,
+                     const rise_thresholds *thr, rise_box *out, int64_t cap,
+                     int64_t *n_boxes);
+
+/* Runs the image part of the path (column histogram onwards, Sec. IV-B) on
+ * a given 8-bit image: img_dev device pointer to T*F bytes, layout above,
+ * F a power of two in [RISE_MIN_FFT, RISE_MAX_FFT], 1 <= T <= RISE_MAX_ROWS.
+ * Same outputs and errors as rise_detect. */
+int rise_detect_image(rise_ctx *ctx, const uint8_t *img_dev, int64_t T, int F,
+                      const rise_thresholds *thr, rise_box *out, int64_t cap,
+                      int64_t *n_boxes);
+
+/* ---- introspection of the last detect call ----------------------------- */
+#define RISE_DBG_POWER_F32 1 /* float [T][F] |X|^2 (needs RISE_OPT_KEEP_POWER)     */
+#define RISE_DBG_IMAGE_U8 2  /* uint8 [T][F] levels                                 */
+#define RISE_DBG_HIST 3      /* uint32 [F][256] column histograms                   */
+#define RISE_DBG_COLSTATS 4  /* rise_colstat [F]                                    */
+#define RISE_DBG_FLOOR 5     /* int64 [8]: N0, delta_psd, delta_pow, P_q, D, T, F, 0 */
+#define RISE_DBG_MASK0 6     /* uint32 [T][F/32] thresholded mask, bit f%32 of word */
+#define RISE_DBG_MASK1 7     /* ... after the first morphological operation pair    */
+#define RISE_DBG_MASK2 8     /* ... after the second pair                           */
+#define RISE_DBG_MASK3 9     /* ... final mask (always kept)                        */
+#define RISE_DBG_MAXPOW 10   /* float [1]: the anchor power (largest |X|^2)          */
+#define RISE_DBG_LEVEL_EDGES 11 /* float [257]: smallest power of each level          */
+#define RISE_DBG_LAUNCHES 12 /* int64 [1]: kernels launched by this library so far,   *
+                              * process-wide (for launch accounting)                */
+
+typedef struct {
+  uint64_t S;    /* column sum of levels                                */
+  int64_t Shat;  /* D-scaled Savitzky-Golay smoothing (0 off the interior) */
+  int32_t keep;  /* 1: column survives theta_PSD                        */
+  int32_t otsu;  /* Otsu threshold, -1 when no split exists             */
+  int32_t eff;   /* smallest foreground level, 256 = none               */
+  int32_t pad;
+} rise_colstat;
+
+/* Copies the named intermediate of the last call into host memory dst
+ * (bytes must be at least its size).  Errors: RISE_EINVAL (unknown `what`,
+ * too small, nothing kept), RISE_ECUDA. */
+int rise_debug_export(rise_ctx *ctx, int what, void *dst, size_t bytes);
+
+/* ---- options -------------------------------------------------------------- */
+#define RISE_OPT_KEEP_POWER 1  /* 1: keep the float |X|^2 image of the next calls  */
+#define RISE_OPT_KEEP_MASKS 2  /* 1: keep MASK0..MASK2 of the next calls           */
+#define RISE_OPT_TIMING 3      /* 1: record per-stage device times                 */
+#define RISE_OPT_RANGE_PATH 4  /* 0: auto; 1: FFT twice (max, then quantise);      *
+                                * 2: FFT once, keep float power, quantise after    */
+
+/* Sets an option; errors: RISE_EINVAL. */
+int rise_set_option(rise_ctx *ctx, int option, int64_t value);
+
+/* Per-stage device milliseconds of the last call with RISE_OPT_TIMING on,
+ * from CUDA events recorded on the context's stream:
+ * [0] first spectrum pass (anchor max, or float power when kept),
+ * [1] level edges + second pass (8-bit image, or quantise + histogram),
+ * [2] column histogram, [3] column statistics, [4] threshold + morphology,
+ * [5] labelling and box reduction, [6] status and box readback, [7] total.
+ * Writes min(nstages, 8) values.  Errors: RISE_EINVAL. */
+int rise_stage_times(rise_ctx *ctx, float *ms, int nstages);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RISE_H */

@@ -1,0 +1,214 @@
+// Shared device helpers and host-side declarations of the RISE CUDA library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rise.h"
+
+namespace rise {
+
+// ---------------------------------------------------------------------------
+// Device error word: kernels record consistency failures here instead of
+// trapping; the host maps a nonzero word to RISE_EINTERNAL / RISE_ETIMEOUT.
+// ---------------------------------------------------------------------------
+enum : uint32_t {
+  ERR_NONE = 0,
+  ERR_RUN_CAPACITY = 1u << 0,   // more runs than the run arrays hold (host regrows)
+  ERR_UNION_LIMIT = 1u << 1,    // a union/find loop hit its iteration limit
+  ERR_ROW_RUNS = 1u << 2,       // a row holds more runs than the morphology allows
+  ERR_INDEX = 1u << 3,          // an index check failed
+};
+
+struct DeviceStatus {
+  uint32_t err;        // OR of ERR_* bits
+  uint32_t pad;
+  int64_t n_runs;      // total runs of the final mask
+  int64_t n_boxes;     // number of components
+  uint32_t max_bits;   // float bits of the anchor power
+  uint32_t pad2;
+};
+
+__device__ __forceinline__ void set_err(DeviceStatus *st, uint32_t bit) {
+  atomicOr(&st->err, bit);
+}
+
+// bits 0..b inclusive
+__device__ __forceinline__ uint32_t mask_upto(int b) {
+  return b >= 31 ? 0xffffffffu : ((2u << b) - 1u);
+}
+
+// Start bits of runs in a row word: set where the pixel is on and the pixel
+// to its left (bit b-1, or the previous word's bit 31) is off.
+__device__ __forceinline__ uint32_t run_starts(uint32_t w, uint32_t prev_word) {
+  return w & ~((w << 1) | (prev_word >> 31));
+}
+// End bits: set where the pixel is on and the pixel to its right is off.
+__device__ __forceinline__ uint32_t run_ends(uint32_t w, uint32_t next_word) {
+  return w & ~((w >> 1) | (next_word << 31));
+}
+
+// ---------------------------------------------------------------------------
+// Lock-free union-find with union by smaller index (parent[x] <= x always),
+// usable on shared or global memory through generic pointers.  Each loop is
+// bounded; hitting the bound records ERR_UNION_LIMIT.
+// ---------------------------------------------------------------------------
+constexpr int UF_LIMIT = 1 << 26;
+
+__device__ __forceinline__ int uf_find(int *parent, int x, DeviceStatus *st) {
+  for (int it = 0; it < UF_LIMIT; ++it) {
+    int p = *(volatile int *)&parent[x];
+    if (p == x) return x;
+    int gp = *(volatile int *)&parent[p];
+    // path halving: x is not a root and never becomes one, so any ancestor
+    // (all smaller than x) is a valid parent; a plain store is enough
+    if (gp != p) *(volatile int *)&parent[x] = gp;
+    x = p;
+  }
+  set_err(st, ERR_UNION_LIMIT);
+  return x;
+}
+
+__device__ __forceinline__ void uf_union(int *parent, int a, int b, DeviceStatus *st) {
+  for (int it = 0; it < UF_LIMIT; ++it) {
+    a = uf_find(parent, a, st);
+    b = uf_find(parent, b, st);
+    if (a == b) return;
+    if (a > b) { int t = a; a = b; b = t; }
+    // link the larger root under the smaller one if it is still a root
+    int old = atomicCAS(&parent[b], b, a);
+    if (old == b) return;
+  }
+  set_err(st, ERR_UNION_LIMIT);
+}
+
+// Block-wide exclusive scan of one value per thread (blockDim.x <= 1024,
+// multiple of 32).  `scratch` needs 32 entries.  Returns the exclusive
+// prefix; *total receives the block sum.
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T *scratch, T *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (blockDim.x + 31) >> 5;
+  T x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) scratch[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    T s = lane < nwarps ? scratch[lane] : T(0);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    scratch[lane] = s;  // inclusive warp-total prefix
+  }
+  __syncthreads();
+  T warp_base = warp > 0 ? scratch[warp - 1] : T(0);
+  T tot = scratch[nwarps - 1];
+  __syncthreads();
+  if (total) *total = tot;
+  return warp_base + x - v;
+}
+
+}  // namespace rise
+
+// ---------------------------------------------------------------------------
+// Host-side launchers implemented in the .cu files (internal, not exported).
+// ---------------------------------------------------------------------------
+namespace rise {
+
+// Kernels launched by the library (process-wide), for launch accounting.
+void count_launches(int k);
+long long launches_so_far();
+
+struct StftArgs {
+  const float2 *iq;       // device, n complex samples
+  int64_t n;
+  int N;                  // FFT size
+  int hop;
+  int64_t T;              // frames
+  uint8_t *img;           // [T][N] levels (quantise mode)
+  float *power;           // [T][N] |X|^2 (power mode / kept)
+  uint32_t *max_bits;     // float bits of the running max (max/power mode)
+  const float *edges;     // [257] level edges (quantise mode)
+  const float *qconst;    // [2]: 1/anchor, dB-per-level scale (quantise mode)
+  const float2 *tw;       // per-N twiddle tables (device)
+  const float *win;       // per-N Hann window (device)
+};
+
+enum StftMode { STFT_MAX = 0, STFT_QUANT = 1, STFT_POWER = 2, STFT_QUANT_POWER = 3 };
+
+// Twiddle and window tables for FFT size N (host-computed, FP64 -> float).
+size_t stft_table_floats(int N);
+void stft_fill_tables(int N, float2 *tw_host, float *win_host);
+cudaError_t launch_stft(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s);
+// Level edges from the anchor (AUTO: read from max_bits; FIXED: hi_power).
+cudaError_t launch_levels(const uint32_t *max_bits, double hi_power, int use_fixed,
+                          double level_db, float *edges, float *qconst, cudaStream_t s);
+// Quantise a stored float power image and build the column histogram.
+cudaError_t launch_quant_hist(const float *power, int64_t T, int F, const float *edges,
+                              const float *qconst, uint8_t *img, uint32_t *hist,
+                              int num_sms, cudaStream_t s);
+
+// Column histogram of an 8-bit image; hist must be zeroed by the caller.
+cudaError_t launch_hist(const uint8_t *img, int64_t T, int F, uint32_t *hist, int num_sms,
+                        cudaStream_t s);
+
+struct ColArgs {
+  const uint32_t *hist;   // [F][256]
+  int64_t T;
+  int F;
+  int m;                  // SG half window
+  int64_t D;              // SG norm
+  const int64_t *sg_c;    // device [m+1] integer SG weights
+  int64_t delta_psd;
+  int64_t delta_pow;
+  int psd_on, pow_on;
+  rise_colstat *cols;     // [F]
+  uint8_t *effm1;         // [F] eff-1 clamped to 0..255 (q > effm1 is foreground)
+  int64_t *floor_out;     // [8]
+};
+cudaError_t launch_colstats(const ColArgs &a, cudaStream_t s);
+
+struct MorphArgs {
+  const uint8_t *img;     // [T][F]
+  const uint8_t *effm1;   // [F]
+  int64_t T;
+  int F;
+  int order;
+  uint32_t *mask;         // [T][F/32] final
+  uint32_t *dbg0, *dbg1, *dbg2;  // optional stage masks
+};
+cudaError_t launch_morph(const MorphArgs &a, cudaStream_t s);
+
+struct CclArgs {
+  const uint32_t *mask;   // [T][W] final mask words, W = F/32
+  const uint8_t *img;     // [T][F]
+  int64_t T;
+  int F;
+  const uint64_t *energy; // [256] energy table
+  int64_t *row_base;      // [T+1] run offsets per row (scan output)
+  uint32_t *row_cnt;      // [T] runs per row
+  int64_t run_cap;        // capacity of the run arrays
+  int32_t *run_parent;    // [run_cap]
+  uint8_t *run_sroot;     // [run_cap] 1 = root of its strip-local component
+  rise_box *rec;          // [run_cap] per-run records (meaningful for roots)
+  int64_t *run_out;       // [run_cap + 1] compaction scan scratch
+  void *scan_tmp;         // scan scratch
+  size_t scan_tmp_bytes;
+  rise_box *boxes;        // [box_cap] output
+  int64_t box_cap;
+  DeviceStatus *status;
+};
+size_t ccl_scan_tmp_bytes(int64_t max_items);
+// Row run counts + scan: fills row_cnt, row_base and status->n_runs.
+cudaError_t launch_ccl_count(const CclArgs &a, int num_sms, cudaStream_t s);
+// Strip unions, boundary merge, reduction and compaction (needs run_cap >= n_runs,
+// checked on the device: on shortfall it sets ERR_RUN_CAPACITY and does nothing).
+cudaError_t launch_ccl_label(const CclArgs &a, int num_sms, cudaStream_t s);
+
+}  // namespace rise

@@ -1,0 +1,576 @@
+// Host side of the RISE library: the context, its device scratch, the
+// stage sequence of one detection and the exported C ABI (include/rise.h).
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace rise;
+
+namespace rise {
+static std::atomic<long long> g_launches{0};
+void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace rise
+
+namespace {
+
+struct Buf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+// Per-FFT-size tables (twiddles + Hann window), built once.
+struct Tables {
+  float2 *tw = nullptr;
+  float *win = nullptr;
+};
+
+struct Small {              // one device block of small per-call data
+  DeviceStatus status;
+  float edges[260];
+  float qconst[4];
+  int64_t floor_out[8];
+  int64_t sgc[32];
+  uint64_t energy[256];
+};
+
+}  // namespace
+
+struct rise_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t mem_budget = 0;
+  size_t allocated = 0;
+  int num_sms = 1;
+  // options
+  int keep_power = 0, keep_masks = 0, timing = 0, range_path = 0;
+  // scratch
+  Buf iq_stage, power, img, hist, cols, effm1, mask, dbg[3], row_cnt, row_base, run_parent,
+      run_sroot, rec, run_out, scan_tmp, boxes;
+  int64_t run_cap = 0;
+  Small *small = nullptr;   // device
+  Small *small_h = nullptr; // pinned host mirror for readback
+  std::map<int, Tables> tables;
+  double energy_level_db = NAN;
+  int sg_m = -1;
+  // last call
+  int64_t last_T = 0;
+  int last_F = 0;
+  const uint8_t *last_img = nullptr;
+  bool last_has_power = false, last_has_masks = false, last_valid = false;
+  double last_anchor = 0.0;
+  cudaEvent_t ev[8] = {};
+  float stage_ms[8] = {};
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) {
+  return e == cudaErrorMemoryAllocation ? RISE_ENOMEM : RISE_ECUDA;
+}
+
+#define CK(expr)                              \
+  do {                                        \
+    cudaError_t _e = (expr);                  \
+    if (_e != cudaSuccess) return cuda_fail(_e); \
+  } while (0)
+
+int ensure(rise_ctx *c, Buf &b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return RISE_OK;
+  size_t grow = bytes + bytes / 8;
+  if (c->mem_budget && c->allocated - b.bytes + grow > c->mem_budget) {
+    grow = bytes;
+    if (c->allocated - b.bytes + grow > c->mem_budget) return RISE_ENOMEM;
+  }
+  if (b.p) {
+    CK(cudaStreamSynchronize(c->stream));
+    cudaFree(b.p);
+    c->allocated -= b.bytes;
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  void *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, grow);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return RISE_ENOMEM;
+  }
+  b.p = p;
+  b.bytes = grow;
+  c->allocated += grow;
+  return RISE_OK;
+}
+
+int get_tables(rise_ctx *c, int N, Tables **out) {
+  auto it = c->tables.find(N);
+  if (it != c->tables.end()) {
+    *out = &it->second;
+    return RISE_OK;
+  }
+  const size_t nf = stft_table_floats(N);
+  std::vector<float> host(nf);
+  const size_t ntw = (nf - N) / 2;
+  stft_fill_tables(N, reinterpret_cast<float2 *>(host.data()), host.data() + 2 * ntw);
+  void *d = nullptr;
+  if (cudaMalloc(&d, nf * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return RISE_ENOMEM;
+  }
+  CK(cudaMemcpy(d, host.data(), nf * sizeof(float), cudaMemcpyHostToDevice));
+  Tables t;
+  t.tw = reinterpret_cast<float2 *>(d);
+  t.win = reinterpret_cast<float *>(d) + 2 * ntw;
+  c->tables[N] = t;
+  *out = &c->tables[N];
+  return RISE_OK;
+}
+
+bool pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int check_thresholds(const rise_thresholds &t, int F) {
+  if (!(t.level_db > 0.0) || !std::isfinite(t.level_db)) return RISE_EINVAL;
+  if (t.range_mode != RISE_RANGE_AUTO_MAX && t.range_mode != RISE_RANGE_FIXED) return RISE_EINVAL;
+  if (t.range_mode == RISE_RANGE_FIXED && !std::isfinite(t.hi_db)) return RISE_EINVAL;
+  if (std::isnan(t.psd_offset_db) || std::isnan(t.power_offset_db)) return RISE_EINVAL;
+  if (std::isinf(t.psd_offset_db) && t.psd_offset_db > 0) return RISE_EINVAL;
+  if (std::isinf(t.power_offset_db) && t.power_offset_db > 0) return RISE_EINVAL;
+  if (t.sg_half_window < 1 || t.sg_half_window > 16 || F < 2 * t.sg_half_window + 3) return RISE_EINVAL;
+  if (t.morph_order != 0 && t.morph_order != 1) return RISE_EINVAL;
+  return RISE_OK;
+}
+
+void record(rise_ctx *c, int i) {
+  if (c->timing) cudaEventRecord(c->ev[i], c->stream);
+}
+
+// Everything from the 8-bit image on: histogram (unless already built),
+// column statistics, morphology, labelling, boxes back to the host.
+int image_path(rise_ctx *c, const uint8_t *img, int64_t T, int F, const rise_thresholds &thr,
+               bool hist_ready, rise_box *out, int64_t cap, int64_t *n_boxes) {
+  Small *sm = c->small;
+  cudaStream_t s = c->stream;
+  const int Wd = F / 32;
+  if (!hist_ready) {
+    CK(cudaMemsetAsync(c->hist.p, 0, (size_t)F * 256 * sizeof(uint32_t), s));
+    CK(launch_hist(img, T, F, reinterpret_cast<uint32_t *>(c->hist.p), c->num_sms, s));
+  }
+  record(c, 3);
+  // column statistics
+  const int m = thr.sg_half_window;
+  const int64_t D = (int64_t)(2 * m - 1) * (2 * m + 1) * (2 * m + 3);
+  if (c->sg_m != m) {
+    int64_t coef[32];
+    for (int i = 0; i <= m; ++i) coef[i] = 3LL * (3LL * m * m + 3LL * m - 1) - 15LL * i * i;
+    CK(cudaMemcpyAsync(sm->sgc, coef, sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    c->sg_m = m;
+  }
+  ColArgs ca;
+  ca.hist = reinterpret_cast<const uint32_t *>(c->hist.p);
+  ca.T = T;
+  ca.F = F;
+  ca.m = m;
+  ca.D = D;
+  ca.sg_c = sm->sgc;
+  ca.psd_on = !(std::isinf(thr.psd_offset_db) && thr.psd_offset_db < 0);
+  ca.pow_on = !(std::isinf(thr.power_offset_db) && thr.power_offset_db < 0);
+  const double DT = (double)(D * T);
+  ca.delta_psd = ca.psd_on ? (int64_t)std::llround(thr.psd_offset_db / thr.level_db * DT) : 0;
+  ca.delta_pow = ca.pow_on ? (int64_t)std::llround(thr.power_offset_db / thr.level_db * DT) : 0;
+  ca.cols = reinterpret_cast<rise_colstat *>(c->cols.p);
+  ca.effm1 = reinterpret_cast<uint8_t *>(c->effm1.p);
+  ca.floor_out = sm->floor_out;
+  CK(launch_colstats(ca, s));
+  record(c, 4);
+  // mask + morphology
+  MorphArgs ma;
+  ma.img = img;
+  ma.effm1 = ca.effm1;
+  ma.T = T;
+  ma.F = F;
+  ma.order = thr.morph_order;
+  ma.mask = reinterpret_cast<uint32_t *>(c->mask.p);
+  ma.dbg0 = c->keep_masks ? reinterpret_cast<uint32_t *>(c->dbg[0].p) : nullptr;
+  ma.dbg1 = c->keep_masks ? reinterpret_cast<uint32_t *>(c->dbg[1].p) : nullptr;
+  ma.dbg2 = c->keep_masks ? reinterpret_cast<uint32_t *>(c->dbg[2].p) : nullptr;
+  CK(launch_morph(ma, s));
+  record(c, 5);
+  // labelling
+  if (c->energy_level_db != thr.level_db) {
+    uint64_t E[256];
+    for (int q = 0; q < 256; ++q)
+      E[q] = (uint64_t)std::llround(std::exp2(32.0) * std::pow(10.0, (double)(q - 255) * thr.level_db / 10.0));
+    CK(cudaMemcpyAsync(sm->energy, E, sizeof(E), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    c->energy_level_db = thr.level_db;
+  }
+  int rc;
+  if ((rc = ensure(c, c->boxes, (size_t)std::max<int64_t>(cap, 1) * sizeof(rise_box)))) return rc;
+  CclArgs la;
+  la.mask = ma.mask;
+  la.img = img;
+  la.T = T;
+  la.F = F;
+  la.energy = sm->energy;
+  la.row_base = reinterpret_cast<int64_t *>(c->row_base.p);
+  la.row_cnt = reinterpret_cast<uint32_t *>(c->row_cnt.p);
+  la.status = &sm->status;
+  la.boxes = reinterpret_cast<rise_box *>(c->boxes.p);
+  la.box_cap = cap;
+  auto bind_runs = [&]() {
+    la.run_cap = c->run_cap;
+    la.run_parent = reinterpret_cast<int32_t *>(c->run_parent.p);
+    la.run_sroot = reinterpret_cast<uint8_t *>(c->run_sroot.p);
+    la.rec = reinterpret_cast<rise_box *>(c->rec.p);
+    la.run_out = reinterpret_cast<int64_t *>(c->run_out.p);
+    la.scan_tmp = c->scan_tmp.p;
+    la.scan_tmp_bytes = c->scan_tmp.bytes;
+  };
+  bind_runs();
+  CK(launch_ccl_count(la, c->num_sms, s));
+  CK(launch_ccl_label(la, c->num_sms, s));
+  record(c, 6);
+  CK(cudaMemcpyAsync(&c->small_h->status, &sm->status, sizeof(DeviceStatus), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  DeviceStatus h = c->small_h->status;
+  if (h.err & ERR_RUN_CAPACITY) {
+    // the run arrays were too small for this mask: grow to fit and relabel
+    int64_t need = h.n_runs + h.n_runs / 4 + 1024;
+    if ((rc = ensure(c, c->run_parent, need * sizeof(int32_t)))) return rc;
+    if ((rc = ensure(c, c->run_sroot, need))) return rc;
+    if ((rc = ensure(c, c->rec, need * sizeof(rise_box)))) return rc;
+    if ((rc = ensure(c, c->run_out, (need + 1) * sizeof(int64_t)))) return rc;
+    if ((rc = ensure(c, c->scan_tmp, ccl_scan_tmp_bytes(std::max<int64_t>(need, T + 1))))) return rc;
+    c->run_cap = need;
+    bind_runs();
+    CK(cudaMemsetAsync(&sm->status.err, 0, sizeof(uint32_t), s));
+    CK(launch_ccl_label(la, c->num_sms, s));
+    record(c, 6);
+    CK(cudaMemcpyAsync(&c->small_h->status, &sm->status, sizeof(DeviceStatus), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    h = c->small_h->status;
+  }
+  if (h.err & ERR_UNION_LIMIT) return RISE_ETIMEOUT;
+  if (h.err) return RISE_EINTERNAL;
+  *n_boxes = h.n_boxes;
+  const int64_t ncopy = std::min<int64_t>(h.n_boxes, cap);
+  if (ncopy > 0 && out) {
+    CK(cudaMemcpyAsync(out, c->boxes.p, (size_t)ncopy * sizeof(rise_box), cudaMemcpyDeviceToHost, s));
+  }
+  record(c, 7);
+  CK(cudaStreamSynchronize(s));
+  if (c->timing) {
+    for (int i = 0; i < 7; ++i) cudaEventElapsedTime(&c->stage_ms[i], c->ev[i], c->ev[i + 1]);
+    cudaEventElapsedTime(&c->stage_ms[7], c->ev[0], c->ev[7]);
+  }
+  return h.n_boxes > cap ? RISE_ETRUNC : RISE_OK;
+}
+
+int prepare_image_buffers(rise_ctx *c, int64_t T, int F) {
+  int rc;
+  const size_t px = (size_t)T * F;
+  if ((rc = ensure(c, c->hist, (size_t)F * 256 * sizeof(uint32_t)))) return rc;
+  if ((rc = ensure(c, c->cols, (size_t)F * sizeof(rise_colstat)))) return rc;
+  if ((rc = ensure(c, c->effm1, (size_t)F))) return rc;
+  if ((rc = ensure(c, c->mask, px / 8))) return rc;
+  if (c->keep_masks)
+    for (auto &d : c->dbg)
+      if ((rc = ensure(c, d, px / 8))) return rc;
+  if ((rc = ensure(c, c->row_cnt, (size_t)T * sizeof(uint32_t)))) return rc;
+  if ((rc = ensure(c, c->row_base, (size_t)(T + 1) * sizeof(int64_t)))) return rc;
+  if (c->run_cap == 0) {
+    int64_t cap0 = std::max<int64_t>(1 << 20, (int64_t)(px / 256));
+    if ((rc = ensure(c, c->run_parent, cap0 * sizeof(int32_t)))) return rc;
+    if ((rc = ensure(c, c->run_sroot, cap0))) return rc;
+    if ((rc = ensure(c, c->rec, cap0 * sizeof(rise_box)))) return rc;
+    if ((rc = ensure(c, c->run_out, (cap0 + 1) * sizeof(int64_t)))) return rc;
+    c->run_cap = cap0;
+  }
+  if ((rc = ensure(c, c->scan_tmp, ccl_scan_tmp_bytes(std::max<int64_t>(c->run_cap, T + 1)))))
+    return rc;
+  return RISE_OK;
+}
+
+int detect_device(rise_ctx *c, const void *iq, int64_t n, int N, int hop,
+                  const rise_thresholds *thr_in, rise_box *out, int64_t cap, int64_t *n_boxes) {
+  rise_thresholds thr;
+  if (thr_in) thr = *thr_in;
+  else rise_thresholds_default(&thr);
+  if (!c || !iq || !n_boxes || (cap > 0 && !out) || cap < 0) return RISE_EINVAL;
+  if (!pow2(N) || N < RISE_MIN_FFT || N > RISE_MAX_FFT || hop < 1 || hop > N || n < N) return RISE_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(iq) & 7) != 0) return RISE_EINVAL;
+  const int64_t T = (n - N) / hop + 1;
+  if (T > RISE_MAX_ROWS) return RISE_EINVAL;
+  int rc = check_thresholds(thr, N);
+  if (rc) return rc;
+  CK(cudaSetDevice(c->device));
+  const int F = N;
+  const size_t px = (size_t)T * F;
+  if ((rc = prepare_image_buffers(c, T, F))) return rc;
+  if ((rc = ensure(c, c->img, px))) return rc;
+  int path = c->range_path;
+  if (path == 0) path = 1;
+  const bool want_power = c->keep_power || (path == 2 && thr.range_mode == RISE_RANGE_AUTO_MAX);
+  if (want_power && (rc = ensure(c, c->power, px * sizeof(float)))) return rc;
+  Tables *tb;
+  if ((rc = get_tables(c, N, &tb))) return rc;
+  cudaStream_t s = c->stream;
+  Small *sm = c->small;
+  record(c, 0);
+  CK(cudaMemsetAsync(&sm->status, 0, sizeof(DeviceStatus), s));
+  StftArgs a;
+  a.iq = reinterpret_cast<const float2 *>(iq);
+  a.n = n;
+  a.N = N;
+  a.hop = hop;
+  a.T = T;
+  a.img = reinterpret_cast<uint8_t *>(c->img.p);
+  a.power = want_power ? reinterpret_cast<float *>(c->power.p) : nullptr;
+  a.max_bits = &sm->status.max_bits;
+  a.edges = sm->edges;
+  a.qconst = sm->qconst;
+  a.tw = tb->tw;
+  a.win = tb->win;
+  bool hist_ready = false;
+  if (thr.range_mode == RISE_RANGE_FIXED) {
+    const double hp = std::pow(10.0, thr.hi_db / 10.0);
+    record(c, 1);
+    CK(launch_levels(a.max_bits, hp, 1, thr.level_db, sm->edges, sm->qconst, s));
+    CK(launch_stft(a, c->keep_power ? STFT_QUANT_POWER : STFT_QUANT, c->num_sms, s));
+    c->last_anchor = hp;
+  } else if (path == 2) {
+    CK(launch_stft(a, STFT_POWER, c->num_sms, s));
+    record(c, 1);
+    CK(launch_levels(a.max_bits, 0.0, 0, thr.level_db, sm->edges, sm->qconst, s));
+    CK(cudaMemsetAsync(c->hist.p, 0, (size_t)F * 256 * sizeof(uint32_t), s));
+    CK(launch_quant_hist(a.power, T, F, sm->edges, sm->qconst, a.img,
+                         reinterpret_cast<uint32_t *>(c->hist.p), c->num_sms, s));
+    hist_ready = true;
+  } else {
+    CK(launch_stft(a, STFT_MAX, c->num_sms, s));
+    record(c, 1);
+    CK(launch_levels(a.max_bits, 0.0, 0, thr.level_db, sm->edges, sm->qconst, s));
+    CK(launch_stft(a, c->keep_power ? STFT_QUANT_POWER : STFT_QUANT, c->num_sms, s));
+  }
+  record(c, 2);
+  c->last_T = T;
+  c->last_F = F;
+  c->last_img = a.img;
+  c->last_has_power = want_power;
+  c->last_has_masks = c->keep_masks != 0;
+  c->last_valid = true;
+  rc = image_path(c, a.img, T, F, thr, hist_ready, out, cap, n_boxes);
+  if (thr.range_mode != RISE_RANGE_FIXED) {
+    uint32_t bits = c->small_h->status.max_bits;
+    float mf;
+    std::memcpy(&mf, &bits, 4);
+    c->last_anchor = mf;
+  }
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+void rise_thresholds_default(rise_thresholds *t) {
+  if (!t) return;
+  t->range_mode = RISE_RANGE_AUTO_MAX;
+  t->hi_db = 0.0;
+  t->level_db = 0.25;
+  t->psd_offset_db = 0.5;
+  t->power_offset_db = 10.0;
+  t->sg_half_window = 5;
+  t->morph_order = 0;
+}
+
+const char *rise_strerror(int code) {
+  switch (code) {
+    case RISE_OK: return "ok";
+    case RISE_EINVAL: return "invalid argument";
+    case RISE_ENOMEM: return "out of device memory or over the memory budget";
+    case RISE_ETRUNC: return "more boxes than the output capacity";
+    case RISE_ECUDA: return "CUDA runtime error";
+    case RISE_ETIMEOUT: return "bounded device-side wait gave up";
+    case RISE_EINTERNAL: return "internal consistency check failed";
+  }
+  return "unknown status";
+}
+
+int rise_create(rise_ctx **out, const rise_config *cfg) {
+  if (!out || !cfg) return RISE_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    cudaGetLastError();
+    return RISE_ECUDA;
+  }
+  if (cfg->device < 0 || cfg->device >= ndev) return RISE_EINVAL;
+  rise_ctx *c = new (std::nothrow) rise_ctx();
+  if (!c) return RISE_ENOMEM;
+  c->device = cfg->device;
+  c->mem_budget = cfg->mem_budget;
+  int rc = RISE_OK;
+  do {
+    if (cudaSetDevice(c->device) != cudaSuccess) { rc = RISE_ECUDA; break; }
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (cfg->cuda_stream) {
+      c->stream = reinterpret_cast<cudaStream_t>(cfg->cuda_stream);
+    } else {
+      if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { rc = RISE_ECUDA; break; }
+      c->own_stream = true;
+    }
+    if (cudaMalloc(&c->small, sizeof(Small)) != cudaSuccess) { rc = RISE_ENOMEM; break; }
+    if (cudaMallocHost(&c->small_h, sizeof(Small)) != cudaSuccess) { rc = RISE_ENOMEM; break; }
+    cudaMemset(c->small, 0, sizeof(Small));
+    for (auto &e : c->ev)
+      if (cudaEventCreate(&e) != cudaSuccess) { rc = RISE_ECUDA; break; }
+    if (rc) break;
+    if (cfg->max_fft && (cfg->max_fft < RISE_MIN_FFT || cfg->max_fft > RISE_MAX_FFT || !pow2(cfg->max_fft))) {
+      rc = RISE_EINVAL;
+      break;
+    }
+    if (cfg->max_samples < 0 || cfg->max_boxes < 0) { rc = RISE_EINVAL; break; }
+    if (cfg->max_samples > 0) {
+      // the 8-bit image of a capture with hop >= F/2 has at most 2 pixels per sample
+      if ((rc = ensure(c, c->img, (size_t)cfg->max_samples * 2))) break;
+    }
+    if (cfg->max_boxes > 0 && (rc = ensure(c, c->boxes, cfg->max_boxes * sizeof(rise_box)))) break;
+  } while (0);
+  if (rc) {
+    cudaGetLastError();
+    rise_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return RISE_OK;
+}
+
+void rise_destroy(rise_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  Buf *bufs[] = {&c->iq_stage, &c->power, &c->img, &c->hist, &c->cols, &c->effm1, &c->mask,
+                 &c->dbg[0], &c->dbg[1], &c->dbg[2], &c->row_cnt, &c->row_base,
+                 &c->run_parent, &c->run_sroot, &c->rec, &c->run_out, &c->scan_tmp, &c->boxes};
+  for (Buf *b : bufs)
+    if (b->p) cudaFree(b->p);
+  for (auto &kv : c->tables) cudaFree(kv.second.tw);
+  if (c->small) cudaFree(c->small);
+  if (c->small_h) cudaFreeHost(c->small_h);
+  for (auto &e : c->ev)
+    if (e) cudaEventDestroy(e);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+int rise_detect(rise_ctx *c, const void *iq_dev, int64_t n, int fft_size, int hop,
+                const rise_thresholds *thr, rise_box *out, int64_t cap, int64_t *n_boxes) {
+  return detect_device(c, iq_dev, n, fft_size, hop, thr, out, cap, n_boxes);
+}
+
+int rise_detect_host(rise_ctx *c, const void *iq_host, int64_t n, int fft_size, int hop,
+                     const rise_thresholds *thr, rise_box *out, int64_t cap, int64_t *n_boxes) {
+  if (!c || !iq_host || n <= 0) return RISE_EINVAL;
+  CK(cudaSetDevice(c->device));
+  int rc = ensure(c, c->iq_stage, (size_t)n * 8);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(c->iq_stage.p, iq_host, (size_t)n * 8, cudaMemcpyHostToDevice, c->stream));
+  return detect_device(c, c->iq_stage.p, n, fft_size, hop, thr, out, cap, n_boxes);
+}
+
+int rise_detect_image(rise_ctx *c, const uint8_t *img_dev, int64_t T, int F,
+                      const rise_thresholds *thr_in, rise_box *out, int64_t cap, int64_t *n_boxes) {
+  rise_thresholds thr;
+  if (thr_in) thr = *thr_in;
+  else rise_thresholds_default(&thr);
+  if (!c || !img_dev || !n_boxes || (cap > 0 && !out) || cap < 0) return RISE_EINVAL;
+  if (!pow2(F) || F < RISE_MIN_FFT || F > RISE_MAX_FFT || T < 1 || T > RISE_MAX_ROWS) return RISE_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(img_dev) & 31) != 0) return RISE_EINVAL;
+  int rc = check_thresholds(thr, F);
+  if (rc) return rc;
+  CK(cudaSetDevice(c->device));
+  if ((rc = prepare_image_buffers(c, T, F))) return rc;
+  record(c, 0);
+  CK(cudaMemsetAsync(&c->small->status, 0, sizeof(DeviceStatus), c->stream));
+  record(c, 1);
+  record(c, 2);
+  c->last_T = T;
+  c->last_F = F;
+  c->last_img = img_dev;
+  c->last_has_power = false;
+  c->last_has_masks = c->keep_masks != 0;
+  c->last_valid = true;
+  return image_path(c, img_dev, T, F, thr, false, out, cap, n_boxes);
+}
+
+int rise_set_option(rise_ctx *c, int option, int64_t value) {
+  if (!c) return RISE_EINVAL;
+  switch (option) {
+    case RISE_OPT_KEEP_POWER: c->keep_power = value != 0; return RISE_OK;
+    case RISE_OPT_KEEP_MASKS: c->keep_masks = value != 0; return RISE_OK;
+    case RISE_OPT_TIMING: c->timing = value != 0; return RISE_OK;
+    case RISE_OPT_RANGE_PATH:
+      if (value < 0 || value > 2) return RISE_EINVAL;
+      c->range_path = (int)value;
+      return RISE_OK;
+  }
+  return RISE_EINVAL;
+}
+
+int rise_stage_times(rise_ctx *c, float *ms, int nstages) {
+  if (!c || !ms || nstages < 0) return RISE_EINVAL;
+  for (int i = 0; i < nstages && i < 8; ++i) ms[i] = c->stage_ms[i];
+  return RISE_OK;
+}
+
+int rise_debug_export(rise_ctx *c, int what, void *dst, size_t bytes) {
+  if (!c || !dst || !c->last_valid) return RISE_EINVAL;
+  CK(cudaSetDevice(c->device));
+  const int64_t T = c->last_T;
+  const int F = c->last_F;
+  const size_t px = (size_t)T * F;
+  const void *src = nullptr;
+  size_t need = 0;
+  switch (what) {
+    case RISE_DBG_POWER_F32:
+      if (!c->last_has_power) return RISE_EINVAL;
+      src = c->power.p; need = px * sizeof(float); break;
+    case RISE_DBG_IMAGE_U8: src = c->last_img; need = px; break;
+    case RISE_DBG_HIST: src = c->hist.p; need = (size_t)F * 256 * sizeof(uint32_t); break;
+    case RISE_DBG_COLSTATS: src = c->cols.p; need = (size_t)F * sizeof(rise_colstat); break;
+    case RISE_DBG_FLOOR: src = c->small->floor_out; need = 8 * sizeof(int64_t); break;
+    case RISE_DBG_MASK0: case RISE_DBG_MASK1: case RISE_DBG_MASK2:
+      if (!c->last_has_masks) return RISE_EINVAL;
+      src = c->dbg[what - RISE_DBG_MASK0].p; need = px / 8; break;
+    case RISE_DBG_MASK3: src = c->mask.p; need = px / 8; break;
+    case RISE_DBG_MAXPOW: {
+      if (bytes < sizeof(float)) return RISE_EINVAL;
+      float v = (float)c->last_anchor;
+      std::memcpy(dst, &v, sizeof v);
+      return RISE_OK;
+    }
+    case RISE_DBG_LEVEL_EDGES: src = c->small->edges; need = 257 * sizeof(float); break;
+    case RISE_DBG_LAUNCHES: {
+      if (bytes < sizeof(int64_t)) return RISE_EINVAL;
+      int64_t v = (int64_t)launches_so_far();
+      std::memcpy(dst, &v, sizeof v);
+      return RISE_OK;
+    }
+    default: return RISE_EINVAL;
+  }
+  if (bytes < need || !src) return RISE_EINVAL;
+  CK(cudaMemcpyAsync(dst, src, need, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return RISE_OK;
+}
+
+}  // extern "C"

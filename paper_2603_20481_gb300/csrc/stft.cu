@@ -1,0 +1,400 @@
+// Windowed STFT, |X|^2 and the 8-bit level image (RISE Sec. III-A-1, the TF
+// plot; the 8-bit image is the library's reading, anchored on a top power).
+//
+// One frame of N complex samples is transformed by N/16 threads, each
+// holding 16 values in registers.  N = 16^a * r (r in {1,2,4,8}): a radix-16
+// passes in registers (each thread one 16-point DFT) plus one pass of radix
+// r (each thread 16/r DFTs).  Between passes the data cross shared memory
+// once, in a layout padded by one slot per 16 so that every 16-lane group
+// hits 16 distinct 8-byte bank pairs.  The decomposition is the
+// decimation-in-frequency four-step recursion: pass i splits the current
+// sub-transform of length M into R interleaved pieces, DFTs over the slow
+// index, applies the twiddle W_M^(j p) and hands output digit p to the
+// next sub-problem, so the last pass leaves X[k] in natural order.
+//
+// Epilogues: MAX (running max of |X|^2 for the anchor), QUANT (8-bit level
+// per bin, stored with DC in column N/2), POWER (float |X|^2 stored plus the
+// running max) and QUANT_POWER (both).
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace rise {
+namespace {
+
+constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
+
+template <int N>
+struct Plan {
+  static constexpr int LOG2N = ilog2c(N);
+  static constexpr int NP16 = LOG2N / 4;
+  static constexpr int RLAST = 1 << (LOG2N % 4);
+  static constexpr int NPASS = NP16 + (RLAST > 1 ? 1 : 0);
+  static constexpr int TPF = N / 16;                       // threads per frame
+  static constexpr int FPB = TPF >= 256 ? 1 : 256 / TPF;   // frames per block step
+  static constexpr int THREADS = TPF * FPB;
+  static constexpr int SLOT = N + N / 16;                  // padded complex per frame
+  static constexpr int radix(int i) { return i < NP16 ? 16 : RLAST; }
+  static constexpr int lprev(int i) { return i == 0 ? 1 : lprev(i - 1) * radix(i - 1); }
+  static constexpr int mi(int i) { return N / lprev(i); }
+  static constexpr int mp(int i) { return mi(i) / radix(i); }
+  // twiddle tables: pass 0 [15][N/16] kept in registers, passes 1..NPASS-2 in smem
+  static constexpr int tw_off(int i) { return i == 0 ? 0 : tw_off(i - 1) + 15 * mp(i - 1); }
+  static constexpr int TW_TOTAL = tw_off(NPASS - 1);
+  static constexpr int TW_REST = TW_TOTAL - 15 * (N / 16);
+};
+
+__device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 w) {
+  return make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+}
+__device__ __forceinline__ float2 mul_negi(float2 a) { return make_float2(a.y, -a.x); }  // a * (-i)
+
+constexpr float kR = 0.70710678118654752440f;   // cos(pi/4)
+constexpr float kC = 0.92387953251128675613f;   // cos(pi/8)
+constexpr float kS = 0.38268343236508977173f;   // sin(pi/8)
+
+// a * (r - i r)  (W_8^1 = W_16^2)
+__device__ __forceinline__ float2 mul_w8_1(float2 a) { return make_float2(kR * (a.x + a.y), kR * (a.y - a.x)); }
+// a * (-r - i r)  (W_8^3 = W_16^6)
+__device__ __forceinline__ float2 mul_w8_3(float2 a) { return make_float2(kR * (a.y - a.x), -kR * (a.x + a.y)); }
+
+// forward DFTs in place, natural order, X[k] = sum_n x[n] e^{-2 pi i n k / R}
+__device__ __forceinline__ void dft2(float2 &a, float2 &b) {
+  float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+__device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3) {
+  float2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = mul_negi(csub(a1, a3));
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  a1 = cadd(t1, t3);
+  a3 = csub(t1, t3);
+}
+__device__ __forceinline__ void dft8(float2 *v) {
+  // n = 2 n1 + n2, k = k1 + 4 k2
+  dft4(v[0], v[2], v[4], v[6]);
+  dft4(v[1], v[3], v[5], v[7]);
+  float2 b1 = mul_w8_1(v[3]), b2 = mul_negi(v[5]), b3 = mul_w8_3(v[7]);
+  float2 x0 = cadd(v[0], v[1]), x4 = csub(v[0], v[1]);
+  float2 x1 = cadd(v[2], b1), x5 = csub(v[2], b1);
+  float2 x2 = cadd(v[4], b2), x6 = csub(v[4], b2);
+  float2 x3 = cadd(v[6], b3), x7 = csub(v[6], b3);
+  v[0] = x0; v[1] = x1; v[2] = x2; v[3] = x3; v[4] = x4; v[5] = x5; v[6] = x6; v[7] = x7;
+}
+__device__ __forceinline__ void dft16(float2 *v) {
+  // n = 4 n1 + n2, k = k1 + 4 k2: DFT4 over n1, twiddle W16^(n2 k1), DFT4 over n2
+  dft4(v[0], v[4], v[8], v[12]);
+  dft4(v[1], v[5], v[9], v[13]);
+  dft4(v[2], v[6], v[10], v[14]);
+  dft4(v[3], v[7], v[11], v[15]);
+  // y[n2][k1] sits at v[4 k1 + n2]
+  v[5] = cmul(v[5], make_float2(kC, -kS));    // n2=1,k1=1: W^1
+  v[9] = mul_w8_1(v[9]);                      // n2=1,k1=2: W^2
+  v[13] = cmul(v[13], make_float2(kS, -kC));  // n2=1,k1=3: W^3
+  v[6] = mul_w8_1(v[6]);                      // n2=2,k1=1: W^2
+  v[10] = mul_negi(v[10]);                    // n2=2,k1=2: W^4
+  v[14] = mul_w8_3(v[14]);                    // n2=2,k1=3: W^6
+  v[7] = cmul(v[7], make_float2(kS, -kC));    // n2=3,k1=1: W^3
+  v[11] = mul_w8_3(v[11]);                    // n2=3,k1=2: W^6
+  v[15] = cmul(v[15], make_float2(-kC, kS));  // n2=3,k1=3: W^9
+  dft4(v[0], v[1], v[2], v[3]);
+  dft4(v[4], v[5], v[6], v[7]);
+  dft4(v[8], v[9], v[10], v[11]);
+  dft4(v[12], v[13], v[14], v[15]);
+  // X[k1 + 4 k2] is at v[4 k1 + k2]: transpose 4x4 to natural order
+  float2 t;
+  t = v[1]; v[1] = v[4]; v[4] = t;
+  t = v[2]; v[2] = v[8]; v[8] = t;
+  t = v[3]; v[3] = v[12]; v[12] = t;
+  t = v[6]; v[6] = v[9]; v[9] = t;
+  t = v[7]; v[7] = v[13]; v[13] = t;
+  t = v[11]; v[11] = v[14]; v[14] = t;
+}
+
+template <int R>
+__device__ __forceinline__ void dft_r(float2 *v) {
+  if constexpr (R == 16) dft16(v);
+  else if constexpr (R == 8) dft8(v);
+  else if constexpr (R == 4) dft4(v[0], v[1], v[2], v[3]);
+  else dft2(v[0], v[1]);
+}
+
+constexpr float kGuard = 1.0e-3f;   // |fast level coordinate error| is below 1e-4
+
+// 8-bit level of power P: the count of edges[1..255] that P reaches.  A fast
+// estimate from log2(P / anchor) is trusted away from level edges; within
+// kGuard of an edge the power is compared against the exact edge table.
+__device__ __forceinline__ int level_of(float P, float inv_anchor, float c1, const float *edges) {
+  float v = fmaf(__log2f(P * inv_anchor), c1, 255.5f);
+  float fl = floorf(v);
+  float fr = v - fl;
+  int q = (int)fminf(fmaxf(fl, 0.0f), 255.0f);
+  if ((fr < kGuard || fr > 1.0f - kGuard) && v > 1.0f - 2.0f * kGuard && v < 255.0f + 2.0f * kGuard) {
+    for (int it = 0; it < 256 && q < 255 && P >= edges[q + 1]; ++it) ++q;
+    for (int it = 0; it < 256 && q > 0 && P < edges[q]; ++it) --q;
+  }
+  return q;
+}
+
+template <int N, int I, bool FIRST>
+__device__ __forceinline__ void fft_pass(float2 (&v)[16], const float2 *src, float2 *dst, int tau,
+                                         const float2 (&tw0)[15], const float2 *twr) {
+  using PL = Plan<N>;
+  constexpr int R = PL::radix(I);
+  constexpr int MI = PL::mi(I), MP = PL::mp(I), NR = N / R;
+  constexpr bool LAST = (I == PL::NPASS - 1);
+  if constexpr (!FIRST) {
+#pragma unroll
+    for (int s = 0; s < 16 / R; ++s) {
+      const int d = tau + (N / 16) * s;
+      const int P = d / MP, j = d % MP;
+#pragma unroll
+      for (int a = 0; a < R; ++a) v[s * R + a] = src[padi(P * MI + a * MP + j)];
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < 16 / R; ++s) dft_r<R>(&v[s * R]);
+  if constexpr (!LAST) {
+    static_assert(R == 16, "only the last pass may have a radix below 16");
+    if constexpr (I == 0) {
+#pragma unroll
+      for (int p = 1; p < 16; ++p) v[p] = cmul(v[p], tw0[p - 1]);
+    } else {
+      const int j = tau % MP;
+      const float2 *t = twr + (PL::tw_off(I) - 15 * (N / 16));
+#pragma unroll
+      for (int p = 1; p < 16; ++p) v[p] = cmul(v[p], t[(p - 1) * MP + j]);
+    }
+#pragma unroll
+    for (int p = 0; p < 16; ++p) dst[padi(tau + p * NR)] = v[p];
+  }
+}
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(Plan<N>::THREADS)
+stft_kernel(StftArgs a, int64_t frames_per_block) {
+  using PL = Plan<N>;
+  constexpr int TPF = PL::TPF, FPB = PL::FPB, SLOT = PL::SLOT, NPASS = PL::NPASS;
+  constexpr bool DO_MAX = (MODE == STFT_MAX || MODE == STFT_POWER);
+  constexpr bool DO_Q = (MODE == STFT_QUANT || MODE == STFT_QUANT_POWER);
+  constexpr bool DO_P = (MODE == STFT_POWER || MODE == STFT_QUANT_POWER);
+  extern __shared__ float2 smem[];
+  float2 *buf[2] = {smem, smem + FPB * SLOT};
+  float2 *twr = smem + 2 * FPB * SLOT;
+  float *edges = reinterpret_cast<float *>(twr + PL::TW_REST);
+  __shared__ float red[32];
+
+  const int tid = threadIdx.x;
+  const int slot = tid / TPF, tau = tid % TPF;
+
+  float win[16];
+  float2 tw0[15];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) win[i] = __ldg(&a.win[i * (N / 16) + tau]);
+#pragma unroll
+  for (int p = 1; p < 16; ++p) tw0[p - 1] = __ldg(&a.tw[(p - 1) * (N / 16) + tau]);
+  for (int i = tid; i < PL::TW_REST; i += PL::THREADS) twr[i] = a.tw[15 * (N / 16) + i];
+  float inv_anchor = 0.f, c1 = 0.f;
+  if constexpr (DO_Q) {
+    for (int i = tid; i < 257; i += PL::THREADS) edges[i] = a.edges[i];
+    inv_anchor = a.qconst[0];
+    c1 = a.qconst[1];
+  }
+  __syncthreads();
+
+  const int64_t f_begin = (int64_t)blockIdx.x * frames_per_block;
+  const int64_t f_end = min(a.T, f_begin + frames_per_block);
+  float run_max = 0.0f;
+  int parity = 0;
+  for (int64_t t0 = f_begin; t0 < f_end; t0 += FPB, parity ^= ((NPASS & 1) == 0)) {
+    const int64_t t = t0 + slot;
+    const bool valid = t < f_end;
+    float2 v[16];
+    {
+      const float2 *x = a.iq + (valid ? t * (int64_t)a.hop : 0) + tau;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        float2 s = valid ? __ldg(x + i * (N / 16)) : make_float2(0.f, 0.f);
+        v[i] = make_float2(s.x * win[i], s.y * win[i]);
+      }
+    }
+    float2 *b0 = buf[parity] + slot * SLOT;
+    float2 *b1 = buf[parity ^ 1] + slot * SLOT;
+    // pass I writes buffer (I + parity) & 1, pass I+1 reads it after one barrier
+    fft_pass<N, 0, true>(v, nullptr, b0, tau, tw0, twr);
+    __syncthreads();
+    if constexpr (NPASS >= 2) {
+      fft_pass<N, 1, false>(v, b0, b1, tau, tw0, twr);
+      if constexpr (NPASS >= 3) {
+        __syncthreads();
+        fft_pass<N, 2, false>(v, b1, b0, tau, tw0, twr);
+        if constexpr (NPASS >= 4) {
+          __syncthreads();
+          fft_pass<N, 3, false>(v, b0, b1, tau, tw0, twr);
+        }
+      }
+    }
+    if (valid) {
+      constexpr int R = PL::radix(NPASS - 1);
+      uint8_t *qrow = DO_Q ? a.img + t * (int64_t)N : nullptr;
+      float *prow = DO_P ? a.power + t * (int64_t)N : nullptr;
+#pragma unroll
+      for (int s = 0; s < 16 / R; ++s) {
+#pragma unroll
+        for (int p = 0; p < R; ++p) {
+          const int k = tau + (N / 16) * s + (N / R) * p;
+          const int f = (k + N / 2) & (N - 1);
+          const float2 z = v[s * R + p];
+          const float P = fmaf(z.x, z.x, z.y * z.y);
+          if constexpr (DO_MAX) run_max = fmaxf(run_max, P);
+          if constexpr (DO_P) prow[f] = P;
+          if constexpr (DO_Q) qrow[f] = (uint8_t)level_of(P, inv_anchor, c1, edges);
+        }
+      }
+    }
+  }
+  if constexpr (DO_MAX) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) run_max = fmaxf(run_max, __shfl_xor_sync(0xffffffffu, run_max, o));
+    if ((tid & 31) == 0) red[tid >> 5] = run_max;
+    __syncthreads();
+    if (tid == 0) {
+      float m = 0.f;
+      for (int w = 0; w < PL::THREADS / 32; ++w) m = fmaxf(m, red[w]);
+      atomicMax(a.max_bits, __float_as_uint(m));   // P >= 0: bit order = value order
+    }
+  }
+}
+
+template <int N>
+size_t smem_bytes() {
+  using PL = Plan<N>;
+  return (size_t)(2 * PL::FPB * PL::SLOT + PL::TW_REST) * sizeof(float2) + 260 * sizeof(float);
+}
+
+template <int N, int MODE>
+cudaError_t launch_n(const StftArgs &a, int num_sms, cudaStream_t s) {
+  using PL = Plan<N>;
+  auto kern = stft_kernel<N, MODE>;
+  const size_t sm = smem_bytes<N>();
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, PL::THREADS, sm);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) occ = 1;
+  const int64_t steps = (a.T + PL::FPB - 1) / PL::FPB;
+  int64_t grid = std::min<int64_t>(steps, (int64_t)num_sms * occ);
+  if (grid < 1) grid = 1;
+  int64_t per = (steps + grid - 1) / grid * PL::FPB;
+  grid = (a.T + per - 1) / per;
+  kern<<<(unsigned)grid, PL::THREADS, sm, s>>>(a, per);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t launch_mode(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s) {
+  switch (mode) {
+    case STFT_MAX: return launch_n<N, STFT_MAX>(a, num_sms, s);
+    case STFT_QUANT: return launch_n<N, STFT_QUANT>(a, num_sms, s);
+    case STFT_POWER: return launch_n<N, STFT_POWER>(a, num_sms, s);
+    case STFT_QUANT_POWER: return launch_n<N, STFT_QUANT_POWER>(a, num_sms, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Edges of the 8-bit levels: level j >= 1 is reached at power
+// anchor * 10^((j - 255.5) * level_db / 10); edges[j] is the smallest float
+// not below that value, so "P >= edges[j]" is the exact comparison for a
+// float P.  edges[0] = 0, edges[256] = +inf.
+__global__ void levels_kernel(const uint32_t *max_bits, double hi_power, int use_fixed,
+                              double level_db, float *edges, float *qconst) {
+  const double M = use_fixed ? hi_power : (double)__uint_as_float(*max_bits);
+  const int j = threadIdx.x;
+  if (j == 0) {
+    edges[0] = 0.0f;
+  } else if (j == 256) {
+    edges[256] = __int_as_float(0x7f800000);
+  } else if (j < 256) {
+    const double b = M * pow(10.0, ((double)j - 255.5) * level_db / 10.0);
+    edges[j] = M > 0.0 ? __double2float_ru(b) : __int_as_float(0x7f800000);
+  }
+  if (j == 0) {
+    qconst[0] = M > 0.0 ? (float)(1.0 / M) : 0.0f;
+    qconst[1] = (float)(10.0 * log10(2.0) / level_db);
+  }
+}
+
+}  // namespace
+
+// Host plan mirror (runtime) for table construction.
+static void host_plan(int N, int &np16, int &rlast, int &npass) {
+  int l = 0;
+  while ((1 << l) < N) ++l;
+  np16 = l / 4;
+  rlast = 1 << (l % 4);
+  npass = np16 + (rlast > 1 ? 1 : 0);
+}
+
+size_t stft_table_floats(int N) {
+  int np16, rl, np;
+  host_plan(N, np16, rl, np);
+  size_t tw = 0;
+  int L = 1;
+  for (int i = 0; i < np - 1; ++i) {
+    int R = i < np16 ? 16 : rl;
+    int Mi = N / L, Mp = Mi / R;
+    tw += 15 * (size_t)Mp;
+    L *= R;
+  }
+  return 2 * tw + N;  // complex twiddles + window
+}
+
+void stft_fill_tables(int N, float2 *tw, float *win) {
+  int np16, rl, np;
+  host_plan(N, np16, rl, np);
+  const double two_pi = 6.283185307179586476925286766559;
+  size_t off = 0;
+  int L = 1;
+  for (int i = 0; i < np - 1; ++i) {
+    int R = i < np16 ? 16 : rl;
+    int Mi = N / L, Mp = Mi / R;
+    for (int p = 1; p < 16; ++p)
+      for (int j = 0; j < Mp; ++j) {
+        long long e = ((long long)j * p) % Mi;   // W_Mi^(j p)
+        double ang = two_pi * (double)e / (double)Mi;
+        tw[off + (size_t)(p - 1) * Mp + j] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+      }
+    off += 15 * (size_t)Mp;
+    L *= R;
+  }
+  for (int m = 0; m < N; ++m) win[m] = (float)(0.5 - 0.5 * std::cos(two_pi * (double)m / (double)N));
+}
+
+cudaError_t launch_stft(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s) {
+  switch (a.N) {
+    case 256: return launch_mode<256>(a, mode, num_sms, s);
+    case 512: return launch_mode<512>(a, mode, num_sms, s);
+    case 1024: return launch_mode<1024>(a, mode, num_sms, s);
+    case 2048: return launch_mode<2048>(a, mode, num_sms, s);
+    case 4096: return launch_mode<4096>(a, mode, num_sms, s);
+    case 8192: return launch_mode<8192>(a, mode, num_sms, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_levels(const uint32_t *max_bits, double hi_power, int use_fixed,
+                          double level_db, float *edges, float *qconst, cudaStream_t s) {
+  levels_kernel<<<1, 288, 0, s>>>(max_bits, hi_power, use_fixed, level_db, edges, qconst);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace rise

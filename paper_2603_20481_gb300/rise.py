@@ -1,0 +1,261 @@
+"""Python binding of the RISE C ABI (include/rise.h): argument marshalling only.
+
+Every step of the detection path runs in the CUDA library `_lib/librise.so`;
+this module converts torch tensors / numpy arrays to pointers and sizes and
+boxes back to arrays.  There is no fallback: if the library is missing the
+first use raises.  PyTorch provides device memory and the current stream.
+
+Boxes are returned as int64 arrays of shape (n, 8) with columns
+(t0, t1, f0, f1, anchor, area, sum_q, energy_fx) in anchor order.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "librise.so")
+
+RISE_OK, RISE_EINVAL, RISE_ENOMEM, RISE_ETRUNC = 0, -1, -2, -3
+RISE_ECUDA, RISE_ETIMEOUT, RISE_EINTERNAL = -4, -5, -6
+RANGE_AUTO_MAX, RANGE_FIXED = 0, 1
+DBG_POWER_F32, DBG_IMAGE_U8, DBG_HIST, DBG_COLSTATS, DBG_FLOOR = 1, 2, 3, 4, 5
+DBG_MASK0, DBG_MASK1, DBG_MASK2, DBG_MASK3, DBG_MAXPOW, DBG_LEVEL_EDGES = 6, 7, 8, 9, 10, 11
+DBG_LAUNCHES = 12
+STAGES = ("spectrum_pass1", "spectrum_pass2", "histogram", "column_stats", "morphology",
+          "labelling", "readback", "total")
+OPT_KEEP_POWER, OPT_KEEP_MASKS, OPT_TIMING, OPT_RANGE_PATH = 1, 2, 3, 4
+BOX_COLS = ("t0", "t1", "f0", "f1", "anchor", "area", "sum_q", "energy_fx")
+
+# Functions the header declares; the ABI test checks the library exports them.
+EXPORTS = ("rise_thresholds_default", "rise_create", "rise_destroy", "rise_strerror",
+           "rise_detect", "rise_detect_host", "rise_detect_image", "rise_debug_export",
+           "rise_set_option", "rise_stage_times")
+
+
+class RiseError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+class Config(C.Structure):
+    _fields_ = [("device", C.c_int), ("cuda_stream", C.c_void_p), ("max_samples", C.c_int64),
+                ("max_fft", C.c_int), ("max_boxes", C.c_int64), ("mem_budget", C.c_size_t)]
+
+
+class Thresholds(C.Structure):
+    _fields_ = [("range_mode", C.c_int), ("hi_db", C.c_double), ("level_db", C.c_double),
+                ("psd_offset_db", C.c_double), ("power_offset_db", C.c_double),
+                ("sg_half_window", C.c_int), ("morph_order", C.c_int)]
+
+
+class Box(C.Structure):
+    _fields_ = [("t0", C.c_int32), ("t1", C.c_int32), ("f0", C.c_int32), ("f1", C.c_int32),
+                ("anchor", C.c_int64), ("area", C.c_int64), ("sum_q", C.c_uint64),
+                ("energy_fx", C.c_uint64)]
+
+
+BOX_DTYPE = np.dtype([("t0", "<i4"), ("t1", "<i4"), ("f0", "<i4"), ("f1", "<i4"),
+                      ("anchor", "<i8"), ("area", "<i8"), ("sum_q", "<u8"), ("energy_fx", "<u8")])
+COLSTAT_DTYPE = np.dtype([("S", "<u8"), ("Shat", "<i8"), ("keep", "<i4"), ("otsu", "<i4"),
+                          ("eff", "<i4"), ("pad", "<i4")])
+assert C.sizeof(Box) == BOX_DTYPE.itemsize == 48
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load librise.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"RISE CUDA library not built: {LIB_PATH} is missing "
+                           "(run paper_2603_20481_gb300/build.py)")
+    L = C.CDLL(LIB_PATH)
+    P, i64, i32 = C.c_void_p, C.c_int64, C.c_int
+    L.rise_thresholds_default.argtypes = [P]
+    L.rise_thresholds_default.restype = None
+    L.rise_create.argtypes = [C.POINTER(P), P]
+    L.rise_create.restype = i32
+    L.rise_destroy.argtypes = [P]
+    L.rise_destroy.restype = None
+    L.rise_strerror.argtypes = [i32]
+    L.rise_strerror.restype = C.c_char_p
+    for name in ("rise_detect", "rise_detect_host"):
+        f = getattr(L, name)
+        f.argtypes = [P, P, i64, i32, i32, P, P, i64, P]
+        f.restype = i32
+    L.rise_detect_image.argtypes = [P, P, i64, i32, P, P, i64, P]
+    L.rise_detect_image.restype = i32
+    L.rise_debug_export.argtypes = [P, i32, P, C.c_size_t]
+    L.rise_debug_export.restype = i32
+    L.rise_set_option.argtypes = [P, i32, i64]
+    L.rise_set_option.restype = i32
+    L.rise_stage_times.argtypes = [P, P, i32]
+    L.rise_stage_times.restype = i32
+    _lib = L
+    return L
+
+
+def strerror(code: int) -> str:
+    try:
+        return lib().rise_strerror(code).decode()
+    except Exception:
+        return "unknown"
+
+
+def default_thresholds(**overrides) -> Thresholds:
+    t = Thresholds()
+    lib().rise_thresholds_default(C.byref(t))
+    for k, v in overrides.items():
+        setattr(t, k, v)
+    return t
+
+
+def boxes_from_raw(raw: np.ndarray, n: int) -> np.ndarray:
+    out = np.empty((n, 8), np.int64)
+    for j, name in enumerate(BOX_COLS):
+        out[:, j] = raw[name][:n].astype(np.int64)
+    return out
+
+
+class Detector:
+    """One library context bound to a device and a CUDA stream."""
+
+    def __init__(self, device: int = 0, stream=None, mem_budget: int = 0,
+                 max_boxes: int = 0, max_samples: int = 0):
+        import torch
+        self._torch = torch
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        cfg = Config(device, C.c_void_p(stream.cuda_stream), max_samples, 0, max_boxes, mem_budget)
+        h = C.c_void_p()
+        rc = lib().rise_create(C.byref(h), C.byref(cfg))
+        if rc != RISE_OK:
+            raise RiseError(rc, "rise_create")
+        self._h = h
+        self.device = device
+        self.stream = stream
+        self.cap = 1 << 16
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rise_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- options ----------------------------------------------------------------
+    def set_option(self, option: int, value: int):
+        rc = lib().rise_set_option(self._h, option, int(value))
+        if rc != RISE_OK:
+            raise RiseError(rc, "rise_set_option")
+
+    def stage_times(self) -> np.ndarray:
+        ms = np.zeros(8, np.float32)
+        lib().rise_stage_times(self._h, ms.ctypes.data, 8)
+        return ms
+
+    def launches(self) -> int:
+        v = np.zeros(1, np.int64)
+        rc = lib().rise_debug_export(self._h, DBG_LAUNCHES, v.ctypes.data, 8)
+        if rc != RISE_OK:
+            raise RiseError(rc, "rise_debug_export")
+        return int(v[0])
+
+    # -- detection --------------------------------------------------------------
+    def _run(self, fn, args, cap):
+        cap = self.cap if cap is None else int(cap)
+        while True:
+            raw = np.zeros(max(cap, 1), BOX_DTYPE)
+            n = C.c_int64(0)
+            rc = fn(*args, raw.ctypes.data if cap > 0 else None, cap, C.byref(n))
+            if rc == RISE_ETRUNC and self._auto_grow:
+                cap = int(n.value)
+                self.cap = max(self.cap, cap)
+                continue
+            if rc not in (RISE_OK, RISE_ETRUNC):
+                raise RiseError(rc, fn.__name__)
+            self.last_status = rc
+            return boxes_from_raw(raw, min(int(n.value), cap))
+
+    _auto_grow = True
+
+    def detect(self, iq, fft_size: int, hop: int, thr: Optional[Thresholds] = None,
+               cap: Optional[int] = None) -> np.ndarray:
+        """Boxes of one capture.  `iq`: CUDA complex64 tensor (1-D, contiguous)."""
+        t = self._torch
+        if not (isinstance(iq, t.Tensor) and iq.is_cuda and iq.dtype == t.complex64
+                and iq.is_contiguous() and iq.dim() == 1):
+            raise TypeError("iq must be a contiguous 1-D CUDA complex64 tensor")
+        args = (self._h, C.c_void_p(iq.data_ptr()), iq.numel(), fft_size, hop,
+                C.byref(thr) if thr is not None else None)
+        return self._run(lib().rise_detect, args, cap)
+
+    def detect_host(self, iq, fft_size: int, hop: int, thr: Optional[Thresholds] = None,
+                    cap: Optional[int] = None) -> np.ndarray:
+        """Boxes of one capture held in host memory (pinned tensor or numpy array)."""
+        t = self._torch
+        if isinstance(iq, t.Tensor):
+            if iq.is_cuda or iq.dtype != t.complex64 or not iq.is_contiguous():
+                raise TypeError("iq must be a contiguous host complex64 tensor")
+            ptr, n = iq.data_ptr(), iq.numel()
+        else:
+            iq = np.ascontiguousarray(iq, dtype=np.complex64)
+            ptr, n = iq.ctypes.data, iq.shape[0]
+        args = (self._h, C.c_void_p(ptr), n, fft_size, hop,
+                C.byref(thr) if thr is not None else None)
+        return self._run(lib().rise_detect_host, args, cap)
+
+    def detect_image(self, img, thr: Optional[Thresholds] = None,
+                     cap: Optional[int] = None) -> np.ndarray:
+        """Boxes of a given 8-bit image: CUDA uint8 tensor [T, F], contiguous."""
+        t = self._torch
+        if not (isinstance(img, t.Tensor) and img.is_cuda and img.dtype == t.uint8
+                and img.is_contiguous() and img.dim() == 2):
+            raise TypeError("img must be a contiguous 2-D CUDA uint8 tensor")
+        T, F = img.shape
+        args = (self._h, C.c_void_p(img.data_ptr()), T, F,
+                C.byref(thr) if thr is not None else None)
+        return self._run(lib().rise_detect_image, args, cap)
+
+    # -- introspection ----------------------------------------------------------
+    def debug(self, what: int, T: int, F: int) -> np.ndarray:
+        shapes = {
+            DBG_POWER_F32: ((T, F), np.float32), DBG_IMAGE_U8: ((T, F), np.uint8),
+            DBG_HIST: ((F, 256), np.uint32), DBG_FLOOR: ((8,), np.int64),
+            DBG_MASK0: ((T, F // 32), np.uint32), DBG_MASK1: ((T, F // 32), np.uint32),
+            DBG_MASK2: ((T, F // 32), np.uint32), DBG_MASK3: ((T, F // 32), np.uint32),
+            DBG_MAXPOW: ((1,), np.float32), DBG_LEVEL_EDGES: ((257,), np.float32),
+        }
+        if what == DBG_COLSTATS:
+            out = np.zeros(F, COLSTAT_DTYPE)
+        else:
+            shape, dt = shapes[what]
+            out = np.zeros(shape, dt)
+        rc = lib().rise_debug_export(self._h, what, out.ctypes.data, out.nbytes)
+        if rc != RISE_OK:
+            raise RiseError(rc, "rise_debug_export")
+        return out
+
+
+def unpack_mask(words: np.ndarray, F: int) -> np.ndarray:
+    """[T, F/32] uint32 bit-packed mask (bit f%32 of word f/32) -> [T, F] uint8."""
+    b = np.unpackbits(words.view(np.uint8).reshape(words.shape[0], -1), axis=1, bitorder="little")
+    return b[:, :F]

@@ -1,0 +1,282 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bars (stated in the design doc):
+* spectrogram: |P_gpu - P_ref| <= 1e-4 P_ref + 1e-6 * mean of the frame's P_ref;
+* 8-bit image: at most ceil(1e-5 * pixels) pixels differ, each by one level,
+  and the GPU's levels equal the oracle's quantiser applied to the GPU's own
+  float power with the GPU's anchor (the decision taken in the same precision);
+* from the 8-bit image on (histograms, column statistics, every mask stage,
+  boxes): bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_20481_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _rise():
+    from paper_2603_20481_gb300 import rise
+    return rise
+
+
+def _thr_pair(**kw):
+    rise = _rise()
+    return rise.default_thresholds(**kw), oracle.params(**kw)
+
+
+def _gpu_detect(det, iq_np, N, hop, thr=None, keep=True):
+    rise = _rise()
+    det.set_option(rise.OPT_KEEP_POWER, int(keep))
+    det.set_option(rise.OPT_KEEP_MASKS, int(keep))
+    x = torch.from_numpy(iq_np).cuda()
+    boxes = det.detect(x, N, hop, thr)
+    torch.cuda.synchronize()
+    return boxes
+
+
+def _check_power(Pg, Pr):
+    floor = 1e-6 * Pr.mean(axis=1, keepdims=True)
+    bad = np.abs(Pg.astype(np.float64) - Pr) > 1e-4 * Pr + floor
+    assert not bad.any(), f"{bad.sum()} spectrogram bins off, worst rel {np.max(np.abs(Pg - Pr) / (Pr + floor))}"
+
+
+def _check_image(qg, qr):
+    d = qg.astype(np.int16) - qr.astype(np.int16)
+    nd = int(np.count_nonzero(d))
+    assert np.abs(d).max(initial=0) <= 1
+    assert nd <= math.ceil(1e-5 * qg.size), f"{nd} of {qg.size} pixels differ"
+    return nd
+
+
+STFT_CASES = [
+    # (N, hop, n, fs, seed)
+    (256, 128, 256 * 37 + 77, 20e6, 1),
+    (256, 1, 2000, 20e6, 2),
+    (512, 512, 512 * 300 + 11, 20e6, 3),
+    (1024, 1024, 1 << 18, 20e6, 4),
+    (1024, 300, 100003, 20e6, 5),
+    (2048, 1024, 2048 * 40 + 5, 61.44e6, 6),
+    (4096, 2048, 4096 * 40 + 123, 100e6, 7),
+    (8192, 2048, 8192 * 12 + 9, 100e6, 8),
+    (4096, 4096, 4096, 100e6, 9),          # T = 1
+]
+
+
+@pytest.mark.parametrize("N,hop,n,fs,seed", STFT_CASES)
+def test_spectrogram_and_image_parity(det, N, hop, n, fs, seed):
+    rise = _rise()
+    cap = synth.make_capture(n, fs, 6, 500 + seed, fft_size=N, hop=hop,
+                             bw_hz=(fs / 200, fs / 20), dur_s=(n / fs / 20, n / fs / 3),
+                             snr_db=(5, 25), tone_fraction=0.3)
+    T = oracle.num_frames(n, N, hop)
+    boxes_g = _gpu_detect(det, cap.iq, N, hop)
+    Pg = det.debug(rise.DBG_POWER_F32, T, N)
+    qg = det.debug(rise.DBG_IMAGE_U8, T, N)
+    Mg = float(det.debug(rise.DBG_MAXPOW, T, N)[0])
+    Pr = oracle.stft_power(cap.iq, N, hop)
+    _check_power(Pg, Pr)
+    assert Mg == float(Pg.max())
+    # same-precision decision: the oracle's quantiser on the GPU's float power
+    q_same = oracle.quantize(Pg.astype(np.float64), oracle.hi_db_of(Mg))
+    assert np.array_equal(q_same, qg)
+    # against the FP64 path end to end
+    boxes_r, qr, Mr = oracle.detect(cap.iq, N, hop)
+    assert abs(Mg - Mr) <= 1e-5 * Mr
+    nd = _check_image(qg, qr)
+    # from the image on, bit-exact: the oracle on the GPU's own image
+    assert np.array_equal(boxes_g, oracle.detect_image(qg))
+    if nd == 0:
+        assert np.array_equal(boxes_g, boxes_r)
+
+
+def _image_stage_check(det, q, thr_g, thr_r):
+    rise = _rise()
+    det.set_option(rise.OPT_KEEP_MASKS, 1)
+    T, F = q.shape
+    boxes_g = det.detect_image(torch.from_numpy(q).cuda(), thr_g)
+    boxes_r, ex = oracle.detect_image(q, thr_r, extras=True)
+    hist_g = det.debug(rise.DBG_HIST, T, F)
+    assert np.array_equal(hist_g, ex["hist"])
+    cols = det.debug(rise.DBG_COLSTATS, T, F)
+    st = oracle.column_thresholds(ex["hist"], T, thr_r)
+    assert np.array_equal(cols["S"], st["S"])
+    assert np.array_equal(cols["Shat"], st["Shat"])
+    assert np.array_equal(cols["keep"], st["keep"].astype(np.int32))
+    assert np.array_equal(cols["otsu"], st["otsu"])
+    assert np.array_equal(cols["eff"], st["eff"])
+    fl = det.debug(rise.DBG_FLOOR, T, F)
+    assert fl[:5].tolist() == [st["N0"], st["delta_psd"], st["delta_pow"], st["P_q"], st["D"]]
+    M0 = oracle.threshold(q, st["eff"])
+    M1, M2, M3 = oracle.morph_chain(M0, thr_r.morph_order)
+    for what, ref in ((rise.DBG_MASK0, M0), (rise.DBG_MASK1, M1), (rise.DBG_MASK2, M2),
+                      (rise.DBG_MASK3, M3)):
+        got = rise.unpack_mask(det.debug(what, T, F), F)
+        assert np.array_equal(got, ref), f"mask stage {what - rise.DBG_MASK0}"
+    assert np.array_equal(boxes_g, boxes_r)
+    return boxes_g
+
+
+def test_image_path_bit_exact_on_oracle_images(det):
+    cap = synth.single_capture(101)
+    _, q, _ = oracle.detect(cap.iq, 1024, 1024)
+    for kw in ({}, dict(morph_order=1), dict(sg_half_window=2, level_db=0.5),
+               dict(psd_offset_db=-math.inf), dict(power_offset_db=-math.inf),
+               dict(psd_offset_db=3.0, power_offset_db=4.0)):
+        thr_g, thr_r = _thr_pair(**kw)
+        _image_stage_check(det, q, thr_g, thr_r)
+
+
+@pytest.mark.parametrize("T,F,seed", [(1, 256, 1), (2, 512, 2), (1000, 512, 3), (37, 8192, 4),
+                                      (300, 2048, 5), (129, 256, 6), (5000, 256, 7)])
+def test_image_path_random_structures(det, T, F, seed):
+    rng = np.random.default_rng(seed)
+    q = rng.integers(90, 150, size=(T, F)).astype(np.uint8)
+    # blocks, stripes and speckle to exercise strips, merges and long components
+    for _ in range(12):
+        t0, f0 = rng.integers(0, T), rng.integers(0, F)
+        q[t0:t0 + rng.integers(1, max(2, T // 3)), f0:f0 + rng.integers(1, F // 4)] = rng.integers(180, 256)
+    q[:, rng.integers(0, F - 3):][:, :3] = 220                 # a full-height line
+    q[rng.random((T, F)) < 0.01] = 250
+    for kw in ({}, dict(psd_offset_db=-math.inf, power_offset_db=-math.inf), dict(morph_order=1)):
+        thr_g, thr_r = _thr_pair(**kw)
+        _image_stage_check(det, q, thr_g, thr_r)
+
+
+def _stripes(T, F, seed):
+    # 3-wide vertical stripes 3 apart (they survive closing and opening), cut
+    # every 64 rows by a 3-row gap, on a flat background (a constant column has
+    # no Otsu split): F/6 runs in most rows, so a strip holds more runs than
+    # fit in shared memory
+    rng = np.random.default_rng(seed)
+    q = np.full((T, F), 50, np.uint8)
+    cols = (np.arange(F) % 6) < 3
+    rows = (np.arange(T) % 64) < 61
+    q[np.ix_(rows, cols)] = rng.integers(200, 256, size=(rows.sum(), cols.sum()))
+    return q
+
+
+def test_dense_foreground_many_components(det):
+    thr_g, thr_r = _thr_pair(psd_offset_db=-math.inf, power_offset_db=-math.inf)
+    q = _stripes(2048, 4096, 12)
+    b = _image_stage_check(det, q, thr_g, thr_r)
+    assert b.shape[0] > 10000
+    # uniform random levels: ~half the pixels pass Otsu, the closing joins them
+    rng = np.random.default_rng(13)
+    q = rng.integers(0, 256, size=(1024, 2048)).astype(np.uint8)
+    _image_stage_check(det, q, thr_g, thr_r)
+
+
+def test_range_paths_and_fixed_anchor_agree(det):
+    rise = _rise()
+    cap = synth.make_capture(1 << 19, 100e6, 10, 33, fft_size=2048, hop=1024,
+                             bw_hz=(1e6, 10e6), dur_s=(0.2e-3, 2e-3), snr_db=(5, 20))
+    x = torch.from_numpy(cap.iq).cuda()
+    T = oracle.num_frames(cap.iq.shape[0], 2048, 1024)
+    out = {}
+    for path in (1, 2):
+        det.set_option(rise.OPT_RANGE_PATH, path)
+        out[path] = (det.detect(x, 2048, 1024), det.debug(rise.DBG_IMAGE_U8, T, 2048).copy())
+    det.set_option(rise.OPT_RANGE_PATH, 0)
+    assert np.array_equal(out[1][0], out[2][0]) and np.array_equal(out[1][1], out[2][1])
+    # a fixed anchor at 3 dB below the max clips the top levels
+    Mg = float(det.debug(rise.DBG_MAXPOW, T, 2048)[0])
+    hi = oracle.hi_db_of(Mg) - 3.0
+    thr_g, thr_r = _thr_pair(range_mode=1, hi_db=hi)
+    bg = det.detect(x, 2048, 1024, thr_g)
+    qg = det.debug(rise.DBG_IMAGE_U8, T, 2048)
+    br, qr, _ = oracle.detect(cap.iq, 2048, 1024, thr_r)
+    _check_image(qg, qr)
+    assert np.array_equal(bg, oracle.detect_image(qg, thr_r))
+
+
+def test_degenerate_inputs(det):
+    rise = _rise()
+    # all-zero capture: every level 0, no boxes
+    z = np.zeros(1 << 14, np.complex64)
+    b = _gpu_detect(det, z, 1024, 512)
+    assert b.shape == (0, 8)
+    q = det.debug(rise.DBG_IMAGE_U8, oracle.num_frames(1 << 14, 1024, 512), 1024)
+    assert not q.any()
+    # constant image: no Otsu split anywhere
+    img = torch.full((64, 256), 77, dtype=torch.uint8, device="cuda")
+    assert det.detect_image(img).shape == (0, 8)
+
+
+def test_truncation_and_invalid_arguments(det):
+    rise = _rise()
+    q = _stripes(512, 1024, 3)
+    thr_g, thr_r = _thr_pair(psd_offset_db=-math.inf, power_offset_db=-math.inf)
+    full = oracle.detect_image(q, thr_r)
+    assert full.shape[0] > 10
+    img = torch.from_numpy(q).cuda()
+    det._auto_grow = False
+    try:
+        part = det.detect_image(img, thr_g, cap=7)
+        assert det.last_status == rise.RISE_ETRUNC
+        assert np.array_equal(part, full[:7])
+    finally:
+        det._auto_grow = True
+    x = torch.zeros(5000, dtype=torch.complex64, device="cuda")
+    for args in ((x, 1000, 500), (x, 128, 64), (x, 16384, 100), (x, 1024, 0), (x, 1024, 1025),
+                 (x[:1000], 1024, 512)):
+        with pytest.raises(rise.RiseError) as e:
+            det.detect(*args)
+        assert e.value.code == rise.RISE_EINVAL
+    with pytest.raises(rise.RiseError):
+        det.detect(x, 1024, 512, rise.default_thresholds(level_db=0.0))
+    with pytest.raises(rise.RiseError):
+        det.detect(x, 1024, 512, rise.default_thresholds(morph_order=2))
+
+
+def test_single_capture_full_config(det):
+    # 2^20 samples, FFT 1024, hop 1024: the whole path against the oracle
+    cap = synth.single_capture(101)
+    boxes_g = _gpu_detect(det, cap.iq, 1024, 1024, keep=False)
+    boxes_r, qr, _ = oracle.detect(cap.iq, 1024, 1024)
+    qg = det.debug(_rise().DBG_IMAGE_U8, 1024, 1024)
+    nd = _check_image(qg, qr)
+    assert np.array_equal(boxes_g, oracle.detect_image(qg))
+    if nd == 0:
+        assert np.array_equal(boxes_g, boxes_r)
+
+
+def test_host_entry_point_matches_device_entry_point(det):
+    cap = synth.single_capture(102)
+    bd = _gpu_detect(det, cap.iq, 1024, 512, keep=False)
+    pinned = torch.from_numpy(cap.iq).pin_memory()
+    bh = det.detect_host(pinned, 1024, 512)
+    assert np.array_equal(bd, bh)
+
+
+@pytest.mark.slow
+def test_wideband_full_size_sampled(det):
+    """2^26 samples, FFT 4096, hop 2048 (the bench workload, same launch path):
+    sampled frames against the oracle's spectrogram, the full image within the
+    quantisation budget, and boxes bit-exact against the oracle on the GPU image."""
+    rise = _rise()
+    cap = synth.wideband_capture(102)
+    N, hop = 4096, 2048
+    T = oracle.num_frames(cap.iq.shape[0], N, hop)
+    det.set_option(rise.OPT_KEEP_POWER, 0)
+    det.set_option(rise.OPT_KEEP_MASKS, 0)
+    x = torch.from_numpy(cap.iq).cuda()
+    boxes_g = det.detect(x, N, hop)
+    qg = det.debug(rise.DBG_IMAGE_U8, T, N)
+    Mg = float(det.debug(rise.DBG_MAXPOW, T, N)[0])
+    Mr = oracle.max_power(cap.iq, N, hop)
+    assert abs(Mg - Mr) <= 1e-5 * Mr
+    rng = np.random.default_rng(0)
+    rows = np.unique(np.concatenate([[0, T - 1], rng.integers(0, T, 62)]))
+    for t in rows:
+        Pr = oracle.stft_power(cap.iq, N, hop, int(t), 1)
+        qr = oracle.quantize(Pr, oracle.hi_db_of(Mr))
+        d = qg[t].astype(int) - qr[0].astype(int)
+        assert np.abs(d).max() <= 1 and np.count_nonzero(d) <= 2
+    assert np.array_equal(boxes_g, oracle.detect_image(qg))
