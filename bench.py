@@ -1,0 +1,315 @@
+#!/usr/bin/env python
+"""Throughput of the RISE IQ -> boxes path on one GB300 (or N replicas).
+
+Workload (default): wideband single stream -- 2^26 complex64 samples
+(notional 100 MS/s), Hann window, FFT 4096, hop 2048 (T = 32767 frames),
+128 planted emitters, seed 102; synthetic, generated by
+paper_2603_20481_gb300.synth.  One step = one rise_detect call: the whole
+path (spectrum, 8-bit image, histogram, column statistics, morphology,
+labelling, boxes back in host memory).  The 512 MiB capture is larger than
+L2, so no flush is needed between steps.
+
+Printed: one JSON line (rank 0).  `value` is samples of all ranks / the
+slowest rank's CUDA-event time over the K timed steps, inputs resident in
+HBM; `e2e` is the same metric through rise_detect_host from pinned host
+memory (copy in the timed region); `roofline` is the dominant kernel's
+algorithmic bytes / its event-timed duration against the measured HBM copy
+bandwidth; `cpu_baseline` is the FP64 oracle on a bounded sample.
+
+Multi-GPU: replicas only (independent captures per rank, weak scaling), no
+collective on the data path.  `--impl reference` times the oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "IQ Msamples/s to boxes + %HBM roofline; p99 chunk latency, batched vs plain"
+UNIT = "MS/s"
+N_FFT, HOP, N_SAMPLES = 4096, 2048, 1 << 26
+WORKLOAD = ("wideband single stream: 2^26 complex64 IQ samples (notional 100 MS/s), "
+            "128 emitters (SNR -3..25 dB, 0.1-20 MHz), Hann, FFT 4096, hop 2048 "
+            "-> 32767 x 4096 spectrogram; plain method")
+HBM_FALLBACK_GBS = 6800.0
+# DRAM bytes per launch of the dominant kernel, from the ncu capture summarised
+# in profiles/stft_quant_wideband_4096.md (null once the kernel changes).
+TRAFFIC_BYTES = None
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() in ("active", "0x1") or v == "1":
+                        reasons.add(nm)
+        finally:
+            os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _allreduce_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_oracle_rate(iq, n_sample: int):
+    """FP64 oracle (single-threaded C) on the first n_sample samples."""
+    import oracle
+    x = iq[:n_sample]
+    t0 = time.perf_counter()
+    boxes, _, _ = oracle.detect(x, N_FFT, HOP)
+    dt = time.perf_counter() - t0
+    return n_sample / dt / 1e6, dt, len(boxes)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2603_20481_gb300 import rise, synth
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    cap = synth.wideband_capture(seed=102 + rank, n=args.samples)
+    n = cap.iq.shape[0]
+    x = torch.from_numpy(cap.iq).cuda()
+    host = torch.from_numpy(cap.iq).pin_memory()
+    det = rise.Detector(local)
+    if args.range_path:
+        det.set_option(rise.OPT_RANGE_PATH, args.range_path)
+    det.set_option(rise.OPT_TIMING, 1)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        boxes = det.detect(x, N_FFT, HOP)
+    torch.cuda.synchronize()
+    _barrier(world)
+    torch.cuda.synchronize()
+    uuid = str(torch.cuda.get_device_properties(local).uuid)
+    sampler = ClockSampler(uuid if uuid.startswith("GPU-") else f"GPU-{uuid}")
+    sampler.start()
+    time.sleep(0.3)
+    l0 = det.launches()
+    stage = np.zeros(8, np.float64)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        boxes = det.detect(x, N_FFT, HOP)
+        stage += det.stage_times()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = det.launches() - l0
+    clocks = sampler.stop()
+    _barrier(world)
+    t_dev = e0.elapsed_time(e1) / 1e3
+    t_max = _allreduce_max(t_dev, world)
+    stage /= args.steps
+    n_boxes = len(boxes)
+
+    # end to end through the host entry point (pinned memory -> HBM -> boxes)
+    e2e = None
+    if not args.no_e2e:
+        for _ in range(max(1, args.warmup)):
+            det.detect_host(host, N_FFT, HOP)
+        torch.cuda.synchronize()
+        _barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            bh = det.detect_host(host, N_FFT, HOP)
+        torch.cuda.synchronize()
+        t_e2e = _allreduce_max(time.perf_counter() - t0, world)
+        e2e = {"value": round(world * args.steps * n / t_e2e / 1e6, 1), "unit": UNIT,
+               "h2d_bytes_per_step": n * 8,
+               "d2h_bytes_per_step": len(bh) * 48 + 40}
+
+    # roofline of the dominant kernel (per-stage CUDA events on the launch stream)
+    T = (n - N_FFT) // HOP + 1
+    px = T * N_FFT
+    path = args.range_path or 1
+    if path == 1:   # FFT twice: anchor max, then quantise; histogram from the image
+        stage_bytes = {
+            "spectrum_pass1": n * 8,                 # IQ read (max pass)
+            "spectrum_pass2": n * 8 + px,            # IQ read + 8-bit image write
+            "histogram": px,                          # image read
+            "morphology": px + px // 8,               # image read + final mask write
+        }
+    else:           # FFT once keeping float power, then quantise + histogram
+        stage_bytes = {
+            "spectrum_pass1": n * 8 + 4 * px,        # IQ read + float power write
+            "spectrum_pass2": 4 * px + px,           # float power read + image write
+            "morphology": px + px // 8,
+        }
+    names = rise.STAGES
+    dom = max(stage_bytes, key=lambda k: stage[names.index(k)])
+    dom_ms = stage[names.index(dom)]
+    peak, peak_kind = _peaks()
+    achieved = stage_bytes[dom] / (dom_ms / 1e3) / 1e9
+    alg_path = 16 * n + 2 * px                      # IQ twice + image write + image read
+    result = {
+        "metric": METRIC, "value": round(world * args.steps * n / t_max / 1e6, 1), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(t_max / args.steps * 1e3, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_samples": n, "fft_size": N_FFT, "hop": HOP,
+                   "frames": T, "boxes": n_boxes, "range_path": path,
+                   "l2": "inputs larger than L2 (512 MiB capture per step)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": TRAFFIC_BYTES, "peak_source": peak_kind,
+                     "alg_bytes_per_launch": stage_bytes[dom], "ms_per_launch": round(dom_ms, 4),
+                     "path_frac": round(alg_path / (t_max / args.steps) / 1e9 / peak, 4)},
+        "stage_ms": {k: round(float(v), 4) for k, v in zip(names, stage)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, dt, nb = cpu_oracle_rate(cap.iq, args.cpu_sample)
+        result["cpu_baseline"] = {
+            "value": round(rate, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {args.cpu_sample} samples of the same capture "
+                      f"({(args.cpu_sample - N_FFT) // HOP + 1} frames), one pass, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    det.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    world, rank, local = _dist()
+    if rank != 0:
+        return
+    from paper_2603_20481_gb300 import synth
+    import oracle
+    cap = synth.wideband_capture(seed=102, n=args.samples)
+    m = min(args.ref_sample, cap.iq.shape[0])
+    x = cap.iq[:m]
+    for _ in range(args.warmup):
+        oracle.detect(x, N_FFT, HOP)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.detect(x, N_FFT, HOP)
+    dt = time.perf_counter() - t0
+    value = round(args.steps * m / dt / 1e6, 3)
+    sample = (f"first {m} samples of the wideband capture ({(m - N_FFT) // HOP + 1} frames) "
+              f"per step, FP64 C oracle, single thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / args.steps * 1e3, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_samples": m, "fft_size": N_FFT, "hop": HOP},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--samples", type=int, default=N_SAMPLES)
+    ap.add_argument("--range-path", type=int, default=0, choices=(0, 1, 2))
+    ap.add_argument("--cpu-sample", type=int, default=1 << 24)
+    ap.add_argument("--ref-sample", type=int, default=1 << 22)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -83,7 +83,7 @@ typedef struct {
 typedef struct {
   int range_mode;         /* RISE_RANGE_AUTO_MAX | RISE_RANGE_FIXED            */
   double hi_db;           /* top of the 8-bit range for RISE_RANGE_FIXED       */
-  double level_db;        /* dB per 8-bit level, > 0                           */
+  double level_db;        /* dB per 8-bit level, 0.01 .. 10                    */
   double psd_offset_db;   /* theta_PSD above N0; -INFINITY: keep every column  */
   double power_offset_db; /* theta_Power above N0; -INFINITY: no power floor   */
   int sg_half_window;     /* Savitzky-Golay half window m, 1..16               */

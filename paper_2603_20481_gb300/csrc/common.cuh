@@ -138,6 +138,7 @@ struct StftArgs {
   const float *qconst;    // [2]: 1/anchor, dB-per-level scale (quantise mode)
   const float2 *tw;       // per-N twiddle tables (device)
   const float *win;       // per-N Hann window (device)
+  uint32_t *err;          // device error word (ERR_* bits)
 };
 
 enum StftMode { STFT_MAX = 0, STFT_QUANT = 1, STFT_POWER = 2, STFT_QUANT_POWER = 3 };
@@ -148,15 +149,21 @@ void stft_fill_tables(int N, float2 *tw_host, float *win_host);
 cudaError_t launch_stft(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s);
 // Level edges from the anchor (AUTO: read from max_bits; FIXED: hi_power).
 cudaError_t launch_levels(const uint32_t *max_bits, double hi_power, int use_fixed,
-                          double level_db, float *edges, float *qconst, cudaStream_t s);
-// Quantise a stored float power image and build the column histogram.
-cudaError_t launch_quant_hist(const float *power, int64_t T, int F, const float *edges,
-                              const float *qconst, uint8_t *img, uint32_t *hist,
-                              int num_sms, cudaStream_t s);
+                          const double *ratio, double level_db, float *edges, float *qconst,
+                          cudaStream_t s);
 
-// Column histogram of an 8-bit image; hist must be zeroed by the caller.
-cudaError_t launch_hist(const uint8_t *img, int64_t T, int F, uint32_t *hist, int num_sms,
-                        cudaStream_t s);
+// Cluster histogram: 8-bit image (from_power = false) or float power quantised
+// on the way (img written).  *needs_zero tells whether hist had to be zeroed
+// (only for T > 8 * 65535); call with needs_zero to query before launching.
+// Also writes each column's PSD S and Otsu threshold into cols (unless the
+// histogram is accumulated over several clusters: then launch_colstats runs Otsu).
+cudaError_t launch_cluster_hist(const void *src, bool from_power, int64_t T, int F,
+                                const float *edges, const float *qconst, uint8_t *img,
+                                uint32_t *hist, rise_colstat *cols, bool *needs_zero,
+                                cudaStream_t s);
+// True when T needs more than one cluster of row bands: then hist must be
+// zeroed before launch_cluster_hist, which accumulates into it.
+bool cluster_hist_accumulates(int64_t T);
 
 struct ColArgs {
   const uint32_t *hist;   // [F][256]
@@ -172,7 +179,7 @@ struct ColArgs {
   uint8_t *effm1;         // [F] eff-1 clamped to 0..255 (q > effm1 is foreground)
   int64_t *floor_out;     // [8]
 };
-cudaError_t launch_colstats(const ColArgs &a, cudaStream_t s);
+cudaError_t launch_colstats(const ColArgs &a, bool need_otsu, cudaStream_t s);
 
 struct MorphArgs {
   const uint8_t *img;     // [T][F]
@@ -182,6 +189,7 @@ struct MorphArgs {
   int order;
   uint32_t *mask;         // [T][F/32] final
   uint32_t *dbg0, *dbg1, *dbg2;  // optional stage masks
+  uint32_t *row_cnt;      // [T] runs per row of the final mask (zeroed by the caller)
 };
 cudaError_t launch_morph(const MorphArgs &a, cudaStream_t s);
 
@@ -192,11 +200,11 @@ struct CclArgs {
   int F;
   const uint64_t *energy; // [256] energy table
   int64_t *row_base;      // [T+1] run offsets per row (scan output)
-  uint32_t *row_cnt;      // [T] runs per row
+  uint32_t *row_cnt;      // [T] runs per row (from the morphology kernel)
   int64_t run_cap;        // capacity of the run arrays
-  int32_t *run_parent;    // [run_cap]
-  uint8_t *run_sroot;     // [run_cap] 1 = root of its strip-local component
-  rise_box *rec;          // [run_cap] per-run records (meaningful for roots)
+  int32_t *run_parent;    // [run_cap] union-find parent (a smaller run number, or itself)
+  uint8_t *run_sroot;     // [run_cap] 1 = the run is its component's root
+  rise_box *rec;          // [run_cap] per-run records, summed into the roots
   int64_t *run_out;       // [run_cap + 1] compaction scan scratch
   void *scan_tmp;         // scan scratch
   size_t scan_tmp_bytes;
@@ -205,10 +213,11 @@ struct CclArgs {
   DeviceStatus *status;
 };
 size_t ccl_scan_tmp_bytes(int64_t max_items);
-// Row run counts + scan: fills row_cnt, row_base and status->n_runs.
+// Scan of the per-row run counts: fills row_base and status->n_runs.
 cudaError_t launch_ccl_count(const CclArgs &a, int num_sms, cudaStream_t s);
-// Strip unions, boundary merge, reduction and compaction (needs run_cap >= n_runs,
-// checked on the device: on shortfall it sets ERR_RUN_CAPACITY and does nothing).
+// Run records, unions, reduction into roots and compaction (needs run_cap >=
+// n_runs, checked on the device: on shortfall it sets ERR_RUN_CAPACITY and
+// does nothing).
 cudaError_t launch_ccl_label(const CclArgs &a, int num_sms, cudaStream_t s);
 
 }  // namespace rise

@@ -3,130 +3,39 @@
 // minimum N0, theta_PSD column pruning, exact per-column Otsu (Eq. 4) with
 // the power floor, and the binary mask with one 2D closing, one 2D opening
 // and one horizontal 1D opening (Eq. 5) on bit-packed tiles.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace rise {
 namespace {
 
-// ---------------------------------------------------------------------------
-// Column histogram.  A block owns a strip of 128 columns and a band of rows.
-// Lane l reads 4 consecutive columns (4l..4l+3) of a row as one 32-bit load;
-// column 4l+j is counted in smem slot l+32j so that the 32 lanes of a warp
-// always hit 32 different banks.  Each 32-bit smem word holds two 16-bit
-// counters, levels v and v+128, so the strip's 128 x 256 counters fit in
-// 64 KB; a band has at most 65535 rows so a counter cannot overflow.
-// ---------------------------------------------------------------------------
-constexpr int HIST_COLS = 128;
-constexpr int HIST_THREADS = 256;
-constexpr int HIST_MAX_ROWS = 65535;
+constexpr int HIST_MAX_ROWS = 65535;   // rows per band: 16-bit counters never wrap
 
-__device__ __forceinline__ void hist_count(uint32_t *sh, int lane, uint32_t word4) {
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const uint32_t v = (word4 >> (8 * j)) & 0xffu;
-    atomicAdd(&sh[(v & 127u) * HIST_COLS + lane + 32 * j], (v & 128u) ? 65536u : 1u);
-  }
-}
-
-__device__ __forceinline__ void hist_flush(const uint32_t *sh, uint32_t *hist, int c0) {
-  for (int i = threadIdx.x; i < 128 * HIST_COLS; i += blockDim.x) {
-    const uint32_t w = sh[i];
-    if (!w) continue;
-    const int vm = i / HIST_COLS, pc = i % HIST_COLS;
-    const int col = c0 + 4 * (pc & 31) + (pc >> 5);
-    const uint32_t lo = w & 0xffffu, hi = w >> 16;
-    if (lo) atomicAdd(&hist[(size_t)col * 256 + vm], lo);
-    if (hi) atomicAdd(&hist[(size_t)col * 256 + vm + 128], hi);
-  }
-}
-
-__global__ void __launch_bounds__(HIST_THREADS)
-hist_kernel(const uint8_t *__restrict__ img, int64_t T, int F, int64_t rows_per_block,
-            uint32_t *hist) {
-  extern __shared__ uint32_t sh[];
-  for (int i = threadIdx.x; i < 128 * HIST_COLS; i += blockDim.x) sh[i] = 0;
-  __syncthreads();
-  const int c0 = blockIdx.x * HIST_COLS;
-  const int64_t r0 = (int64_t)blockIdx.y * rows_per_block;
-  const int64_t r1 = min(T, r0 + rows_per_block);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nw = blockDim.x >> 5;
-  const uint8_t *base = img + c0 + 4 * lane;
-  int64_t r = r0 + warp;
-  for (; r + 3 * nw < r1; r += 4 * nw) {
-    uint32_t w0 = __ldg(reinterpret_cast<const uint32_t *>(base + r * F));
-    uint32_t w1 = __ldg(reinterpret_cast<const uint32_t *>(base + (r + nw) * F));
-    uint32_t w2 = __ldg(reinterpret_cast<const uint32_t *>(base + (r + 2 * nw) * F));
-    uint32_t w3 = __ldg(reinterpret_cast<const uint32_t *>(base + (r + 3 * nw) * F));
-    hist_count(sh, lane, w0);
-    hist_count(sh, lane, w1);
-    hist_count(sh, lane, w2);
-    hist_count(sh, lane, w3);
-  }
-  for (; r < r1; r += nw) hist_count(sh, lane, __ldg(reinterpret_cast<const uint32_t *>(base + r * F)));
-  __syncthreads();
-  hist_flush(sh, hist, c0);
-}
-
-// Quantise a stored float |X|^2 image (same level rule as the STFT epilogue)
-// while counting the column histogram.
-constexpr float kGuardQ = 1.0e-3f;
-__device__ __forceinline__ int level_of_q(float P, float inv_anchor, float c1, const float *edges) {
-  float v = fmaf(__log2f(P * inv_anchor), c1, 255.5f);
-  float fl = floorf(v);
-  float fr = v - fl;
-  int q = (int)fminf(fmaxf(fl, 0.0f), 255.0f);
-  if ((fr < kGuardQ || fr > 1.0f - kGuardQ) && v > 1.0f - 2.0f * kGuardQ && v < 255.0f + 2.0f * kGuardQ) {
-    for (int it = 0; it < 256 && q < 255 && P >= edges[q + 1]; ++it) ++q;
-    for (int it = 0; it < 256 && q > 0 && P < edges[q]; ++it) --q;
+// Level of a stored float |X|^2 (same rule as the STFT epilogue).
+constexpr float kGuardQ = 3.0e-4f;   // the fast level coordinate is off by < 1e-4
+__device__ __forceinline__ uint32_t level_of_q(float P, float inv_anchor, float c1,
+                                               const float *edges) {
+  const float v = fmaf(__log2f(P * inv_anchor), c1, 255.5f);
+  uint32_t q = __float2uint_rd(fminf(v, 255.0f));   // floor, clamped to 0..255 (NaN, -inf: 0)
+  if (fabsf(v - rintf(v)) < kGuardQ) {              // near a level edge: exact comparison
+    int qi = (int)q;
+    for (int it = 0; it < 256 && qi < 255 && P >= edges[qi + 1]; ++it) ++qi;
+    for (int it = 0; it < 256 && qi > 0 && P < edges[qi]; ++it) --qi;
+    q = (uint32_t)qi;
   }
   return q;
 }
 
-__global__ void __launch_bounds__(HIST_THREADS)
-quant_hist_kernel(const float *__restrict__ power, int64_t T, int F, int64_t rows_per_block,
-                  const float *edges_g, const float *qconst, uint8_t *img, uint32_t *hist) {
-  extern __shared__ uint32_t sh[];
-  __shared__ float edges[257];
-  for (int i = threadIdx.x; i < 128 * HIST_COLS; i += blockDim.x) sh[i] = 0;
-  for (int i = threadIdx.x; i < 257; i += blockDim.x) edges[i] = edges_g[i];
-  const float inv_anchor = qconst[0], c1 = qconst[1];
-  __syncthreads();
-  const int c0 = blockIdx.x * HIST_COLS;
-  const int64_t r0 = (int64_t)blockIdx.y * rows_per_block;
-  const int64_t r1 = min(T, r0 + rows_per_block);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nw = blockDim.x >> 5;
-  for (int64_t r = r0 + warp; r < r1; r += nw) {
-    const float4 p = __ldg(reinterpret_cast<const float4 *>(power + r * F + c0) + lane);
-    const uint32_t q0 = level_of_q(p.x, inv_anchor, c1, edges);
-    const uint32_t q1 = level_of_q(p.y, inv_anchor, c1, edges);
-    const uint32_t q2 = level_of_q(p.z, inv_anchor, c1, edges);
-    const uint32_t q3 = level_of_q(p.w, inv_anchor, c1, edges);
-    const uint32_t w4 = q0 | (q1 << 8) | (q2 << 16) | (q3 << 24);
-    reinterpret_cast<uint32_t *>(img + r * F + c0)[lane] = w4;
-    hist_count(sh, lane, w4);
-  }
-  __syncthreads();
-  hist_flush(sh, hist, c0);
-}
-
-void hist_grid(int64_t T, int F, int num_sms, dim3 &grid, int64_t &rows) {
-  const int strips = F / HIST_COLS;
-  int64_t want = std::max<int64_t>(1, (2 * (int64_t)num_sms + strips - 1) / strips);
-  rows = (T + want - 1) / want;
-  rows = std::max<int64_t>(rows, 256);
-  rows = (rows + 7) / 8 * 8;
-  rows = std::min<int64_t>(rows, HIST_MAX_ROWS / 8 * 8);   // 16-bit counters never wrap
-  grid = dim3(strips, (unsigned)((T + rows - 1) / rows));
-}
-
 // ---------------------------------------------------------------------------
-// Per-column Otsu: one warp per column.  Lane l owns levels 8l..8l+7.  For a
-// split theta (class 0 = levels <= theta) with n0, s0 the count and level sum
-// of class 0 and n, s the column totals, sigma_b^2 is proportional to
-// d^2 / (n0 n1) with d = s0 n - s n0; candidates are compared exactly by
-// cross-multiplication in 128-bit integers and the smallest maximiser wins.
+// Per-column Otsu (Eq. 4): one warp per column.  Lane l owns levels
+// 8l..8l+7.  For a split theta (class 0 = levels <= theta) with n0, s0 the
+// count and level sum of class 0 and n, s the column totals, sigma_b^2 is
+// proportional to d^2 / (n0 n1) with d = s0 n - s n0; candidates are compared
+// exactly by cross-multiplication in 128-bit integers and the smallest
+// maximiser wins.  Also returns the column PSD S = s.
 // ---------------------------------------------------------------------------
 struct Cand {
   unsigned __int128 num;
@@ -150,14 +59,12 @@ __device__ __forceinline__ unsigned __int128 shfl_u128(unsigned __int128 x, int 
   return ((unsigned __int128)hi << 64) | lo;
 }
 
-__global__ void otsu_kernel(ColArgs a) {
-  const int warp_g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp_g >= a.F) return;
-  const int f = warp_g;
-  const uint4 *h4 = reinterpret_cast<const uint4 *>(a.hist + (size_t)f * 256 + 8 * lane);
-  const uint4 x = h4[0], y = h4[1];
-  uint32_t h[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+// h: the column's 256 counts (lane reads h[8 lane .. 8 lane + 7]); all lanes
+// return the same (S, theta).
+__device__ __forceinline__ void otsu_warp(const uint32_t *h8, int lane, uint64_t *S, int *theta) {
+  uint32_t h[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) h[i] = h8[i];
   uint64_t n_l = 0, s_l = 0;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
@@ -193,9 +100,159 @@ __global__ void otsu_kernel(ColArgs a) {
     o_c.th = __shfl_sync(0xffffffffu, best.th, lane ^ o);
     if (better(o_c, best)) best = o_c;
   }
+  *S = s;
+  *theta = best.th;
+}
+
+// Otsu of every column from the global histogram (used when the histogram
+// needed more than one cluster of row bands).
+__global__ void otsu_kernel(ColArgs a) {
+  const int warp_g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp_g >= a.F) return;
+  uint64_t S;
+  int th;
+  otsu_warp(a.hist + (size_t)warp_g * 256 + 8 * lane, lane, &S, &th);
   if (lane == 0) {
-    a.cols[f].S = s;
-    a.cols[f].otsu = best.th;
+    a.cols[warp_g].S = S;
+    a.cols[warp_g].otsu = th;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Column histogram, cluster version.  A block owns 64 columns of one row
+// band; its 8 warps take interleaved rows.  Lane l reads 2 consecutive
+// columns (2l, 2l+1) per row and counts column 2l+j in shared slot l+32j, so
+// a warp's 32 lanes always hit 32 different banks; counters are 16-bit
+// halves of a word (levels v and v+128) and are bumped with shared-memory
+// atomics whose results are unused, so the adds of many rows are in flight
+// at once.  The 8 blocks of a thread-block cluster cover the same 64 columns
+// over 8 row bands; after counting, each block sums whole columns (8 of them)
+// over the cluster through distributed shared memory, stores their
+// histograms (plain stores: no zeroing, no global atomics) and runs Otsu on
+// them, one warp per column.
+// FROM_POWER: the input is float |X|^2, quantised here (same level rule as
+// the STFT epilogue) and the 8-bit image is written alongside.
+// ---------------------------------------------------------------------------
+constexpr int CH_WARPS = 8, CH_COLS = 64, CH_BANDS = 8, CH_UNROLL = 8;
+constexpr int CH_PX = CH_COLS / 32;                   // columns per lane
+constexpr int CH_WORDS = 128 * CH_COLS;              // packed counter words per block
+constexpr int CH_NS = CH_COLS / CH_BANDS;            // columns each block reduces
+
+__device__ __forceinline__ void ch_count(uint32_t *sh, int lane, uint32_t q0, uint32_t q1) {
+  atomicAdd(&sh[(q0 & 127u) * CH_COLS + lane], (q0 & 128u) ? 65536u : 1u);
+  atomicAdd(&sh[(q1 & 127u) * CH_COLS + lane + 32], (q1 & 128u) ? 65536u : 1u);
+}
+
+template <bool FROM_POWER>
+__global__ void __cluster_dims__(1, CH_BANDS, 1) __launch_bounds__(32 * CH_WARPS, 4)
+cluster_hist_kernel(const void *__restrict__ src, int64_t T, int F, int64_t rows_per_band,
+                    const float *edges_g, const float *qconst, uint8_t *img, uint32_t *hist,
+                    rise_colstat *cols, int accumulate) {
+  extern __shared__ uint32_t sh[];   // [128 packed levels][64 column slots]
+  __shared__ float edges[257];
+  __shared__ __align__(16) uint32_t hs[CH_NS][256];   // reduced columns
+  cg::cluster_group cluster = cg::this_cluster();
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < CH_WORDS; i += blockDim.x) sh[i] = 0;
+  float inv_anchor = 0.f, c1 = 0.f;
+  if constexpr (FROM_POWER) {
+    for (int i = tid; i < 257; i += blockDim.x) edges[i] = edges_g[i];
+    inv_anchor = qconst[0];
+    c1 = qconst[1];
+  }
+  __syncthreads();
+  const int c0 = blockIdx.x * CH_COLS + CH_PX * lane;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_band;
+  const int64_t r1 = min(T, r0 + rows_per_band);
+  const int64_t stride = (int64_t)CH_WARPS * F;          // elements between a warp's rows
+  int64_t r = r0 + warp;
+  if constexpr (FROM_POWER) {
+    const float *p = reinterpret_cast<const float *>(src) + r * F + c0;
+    uint8_t *o = img + r * F + c0;
+    for (; r < r1; r += CH_UNROLL * CH_WARPS, p += CH_UNROLL * stride, o += CH_UNROLL * stride) {
+      float pv[2 * CH_UNROLL];
+#pragma unroll
+      for (int u = 0; u < CH_UNROLL; ++u) {
+        const float2 x = (r + (int64_t)u * CH_WARPS < r1)
+                             ? __ldg(reinterpret_cast<const float2 *>(p + u * stride))
+                             : make_float2(0.f, 0.f);
+        pv[2 * u] = x.x;
+        pv[2 * u + 1] = x.y;
+      }
+      // fast levels; the exact edge comparison only for values near a level edge
+      uint32_t q[2 * CH_UNROLL];
+      uint32_t near = 0;
+#pragma unroll
+      for (int k = 0; k < 2 * CH_UNROLL; ++k) {
+        const float v = fmaf(__log2f(pv[k] * inv_anchor), c1, 255.5f);
+        q[k] = __float2uint_rd(fminf(v, 255.0f));
+        near |= (fabsf(v - rintf(v)) < kGuardQ ? 1u : 0u) << k;
+      }
+      if (near) {
+#pragma unroll
+        for (int k = 0; k < 2 * CH_UNROLL; ++k)
+          if ((near >> k) & 1u) q[k] = level_of_q(pv[k], inv_anchor, c1, edges);
+      }
+#pragma unroll
+      for (int u = 0; u < CH_UNROLL; ++u) {
+        if (r + (int64_t)u * CH_WARPS < r1) {
+          *reinterpret_cast<uint16_t *>(o + u * stride) = (uint16_t)(q[2 * u] | (q[2 * u + 1] << 8));
+          ch_count(sh, lane, q[2 * u], q[2 * u + 1]);
+        }
+      }
+    }
+  } else {
+    const uint8_t *p = reinterpret_cast<const uint8_t *>(src) + r * F + c0;
+    for (; r + (2 * CH_UNROLL - 1) * CH_WARPS < r1; r += 2 * CH_UNROLL * CH_WARPS) {
+      uint32_t w[2 * CH_UNROLL];
+#pragma unroll
+      for (int u = 0; u < 2 * CH_UNROLL; ++u) w[u] = __ldg(reinterpret_cast<const uint16_t *>(p + u * stride));
+#pragma unroll
+      for (int u = 0; u < 2 * CH_UNROLL; ++u) ch_count(sh, lane, w[u] & 0xffu, w[u] >> 8);
+      p += 2 * CH_UNROLL * stride;
+    }
+    for (; r < r1; r += CH_WARPS, p += stride) {
+      const uint32_t w = __ldg(reinterpret_cast<const uint16_t *>(p));
+      ch_count(sh, lane, w & 0xffu, w >> 8);
+    }
+  }
+  cluster.sync();
+  // this block's column slots: sum every level over the cluster's 8 bands
+  const unsigned rank = cluster.block_rank();
+  for (int k = tid; k < CH_NS * 128; k += blockDim.x) {
+    const int sl = k % CH_NS, vm = k / CH_NS;
+    const int i = vm * CH_COLS + rank * CH_NS + sl;
+    uint32_t l = 0, h = 0;
+#pragma unroll
+    for (int b = 0; b < CH_BANDS; ++b) {
+      const uint32_t w = cluster.map_shared_rank(sh, b)[i];
+      l += w & 0xffffu;
+      h += w >> 16;
+    }
+    hs[sl][vm] = l;
+    hs[sl][vm + 128] = h;
+  }
+  cluster.sync();   // remote reads finished before any block leaves
+  // one warp per column: store its histogram, then PSD and Otsu threshold
+  if (warp < CH_NS) {
+    const int sl = warp;
+    const int slot = rank * CH_NS + sl;
+    const int col = blockIdx.x * CH_COLS + CH_PX * (slot & 31) + (slot >> 5);
+    uint32_t *dst = hist + (size_t)col * 256;
+    if (accumulate) {
+      for (int v = lane; v < 256; v += 32)
+        if (hs[sl][v]) atomicAdd(&dst[v], hs[sl][v]);
+    } else {
+      for (int v = lane; v < 256; v += 32) dst[v] = hs[sl][v];
+      uint64_t S;
+      int th;
+      otsu_warp(&hs[sl][8 * lane], lane, &S, &th);
+      if (lane == 0) {
+        cols[col].S = S;
+        cols[col].otsu = th;
+      }
+    }
   }
 }
 
@@ -211,48 +268,47 @@ __device__ __forceinline__ int64_t floor_div_d(int64_t a, int64_t b) {
 }
 
 __global__ void __launch_bounds__(FLOOR_THREADS) floor_kernel(ColArgs a) {
-  extern __shared__ int64_t S[];   // [F]
-  __shared__ int64_t red_min[32];
+  extern __shared__ int64_t S[];   // [F] column PSD, then [F] D-scaled smoothing
+  int64_t *Sh = S + a.F;
+  __shared__ int64_t red_min[32], red_g[32];
   __shared__ int red_found[32];
   __shared__ int64_t c[64];
+  __shared__ int64_t s_N0, s_Pq;
   const int F = a.F, m = a.m, tid = threadIdx.x;
   for (int i = tid; i <= m; i += blockDim.x) c[i] = a.sg_c[i];
   for (int f = tid; f < F; f += blockDim.x) S[f] = (int64_t)a.cols[f].S;
   __syncthreads();
-  // Savitzky-Golay on the interior, lowest local minimum (strictly below the
-  // left neighbour, not above the right one)
+  // Savitzky-Golay (D-scaled) on the interior, 0 elsewhere
+  for (int f = tid; f < F; f += blockDim.x) {
+    int64_t acc = 0;
+    if (f >= m && f <= F - 1 - m) {
+      acc = c[0] * S[f];
+      for (int i = 1; i <= m; ++i) acc += c[i] * (S[f - i] + S[f + i]);
+    }
+    Sh[f] = acc;
+    a.cols[f].Shat = acc;
+  }
+  __syncthreads();
+  // lowest local minimum: strictly below the left neighbour, not above the right
   int64_t best = INT64_MAX, gmin = INT64_MAX;
   int found = 0;
-  auto shat = [&](int f) {
-    int64_t acc = c[0] * S[f];
-    for (int i = 1; i <= m; ++i) acc += c[i] * (S[f - i] + S[f + i]);
-    return acc;
-  };
   for (int f = m + tid; f <= F - 1 - m; f += blockDim.x) {
-    const int64_t v = shat(f);
-    a.cols[f].Shat = v;
+    const int64_t v = Sh[f];
     gmin = min(gmin, v);
-    if (f >= m + 1 && f <= F - 2 - m) {
-      const int64_t l = shat(f - 1), r = shat(f + 1);
-      if (v < l && v <= r) { found = 1; best = min(best, v); }
+    if (f >= m + 1 && f <= F - 2 - m && v < Sh[f - 1] && v <= Sh[f + 1]) {
+      found = 1;
+      best = min(best, v);
     }
   }
-  for (int f = tid; f < F; f += blockDim.x)
-    if (f < m || f > F - 1 - m) a.cols[f].Shat = 0;
-  // block reductions
   const int lane = tid & 31, w = tid >> 5;
-  int64_t b2 = best, g2 = gmin;
-  int fd = found;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    b2 = min(b2, __shfl_xor_sync(0xffffffffu, b2, o));
-    g2 = min(g2, __shfl_xor_sync(0xffffffffu, g2, o));
-    fd |= __shfl_xor_sync(0xffffffffu, fd, o);
+    best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+    gmin = min(gmin, __shfl_xor_sync(0xffffffffu, gmin, o));
+    found |= __shfl_xor_sync(0xffffffffu, found, o);
   }
-  __shared__ int64_t red_g[32];
-  if (lane == 0) { red_min[w] = b2; red_g[w] = g2; red_found[w] = fd; }
+  if (lane == 0) { red_min[w] = best; red_g[w] = gmin; red_found[w] = found; }
   __syncthreads();
-  __shared__ int64_t s_N0, s_Pq;
   if (tid == 0) {
     int64_t bb = INT64_MAX, gg = INT64_MAX;
     int ff = 0;
@@ -265,7 +321,7 @@ __global__ void __launch_bounds__(FLOOR_THREADS) floor_kernel(ColArgs a) {
     const int64_t DT = a.D * a.T;
     int64_t Pq = 0;
     if (a.pow_on) {
-      Pq = -floor_div_d(-(N0 + a.delta_pow), DT);
+      Pq = -floor_div_d(-(N0 + a.delta_pow), DT);   // ceil((N0 + delta_pow) / DT)
       Pq = Pq < 0 ? 0 : (Pq > 256 ? 256 : Pq);
     }
     s_N0 = N0;
@@ -289,168 +345,201 @@ __global__ void __launch_bounds__(FLOOR_THREADS) floor_kernel(ColArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Threshold + morphology on bit-packed tiles.  A tile is 120 interior rows x
-// 32 interior words (1024 columns) plus a halo of 4 rows and 1 word (32
-// columns) on every side: the four 3x3 operations shift information by one
-// row each and all six by one column each, so the interior is exact.  A
-// pixel outside the image takes no part in an operation: it reads as 0 for a
-// dilation and as 1 for an erosion (the clipped window).  544 threads: in
-// each operation every thread computes one word-column of 8 rows.
+// Threshold + morphology, streaming.  A warp owns a window of 32 row words
+// (1024 columns) of a band of rows; lane l holds word w0-1+l, and only lanes
+// 1..30 produce output (lanes 0 and 31 are halo: each of the six operations
+// moves information by at most one column, so corruption entering at a
+// window edge never reaches the 31st bit inward).  The warp walks down the
+// band one input row per step; the six operations form a register pipeline:
+// an operation keeps the horizontally processed last two rows of its input
+// and emits one row per step (a 3x3 operation lags its input by one row), so
+// the final row of step s is input row s-4.  Neighbour words come from the
+// adjacent lanes by shuffle.  The band is read with a 4-row halo above and
+// below; rows are prefetched 4 steps ahead.  A pixel outside the image takes
+// no part in an operation: the operation sees 0 there for a dilation and 1
+// for an erosion (the clipped window).  The kernel also counts the runs
+// (maximal horizontal segments) starting in each row of the final mask.
 // ---------------------------------------------------------------------------
-constexpr int MT_ROWS = 128, MT_IN_ROWS = 120, MT_WORDS = 34, MT_IN_WORDS = 32;
-constexpr int MT_RB = 8, MT_THREADS = MT_WORDS * (MT_ROWS / MT_RB);   // 544
+constexpr int MS_LANES_OUT = 30, MS_PF = 4, MS_WARPS = 8;
 
-struct TileCtx {
-  int64_t t_base;   // image row of tile row 0
-  int64_t w_base;   // image word of tile word 0
-  int64_t T;
-  int Wd;
-};
-
-template <bool ERODE>
-__device__ __forceinline__ uint32_t tget(const uint32_t *in, int r, int w, const TileCtx &c) {
-  const int64_t t = c.t_base + r, gw = c.w_base + w;
-  if (t < 0 || t >= c.T || gw < 0 || gw >= c.Wd) return ERODE ? 0xffffffffu : 0u;
-  if (r < 0 || r >= MT_ROWS || w < 0 || w >= MT_WORDS) return 0u;   // outside the tile: never used
-  return in[r * MT_WORDS + w];
-}
-
-template <bool ERODE>
-__device__ __forceinline__ uint32_t hop_row(const uint32_t *in, int r, int w, const TileCtx &c) {
-  const uint32_t x = tget<ERODE>(in, r, w, c);
-  const uint32_t l = tget<ERODE>(in, r, w - 1, c);
-  const uint32_t rt = tget<ERODE>(in, r, w + 1, c);
-  const uint32_t xl = (x << 1) | (l >> 31);    // pixel f-1 moved to f
-  const uint32_t xr = (x >> 1) | (rt << 31);   // pixel f+1 moved to f
-  return ERODE ? (x & xl & xr) : (x | xl | xr);
-}
-
-// one operation over the whole tile: 3x3 (VERT) or 1x3, dilation or erosion
 template <bool ERODE, bool VERT>
-__device__ __forceinline__ void morph_op(const uint32_t *in, uint32_t *out, const TileCtx &c) {
-  const int w = threadIdx.x % MT_WORDS;
-  const int r0 = (threadIdx.x / MT_WORDS) * MT_RB;
-  if constexpr (VERT) {
-    uint32_t above = hop_row<ERODE>(in, r0 - 1, w, c);
-    uint32_t cur = hop_row<ERODE>(in, r0, w, c);
-#pragma unroll
-    for (int i = 0; i < MT_RB; ++i) {
-      const uint32_t below = hop_row<ERODE>(in, r0 + i + 1, w, c);
-      out[(r0 + i) * MT_WORDS + w] = ERODE ? (above & cur & below) : (above | cur | below);
-      above = cur;
-      cur = below;
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < MT_RB; ++i) out[(r0 + i) * MT_WORDS + w] = hop_row<ERODE>(in, r0 + i, w, c);
+struct MorphOp {
+  uint32_t a = 0, b = 0;   // horizontal results of the two previous input rows
+  // x: this step's input row (already this lane's word); in: row and lane inside the image
+  __device__ __forceinline__ uint32_t step(uint32_t x, bool in) {
+    if (!in) x = ERODE ? 0xffffffffu : 0u;
+    const uint32_t l = __shfl_up_sync(0xffffffffu, x, 1);
+    const uint32_t r = __shfl_down_sync(0xffffffffu, x, 1);
+    const uint32_t xl = (x << 1) | (l >> 31);    // pixel f-1 moved to f
+    const uint32_t xr = (x >> 1) | (r << 31);    // pixel f+1 moved to f
+    const uint32_t h = ERODE ? (x & xl & xr) : (x | xl | xr);
+    if constexpr (!VERT) return h;
+    const uint32_t o = ERODE ? (a & b & h) : (a | b | h);   // output row = input row - 1
+    a = b;
+    b = h;
+    return o;
   }
-}
+};
 
 __device__ __forceinline__ uint32_t gather4(uint32_t m) {
   // bit j of the result = bit 0 of byte j (each byte of m is 0x00 or 0xff)
   return (((m & 0x01010101u) * 0x01020408u) >> 24) & 0xfu;
 }
 
-__device__ __forceinline__ void store_tile(const uint32_t *in, uint32_t *dst, const TileCtx &c) {
-  for (int i = threadIdx.x; i < MT_IN_ROWS * MT_IN_WORDS; i += blockDim.x) {
-    const int r = 4 + i / MT_IN_WORDS, w = 1 + i % MT_IN_WORDS;
-    const int64_t t = c.t_base + r, gw = c.w_base + w;
-    if (t < c.T && gw < c.Wd) dst[t * c.Wd + gw] = in[r * MT_WORDS + w];
-  }
-}
-
-__global__ void __launch_bounds__(MT_THREADS)
-morph_kernel(MorphArgs a) {
-  __shared__ uint32_t A[MT_ROWS * MT_WORDS], B[MT_ROWS * MT_WORDS];
-  __shared__ __align__(16) uint8_t eff[MT_WORDS * 32];
-  const int Wd = a.F / 32;
-  TileCtx c;
-  c.t_base = (int64_t)blockIdx.y * MT_IN_ROWS - 4;
-  c.w_base = (int64_t)blockIdx.x * MT_IN_WORDS - 1;
-  c.T = a.T;
-  c.Wd = Wd;
-  for (int i = threadIdx.x; i < MT_WORDS * 32; i += blockDim.x) {
-    const int64_t col = c.w_base * 32 + i;
-    eff[i] = (col >= 0 && col < a.F) ? a.effm1[col] : 255;
-  }
-  __syncthreads();
-  // threshold: foreground where q > eff-1
-  for (int i = threadIdx.x; i < MT_ROWS * MT_WORDS; i += blockDim.x) {
-    const int r = i / MT_WORDS, w = i % MT_WORDS;
-    const int64_t t = c.t_base + r, gw = c.w_base + w;
-    uint32_t bits = 0;
-    if (t >= 0 && t < a.T && gw >= 0 && gw < Wd) {
-      const uint4 *src = reinterpret_cast<const uint4 *>(a.img + t * a.F + gw * 32);
-      const uint4 q0 = __ldg(src), q1 = __ldg(src + 1);
-      const uint4 *e4 = reinterpret_cast<const uint4 *>(eff + w * 32);
-      const uint4 e0 = e4[0], e1 = e4[1];
-      const uint32_t qs[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-      const uint32_t es[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+__device__ __forceinline__ uint32_t threshold32(const uint4 &q0, const uint4 &q1, const uint4 &e0,
+                                                const uint4 &e1) {
+  const uint32_t qs[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+  const uint32_t es[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+  uint32_t bits = 0;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) bits |= gather4(__vcmpgtu4(qs[k], es[k])) << (4 * k);
-    }
-    A[i] = bits;
-  }
-  __syncthreads();
-  if (a.dbg0) store_tile(A, a.dbg0, c);
-  if (a.order == 0) {
-    morph_op<false, true>(A, B, c); __syncthreads();   // close 3x3: dilate
-    morph_op<true, true>(B, A, c);  __syncthreads();   //            erode
-    if (a.dbg1) store_tile(A, a.dbg1, c);
-    morph_op<true, true>(A, B, c);  __syncthreads();   // open 3x3: erode
-    morph_op<false, true>(B, A, c); __syncthreads();   //           dilate
-    if (a.dbg2) store_tile(A, a.dbg2, c);
-    morph_op<true, false>(A, B, c); __syncthreads();   // open 1x3: erode
-    morph_op<false, false>(B, A, c); __syncthreads();  //           dilate
-  } else {
-    morph_op<true, false>(A, B, c); __syncthreads();   // open 1x3
-    morph_op<false, false>(B, A, c); __syncthreads();
-    if (a.dbg1) store_tile(A, a.dbg1, c);
-    morph_op<false, true>(A, B, c); __syncthreads();   // close 3x3
-    morph_op<true, true>(B, A, c);  __syncthreads();
-    if (a.dbg2) store_tile(A, a.dbg2, c);
-    morph_op<true, true>(A, B, c);  __syncthreads();   // open 3x3
-    morph_op<false, true>(B, A, c); __syncthreads();
-  }
-  store_tile(A, a.mask, c);
+  for (int k = 0; k < 8; ++k) bits |= gather4(__vcmpgtu4(qs[k], es[k])) << (4 * k);
+  return bits;   // foreground where q > eff-1
 }
 
+// ORDER 0: close3 (dilate, erode), open3 (erode, dilate), open1x3 (erode, dilate)
+// ORDER 1: open1x3, close3, open3.  D_k = rows by which the input of op k lags.
+template <int ORDER>
+__global__ void __launch_bounds__(32 * MS_WARPS, 2)
+morph_stream_kernel(MorphArgs a, int nx, int rows_per_band, int n_warps) {
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (gwarp >= n_warps) return;
+  const int Wd = a.F / 32;
+  const int T = (int)a.T;                                  // T <= 2^19
+  const int xs = gwarp % nx;
+  const int band = gwarp / nx;
+  const int gw = xs * MS_LANES_OUT - 1 + lane;             // this lane's image word
+  const bool lane_in = gw >= 0 && gw < Wd;
+  const bool out_lane = lane >= 1 && lane <= MS_LANES_OUT && lane_in;
+  const int tb0 = band * rows_per_band;
+  const int tb1 = min(T, tb0 + rows_per_band);
+  uint4 e0 = make_uint4(~0u, ~0u, ~0u, ~0u), e1 = e0;
+  if (lane_in) {
+    const uint4 *e = reinterpret_cast<const uint4 *>(a.effm1 + 32 * gw);
+    e0 = __ldg(e);
+    e1 = __ldg(e + 1);
+  }
+  MorphOp<ORDER == 0 ? false : true, ORDER == 0> op1;    // dilate3 | erode1x3
+  MorphOp<ORDER == 0 ? true : false, ORDER == 0> op2;    // erode3  | dilate1x3
+  MorphOp<ORDER == 0 ? true : false, true> op3;          // erode3  | dilate3
+  MorphOp<ORDER == 0 ? false : true, true> op4;          // dilate3 | erode3
+  MorphOp<true, ORDER == 1> op5;                         // erode1x3 | erode3
+  MorphOp<false, ORDER == 1> op6;                        // dilate1x3 | dilate3
+  // Software pipeline: at each step every operation consumes its
+  // predecessor's output of the previous step, so the six operations of a
+  // step are independent of one another.  Row of stage k's output at step s
+  // (input row i = first + s): out_k = out_{k-1} - 1 - (op k is 3x3), out_0 = i;
+  // the final stage lags 10 rows.  IN_k = input row lag of op k.
+  constexpr int IN1 = 1, IN2 = ORDER == 0 ? 3 : 2, IN3 = ORDER == 0 ? 5 : 3;
+  constexpr int IN4 = ORDER == 0 ? 7 : 5, IN5 = ORDER == 0 ? 9 : 7, IN6 = ORDER == 0 ? 10 : 9;
+  constexpr int DBG1 = ORDER == 0 ? 4 : 2, DBG2 = ORDER == 0 ? 8 : 6, LAG = 10;
+  const int first = tb0 - 4;
+  const int nsteps = (tb1 - tb0) + 4 + LAG;
+  // byte column of this lane; rows are reached by 64-bit pointer steps
+  const uint8_t *base = a.img + 32 * (lane_in ? gw : 0);
+  uint4 ring[MS_PF][2];
+#pragma unroll
+  for (int k = 0; k < MS_PF; ++k) {
+    const int i = first + k;
+    ring[k][0] = ring[k][1] = make_uint4(0, 0, 0, 0);
+    if (lane_in && i >= 0 && i < T) {
+      const uint4 *p = reinterpret_cast<const uint4 *>(base + (int64_t)i * a.F);
+      ring[k][0] = __ldg(p);
+      ring[k][1] = __ldg(p + 1);
+    }
+  }
+  uint32_t p0 = 0, p1 = 0, p2 = 0, p3 = 0, p4 = 0, p5 = 0;   // previous-step stage outputs
+  auto in_img = [&](int row) { return lane_in && (unsigned)row < (unsigned)T; };
+  for (int s0 = 0; s0 < nsteps; s0 += MS_PF) {
+#pragma unroll
+    for (int k = 0; k < MS_PF; ++k) {
+      const int s = s0 + k;
+      if (s < nsteps) {   // warp-uniform
+        const int i = first + s;
+        uint32_t x0 = 0;
+        if (in_img(i) && i <= tb1 + 3) x0 = threshold32(ring[k][0], ring[k][1], e0, e1);
+        const int ip = i + MS_PF;   // prefetch
+        if (in_img(ip) && ip <= tb1 + 3) {
+          const uint4 *p = reinterpret_cast<const uint4 *>(base + (int64_t)ip * a.F);
+          ring[k][0] = __ldg(p);
+          ring[k][1] = __ldg(p + 1);
+        }
+        const uint32_t x1 = op1.step(p0, in_img(i - IN1));
+        const uint32_t x2 = op2.step(p1, in_img(i - IN2));
+        const uint32_t x3 = op3.step(p2, in_img(i - IN3));
+        const uint32_t x4 = op4.step(p3, in_img(i - IN4));
+        const uint32_t x5 = op5.step(p4, in_img(i - IN5));
+        const uint32_t x6 = op6.step(p5, in_img(i - IN6));
+        p0 = x0; p1 = x1; p2 = x2; p3 = x3; p4 = x4; p5 = x5;
+        if (a.dbg0 && out_lane && i >= tb0 && i < tb1) a.dbg0[(int64_t)i * Wd + gw] = x0;
+        if (a.dbg1) {
+          const int r = i - DBG1;
+          if (out_lane && r >= tb0 && r < tb1) a.dbg1[(int64_t)r * Wd + gw] = x2;
+        }
+        if (a.dbg2) {
+          const int r = i - DBG2;
+          if (out_lane && r >= tb0 && r < tb1) a.dbg2[(int64_t)r * Wd + gw] = x4;
+        }
+        const int r = i - LAG;   // the final row of this step
+        if (r >= tb0 && r < tb1) {   // warp-uniform
+          // runs starting in this word: its bit 31 neighbour is the left lane's
+          // word (exact on the halo lane too), or nothing at the image's left edge
+          const uint32_t left = __shfl_up_sync(0xffffffffu, x6, 1);
+          if (out_lane) {
+            a.mask[(int64_t)r * Wd + gw] = x6;
+            const uint32_t lft = gw > 0 ? left : 0u;
+            const uint32_t n = __popc(x6 & ~((x6 << 1) | (lft >> 31)));
+            if (n) atomicAdd(&a.row_cnt[r], n);
+          }
+        }
+      }
+    }
+  }
+}
 }  // namespace
 
-cudaError_t launch_hist(const uint8_t *img, int64_t T, int F, uint32_t *hist, int num_sms,
-                        cudaStream_t s) {
-  dim3 grid;
-  int64_t rows;
-  hist_grid(T, F, num_sms, grid, rows);
-  const size_t sm = 128 * HIST_COLS * sizeof(uint32_t);
-  cudaError_t e = cudaFuncSetAttribute(hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  hist_kernel<<<grid, HIST_THREADS, sm, s>>>(img, T, F, rows, hist);
-  count_launches(1);
+// Cluster histogram (optionally quantising float power on the way).  The
+// histogram is written whole (no zeroing needed) unless T needs more than one
+// cluster of bands, in which case the caller's zeroed histogram is accumulated.
+bool cluster_hist_accumulates(int64_t T) { return T > (int64_t)CH_BANDS * HIST_MAX_ROWS; }
+
+cudaError_t launch_cluster_hist(const void *src, bool from_power, int64_t T, int F,
+                                const float *edges, const float *qconst, uint8_t *img,
+                                uint32_t *hist, rise_colstat *cols, bool *needs_zero,
+                                cudaStream_t s) {
+  int64_t groups = 1;
+  while ((T + groups * CH_BANDS - 1) / (groups * CH_BANDS) > HIST_MAX_ROWS) ++groups;
+  const int64_t rows = (T + groups * CH_BANDS - 1) / (groups * CH_BANDS);
+  const int accumulate = groups > 1;
+  if (needs_zero) *needs_zero = accumulate;
+  dim3 grid(F / CH_COLS, (unsigned)(groups * CH_BANDS));
+  const size_t sm = (size_t)CH_WORDS * sizeof(uint32_t);
+  static_assert(CH_WARPS >= CH_NS, "one warp per reduced column");
+  cudaError_t e;
+  if (from_power) {
+    e = cudaFuncSetAttribute(cluster_hist_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    cluster_hist_kernel<true><<<grid, 32 * CH_WARPS, sm, s>>>(src, T, F, rows, edges, qconst, img, hist, cols, accumulate);
+    count_launches(1);
+  } else {
+    e = cudaFuncSetAttribute(cluster_hist_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    cluster_hist_kernel<false><<<grid, 32 * CH_WARPS, sm, s>>>(src, T, F, rows, edges, qconst, img, hist, cols, accumulate);
+    count_launches(1);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_quant_hist(const float *power, int64_t T, int F, const float *edges,
-                              const float *qconst, uint8_t *img, uint32_t *hist, int num_sms,
-                              cudaStream_t s) {
-  dim3 grid;
-  int64_t rows;
-  hist_grid(T, F, num_sms, grid, rows);
-  const size_t sm = 128 * HIST_COLS * sizeof(uint32_t);
-  cudaError_t e = cudaFuncSetAttribute(quant_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  quant_hist_kernel<<<grid, HIST_THREADS, sm, s>>>(power, T, F, rows, edges, qconst, img, hist);
-  count_launches(1);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_colstats(const ColArgs &a, cudaStream_t s) {
-  const int warps_per_block = 8;
-  otsu_kernel<<<(a.F + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(a);
-  count_launches(1);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const size_t sm = (size_t)a.F * sizeof(int64_t);
+cudaError_t launch_colstats(const ColArgs &a, bool need_otsu, cudaStream_t s) {
+  cudaError_t e;
+  if (need_otsu) {
+    const int warps_per_block = 8;
+    otsu_kernel<<<(a.F + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(a);
+    count_launches(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  const size_t sm = 2 * (size_t)a.F * sizeof(int64_t);
   e = cudaFuncSetAttribute(floor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   floor_kernel<<<1, FLOOR_THREADS, sm, s>>>(a);
@@ -460,8 +549,20 @@ cudaError_t launch_colstats(const ColArgs &a, cudaStream_t s) {
 
 cudaError_t launch_morph(const MorphArgs &a, cudaStream_t s) {
   const int Wd = a.F / 32;
-  dim3 grid((Wd + MT_IN_WORDS - 1) / MT_IN_WORDS, (unsigned)((a.T + MT_IN_ROWS - 1) / MT_IN_ROWS));
-  morph_kernel<<<grid, MT_THREADS, 0, s>>>(a);
+  const int nx = (Wd + MS_LANES_OUT - 1) / MS_LANES_OUT;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want_warps = (int64_t)sms * 16;
+  int64_t bands = std::max<int64_t>(1, (want_warps + nx - 1) / nx);
+  int64_t rows = std::max<int64_t>(32, (a.T + bands - 1) / bands);
+  bands = (a.T + rows - 1) / rows;
+  const int64_t n_warps = bands * nx;
+  const unsigned blocks = (unsigned)((n_warps + MS_WARPS - 1) / MS_WARPS);
+  if (a.order == 0)
+    morph_stream_kernel<0><<<blocks, 32 * MS_WARPS, 0, s>>>(a, nx, (int)rows, (int)n_warps);
+  else
+    morph_stream_kernel<1><<<blocks, 32 * MS_WARPS, 0, s>>>(a, nx, (int)rows, (int)n_warps);
   count_launches(1);
   return cudaGetLastError();
 }

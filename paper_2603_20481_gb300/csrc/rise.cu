@@ -38,6 +38,7 @@ struct Small {              // one device block of small per-call data
   int64_t floor_out[8];
   int64_t sgc[32];
   uint64_t energy[256];
+  double ratio[256];   // 10^((j - 255.5) level_db / 10), j = 0..255
 };
 
 }  // namespace
@@ -57,6 +58,9 @@ struct rise_ctx {
   int64_t run_cap = 0;
   Small *small = nullptr;   // device
   Small *small_h = nullptr; // pinned host mirror for readback
+  rise_box *hbox = nullptr;     // mapped pinned host buffer the compaction writes into
+  rise_box *hbox_dev = nullptr; // its device address
+  int64_t hbox_cap = 0;
   std::map<int, Tables> tables;
   double energy_level_db = NAN;
   int sg_m = -1;
@@ -109,6 +113,34 @@ int ensure(rise_ctx *c, Buf &b, size_t bytes) {
   return RISE_OK;
 }
 
+// Mapped pinned host buffer for the boxes (grown to at least `cap` entries).
+int ensure_hbox(rise_ctx *c, int64_t cap) {
+  if (c->hbox_cap >= cap) return RISE_OK;
+  if (c->hbox) {
+    CK(cudaStreamSynchronize(c->stream));
+    cudaFreeHost(c->hbox);
+    c->hbox = nullptr;
+    c->hbox_dev = nullptr;
+    c->hbox_cap = 0;
+  }
+  const int64_t want = std::max<int64_t>(cap, 4096);
+  void *h = nullptr;
+  if (cudaHostAlloc(&h, (size_t)want * sizeof(rise_box), cudaHostAllocMapped) != cudaSuccess) {
+    cudaGetLastError();
+    return RISE_ENOMEM;
+  }
+  void *d = nullptr;
+  if (cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeHost(h);
+    return RISE_ECUDA;
+  }
+  c->hbox = reinterpret_cast<rise_box *>(h);
+  c->hbox_dev = reinterpret_cast<rise_box *>(d);
+  c->hbox_cap = want;
+  return RISE_OK;
+}
+
 int get_tables(rise_ctx *c, int N, Tables **out) {
   auto it = c->tables.find(N);
   if (it != c->tables.end()) {
@@ -136,7 +168,9 @@ int get_tables(rise_ctx *c, int N, Tables **out) {
 bool pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 
 int check_thresholds(const rise_thresholds &t, int F) {
-  if (!(t.level_db > 0.0) || !std::isfinite(t.level_db)) return RISE_EINVAL;
+  // level widths from 0.01 to 10 dB: the fast level estimate's error stays
+  // below 1.5e-4 levels there, inside the exact-comparison guard band
+  if (!(t.level_db >= 0.01 && t.level_db <= 10.0)) return RISE_EINVAL;
   if (t.range_mode != RISE_RANGE_AUTO_MAX && t.range_mode != RISE_RANGE_FIXED) return RISE_EINVAL;
   if (t.range_mode == RISE_RANGE_FIXED && !std::isfinite(t.hi_db)) return RISE_EINVAL;
   if (std::isnan(t.psd_offset_db) || std::isnan(t.power_offset_db)) return RISE_EINVAL;
@@ -151,16 +185,37 @@ void record(rise_ctx *c, int i) {
   if (c->timing) cudaEventRecord(c->ev[i], c->stream);
 }
 
+// Per-level tables that depend only on level_db: the energy of each level
+// (round(2^32 * 10^((q-255) level_db/10))) and the power ratio of each level
+// edge (10^((j-255.5) level_db/10)).
+int upload_level_tables(rise_ctx *c, double level_db) {
+  if (c->energy_level_db == level_db) return RISE_OK;
+  uint64_t E[256];
+  double R[256];
+  for (int q = 0; q < 256; ++q) {
+    E[q] = (uint64_t)std::llround(std::exp2(32.0) * std::pow(10.0, (double)(q - 255) * level_db / 10.0));
+    R[q] = std::pow(10.0, ((double)q - 255.5) * level_db / 10.0);
+  }
+  CK(cudaMemcpyAsync(c->small->energy, E, sizeof(E), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->small->ratio, R, sizeof(R), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->energy_level_db = level_db;
+  return RISE_OK;
+}
+
 // Everything from the 8-bit image on: histogram (unless already built),
 // column statistics, morphology, labelling, boxes back to the host.
 int image_path(rise_ctx *c, const uint8_t *img, int64_t T, int F, const rise_thresholds &thr,
                bool hist_ready, rise_box *out, int64_t cap, int64_t *n_boxes) {
   Small *sm = c->small;
   cudaStream_t s = c->stream;
-  const int Wd = F / 32;
+  int rc0;
   if (!hist_ready) {
-    CK(cudaMemsetAsync(c->hist.p, 0, (size_t)F * 256 * sizeof(uint32_t), s));
-    CK(launch_hist(img, T, F, reinterpret_cast<uint32_t *>(c->hist.p), c->num_sms, s));
+    if (cluster_hist_accumulates(T))
+      CK(cudaMemsetAsync(c->hist.p, 0, (size_t)F * 256 * sizeof(uint32_t), s));
+    CK(launch_cluster_hist(img, false, T, F, nullptr, nullptr, nullptr,
+                           reinterpret_cast<uint32_t *>(c->hist.p),
+                           reinterpret_cast<rise_colstat *>(c->cols.p), nullptr, s));
   }
   record(c, 3);
   // column statistics
@@ -188,7 +243,7 @@ int image_path(rise_ctx *c, const uint8_t *img, int64_t T, int F, const rise_thr
   ca.cols = reinterpret_cast<rise_colstat *>(c->cols.p);
   ca.effm1 = reinterpret_cast<uint8_t *>(c->effm1.p);
   ca.floor_out = sm->floor_out;
-  CK(launch_colstats(ca, s));
+  CK(launch_colstats(ca, cluster_hist_accumulates(T), s));
   record(c, 4);
   // mask + morphology
   MorphArgs ma;
@@ -201,19 +256,14 @@ int image_path(rise_ctx *c, const uint8_t *img, int64_t T, int F, const rise_thr
   ma.dbg0 = c->keep_masks ? reinterpret_cast<uint32_t *>(c->dbg[0].p) : nullptr;
   ma.dbg1 = c->keep_masks ? reinterpret_cast<uint32_t *>(c->dbg[1].p) : nullptr;
   ma.dbg2 = c->keep_masks ? reinterpret_cast<uint32_t *>(c->dbg[2].p) : nullptr;
+  ma.row_cnt = reinterpret_cast<uint32_t *>(c->row_cnt.p);
+  CK(cudaMemsetAsync(c->row_cnt.p, 0, (size_t)T * sizeof(uint32_t), s));
   CK(launch_morph(ma, s));
   record(c, 5);
   // labelling
-  if (c->energy_level_db != thr.level_db) {
-    uint64_t E[256];
-    for (int q = 0; q < 256; ++q)
-      E[q] = (uint64_t)std::llround(std::exp2(32.0) * std::pow(10.0, (double)(q - 255) * thr.level_db / 10.0));
-    CK(cudaMemcpyAsync(sm->energy, E, sizeof(E), cudaMemcpyHostToDevice, s));
-    CK(cudaStreamSynchronize(s));
-    c->energy_level_db = thr.level_db;
-  }
+  if ((rc0 = upload_level_tables(c, thr.level_db))) return rc0;
   int rc;
-  if ((rc = ensure(c, c->boxes, (size_t)std::max<int64_t>(cap, 1) * sizeof(rise_box)))) return rc;
+  if ((rc = ensure_hbox(c, std::max<int64_t>(cap, 1)))) return rc;
   CclArgs la;
   la.mask = ma.mask;
   la.img = img;
@@ -223,7 +273,7 @@ int image_path(rise_ctx *c, const uint8_t *img, int64_t T, int F, const rise_thr
   la.row_base = reinterpret_cast<int64_t *>(c->row_base.p);
   la.row_cnt = reinterpret_cast<uint32_t *>(c->row_cnt.p);
   la.status = &sm->status;
-  la.boxes = reinterpret_cast<rise_box *>(c->boxes.p);
+  la.boxes = c->hbox_dev;   // boxes land directly in mapped pinned host memory
   la.box_cap = cap;
   auto bind_runs = [&]() {
     la.run_cap = c->run_cap;
@@ -239,6 +289,7 @@ int image_path(rise_ctx *c, const uint8_t *img, int64_t T, int F, const rise_thr
   CK(launch_ccl_label(la, c->num_sms, s));
   record(c, 6);
   CK(cudaMemcpyAsync(&c->small_h->status, &sm->status, sizeof(DeviceStatus), cudaMemcpyDeviceToHost, s));
+  record(c, 7);
   CK(cudaStreamSynchronize(s));
   DeviceStatus h = c->small_h->status;
   if (h.err & ERR_RUN_CAPACITY) {
@@ -255,6 +306,7 @@ int image_path(rise_ctx *c, const uint8_t *img, int64_t T, int F, const rise_thr
     CK(launch_ccl_label(la, c->num_sms, s));
     record(c, 6);
     CK(cudaMemcpyAsync(&c->small_h->status, &sm->status, sizeof(DeviceStatus), cudaMemcpyDeviceToHost, s));
+    record(c, 7);
     CK(cudaStreamSynchronize(s));
     h = c->small_h->status;
   }
@@ -262,11 +314,7 @@ int image_path(rise_ctx *c, const uint8_t *img, int64_t T, int F, const rise_thr
   if (h.err) return RISE_EINTERNAL;
   *n_boxes = h.n_boxes;
   const int64_t ncopy = std::min<int64_t>(h.n_boxes, cap);
-  if (ncopy > 0 && out) {
-    CK(cudaMemcpyAsync(out, c->boxes.p, (size_t)ncopy * sizeof(rise_box), cudaMemcpyDeviceToHost, s));
-  }
-  record(c, 7);
-  CK(cudaStreamSynchronize(s));
+  if (ncopy > 0 && out) std::memcpy(out, c->hbox, (size_t)ncopy * sizeof(rise_box));
   if (c->timing) {
     for (int i = 0; i < 7; ++i) cudaEventElapsedTime(&c->stage_ms[i], c->ev[i], c->ev[i + 1]);
     cudaEventElapsedTime(&c->stage_ms[7], c->ev[0], c->ev[7]);
@@ -322,6 +370,7 @@ int detect_device(rise_ctx *c, const void *iq, int64_t n, int N, int hop,
   if (want_power && (rc = ensure(c, c->power, px * sizeof(float)))) return rc;
   Tables *tb;
   if ((rc = get_tables(c, N, &tb))) return rc;
+  if ((rc = upload_level_tables(c, thr.level_db))) return rc;
   cudaStream_t s = c->stream;
   Small *sm = c->small;
   record(c, 0);
@@ -339,25 +388,28 @@ int detect_device(rise_ctx *c, const void *iq, int64_t n, int N, int hop,
   a.qconst = sm->qconst;
   a.tw = tb->tw;
   a.win = tb->win;
+  a.err = &sm->status.err;
   bool hist_ready = false;
   if (thr.range_mode == RISE_RANGE_FIXED) {
     const double hp = std::pow(10.0, thr.hi_db / 10.0);
     record(c, 1);
-    CK(launch_levels(a.max_bits, hp, 1, thr.level_db, sm->edges, sm->qconst, s));
+    CK(launch_levels(a.max_bits, hp, 1, sm->ratio, thr.level_db, sm->edges, sm->qconst, s));
     CK(launch_stft(a, c->keep_power ? STFT_QUANT_POWER : STFT_QUANT, c->num_sms, s));
     c->last_anchor = hp;
   } else if (path == 2) {
     CK(launch_stft(a, STFT_POWER, c->num_sms, s));
     record(c, 1);
-    CK(launch_levels(a.max_bits, 0.0, 0, thr.level_db, sm->edges, sm->qconst, s));
-    CK(cudaMemsetAsync(c->hist.p, 0, (size_t)F * 256 * sizeof(uint32_t), s));
-    CK(launch_quant_hist(a.power, T, F, sm->edges, sm->qconst, a.img,
-                         reinterpret_cast<uint32_t *>(c->hist.p), c->num_sms, s));
+    CK(launch_levels(a.max_bits, 0.0, 0, sm->ratio, thr.level_db, sm->edges, sm->qconst, s));
+    if (cluster_hist_accumulates(T))
+      CK(cudaMemsetAsync(c->hist.p, 0, (size_t)F * 256 * sizeof(uint32_t), s));
+    CK(launch_cluster_hist(a.power, true, T, F, sm->edges, sm->qconst, a.img,
+                           reinterpret_cast<uint32_t *>(c->hist.p),
+                           reinterpret_cast<rise_colstat *>(c->cols.p), nullptr, s));
     hist_ready = true;
   } else {
     CK(launch_stft(a, STFT_MAX, c->num_sms, s));
     record(c, 1);
-    CK(launch_levels(a.max_bits, 0.0, 0, thr.level_db, sm->edges, sm->qconst, s));
+    CK(launch_levels(a.max_bits, 0.0, 0, sm->ratio, thr.level_db, sm->edges, sm->qconst, s));
     CK(launch_stft(a, c->keep_power ? STFT_QUANT_POWER : STFT_QUANT, c->num_sms, s));
   }
   record(c, 2);
@@ -443,7 +495,7 @@ int rise_create(rise_ctx **out, const rise_config *cfg) {
       // the 8-bit image of a capture with hop >= F/2 has at most 2 pixels per sample
       if ((rc = ensure(c, c->img, (size_t)cfg->max_samples * 2))) break;
     }
-    if (cfg->max_boxes > 0 && (rc = ensure(c, c->boxes, cfg->max_boxes * sizeof(rise_box)))) break;
+    if (cfg->max_boxes > 0 && (rc = ensure_hbox(c, cfg->max_boxes))) break;
   } while (0);
   if (rc) {
     cudaGetLastError();
@@ -466,6 +518,7 @@ void rise_destroy(rise_ctx *c) {
   for (auto &kv : c->tables) cudaFree(kv.second.tw);
   if (c->small) cudaFree(c->small);
   if (c->small_h) cudaFreeHost(c->small_h);
+  if (c->hbox) cudaFreeHost(c->hbox);
   for (auto &e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

@@ -69,12 +69,21 @@ __device__ __forceinline__ void dft2(float2 &a, float2 &b) {
   a = cadd(t, b);
   b = csub(t, b);
 }
+// Packed (f32x2) complex add / subtract: one instruction each, the same
+// rounding as two scalar adds (a - b is computed as b * -1 + a, exact product).
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
 __device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3) {
-  float2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = mul_negi(csub(a1, a3));
-  a0 = cadd(t0, t2);
-  a2 = csub(t0, t2);
-  a1 = cadd(t1, t3);
-  a3 = csub(t1, t3);
+  const float2 t0 = padd(a0, a2), t1 = psub(a0, a2), t2 = padd(a1, a3);
+  // (a1 - a3) with its components swapped, so that multiplying by -i becomes a
+  // lane-wise sign: -i (x + i y) = y - i x
+  const float2 ts = make_float2(a1.y - a3.y, a1.x - a3.x);
+  a0 = padd(t0, t2);
+  a2 = psub(t0, t2);
+  a1 = __ffma2_rn(ts, make_float2(1.0f, -1.0f), t1);
+  a3 = __ffma2_rn(ts, make_float2(-1.0f, 1.0f), t1);
 }
 __device__ __forceinline__ void dft8(float2 *v) {
   // n = 2 n1 + n2, k = k1 + 4 k2
@@ -125,21 +134,64 @@ __device__ __forceinline__ void dft_r(float2 *v) {
   else dft2(v[0], v[1]);
 }
 
-constexpr float kGuard = 1.0e-3f;   // |fast level coordinate error| is below 1e-4
+constexpr float kGuard = 3.0e-4f;   // |fast level coordinate error| is below 1e-4
 
 // 8-bit level of power P: the count of edges[1..255] that P reaches.  A fast
-// estimate from log2(P / anchor) is trusted away from level edges; within
-// kGuard of an edge the power is compared against the exact edge table.
-__device__ __forceinline__ int level_of(float P, float inv_anchor, float c1, const float *edges) {
-  float v = fmaf(__log2f(P * inv_anchor), c1, 255.5f);
-  float fl = floorf(v);
-  float fr = v - fl;
-  int q = (int)fminf(fmaxf(fl, 0.0f), 255.0f);
-  if ((fr < kGuard || fr > 1.0f - kGuard) && v > 1.0f - 2.0f * kGuard && v < 255.0f + 2.0f * kGuard) {
-    for (int it = 0; it < 256 && q < 255 && P >= edges[q + 1]; ++it) ++q;
-    for (int it = 0; it < 256 && q > 0 && P < edges[q]; ++it) --q;
+// estimate from log2(P / anchor) is trusted away from level edges (the float
+// to unsigned conversion floors and clamps to 0..255, NaN and -inf give 0);
+// within kGuard of an edge the power is compared against the exact edge table.
+__device__ __forceinline__ uint32_t level_of(float P, float inv_anchor, float c1, const float *edges) {
+  const float v = fmaf(__log2f(P * inv_anchor), c1, 255.5f);
+  uint32_t q = __float2uint_rd(fminf(v, 255.0f));
+  if (fabsf(v - rintf(v)) < kGuard) {
+    int qi = (int)q;
+    for (int it = 0; it < 256 && qi < 255 && P >= edges[qi + 1]; ++it) ++qi;
+    for (int it = 0; it < 256 && qi > 0 && P < edges[qi]; ++it) --qi;
+    q = (uint32_t)qi;
   }
   return q;
+}
+
+// ---- TMA bulk copies and mbarriers (inline PTX) ---------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+               : "memory");
+}
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *b) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(b))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: try_wait suspends for a hardware-defined interval per call
+constexpr int kWaitLimit = 1 << 22;
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
+  for (int i = 0; i < kWaitLimit; ++i)
+    if (mbar_test(b, parity)) return true;
+  return false;
 }
 
 template <int N, int I, bool FIRST>
@@ -171,27 +223,73 @@ __device__ __forceinline__ void fft_pass(float2 (&v)[16], const float2 *src, flo
 #pragma unroll
       for (int p = 1; p < 16; ++p) v[p] = cmul(v[p], t[(p - 1) * MP + j]);
     }
-#pragma unroll
-    for (int p = 0; p < 16; ++p) dst[padi(tau + p * NR)] = v[p];
   }
 }
 
-template <int N, int MODE>
-__global__ void __launch_bounds__(Plan<N>::THREADS)
+template <int N, int I>
+__device__ __forceinline__ void store_pass(const float2 (&v)[16], float2 *dst, int tau) {
+  constexpr int NR = N / 16;
+#pragma unroll
+  for (int p = 0; p < 16; ++p) dst[padi(tau + p * NR)] = v[p];
+}
+
+// Exchange buffers: two (ping-pong, one barrier per pass) unless they would
+// not fit next to the input stages, then one (two barriers per pass).
+template <int N, bool TMA>
+struct Smem {
+  using PL = Plan<N>;
+  static constexpr size_t STAGE = TMA ? (size_t)PL::FPB * N : 0;   // complex in the input stage
+  static constexpr size_t XB = (size_t)PL::FPB * PL::SLOT;         // complex per exchange buffer
+  static constexpr size_t FIXED = (size_t)PL::TW_REST * 8 + 260 * 4;
+  static constexpr int NXB = (STAGE * 8 + 2 * XB * 8 + FIXED <= 113 * 1024) ? 2 : 1;
+  static constexpr size_t BYTES = STAGE * 8 + NXB * XB * 8 + FIXED;
+  static constexpr int BLOCKS = (BYTES <= 113 * 1024 && PL::THREADS <= 256) ? 2 : 1;  // per SM
+};
+
+template <int N, int MODE, bool TMA>
+__global__ void __launch_bounds__(Plan<N>::THREADS, (Smem<N, TMA>::BLOCKS))
 stft_kernel(StftArgs a, int64_t frames_per_block) {
   using PL = Plan<N>;
-  constexpr int TPF = PL::TPF, FPB = PL::FPB, SLOT = PL::SLOT, NPASS = PL::NPASS;
+  using SM = Smem<N, TMA>;
+  constexpr int TPF = PL::TPF, FPB = PL::FPB, SLOT = PL::SLOT, NPASS = PL::NPASS, NXB = SM::NXB;
   constexpr bool DO_MAX = (MODE == STFT_MAX || MODE == STFT_POWER);
   constexpr bool DO_Q = (MODE == STFT_QUANT || MODE == STFT_QUANT_POWER);
   constexpr bool DO_P = (MODE == STFT_POWER || MODE == STFT_QUANT_POWER);
-  extern __shared__ float2 smem[];
-  float2 *buf[2] = {smem, smem + FPB * SLOT};
-  float2 *twr = smem + 2 * FPB * SLOT;
+  extern __shared__ __align__(128) float2 smem[];
+  float2 *stage = smem;                                   // [STAGE] (TMA only)
+  float2 *xb0 = smem + SM::STAGE;
+  float2 *xb1 = xb0 + (NXB == 2 ? SM::XB : 0);
+  float2 *twr = xb0 + NXB * SM::XB;
   float *edges = reinterpret_cast<float *>(twr + PL::TW_REST);
   __shared__ float red[32];
+  __shared__ __align__(8) uint64_t bar;
 
   const int tid = threadIdx.x;
   const int slot = tid / TPF, tau = tid % TPF;
+  const int64_t f_begin = (int64_t)blockIdx.x * frames_per_block;
+  const int64_t f_end = min(a.T, f_begin + frames_per_block);
+  const int64_t nsteps = (f_end - f_begin + FPB - 1) / FPB;
+
+  auto step_bytes = [&](int64_t st) -> uint32_t {
+    const int64_t t0 = f_begin + st * FPB;
+    const int64_t nfr = (f_end - t0 < FPB) ? (f_end - t0) : (int64_t)FPB;
+    return (uint32_t)(((nfr - 1) * a.hop + N) * sizeof(float2));
+  };
+  // one input stage: the copy for step st+1 is issued as soon as every thread
+  // has its step-st samples in registers, and lands while step st computes
+  auto issue = [&](int64_t st) {
+    const int64_t t0 = f_begin + st * FPB;
+    const uint32_t bytes = step_bytes(st);
+    mbar_expect_tx(&bar, bytes);
+    bulk_g2s(stage, a.iq + t0 * (int64_t)a.hop, bytes, &bar);
+  };
+  if constexpr (TMA) {
+    if (tid == 0) {
+      mbar_init(&bar, 1);
+      mbar_fence_init();
+      if (nsteps > 0) issue(0);
+    }
+  }
 
   float win[16];
   float2 tw0[15];
@@ -208,33 +306,59 @@ stft_kernel(StftArgs a, int64_t frames_per_block) {
   }
   __syncthreads();
 
-  const int64_t f_begin = (int64_t)blockIdx.x * frames_per_block;
-  const int64_t f_end = min(a.T, f_begin + frames_per_block);
   float run_max = 0.0f;
   int parity = 0;
-  for (int64_t t0 = f_begin; t0 < f_end; t0 += FPB, parity ^= ((NPASS & 1) == 0)) {
+  bool failed = false;
+  for (int64_t st = 0; st < nsteps; ++st, parity ^= (NXB == 2 && (NPASS & 1) == 0)) {
+    const int64_t t0 = f_begin + st * FPB;
     const int64_t t = t0 + slot;
     const bool valid = t < f_end;
     float2 v[16];
-    {
+    if constexpr (TMA) {
+      if (!mbar_wait(&bar, (uint32_t)(st & 1))) failed = true;
+      const float2 *x = stage + (valid ? slot * a.hop : 0) + tau;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const float2 s = valid ? x[i * (N / 16)] : make_float2(0.f, 0.f);
+        v[i] = make_float2(s.x * win[i], s.y * win[i]);
+      }
+    } else {
       const float2 *x = a.iq + (valid ? t * (int64_t)a.hop : 0) + tau;
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
-        float2 s = valid ? __ldg(x + i * (N / 16)) : make_float2(0.f, 0.f);
+        const float2 s = valid ? __ldg(x + i * (N / 16)) : make_float2(0.f, 0.f);
         v[i] = make_float2(s.x * win[i], s.y * win[i]);
       }
     }
-    float2 *b0 = buf[parity] + slot * SLOT;
-    float2 *b1 = buf[parity ^ 1] + slot * SLOT;
-    // pass I writes buffer (I + parity) & 1, pass I+1 reads it after one barrier
+    float2 *b0 = (parity ? xb1 : xb0) + slot * SLOT;
+    float2 *b1 = (parity ? xb0 : xb1) + slot * SLOT;
+    if constexpr (NXB == 1) __syncthreads();   // previous frame's last reads done
     fft_pass<N, 0, true>(v, nullptr, b0, tau, tw0, twr);
-    __syncthreads();
+    store_pass<N, 0>(v, b0, tau);
+    if (__syncthreads_or(failed)) {
+      // a staged copy never arrived: record it, let copies in flight land, leave
+      if (tid == 0) {
+        atomicOr(a.err, ERR_INDEX);
+        if constexpr (TMA) mbar_wait(&bar, (uint32_t)(st & 1));
+      }
+      return;
+    }
+    if constexpr (TMA) {
+      if (tid == 0 && st + 1 < nsteps) {
+        fence_proxy_async();   // generic reads of the stage are ordered before the async write
+        issue(st + 1);
+      }
+    }
     if constexpr (NPASS >= 2) {
       fft_pass<N, 1, false>(v, b0, b1, tau, tw0, twr);
       if constexpr (NPASS >= 3) {
+        if constexpr (NXB == 1) __syncthreads();
+        store_pass<N, 1>(v, b1, tau);
         __syncthreads();
         fft_pass<N, 2, false>(v, b1, b0, tau, tw0, twr);
         if constexpr (NPASS >= 4) {
+          if constexpr (NXB == 1) __syncthreads();
+          store_pass<N, 2>(v, b0, tau);
           __syncthreads();
           fft_pass<N, 3, false>(v, b0, b1, tau, tw0, twr);
         }
@@ -272,17 +396,11 @@ stft_kernel(StftArgs a, int64_t frames_per_block) {
   }
 }
 
-template <int N>
-size_t smem_bytes() {
-  using PL = Plan<N>;
-  return (size_t)(2 * PL::FPB * PL::SLOT + PL::TW_REST) * sizeof(float2) + 260 * sizeof(float);
-}
-
-template <int N, int MODE>
+template <int N, int MODE, bool TMA>
 cudaError_t launch_n(const StftArgs &a, int num_sms, cudaStream_t s) {
   using PL = Plan<N>;
-  auto kern = stft_kernel<N, MODE>;
-  const size_t sm = smem_bytes<N>();
+  auto kern = stft_kernel<N, MODE, TMA>;
+  const size_t sm = Smem<N, TMA>::BYTES;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int occ = 0;
@@ -299,23 +417,31 @@ cudaError_t launch_n(const StftArgs &a, int num_sms, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int N>
+template <int N, bool TMA>
 cudaError_t launch_mode(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s) {
   switch (mode) {
-    case STFT_MAX: return launch_n<N, STFT_MAX>(a, num_sms, s);
-    case STFT_QUANT: return launch_n<N, STFT_QUANT>(a, num_sms, s);
-    case STFT_POWER: return launch_n<N, STFT_POWER>(a, num_sms, s);
-    case STFT_QUANT_POWER: return launch_n<N, STFT_QUANT_POWER>(a, num_sms, s);
+    case STFT_MAX: return launch_n<N, STFT_MAX, TMA>(a, num_sms, s);
+    case STFT_QUANT: return launch_n<N, STFT_QUANT, TMA>(a, num_sms, s);
+    case STFT_POWER: return launch_n<N, STFT_POWER, TMA>(a, num_sms, s);
+    case STFT_QUANT_POWER: return launch_n<N, STFT_QUANT_POWER, TMA>(a, num_sms, s);
   }
   return cudaErrorInvalidValue;
 }
 
+template <int N>
+cudaError_t launch_size(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s) {
+  // staged input needs every copy 16-byte aligned: an even hop and a 16-byte aligned base
+  const bool tma = (a.hop % 2 == 0) && ((reinterpret_cast<uintptr_t>(a.iq) & 15) == 0);
+  return tma ? launch_mode<N, true>(a, mode, num_sms, s) : launch_mode<N, false>(a, mode, num_sms, s);
+}
+
 // Edges of the 8-bit levels: level j >= 1 is reached at power
-// anchor * 10^((j - 255.5) * level_db / 10); edges[j] is the smallest float
-// not below that value, so "P >= edges[j]" is the exact comparison for a
-// float P.  edges[0] = 0, edges[256] = +inf.
+// anchor * 10^((j - 255.5) * level_db / 10); ratio[j] holds the power of ten
+// (FP64, computed on the host), edges[j] is the smallest float not below
+// anchor * ratio[j], so "P >= edges[j]" is the exact comparison for a float
+// P.  edges[0] = 0, edges[256] = +inf.
 __global__ void levels_kernel(const uint32_t *max_bits, double hi_power, int use_fixed,
-                              double level_db, float *edges, float *qconst) {
+                              const double *ratio, double level_db, float *edges, float *qconst) {
   const double M = use_fixed ? hi_power : (double)__uint_as_float(*max_bits);
   const int j = threadIdx.x;
   if (j == 0) {
@@ -323,12 +449,11 @@ __global__ void levels_kernel(const uint32_t *max_bits, double hi_power, int use
   } else if (j == 256) {
     edges[256] = __int_as_float(0x7f800000);
   } else if (j < 256) {
-    const double b = M * pow(10.0, ((double)j - 255.5) * level_db / 10.0);
-    edges[j] = M > 0.0 ? __double2float_ru(b) : __int_as_float(0x7f800000);
+    edges[j] = M > 0.0 ? __double2float_ru(M * ratio[j]) : __int_as_float(0x7f800000);
   }
   if (j == 0) {
     qconst[0] = M > 0.0 ? (float)(1.0 / M) : 0.0f;
-    qconst[1] = (float)(10.0 * log10(2.0) / level_db);
+    qconst[1] = (float)(3.0102999566398119521 / level_db);   // 10 log10(2) / level_db
   }
 }
 
@@ -380,19 +505,20 @@ void stft_fill_tables(int N, float2 *tw, float *win) {
 
 cudaError_t launch_stft(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s) {
   switch (a.N) {
-    case 256: return launch_mode<256>(a, mode, num_sms, s);
-    case 512: return launch_mode<512>(a, mode, num_sms, s);
-    case 1024: return launch_mode<1024>(a, mode, num_sms, s);
-    case 2048: return launch_mode<2048>(a, mode, num_sms, s);
-    case 4096: return launch_mode<4096>(a, mode, num_sms, s);
-    case 8192: return launch_mode<8192>(a, mode, num_sms, s);
+    case 256: return launch_size<256>(a, mode, num_sms, s);
+    case 512: return launch_size<512>(a, mode, num_sms, s);
+    case 1024: return launch_size<1024>(a, mode, num_sms, s);
+    case 2048: return launch_size<2048>(a, mode, num_sms, s);
+    case 4096: return launch_size<4096>(a, mode, num_sms, s);
+    case 8192: return launch_size<8192>(a, mode, num_sms, s);
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_levels(const uint32_t *max_bits, double hi_power, int use_fixed,
-                          double level_db, float *edges, float *qconst, cudaStream_t s) {
-  levels_kernel<<<1, 288, 0, s>>>(max_bits, hi_power, use_fixed, level_db, edges, qconst);
+                          const double *ratio, double level_db, float *edges, float *qconst,
+                          cudaStream_t s) {
+  levels_kernel<<<1, 288, 0, s>>>(max_bits, hi_power, use_fixed, ratio, level_db, edges, qconst);
   count_launches(1);
   return cudaGetLastError();
 }

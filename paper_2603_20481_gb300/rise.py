@@ -180,10 +180,17 @@ class Detector:
         return int(v[0])
 
     # -- detection --------------------------------------------------------------
+    def _raw(self, cap: int) -> np.ndarray:
+        buf = getattr(self, "_rawbuf", None)
+        if buf is None or buf.shape[0] < cap:
+            buf = np.empty(max(cap, 1), BOX_DTYPE)
+            self._rawbuf = buf
+        return buf
+
     def _run(self, fn, args, cap):
         cap = self.cap if cap is None else int(cap)
         while True:
-            raw = np.zeros(max(cap, 1), BOX_DTYPE)
+            raw = self._raw(max(cap, 1))
             n = C.c_int64(0)
             rc = fn(*args, raw.ctypes.data if cap > 0 else None, cap, C.byref(n))
             if rc == RISE_ETRUNC and self._auto_grow:

@@ -48,10 +48,15 @@ def _check_power(Pg, Pr):
 
 
 def _check_image(qg, qr):
+    """Levels differ by at most one; returns how many pixels differ.  The
+    1e-5 bar is a rate: it is asserted on pooled and full-size images
+    (test_image_level_mismatch_rate, test_wideband_full_size), where the
+    count is large enough to measure it; a single small image only gets a
+    Poisson-tail guard."""
     d = qg.astype(np.int16) - qr.astype(np.int16)
     nd = int(np.count_nonzero(d))
     assert np.abs(d).max(initial=0) <= 1
-    assert nd <= math.ceil(1e-5 * qg.size), f"{nd} of {qg.size} pixels differ"
+    assert nd <= math.ceil(1e-5 * qg.size) + 6, f"{nd} of {qg.size} pixels differ"
     return nd
 
 
@@ -94,6 +99,37 @@ def test_spectrogram_and_image_parity(det, N, hop, n, fs, seed):
     assert np.array_equal(boxes_g, oracle.detect_image(qg))
     if nd == 0:
         assert np.array_equal(boxes_g, boxes_r)
+
+
+def test_image_level_mismatch_rate(det):
+    """At most 1e-5 of pixels may differ by one 8-bit level from the FP64
+    oracle (the fp32 FFT's rounding puts a few pixels on the other side of a
+    level edge).  Pooled over the STFT cases plus 1024 x 1024 and
+    1023 x 4096 captures, about 11 million pixels."""
+    rise = _rise()
+    det.set_option(rise.OPT_KEEP_POWER, 0)
+    det.set_option(rise.OPT_KEEP_MASKS, 0)
+    caps = [(synth.make_capture(n, fs, 6, 500 + seed, fft_size=N, hop=hop,
+                                bw_hz=(fs / 200, fs / 20), dur_s=(n / fs / 20, n / fs / 3),
+                                snr_db=(5, 25), tone_fraction=0.3), N, hop)
+            for N, hop, n, fs, seed in STFT_CASES]
+    caps += [(synth.single_capture(101), 1024, 1024), (synth.single_capture(103), 1024, 1024)]
+    for seed in range(2):
+        caps.append((synth.make_capture(1 << 21, 100e6, 20, 700 + seed, fft_size=4096, hop=2048,
+                                        bw_hz=(0.1e6, 20e6), dur_s=(0.5e-3, 5e-3),
+                                        snr_db=(-3, 25), tone_fraction=0.25), 4096, 2048))
+    px = diff = 0
+    for cap, N, hop in caps:
+        T = oracle.num_frames(cap.iq.shape[0], N, hop)
+        det.detect(torch.from_numpy(cap.iq).cuda(), N, hop)
+        qg = det.debug(rise.DBG_IMAGE_U8, T, N)
+        _, qr, _ = oracle.detect(cap.iq, N, hop)
+        d = qg.astype(np.int16) - qr.astype(np.int16)
+        assert np.abs(d).max(initial=0) <= 1
+        px += qg.size
+        diff += int(np.count_nonzero(d))
+    assert px > 10_000_000
+    assert diff <= 1e-5 * px, f"{diff} of {px} pixels differ ({diff / px:.2e})"
 
 
 def _image_stage_check(det, q, thr_g, thr_r):
@@ -270,13 +306,19 @@ def test_wideband_full_size_sampled(det):
     boxes_g = det.detect(x, N, hop)
     qg = det.debug(rise.DBG_IMAGE_U8, T, N)
     Mg = float(det.debug(rise.DBG_MAXPOW, T, N)[0])
-    Mr = oracle.max_power(cap.iq, N, hop)
+    boxes_r, qr, Mr = oracle.detect(cap.iq, N, hop)
     assert abs(Mg - Mr) <= 1e-5 * Mr
+    # the whole 32767 x 4096 image within the level budget
+    d = qg.astype(np.int16) - qr.astype(np.int16)
+    assert np.abs(d).max() <= 1
+    assert np.count_nonzero(d) <= 1e-5 * d.size
+    # sampled frames: the spectrogram itself within tolerance
     rng = np.random.default_rng(0)
-    rows = np.unique(np.concatenate([[0, T - 1], rng.integers(0, T, 62)]))
-    for t in rows:
-        Pr = oracle.stft_power(cap.iq, N, hop, int(t), 1)
-        qr = oracle.quantize(Pr, oracle.hi_db_of(Mr))
-        d = qg[t].astype(int) - qr[0].astype(int)
-        assert np.abs(d).max() <= 1 and np.count_nonzero(d) <= 2
+    det.set_option(rise.OPT_KEEP_POWER, 1)
+    det.detect(x, N, hop)
+    Pg_rows = det.debug(rise.DBG_POWER_F32, T, N)
+    det.set_option(rise.OPT_KEEP_POWER, 0)
+    for t in np.unique(np.concatenate([[0, T - 1], rng.integers(0, T, 30)])):
+        _check_power(Pg_rows[t:t + 1], oracle.stft_power(cap.iq, N, hop, int(t), 1))
+    # from the image on, bit-exact
     assert np.array_equal(boxes_g, oracle.detect_image(qg))
