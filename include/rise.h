@@ -45,6 +45,8 @@ extern "C" {
 #define RISE_ECUDA (-4)     /* a CUDA runtime call failed                       */
 #define RISE_ETIMEOUT (-5)  /* a bounded device-side wait gave up               */
 #define RISE_EINTERNAL (-6) /* a kernel's own consistency check failed          */
+#define RISE_ESCRATCH (-7)  /* size beyond the fixed scratch of an allocation-  *
+                            * free entry point                                 */
 
 /* ---- limits ------------------------------------------------------------ */
 #define RISE_MIN_FFT 256
@@ -198,6 +200,39 @@ int rise_set_option(rise_ctx *ctx, int option, int64_t value);
  * [5] labelling and box reduction, [6] status and box readback, [7] total.
  * Writes min(nstages, 8) values.  Errors: RISE_EINVAL. */
 int rise_stage_times(rise_ctx *ctx, float *ms, int nstages);
+
+/* ---- allocation-free column statistics ----------------------------------- */
+/* The paper has no counterpart of this call.  It is for callers that may not
+ * allocate device memory: a host framework that owns all device memory and
+ * forbids allocation inside its per-frame callbacks, or a real-time loop in
+ * which a cudaMalloc / cudaFree (which can synchronise the whole device)
+ * would stall the other streams.  It needs no context and allocates nothing;
+ * its column histograms live in one fixed device array of
+ * RISE_NOALLOC_MAX_COLS x 256 counters (4 MiB), which every GPU that loads
+ * the library holds until the process exits.
+ *
+ * For the 8-bit image img_dev ([T][F] uint8 on the current device, layout
+ * above, 2-byte aligned) it writes, per column f, cols_dev[f].S = sum of the
+ * column's levels and cols_dev[f].otsu = its exact Otsu threshold (Eq. 4;
+ * -1 when no split exists), the same values rise_detect_image reports;
+ * Shat, keep, eff and pad are set to 0.  cols_dev: device rise_colstat[F],
+ * 8-byte aligned.  F a power of two in [RISE_MIN_FFT, RISE_NOALLOC_MAX_COLS],
+ * 1 <= T <= RISE_MAX_ROWS.
+ *
+ * The work is queued on cuda_stream (NULL: the legacy default stream) of the
+ * current device and the call returns without waiting; the results are
+ * valid once the stream reaches them.  The first call on a device looks up
+ * the array's device address (a one-time set-up per device); make that first
+ * call before any stream capture.  Every call, on any stream or thread,
+ * shares the one array per device and clears the part it uses before
+ * counting: calls whose work overlaps on the GPU race and give wrong
+ * results, so order them (one stream, or events).
+ * Errors (nothing is queued): RISE_EINVAL (NULL or misaligned pointers,
+ * pointers not in the current device's memory, bad T or F), RISE_ESCRATCH
+ * (F > RISE_NOALLOC_MAX_COLS), RISE_ECUDA. */
+#define RISE_NOALLOC_MAX_COLS 4096
+int rise_column_stats_noalloc(const uint8_t *img_dev, int64_t T, int F, rise_colstat *cols_dev,
+                              void *cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -180,6 +180,9 @@ struct ColArgs {
   int64_t *floor_out;     // [8]
 };
 cudaError_t launch_colstats(const ColArgs &a, bool need_otsu, cudaStream_t s);
+// S and Otsu threshold of every column of a given [F][256] histogram.
+cudaError_t launch_column_otsu(const uint32_t *hist, int64_t T, int F, rise_colstat *cols,
+                               cudaStream_t s);
 
 struct MorphArgs {
   const uint8_t *img;     // [T][F]

@@ -547,6 +547,19 @@ cudaError_t launch_colstats(const ColArgs &a, bool need_otsu, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_column_otsu(const uint32_t *hist, int64_t T, int F, rise_colstat *cols,
+                               cudaStream_t s) {
+  ColArgs a{};
+  a.hist = hist;
+  a.T = T;
+  a.F = F;
+  a.cols = cols;
+  const int warps_per_block = 8;
+  otsu_kernel<<<(F + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_morph(const MorphArgs &a, cudaStream_t s) {
   const int Wd = a.F / 32;
   const int nx = (Wd + MS_LANES_OUT - 1) / MS_LANES_OUT;

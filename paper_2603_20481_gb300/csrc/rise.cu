@@ -453,6 +453,7 @@ const char *rise_strerror(int code) {
     case RISE_ECUDA: return "CUDA runtime error";
     case RISE_ETIMEOUT: return "bounded device-side wait gave up";
     case RISE_EINTERNAL: return "internal consistency check failed";
+    case RISE_ESCRATCH: return "size exceeds the fixed scratch of the allocation-free entry point";
   }
   return "unknown status";
 }

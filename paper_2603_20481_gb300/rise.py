@@ -21,7 +21,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "librise.so")
 
 RISE_OK, RISE_EINVAL, RISE_ENOMEM, RISE_ETRUNC = 0, -1, -2, -3
-RISE_ECUDA, RISE_ETIMEOUT, RISE_EINTERNAL = -4, -5, -6
+RISE_ECUDA, RISE_ETIMEOUT, RISE_EINTERNAL, RISE_ESCRATCH = -4, -5, -6, -7
+NOALLOC_MAX_COLS = 4096
 RANGE_AUTO_MAX, RANGE_FIXED = 0, 1
 DBG_POWER_F32, DBG_IMAGE_U8, DBG_HIST, DBG_COLSTATS, DBG_FLOOR = 1, 2, 3, 4, 5
 DBG_MASK0, DBG_MASK1, DBG_MASK2, DBG_MASK3, DBG_MAXPOW, DBG_LEVEL_EDGES = 6, 7, 8, 9, 10, 11
@@ -34,7 +35,7 @@ BOX_COLS = ("t0", "t1", "f0", "f1", "anchor", "area", "sum_q", "energy_fx")
 # Functions the header declares; the ABI test checks the library exports them.
 EXPORTS = ("rise_thresholds_default", "rise_create", "rise_destroy", "rise_strerror",
            "rise_detect", "rise_detect_host", "rise_detect_image", "rise_debug_export",
-           "rise_set_option", "rise_stage_times")
+           "rise_set_option", "rise_stage_times", "rise_column_stats_noalloc")
 
 
 class RiseError(RuntimeError):
@@ -99,6 +100,8 @@ def lib() -> C.CDLL:
     L.rise_set_option.restype = i32
     L.rise_stage_times.argtypes = [P, P, i32]
     L.rise_stage_times.restype = i32
+    L.rise_column_stats_noalloc.argtypes = [P, i64, i32, P, P]
+    L.rise_column_stats_noalloc.restype = i32
     _lib = L
     return L
 
@@ -260,6 +263,30 @@ class Detector:
         if rc != RISE_OK:
             raise RiseError(rc, "rise_debug_export")
         return out
+
+
+def column_stats_noalloc(img, cols, stream=None) -> int:
+    """Allocation-free column statistics (rise_column_stats_noalloc).
+
+    `img`: contiguous 2-D CUDA uint8 tensor [T, F]; `cols`: CUDA tensor of at
+    least F * 32 bytes (rise_colstat[F]) on the same device, which receives S
+    and the Otsu threshold of every column.  Work is queued on `stream` (the
+    current torch stream by default) and not waited for.  Returns the status
+    code; the caller decides what to do with a non-zero one.
+    """
+    import torch
+    if not (isinstance(img, torch.Tensor) and img.is_cuda and img.dtype == torch.uint8
+            and img.is_contiguous() and img.dim() == 2):
+        raise TypeError("img must be a contiguous 2-D CUDA uint8 tensor")
+    if not (isinstance(cols, torch.Tensor) and cols.is_cuda and cols.is_contiguous()):
+        raise TypeError("cols must be a contiguous CUDA tensor")
+    if cols.numel() * cols.element_size() < img.shape[1] * COLSTAT_DTYPE.itemsize:
+        raise ValueError("cols is smaller than rise_colstat[F]")
+    if stream is None:
+        stream = torch.cuda.current_stream(img.device)
+    return int(lib().rise_column_stats_noalloc(C.c_void_p(img.data_ptr()), img.shape[0],
+                                               img.shape[1], C.c_void_p(cols.data_ptr()),
+                                               C.c_void_p(stream.cuda_stream)))
 
 
 def unpack_mask(words: np.ndarray, F: int) -> np.ndarray:

@@ -34,7 +34,7 @@ def test_defaults_and_strerror_without_a_gpu(built_lib):
     t = rise.default_thresholds()
     assert (t.range_mode, t.level_db, t.psd_offset_db, t.power_offset_db,
             t.sg_half_window, t.morph_order) == (0, 0.25, 0.5, 10.0, 5, 0)
-    for code in (0, -1, -2, -3, -4, -5, -6):
+    for code in (0, -1, -2, -3, -4, -5, -6, -7):
         assert rise.strerror(code) != "unknown status"
 
 
