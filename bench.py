@@ -22,6 +22,7 @@ collective on the data path.  `--impl reference` times the oracle instead.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import statistics
@@ -41,9 +42,10 @@ WORKLOAD = ("wideband single stream: 2^26 complex64 IQ samples (notional 100 MS/
             "128 emitters (SNR -3..25 dB, 0.1-20 MHz), Hann, FFT 4096, hop 2048 "
             "-> 32767 x 4096 spectrogram; plain method")
 HBM_FALLBACK_GBS = 6800.0
-# DRAM bytes per launch of the dominant kernel, from the ncu capture summarised
-# in profiles/stft_quant_wideband_4096.md (null once the kernel changes).
-TRAFFIC_BYTES = None
+# DRAM bytes (read + write) per launch of the dominant kernel at this workload,
+# from the ncu capture summarised in profiles/stft_power_wideband_2e26_fft4096.md
+# (set to None whenever that kernel changes).
+TRAFFIC_BYTES = {2: 541992192 + 493447680}
 
 
 def _peaks():
@@ -57,7 +59,7 @@ def _peaks():
 
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -77,7 +79,8 @@ class ClockSampler:
         except Exception:
             self.proc = None
 
-    def stop(self):
+    def stop(self, t0: float, t1: float):
+        """Median SM clock and throttle reasons of the samples taken in [t0, t1]."""
         if self.proc is None:
             return None
         time.sleep(0.25)
@@ -91,14 +94,17 @@ class ClockSampler:
         try:
             for line in open(self.path):
                 f = [x.strip() for x in line.split(",")]
-                if len(f) < 9:
+                if len(f) < 10:
                     continue
                 try:
-                    sm.append(float(f[1]))
-                    mx.append(float(f[2]))
+                    ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    if not t0 <= ts <= t1:
+                        continue
+                    sm.append(float(f[2]))
+                    mx.append(float(f[3]))
                 except ValueError:
                     continue
-                for nm, v in zip(names, f[5:9]):
+                for nm, v in zip(names, f[6:10]):
                     if v.lower() in ("active", "0x1") or v == "1":
                         reasons.add(nm)
         finally:
@@ -170,10 +176,11 @@ def run_ours(args):
     uuid = str(torch.cuda.get_device_properties(local).uuid)
     sampler = ClockSampler(uuid if uuid.startswith("GPU-") else f"GPU-{uuid}")
     sampler.start()
-    time.sleep(0.3)
+    time.sleep(0.5)
     l0 = det.launches()
     stage = np.zeros(8, np.float64)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0 = time.time()
     e0.record(stream)
     for _ in range(args.steps):
         boxes = det.detect(x, N_FFT, HOP)
@@ -181,7 +188,15 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     launches = det.launches() - l0
-    clocks = sampler.stop()
+    # a timed region shorter than a few 200 ms clock samples is followed by
+    # identical untimed steps, so that the clock record covers the same load
+    while time.time() - w0 < args.clock_window:
+        det.detect(x, N_FFT, HOP)
+    torch.cuda.synchronize()
+    w1 = time.time()
+    clocks = sampler.stop(w0, w1)
+    if clocks is not None:
+        clocks["window_s"] = round(w1 - w0, 3)
     _barrier(world)
     t_dev = e0.elapsed_time(e1) / 1e3
     t_max = _allreduce_max(t_dev, world)
@@ -207,7 +222,7 @@ def run_ours(args):
     # roofline of the dominant kernel (per-stage CUDA events on the launch stream)
     T = (n - N_FFT) // HOP + 1
     px = T * N_FFT
-    path = args.range_path or 1
+    path = args.range_path or 2   # the library's auto choice without a memory budget
     if path == 1:   # FFT twice: anchor max, then quantise; histogram from the image
         stage_bytes = {
             "spectrum_pass1": n * 8,                 # IQ read (max pass)
@@ -238,7 +253,9 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": TRAFFIC_BYTES, "peak_source": peak_kind,
+                     "traffic": (TRAFFIC_BYTES.get(path) if dom == "spectrum_pass1" and n == N_SAMPLES
+                                 else None),
+                     "peak_source": peak_kind,
                      "alg_bytes_per_launch": stage_bytes[dom], "ms_per_launch": round(dom_ms, 4),
                      "path_frac": round(alg_path / (t_max / args.steps) / 1e9 / peak, 4)},
         "stage_ms": {k: round(float(v), 4) for k, v in zip(names, stage)},
@@ -298,9 +315,11 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--samples", type=int, default=N_SAMPLES)
     ap.add_argument("--range-path", type=int, default=0, choices=(0, 1, 2))
-    ap.add_argument("--cpu-sample", type=int, default=1 << 24)
+    ap.add_argument("--cpu-sample", type=int, default=1 << 26)
     ap.add_argument("--ref-sample", type=int, default=1 << 22)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--clock-window", type=float, default=1.0,
+                    help="seconds of steady load the clock samples span (0: the timed steps only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -186,8 +186,10 @@ int rise_debug_export(rise_ctx *ctx, int what, void *dst, size_t bytes);
 #define RISE_OPT_KEEP_POWER 1  /* 1: keep the float |X|^2 image of the next calls  */
 #define RISE_OPT_KEEP_MASKS 2  /* 1: keep MASK0..MASK2 of the next calls           */
 #define RISE_OPT_TIMING 3      /* 1: record per-stage device times                 */
-#define RISE_OPT_RANGE_PATH 4  /* 0: auto; 1: FFT twice (max, then quantise);      *
-                                * 2: FFT once, keep float power, quantise after    */
+#define RISE_OPT_RANGE_PATH 4  /* 0: auto (2 when the float power image fits     *
+                                * mem_budget, else 1); 1: FFT twice (max, then    *
+                                * quantise); 2: FFT once, keep float power,       *
+                                * quantise after                                  */
 
 /* Sets an option; errors: RISE_EINVAL. */
 int rise_set_option(rise_ctx *ctx, int option, int64_t value);

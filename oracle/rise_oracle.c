@@ -18,6 +18,11 @@
  *   4-connected CCL, visited marks, min/max box . Sec. IV-B, "Bounding box generation",
  *                                                 box tuple of Eq. (1)
  *
+ * Parity unpinned: the offsets behind theta_PSD and theta_Power.  The paper
+ * gives neither their formula nor their values; ro_column_thresholds follows a
+ * stated reading whose closed forms are pinned, but how its defaults compare
+ * with the paper's own thresholds is not.
+ *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared (no fast-math), so
  * x86-64 and aarch64 give the same doubles.
  */

@@ -124,6 +124,7 @@ __global__ void runs_init_kernel(CclArgs a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) set_err(st, ERR_RUN_CAPACITY);
     return;
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->n_merge = 0;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
        g += (int64_t)gridDim.x * blockDim.x) {
     a.run_parent[g] = (int)g;
@@ -237,9 +238,18 @@ runs_row_kernel(CclArgs a) {
       while (os) {
         const int c = __ffs(os) - 1;
         os &= os - 1;
-        const int64_t ia = base + bs + __popc(sx & mask_upto(c)) - 1;
-        const int64_t ib = base2 + by + __popc(sy & mask_upto(c)) - 1;
-        uf_union(a.run_parent, (int)ia, (int)ib, st);
+        const int ia = (int)(base + bs + __popc(sx & mask_upto(c)) - 1);
+        const int ib = (int)(base2 + by + __popc(sy & mask_upto(c)) - 1);
+        // a lower run touched by one upper run (the common case) hangs under
+        // it with one CAS: ib is still a root and ia < ib, so this is a union.
+        // A failed CAS means ib already hangs elsewhere (it touches a second
+        // upper run): that union is deferred until the chains built here are
+        // flattened, so this pass walks no chains.
+        if (atomicCAS(&a.run_parent[ib], ib, ia) != ib) {
+          const unsigned long long k = atomicAdd(reinterpret_cast<unsigned long long *>(&st->n_merge), 1ull);
+          if ((int64_t)k < a.run_cap) a.merge[k] = make_int2(ia, ib);
+          else uf_union(a.run_parent, ia, ib, st);   // list full: unite now (slower)
+        }
       }
     }
     nst += tot_s;
@@ -247,6 +257,32 @@ runs_row_kernel(CclArgs a) {
     nsy += tot_y;
     cx = __shfl_sync(0xffffffffu, x, 31);
     cy = __shfl_sync(0xffffffffu, y, 31);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3b. point every run straight at its root (the row pass leaves chains as
+//     tall as the component), then apply the deferred unions on flat trees.
+// ---------------------------------------------------------------------------
+__global__ void ccl_flatten_kernel(CclArgs a) {
+  DeviceStatus *st = a.status;
+  const int64_t n = st->n_runs;
+  if (n > a.run_cap) return;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int r = uf_find(a.run_parent, (int)g, st);
+    if (r != (int)g) *(volatile int *)&a.run_parent[g] = r;   // an ancestor: still valid
+  }
+}
+
+__global__ void ccl_merge_kernel(CclArgs a) {
+  DeviceStatus *st = a.status;
+  if (st->n_runs > a.run_cap) return;
+  const int64_t m = min(st->n_merge, a.run_cap);
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int2 e = a.merge[k];
+    uf_union(a.run_parent, e.x, e.y, st);
   }
 }
 
@@ -339,6 +375,10 @@ cudaError_t launch_ccl_label(const CclArgs &a, int num_sms, cudaStream_t s) {
   runs_init_kernel<<<g, 256, 0, s>>>(a);
   count_launches(1);
   runs_row_kernel<<<(unsigned)((a.T + ROW_WARPS - 1) / ROW_WARPS), 32 * ROW_WARPS, 0, s>>>(a);
+  count_launches(1);
+  ccl_flatten_kernel<<<g, 256, 0, s>>>(a);
+  count_launches(1);
+  ccl_merge_kernel<<<g, 256, 0, s>>>(a);
   count_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -27,6 +27,7 @@ struct DeviceStatus {
   int64_t n_boxes;     // number of components
   uint32_t max_bits;   // float bits of the anchor power
   uint32_t pad2;
+  int64_t n_merge;     // deferred unions recorded by the labelling row pass
 };
 
 __device__ __forceinline__ void set_err(DeviceStatus *st, uint32_t bit) {
@@ -208,6 +209,7 @@ struct CclArgs {
   int32_t *run_parent;    // [run_cap] union-find parent (a smaller run number, or itself)
   uint8_t *run_sroot;     // [run_cap] 1 = the run is its component's root
   rise_box *rec;          // [run_cap] per-run records, summed into the roots
+  int2 *merge;            // [run_cap] deferred unions (upper run, lower run)
   int64_t *run_out;       // [run_cap + 1] compaction scan scratch
   void *scan_tmp;         // scan scratch
   size_t scan_tmp_bytes;

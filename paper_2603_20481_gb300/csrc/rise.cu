@@ -54,7 +54,7 @@ struct rise_ctx {
   int keep_power = 0, keep_masks = 0, timing = 0, range_path = 0;
   // scratch
   Buf iq_stage, power, img, hist, cols, effm1, mask, dbg[3], row_cnt, row_base, run_parent,
-      run_sroot, rec, run_out, scan_tmp, boxes;
+      run_sroot, rec, run_out, scan_tmp, boxes, merge;
   int64_t run_cap = 0;
   Small *small = nullptr;   // device
   Small *small_h = nullptr; // pinned host mirror for readback
@@ -280,6 +280,7 @@ int image_path(rise_ctx *c, const uint8_t *img, int64_t T, int F, const rise_thr
     la.run_parent = reinterpret_cast<int32_t *>(c->run_parent.p);
     la.run_sroot = reinterpret_cast<uint8_t *>(c->run_sroot.p);
     la.rec = reinterpret_cast<rise_box *>(c->rec.p);
+    la.merge = reinterpret_cast<int2 *>(c->merge.p);
     la.run_out = reinterpret_cast<int64_t *>(c->run_out.p);
     la.scan_tmp = c->scan_tmp.p;
     la.scan_tmp_bytes = c->scan_tmp.bytes;
@@ -298,6 +299,7 @@ int image_path(rise_ctx *c, const uint8_t *img, int64_t T, int F, const rise_thr
     if ((rc = ensure(c, c->run_parent, need * sizeof(int32_t)))) return rc;
     if ((rc = ensure(c, c->run_sroot, need))) return rc;
     if ((rc = ensure(c, c->rec, need * sizeof(rise_box)))) return rc;
+    if ((rc = ensure(c, c->merge, need * sizeof(int2)))) return rc;
     if ((rc = ensure(c, c->run_out, (need + 1) * sizeof(int64_t)))) return rc;
     if ((rc = ensure(c, c->scan_tmp, ccl_scan_tmp_bytes(std::max<int64_t>(need, T + 1))))) return rc;
     c->run_cap = need;
@@ -339,6 +341,7 @@ int prepare_image_buffers(rise_ctx *c, int64_t T, int F) {
     if ((rc = ensure(c, c->run_parent, cap0 * sizeof(int32_t)))) return rc;
     if ((rc = ensure(c, c->run_sroot, cap0))) return rc;
     if ((rc = ensure(c, c->rec, cap0 * sizeof(rise_box)))) return rc;
+    if ((rc = ensure(c, c->merge, cap0 * sizeof(int2)))) return rc;
     if ((rc = ensure(c, c->run_out, (cap0 + 1) * sizeof(int64_t)))) return rc;
     c->run_cap = cap0;
   }
@@ -365,7 +368,12 @@ int detect_device(rise_ctx *c, const void *iq, int64_t n, int N, int hop,
   if ((rc = prepare_image_buffers(c, T, F))) return rc;
   if ((rc = ensure(c, c->img, px))) return rc;
   int path = c->range_path;
-  if (path == 0) path = 1;
+  if (path == 0) {
+    // FFT once keeping float power when that image fits the budget, else twice
+    const size_t need = px * sizeof(float);
+    path = (!c->mem_budget || c->power.bytes >= need ||
+            c->allocated - c->power.bytes + need <= c->mem_budget) ? 2 : 1;
+  }
   const bool want_power = c->keep_power || (path == 2 && thr.range_mode == RISE_RANGE_AUTO_MAX);
   if (want_power && (rc = ensure(c, c->power, px * sizeof(float)))) return rc;
   Tables *tb;
@@ -373,8 +381,8 @@ int detect_device(rise_ctx *c, const void *iq, int64_t n, int N, int hop,
   if ((rc = upload_level_tables(c, thr.level_db))) return rc;
   cudaStream_t s = c->stream;
   Small *sm = c->small;
-  record(c, 0);
   CK(cudaMemsetAsync(&sm->status, 0, sizeof(DeviceStatus), s));
+  record(c, 0);
   StftArgs a;
   a.iq = reinterpret_cast<const float2 *>(iq);
   a.n = n;
@@ -513,7 +521,7 @@ void rise_destroy(rise_ctx *c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   Buf *bufs[] = {&c->iq_stage, &c->power, &c->img, &c->hist, &c->cols, &c->effm1, &c->mask,
                  &c->dbg[0], &c->dbg[1], &c->dbg[2], &c->row_cnt, &c->row_base,
-                 &c->run_parent, &c->run_sroot, &c->rec, &c->run_out, &c->scan_tmp, &c->boxes};
+                 &c->run_parent, &c->run_sroot, &c->rec, &c->run_out, &c->scan_tmp, &c->boxes, &c->merge};
   for (Buf *b : bufs)
     if (b->p) cudaFree(b->p);
   for (auto &kv : c->tables) cudaFree(kv.second.tw);
