@@ -153,6 +153,41 @@ int rise_detect_image(rise_ctx *ctx, const uint8_t *img_dev, int64_t T, int F,
                       const rise_thresholds *thr, rise_box *out, int64_t cap,
                       int64_t *n_boxes);
 
+/* ---- batches ------------------------------------------------------------ */
+/* One capture of a batch: iq_dev device pointer to n complex64 samples
+ * (8-byte aligned; 16-byte aligned with an even hop lets the STFT stage the
+ * frames with bulk copies), FFT size and hop as for rise_detect. */
+typedef struct {
+  const void *iq_dev;
+  int64_t n;
+  int fft_size;
+  int hop;
+} rise_capture;
+
+#define RISE_BATCH_MAX_ROWS 524280 /* frames per capture in a batch (8 x 65535) */
+
+/* Detects the energy blocks of ncap captures in one call, each exactly as
+ * rise_detect would (the same thresholds for all; each capture keeps its own
+ * 8-bit range anchor, noise floor, Otsu thresholds and components).  The
+ * captures share the launches instead: one launch per stage for the whole
+ * batch (one STFT launch per FFT size, a persistent grid that takes
+ * frame ranges of any capture), so many small captures fill the GPU
+ * together.  The first call with a given composition (the list of n,
+ * fft_size, hop and alignment) times a few launch shapes and keeps the
+ * fastest (RISE_OPT_AUTOTUNE), and records the chain as a CUDA graph that
+ * later calls with the same composition replay (RISE_OPT_BATCH_GRAPH).
+ *  caps     ncap captures (host array); ncap >= 0.
+ *  out      host array of `cap` boxes: the boxes of capture 0 in anchor
+ *           order, then those of capture 1, and so on.
+ *  offsets  host array of ncap + 1 entries: capture c's boxes are
+ *           [offsets[c], offsets[c+1]) of the full list; offsets[ncap] is
+ *           the total, also on RISE_ETRUNC (then `out` holds the first cap).
+ * Per capture T = (n - fft_size) / hop + 1 must be in 1..RISE_BATCH_MAX_ROWS.
+ * Errors: RISE_EINVAL, RISE_ENOMEM, RISE_ETRUNC, RISE_ECUDA, RISE_ETIMEOUT,
+ * RISE_EINTERNAL.  rise_debug_export intermediates are not kept for batches. */
+int rise_detect_batch(rise_ctx *ctx, const rise_capture *caps, int ncap,
+                      const rise_thresholds *thr, rise_box *out, int64_t cap, int64_t *offsets);
+
 /* ---- introspection of the last detect call ----------------------------- */
 #define RISE_DBG_POWER_F32 1 /* float [T][F] |X|^2 (needs RISE_OPT_KEEP_POWER)     */
 #define RISE_DBG_IMAGE_U8 2  /* uint8 [T][F] levels                                 */
@@ -167,6 +202,10 @@ int rise_detect_image(rise_ctx *ctx, const uint8_t *img_dev, int64_t T, int F,
 #define RISE_DBG_LEVEL_EDGES 11 /* float [257]: smallest power of each level          */
 #define RISE_DBG_LAUNCHES 12 /* int64 [1]: kernels launched by this library so far,   *
                               * process-wide (for launch accounting)                */
+#define RISE_DBG_BATCH_INFO 13 /* int64 [16] of the last batch: [0] STFT groups G,   *
+                                * [1] replayed from a graph (0/1), [2..2+G) frames  *
+                                * per STFT item in steps, [2+G] morphology warps    *
+                                * per SM                                            */
 
 typedef struct {
   uint64_t S;    /* column sum of levels                                */
@@ -190,6 +229,10 @@ int rise_debug_export(rise_ctx *ctx, int what, void *dst, size_t bytes);
                                 * mem_budget, else 1); 1: FFT twice (max, then    *
                                 * quantise); 2: FFT once, keep float power,       *
                                 * quantise after                                  */
+
+#define RISE_OPT_BATCH_GRAPH 5 /* 1 (default): batches replay a captured graph   */
+#define RISE_OPT_AUTOTUNE 6    /* 1 (default): tune batch launch shapes once per   *
+                                * composition; 0: fixed defaults                   */
 
 /* Sets an option; errors: RISE_EINVAL. */
 int rise_set_option(rise_ctx *ctx, int option, int64_t value);

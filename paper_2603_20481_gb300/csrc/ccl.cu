@@ -155,24 +155,19 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane, int *total) {
   return x - v;
 }
 
-__global__ void __launch_bounds__(32 * ROW_WARPS, 4)
-runs_row_kernel(CclArgs a) {
-  __shared__ unsigned long long Es[256];
-  __shared__ __align__(16) uint8_t qs[ROW_WARPS][32][32];   // each lane's 32 levels
-  for (int i = threadIdx.x; i < 256; i += blockDim.x) Es[i] = a.energy[i];
-  __syncthreads();
+// Row t (of T) of an image of width F whose mask and levels start at
+// mask0 / img0; tg is the row's index in the run-count arrays (the same as t
+// for a single image).  Rows without runs are skipped by the callers.
+__device__ __forceinline__ void runs_row_body(const CclArgs &a, const unsigned long long *Es,
+                                              uint8_t *myq, int64_t tg, int64_t t, int64_t T, int F,
+                                              const uint32_t *mask0, const uint8_t *img0) {
   DeviceStatus *st = a.status;
-  if (st->n_runs > a.run_cap) return;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int64_t t = (int64_t)blockIdx.x * ROW_WARPS + wib;
-  if (t >= a.T) return;
-  if (a.row_cnt[t] == 0) return;   // no runs in this row: nothing to label or unite
-  const int F = a.F, Wd = F / 32;
-  const uint32_t *m = a.mask + t * Wd;
-  const bool has_next = t + 1 < a.T && a.row_cnt[t + 1] != 0;
-  const uint32_t *m2 = has_next ? a.mask + (t + 1) * Wd : nullptr;
-  const int64_t base = a.row_base[t], base2 = has_next ? a.row_base[t + 1] : 0;
-  uint8_t *myq = qs[wib][lane];
+  const int lane = threadIdx.x & 31;
+  const int Wd = F / 32;
+  const uint32_t *m = mask0 + t * Wd;
+  const bool has_next = t + 1 < T && a.row_cnt[tg + 1] != 0;
+  const uint32_t *m2 = has_next ? mask0 + (t + 1) * Wd : nullptr;
+  const int64_t base = a.row_base[tg], base2 = has_next ? a.row_base[tg + 1] : 0;
   uint32_t cx = 0, cy = 0;       // previous chunk's last words
   int nst = 0, nen = 0, nsy = 0; // runs started / ended before this chunk
   for (int w0 = 0; w0 < Wd; w0 += 32) {
@@ -209,7 +204,7 @@ runs_row_kernel(CclArgs a) {
         a.rec[base + id++].f1 = 32 * w + b;
       }
       // area, level and energy sums of each segment of set bits in the word
-      const uint4 *qv = reinterpret_cast<const uint4 *>(a.img + t * F + 32 * w);
+      const uint4 *qv = reinterpret_cast<const uint4 *>(img0 + t * F + 32 * w);
       reinterpret_cast<uint4 *>(myq)[0] = __ldg(qv);
       reinterpret_cast<uint4 *>(myq)[1] = __ldg(qv + 1);   // read back by this lane only
       uint32_t mm = x;
@@ -258,6 +253,63 @@ runs_row_kernel(CclArgs a) {
     cx = __shfl_sync(0xffffffffu, x, 31);
     cy = __shfl_sync(0xffffffffu, y, 31);
   }
+}
+
+__global__ void __launch_bounds__(32 * ROW_WARPS, 4)
+runs_row_kernel(CclArgs a) {
+  __shared__ unsigned long long Es[256];
+  __shared__ __align__(16) uint8_t qs[ROW_WARPS][32][32];   // each lane's 32 levels
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) Es[i] = a.energy[i];
+  __syncthreads();
+  if (a.status->n_runs > a.run_cap) return;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t t = (int64_t)blockIdx.x * ROW_WARPS + wib;
+  if (t >= a.T) return;
+  if (a.row_cnt[t] == 0) return;   // no runs in this row: nothing to label or unite
+  runs_row_body(a, Es, qs[wib][lane], t, t, a.T, a.F, a.mask, a.img);
+}
+
+// Batch: rows of all captures, concatenated (a.T = total rows); row0[c] is
+// the first row of capture c (ncap + 1 entries).  Rows of different
+// captures are never united: has_next stops at the capture's last row.
+__global__ void __launch_bounds__(32 * ROW_WARPS, 4)
+runs_row_batch_kernel(CclArgs a, const RowSeg *segs, const int64_t *row0, int ncap) {
+  __shared__ unsigned long long Es[256];
+  __shared__ __align__(16) uint8_t qs[ROW_WARPS][32][32];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) Es[i] = a.energy[i];
+  __syncthreads();
+  if (a.status->n_runs > a.run_cap) return;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t tg = (int64_t)blockIdx.x * ROW_WARPS + wib;
+  if (tg >= a.T) return;
+  if (a.row_cnt[tg] == 0) return;
+  int lo = 0, hi = ncap - 1;   // the last capture whose first row is <= tg
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&row0[mid]) <= tg) lo = mid;
+    else hi = mid - 1;
+  }
+  const RowSeg rs = segs[lo];
+  runs_row_body(a, Es, qs[wib][lane], tg, tg - __ldg(&row0[lo]), rs.T, rs.F, rs.mask, rs.img);
+}
+
+// Batch: offs[c] = index of capture c's first box in the output (boxes of a
+// batch are ordered by capture, then anchor); offs[ncap] = all boxes.
+__global__ void ccl_offsets_kernel(CclArgs a, const int64_t *row0, int ncap, int64_t *offs) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c > ncap) return;
+  const DeviceStatus *st = a.status;
+  const int64_t n = st->n_runs;
+  if (n > a.run_cap) {
+    offs[c] = 0;
+    return;
+  }
+  if (c == ncap) {
+    offs[c] = st->n_boxes;
+    return;
+  }
+  const int64_t r = a.row_base[row0[c]];   // the capture's first run
+  offs[c] = r < n ? a.run_out[r] : st->n_boxes;
 }
 
 // ---------------------------------------------------------------------------
@@ -370,11 +422,17 @@ cudaError_t launch_ccl_count(const CclArgs &a, int num_sms, cudaStream_t s) {
                                reinterpret_cast<int64_t *>(a.scan_tmp), s);
 }
 
-cudaError_t launch_ccl_label(const CclArgs &a, int num_sms, cudaStream_t s) {
+namespace {
+cudaError_t label_common(const CclArgs &a, const RowSeg *segs, const int64_t *row0, int ncap,
+                         int64_t *offs, int num_sms, cudaStream_t s) {
   const int g = grid_for(a.run_cap, 256, num_sms);
   runs_init_kernel<<<g, 256, 0, s>>>(a);
   count_launches(1);
-  runs_row_kernel<<<(unsigned)((a.T + ROW_WARPS - 1) / ROW_WARPS), 32 * ROW_WARPS, 0, s>>>(a);
+  const unsigned row_blocks = (unsigned)((a.T + ROW_WARPS - 1) / ROW_WARPS);
+  if (segs)
+    runs_row_batch_kernel<<<row_blocks, 32 * ROW_WARPS, 0, s>>>(a, segs, row0, ncap);
+  else
+    runs_row_kernel<<<row_blocks, 32 * ROW_WARPS, 0, s>>>(a);
   count_launches(1);
   ccl_flatten_kernel<<<g, 256, 0, s>>>(a);
   count_launches(1);
@@ -393,7 +451,21 @@ cudaError_t launch_ccl_label(const CclArgs &a, int num_sms, cudaStream_t s) {
   count_launches(1);
   zero_if_over_kernel<<<1, 1, 0, s>>>(a.status, a.run_cap);
   count_launches(1);
+  if (segs) {
+    ccl_offsets_kernel<<<(ncap + 1 + 255) / 256, 256, 0, s>>>(a, row0, ncap, offs);
+    count_launches(1);
+  }
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_ccl_label(const CclArgs &a, int num_sms, cudaStream_t s) {
+  return label_common(a, nullptr, nullptr, 0, nullptr, num_sms, s);
+}
+
+cudaError_t launch_ccl_label_batch(const CclArgs &a, const RowSeg *segs, const int64_t *row0,
+                                   int ncap, int64_t *offs, int num_sms, cudaStream_t s) {
+  return label_common(a, segs, row0, ncap, offs, num_sms, s);
 }
 
 }  // namespace rise

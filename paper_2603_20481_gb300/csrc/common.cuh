@@ -144,6 +144,28 @@ struct StftArgs {
 
 enum StftMode { STFT_MAX = 0, STFT_QUANT = 1, STFT_POWER = 2, STFT_QUANT_POWER = 3 };
 
+// ---------------------------------------------------------------------------
+// Batches: one launch per stage covers many captures; each block or warp
+// reads its capture's arguments from a device table.
+// ---------------------------------------------------------------------------
+struct CapSmall {             // per-capture small state of a batch
+  uint32_t max_bits;          // float bits of the capture's largest |X|^2
+  uint32_t pad;
+  float qconst[4];
+  float edges[260];
+  int64_t floor_out[8];
+};
+struct StftItem {             // frames [f0, f1) of capture `seg`
+  int32_t seg, pad;
+  int64_t f0, f1;
+};
+cudaError_t launch_stft_batch(int N, bool tma, StftMode mode, const StftArgs *segs,
+                              const StftItem *items, int n_items, int *counter, int num_sms,
+                              cudaStream_t s);
+int stft_frames_per_step(int N);
+cudaError_t launch_levels_batch(CapSmall *cs, int ncap, double hi_power, int use_fixed,
+                                const double *ratio, double level_db, cudaStream_t s);
+
 // Twiddle and window tables for FFT size N (host-computed, FP64 -> float).
 size_t stft_table_floats(int N);
 void stft_fill_tables(int N, float2 *tw_host, float *win_host);
@@ -181,6 +203,26 @@ struct ColArgs {
   int64_t *floor_out;     // [8]
 };
 cudaError_t launch_colstats(const ColArgs &a, bool need_otsu, cudaStream_t s);
+
+struct HistArgs {             // one image for the cluster histogram
+  const void *src;            // float [T][F] power or uint8 [T][F] levels
+  int64_t T;
+  int F;
+  int64_t rows_per_band;
+  const float *edges;         // [257] level edges (float source)
+  const float *qconst;        // fast-level constants (float source)
+  uint8_t *img;               // [T][F] levels written (float source)
+  uint32_t *hist;             // [F][256]
+  rise_colstat *cols;         // [F] S and Otsu threshold
+  int accumulate;             // add into a zeroed hist (no Otsu) instead of storing
+};
+struct HistItem {             // column group cg of capture seg
+  int32_t seg, cg;
+};
+int64_t cluster_hist_rows_per_band(int64_t T);   // single cluster of bands
+cudaError_t launch_cluster_hist_batch(bool from_power, const HistArgs *segs, const HistItem *items,
+                                      int n_items, cudaStream_t s);
+cudaError_t launch_floor_batch(const ColArgs *segs, int ncap, int max_F, cudaStream_t s);
 // S and Otsu threshold of every column of a given [F][256] histogram.
 cudaError_t launch_column_otsu(const uint32_t *hist, int64_t T, int F, rise_colstat *cols,
                                cudaStream_t s);
@@ -196,6 +238,13 @@ struct MorphArgs {
   uint32_t *row_cnt;      // [T] runs per row of the final mask (zeroed by the caller)
 };
 cudaError_t launch_morph(const MorphArgs &a, cudaStream_t s);
+struct MorphItem {            // launch shape of one capture in a batch
+  int nx, rows;
+};
+void morph_plan(int64_t T, int F, int sms, int warps_per_sm, int min_rows, int *nx, int *rows,
+                int *n_warps);
+cudaError_t launch_morph_batch(int order, const MorphArgs *segs, const MorphItem *items,
+                               const int *warp_base, int ncap, int total_warps, cudaStream_t s);
 
 struct CclArgs {
   const uint32_t *mask;   // [T][W] final mask words, W = F/32
@@ -224,5 +273,15 @@ cudaError_t launch_ccl_count(const CclArgs &a, int num_sms, cudaStream_t s);
 // n_runs, checked on the device: on shortfall it sets ERR_RUN_CAPACITY and
 // does nothing).
 cudaError_t launch_ccl_label(const CclArgs &a, int num_sms, cudaStream_t s);
+struct RowSeg {               // one capture's image in a batch
+  const uint32_t *mask;       // [T][F/32]
+  const uint8_t *img;         // [T][F]
+  int64_t T;
+  int F, pad;
+};
+// Batch labelling: a.T = rows of all captures; boxes come out ordered by
+// capture then anchor, offs[c] (device, ncap + 1) = first box of capture c.
+cudaError_t launch_ccl_label_batch(const CclArgs &a, const RowSeg *segs, const int64_t *row0,
+                                   int ncap, int64_t *offs, int num_sms, cudaStream_t s);
 
 }  // namespace rise

@@ -1,0 +1,128 @@
+// Private to the library: the context behind the opaque rise_ctx handle and
+// the host helpers the entry points share (device scratch, tables, checks).
+#pragma once
+
+#include <cmath>
+#include <map>
+#include <vector>
+
+#include "common.cuh"
+
+namespace rise {
+namespace host {
+
+struct Buf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+// Per-FFT-size tables (twiddles + Hann window), built once.
+struct Tables {
+  float2 *tw = nullptr;
+  float *win = nullptr;
+};
+
+struct Small {              // one device block of small per-call data
+  DeviceStatus status;
+  float edges[260];
+  float qconst[4];
+  int64_t floor_out[8];
+  int64_t sgc[32];
+  uint64_t energy[256];
+  double ratio[256];   // 10^((j - 255.5) level_db / 10), j = 0..255
+};
+
+// Per-call tables of a batch: host staging (pinned) and device copy.
+struct BatchState {
+  Buf tab;                       // device blob of per-capture tables
+  void *tab_h = nullptr;         // pinned host staging of the same blob
+  size_t tab_h_bytes = 0;
+  Buf small;                     // CapSmall[ncap]
+  Buf counters;                  // int work counters of persistent launches
+  int64_t *offs_h = nullptr;     // mapped pinned [ncap + 1] box offsets
+  int64_t *offs_dev = nullptr;
+  int64_t offs_cap = 0;
+  // captured launch sequences, keyed by the batch's composition
+  struct Graph {
+    uint64_t key = 0;
+    cudaGraphExec_t exec = nullptr;
+    int launches = 0;            // kernels one replay runs
+  };
+  std::vector<Graph> graphs;
+  // tuned launch parameters, keyed by the batch's shape
+  std::map<uint64_t, std::vector<int>> tuned;
+  // the last batch: STFT groups, its launch parameters, replayed from a graph
+  int last_groups = 0;
+  std::vector<int> last_params;
+  bool last_graph = false;
+};
+
+}  // namespace host
+}  // namespace rise
+
+struct rise_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t mem_budget = 0;
+  size_t allocated = 0;
+  int num_sms = 1;
+  // options
+  int keep_power = 0, keep_masks = 0, timing = 0, range_path = 0;
+  int batch_graph = 1, autotune = 1;
+  // scratch
+  rise::host::Buf iq_stage, power, img, hist, cols, effm1, mask, dbg[3], row_cnt, row_base, run_parent,
+      run_sroot, rec, run_out, scan_tmp, boxes, merge;
+  int64_t run_cap = 0;
+  rise::host::Small *small = nullptr;   // device
+  rise::host::Small *small_h = nullptr; // pinned host mirror for readback
+  rise_box *hbox = nullptr;     // mapped pinned host buffer the compaction writes into
+  rise_box *hbox_dev = nullptr; // its device address
+  int64_t hbox_cap = 0;
+  std::map<int, rise::host::Tables> tables;
+  double energy_level_db = NAN;
+  int sg_m = -1;
+  // last call
+  int64_t last_T = 0;
+  int last_F = 0;
+  const uint8_t *last_img = nullptr;
+  bool last_has_power = false, last_has_masks = false, last_valid = false;
+  double last_anchor = 0.0;
+  cudaEvent_t ev[8] = {};
+  float stage_ms[8] = {};
+  uint64_t gen = 0;              // bumped whenever a scratch buffer moves
+  rise::host::BatchState batch;
+};
+
+namespace rise {
+namespace host {
+
+inline int cuda_fail(cudaError_t e) {
+  return e == cudaErrorMemoryAllocation ? RISE_ENOMEM : RISE_ECUDA;
+}
+
+#define CK(expr)                              \
+  do {                                        \
+    cudaError_t _e = (expr);                  \
+    if (_e != cudaSuccess) return rise::host::cuda_fail(_e); \
+  } while (0)
+
+// Grows b to at least `bytes` (with 1/8 headroom), within the memory budget.
+int ensure(rise_ctx *c, Buf &b, size_t bytes);
+// Mapped pinned host buffer for the boxes (grown to at least `cap` entries).
+int ensure_hbox(rise_ctx *c, int64_t cap);
+// Twiddle and window tables of FFT size N (built once per context).
+int get_tables(rise_ctx *c, int N, Tables **out);
+bool pow2(int64_t v);
+int check_thresholds(const rise_thresholds &t, int F);
+void record(rise_ctx *c, int i);
+// Energy and level-edge ratio tables of level_db (uploaded when it changes).
+int upload_level_tables(rise_ctx *c, double level_db);
+// The Savitzky-Golay weights of half window m (uploaded when m changes).
+int upload_sg(rise_ctx *c, int m);
+void destroy_batch(rise_ctx *c);
+int detect_batch(rise_ctx *c, const rise_capture *caps, int ncap, const rise_thresholds *thr,
+                 rise_box *out, int64_t cap, int64_t *offsets);
+
+}  // namespace host
+}  // namespace rise

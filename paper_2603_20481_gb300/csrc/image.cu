@@ -144,32 +144,33 @@ __device__ __forceinline__ void ch_count(uint32_t *sh, int lane, uint32_t q0, ui
   atomicAdd(&sh[(q1 & 127u) * CH_COLS + lane + 32], (q1 & 128u) ? 65536u : 1u);
 }
 
+// Column group cg, row band `band` of one image (the 8 bands of a column
+// group form one cluster).
 template <bool FROM_POWER>
-__global__ void __cluster_dims__(1, CH_BANDS, 1) __launch_bounds__(32 * CH_WARPS, 4)
-cluster_hist_kernel(const void *__restrict__ src, int64_t T, int F, int64_t rows_per_band,
-                    const float *edges_g, const float *qconst, uint8_t *img, uint32_t *hist,
-                    rise_colstat *cols, int accumulate) {
+__device__ __forceinline__ void cluster_hist_body(const HistArgs &a, int cgx, int band) {
   extern __shared__ uint32_t sh[];   // [128 packed levels][64 column slots]
   __shared__ float edges[257];
   __shared__ __align__(16) uint32_t hs[CH_NS][256];   // reduced columns
   cg::cluster_group cluster = cg::this_cluster();
+  const int64_t T = a.T;
+  const int F = a.F;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int i = tid; i < CH_WORDS; i += blockDim.x) sh[i] = 0;
   float inv_anchor = 0.f, c1 = 0.f;
   if constexpr (FROM_POWER) {
-    for (int i = tid; i < 257; i += blockDim.x) edges[i] = edges_g[i];
-    inv_anchor = qconst[0];
-    c1 = qconst[1];
+    for (int i = tid; i < 257; i += blockDim.x) edges[i] = a.edges[i];
+    inv_anchor = a.qconst[0];
+    c1 = a.qconst[1];
   }
   __syncthreads();
-  const int c0 = blockIdx.x * CH_COLS + CH_PX * lane;
-  const int64_t r0 = (int64_t)blockIdx.y * rows_per_band;
-  const int64_t r1 = min(T, r0 + rows_per_band);
+  const int c0 = cgx * CH_COLS + CH_PX * lane;
+  const int64_t r0 = (int64_t)band * a.rows_per_band;
+  const int64_t r1 = min(T, r0 + a.rows_per_band);
   const int64_t stride = (int64_t)CH_WARPS * F;          // elements between a warp's rows
   int64_t r = r0 + warp;
   if constexpr (FROM_POWER) {
-    const float *p = reinterpret_cast<const float *>(src) + r * F + c0;
-    uint8_t *o = img + r * F + c0;
+    const float *p = reinterpret_cast<const float *>(a.src) + r * F + c0;
+    uint8_t *o = a.img + r * F + c0;
     for (; r < r1; r += CH_UNROLL * CH_WARPS, p += CH_UNROLL * stride, o += CH_UNROLL * stride) {
       float pv[2 * CH_UNROLL];
 #pragma unroll
@@ -203,7 +204,7 @@ cluster_hist_kernel(const void *__restrict__ src, int64_t T, int F, int64_t rows
       }
     }
   } else {
-    const uint8_t *p = reinterpret_cast<const uint8_t *>(src) + r * F + c0;
+    const uint8_t *p = reinterpret_cast<const uint8_t *>(a.src) + r * F + c0;
     for (; r + (2 * CH_UNROLL - 1) * CH_WARPS < r1; r += 2 * CH_UNROLL * CH_WARPS) {
       uint32_t w[2 * CH_UNROLL];
 #pragma unroll
@@ -238,9 +239,9 @@ cluster_hist_kernel(const void *__restrict__ src, int64_t T, int F, int64_t rows
   if (warp < CH_NS) {
     const int sl = warp;
     const int slot = rank * CH_NS + sl;
-    const int col = blockIdx.x * CH_COLS + CH_PX * (slot & 31) + (slot >> 5);
-    uint32_t *dst = hist + (size_t)col * 256;
-    if (accumulate) {
+    const int col = cgx * CH_COLS + CH_PX * (slot & 31) + (slot >> 5);
+    uint32_t *dst = a.hist + (size_t)col * 256;
+    if (a.accumulate) {
       for (int v = lane; v < 256; v += 32)
         if (hs[sl][v]) atomicAdd(&dst[v], hs[sl][v]);
     } else {
@@ -249,11 +250,29 @@ cluster_hist_kernel(const void *__restrict__ src, int64_t T, int F, int64_t rows
       int th;
       otsu_warp(&hs[sl][8 * lane], lane, &S, &th);
       if (lane == 0) {
-        cols[col].S = S;
-        cols[col].otsu = th;
+        a.cols[col].S = S;
+        a.cols[col].otsu = th;
       }
     }
   }
+}
+
+template <bool FROM_POWER>
+__global__ void __cluster_dims__(1, CH_BANDS, 1) __launch_bounds__(32 * CH_WARPS, 4)
+cluster_hist_kernel(HistArgs a) {
+  cluster_hist_body<FROM_POWER>(a, blockIdx.x, blockIdx.y);
+}
+
+// Batch: blockIdx.x indexes (capture, column group) items; the arguments of
+// the item's capture are copied to shared memory first.
+template <bool FROM_POWER>
+__global__ void __cluster_dims__(1, CH_BANDS, 1) __launch_bounds__(32 * CH_WARPS, 4)
+cluster_hist_batch_kernel(const HistArgs *segs, const HistItem *items) {
+  __shared__ HistArgs sa;
+  const HistItem it = items[blockIdx.x];
+  if (threadIdx.x == 0) sa = segs[it.seg];
+  __syncthreads();
+  cluster_hist_body<FROM_POWER>(sa, it.cg, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -267,7 +286,7 @@ __device__ __forceinline__ int64_t floor_div_d(int64_t a, int64_t b) {
   return q;
 }
 
-__global__ void __launch_bounds__(FLOOR_THREADS) floor_kernel(ColArgs a) {
+__device__ __forceinline__ void floor_body(const ColArgs &a) {
   extern __shared__ int64_t S[];   // [F] column PSD, then [F] D-scaled smoothing
   int64_t *Sh = S + a.F;
   __shared__ int64_t red_min[32], red_g[32];
@@ -344,6 +363,16 @@ __global__ void __launch_bounds__(FLOOR_THREADS) floor_kernel(ColArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(FLOOR_THREADS) floor_kernel(ColArgs a) { floor_body(a); }
+
+// Batch: one block per capture.
+__global__ void __launch_bounds__(FLOOR_THREADS) floor_batch_kernel(const ColArgs *segs) {
+  __shared__ ColArgs sa;
+  if (threadIdx.x == 0) sa = segs[blockIdx.x];
+  __syncthreads();
+  floor_body(sa);
+}
+
 // ---------------------------------------------------------------------------
 // Threshold + morphology, streaming.  A warp owns a window of 32 row words
 // (1024 columns) of a band of rows; lane l holds word w0-1+l, and only lanes
@@ -399,11 +428,8 @@ __device__ __forceinline__ uint32_t threshold32(const uint4 &q0, const uint4 &q1
 // ORDER 0: close3 (dilate, erode), open3 (erode, dilate), open1x3 (erode, dilate)
 // ORDER 1: open1x3, close3, open3.  D_k = rows by which the input of op k lags.
 template <int ORDER>
-__global__ void __launch_bounds__(32 * MS_WARPS, 2)
-morph_stream_kernel(MorphArgs a, int nx, int rows_per_band, int n_warps) {
+__device__ __forceinline__ void morph_body(const MorphArgs &a, int nx, int rows_per_band, int gwarp) {
   const int lane = threadIdx.x & 31;
-  const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  if (gwarp >= n_warps) return;
   const int Wd = a.F / 32;
   const int T = (int)a.T;                                  // T <= 2^19
   const int xs = gwarp % nx;
@@ -496,6 +522,37 @@ morph_stream_kernel(MorphArgs a, int nx, int rows_per_band, int n_warps) {
     }
   }
 }
+
+template <int ORDER>
+__global__ void __launch_bounds__(32 * MS_WARPS, 2)
+morph_stream_kernel(MorphArgs a, int nx, int rows_per_band, int n_warps) {
+  const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (gwarp >= n_warps) return;
+  morph_body<ORDER>(a, nx, rows_per_band, gwarp);
+}
+
+// Batch: warps are numbered over all captures; warp_base[c] is the first
+// warp of capture c (ncap + 1 entries).  Each warp copies its capture's
+// arguments to its own shared slot.
+template <int ORDER>
+__global__ void __launch_bounds__(32 * MS_WARPS, 2)
+morph_batch_kernel(const MorphArgs *segs, const MorphItem *mi, const int *warp_base, int ncap,
+                   int total_warps) {
+  __shared__ MorphArgs sa[MS_WARPS];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int gwarp = blockIdx.x * MS_WARPS + wib;
+  if (gwarp >= total_warps) return;
+  int lo = 0, hi = ncap - 1;   // the last capture whose first warp is <= gwarp
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&warp_base[mid]) <= gwarp) lo = mid;
+    else hi = mid - 1;
+  }
+  if (lane == 0) sa[wib] = segs[lo];
+  __syncwarp();
+  const MorphItem it = mi[lo];
+  morph_body<ORDER>(sa[wib], it.nx, it.rows, gwarp - __ldg(&warp_base[lo]));
+}
 }  // namespace
 
 // Cluster histogram (optionally quantising float power on the way).  The
@@ -515,18 +572,75 @@ cudaError_t launch_cluster_hist(const void *src, bool from_power, int64_t T, int
   dim3 grid(F / CH_COLS, (unsigned)(groups * CH_BANDS));
   const size_t sm = (size_t)CH_WORDS * sizeof(uint32_t);
   static_assert(CH_WARPS >= CH_NS, "one warp per reduced column");
+  HistArgs ha{src, T, F, rows, edges, qconst, img, hist, cols, accumulate};
   cudaError_t e;
   if (from_power) {
     e = cudaFuncSetAttribute(cluster_hist_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    cluster_hist_kernel<true><<<grid, 32 * CH_WARPS, sm, s>>>(src, T, F, rows, edges, qconst, img, hist, cols, accumulate);
+    cluster_hist_kernel<true><<<grid, 32 * CH_WARPS, sm, s>>>(ha);
     count_launches(1);
   } else {
     e = cudaFuncSetAttribute(cluster_hist_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    cluster_hist_kernel<false><<<grid, 32 * CH_WARPS, sm, s>>>(src, T, F, rows, edges, qconst, img, hist, cols, accumulate);
+    cluster_hist_kernel<false><<<grid, 32 * CH_WARPS, sm, s>>>(ha);
     count_launches(1);
   }
+  return cudaGetLastError();
+}
+
+int64_t cluster_hist_rows_per_band(int64_t T) { return (T + CH_BANDS - 1) / CH_BANDS; }
+
+cudaError_t launch_cluster_hist_batch(bool from_power, const HistArgs *segs, const HistItem *items,
+                                      int n_items, cudaStream_t s) {
+  if (n_items < 1) return cudaSuccess;
+  dim3 grid((unsigned)n_items, CH_BANDS);
+  const size_t sm = (size_t)CH_WORDS * sizeof(uint32_t);
+  cudaError_t e;
+  if (from_power) {
+    e = cudaFuncSetAttribute(cluster_hist_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    cluster_hist_batch_kernel<true><<<grid, 32 * CH_WARPS, sm, s>>>(segs, items);
+  } else {
+    e = cudaFuncSetAttribute(cluster_hist_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    cluster_hist_batch_kernel<false><<<grid, 32 * CH_WARPS, sm, s>>>(segs, items);
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_floor_batch(const ColArgs *segs, int ncap, int max_F, cudaStream_t s) {
+  const size_t sm = 2 * (size_t)max_F * sizeof(int64_t);
+  cudaError_t e = cudaFuncSetAttribute(floor_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  floor_batch_kernel<<<ncap, FLOOR_THREADS, sm, s>>>(segs);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// Warps and rows per band of the streaming morphology on a T x F image
+// (target: about `warps_per_sm` warps per SM for the whole launch).
+void morph_plan(int64_t T, int F, int sms, int warps_per_sm, int min_rows, int *nx, int *rows,
+                int *n_warps) {
+  const int Wd = F / 32;
+  *nx = (Wd + MS_LANES_OUT - 1) / MS_LANES_OUT;
+  const int64_t want_warps = (int64_t)sms * warps_per_sm;
+  int64_t bands = std::max<int64_t>(1, (want_warps + *nx - 1) / *nx);
+  int64_t r = std::max<int64_t>(min_rows, (T + bands - 1) / bands);
+  bands = (T + r - 1) / r;
+  *rows = (int)r;
+  *n_warps = (int)(bands * *nx);
+}
+
+cudaError_t launch_morph_batch(int order, const MorphArgs *segs, const MorphItem *items,
+                               const int *warp_base, int ncap, int total_warps, cudaStream_t s) {
+  if (total_warps < 1) return cudaSuccess;
+  const unsigned blocks = (unsigned)((total_warps + MS_WARPS - 1) / MS_WARPS);
+  if (order == 0)
+    morph_batch_kernel<0><<<blocks, 32 * MS_WARPS, 0, s>>>(segs, items, warp_base, ncap, total_warps);
+  else
+    morph_batch_kernel<1><<<blocks, 32 * MS_WARPS, 0, s>>>(segs, items, warp_base, ncap, total_warps);
+  count_launches(1);
   return cudaGetLastError();
 }
 

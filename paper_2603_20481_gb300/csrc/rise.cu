@@ -8,7 +8,7 @@
 #include <new>
 #include <vector>
 
-#include "common.cuh"
+#include "context.cuh"
 
 using namespace rise;
 
@@ -18,74 +18,8 @@ void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed);
 long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace rise
 
-namespace {
-
-struct Buf {
-  void *p = nullptr;
-  size_t bytes = 0;
-};
-
-// Per-FFT-size tables (twiddles + Hann window), built once.
-struct Tables {
-  float2 *tw = nullptr;
-  float *win = nullptr;
-};
-
-struct Small {              // one device block of small per-call data
-  DeviceStatus status;
-  float edges[260];
-  float qconst[4];
-  int64_t floor_out[8];
-  int64_t sgc[32];
-  uint64_t energy[256];
-  double ratio[256];   // 10^((j - 255.5) level_db / 10), j = 0..255
-};
-
-}  // namespace
-
-struct rise_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  size_t mem_budget = 0;
-  size_t allocated = 0;
-  int num_sms = 1;
-  // options
-  int keep_power = 0, keep_masks = 0, timing = 0, range_path = 0;
-  // scratch
-  Buf iq_stage, power, img, hist, cols, effm1, mask, dbg[3], row_cnt, row_base, run_parent,
-      run_sroot, rec, run_out, scan_tmp, boxes, merge;
-  int64_t run_cap = 0;
-  Small *small = nullptr;   // device
-  Small *small_h = nullptr; // pinned host mirror for readback
-  rise_box *hbox = nullptr;     // mapped pinned host buffer the compaction writes into
-  rise_box *hbox_dev = nullptr; // its device address
-  int64_t hbox_cap = 0;
-  std::map<int, Tables> tables;
-  double energy_level_db = NAN;
-  int sg_m = -1;
-  // last call
-  int64_t last_T = 0;
-  int last_F = 0;
-  const uint8_t *last_img = nullptr;
-  bool last_has_power = false, last_has_masks = false, last_valid = false;
-  double last_anchor = 0.0;
-  cudaEvent_t ev[8] = {};
-  float stage_ms[8] = {};
-};
-
-namespace {
-
-int cuda_fail(cudaError_t e) {
-  return e == cudaErrorMemoryAllocation ? RISE_ENOMEM : RISE_ECUDA;
-}
-
-#define CK(expr)                              \
-  do {                                        \
-    cudaError_t _e = (expr);                  \
-    if (_e != cudaSuccess) return cuda_fail(_e); \
-  } while (0)
-
+namespace rise {
+namespace host {
 int ensure(rise_ctx *c, Buf &b, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (b.bytes >= bytes) return RISE_OK;
@@ -110,6 +44,7 @@ int ensure(rise_ctx *c, Buf &b, size_t bytes) {
   b.p = p;
   b.bytes = grow;
   c->allocated += grow;
+  ++c->gen;
   return RISE_OK;
 }
 
@@ -138,6 +73,7 @@ int ensure_hbox(rise_ctx *c, int64_t cap) {
   c->hbox = reinterpret_cast<rise_box *>(h);
   c->hbox_dev = reinterpret_cast<rise_box *>(d);
   c->hbox_cap = want;
+  ++c->gen;
   return RISE_OK;
 }
 
@@ -203,6 +139,25 @@ int upload_level_tables(rise_ctx *c, double level_db) {
   return RISE_OK;
 }
 
+// Integer Savitzky-Golay weights of the quadratic fit over 2m+1 points:
+// c_i = 3(3m^2 + 3m - 1) - 15 i^2, norm D = (2m-1)(2m+1)(2m+3).
+int upload_sg(rise_ctx *c, int m) {
+  if (c->sg_m == m) return RISE_OK;
+  int64_t coef[32];
+  for (int i = 0; i <= m; ++i) coef[i] = 3LL * (3LL * m * m + 3LL * m - 1) - 15LL * i * i;
+  CK(cudaMemcpyAsync(c->small->sgc, coef, sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->sg_m = m;
+  return RISE_OK;
+}
+
+}  // namespace host
+}  // namespace rise
+
+using namespace rise::host;
+
+namespace {
+
 // Everything from the 8-bit image on: histogram (unless already built),
 // column statistics, morphology, labelling, boxes back to the host.
 int image_path(rise_ctx *c, const uint8_t *img, int64_t T, int F, const rise_thresholds &thr,
@@ -221,13 +176,7 @@ int image_path(rise_ctx *c, const uint8_t *img, int64_t T, int F, const rise_thr
   // column statistics
   const int m = thr.sg_half_window;
   const int64_t D = (int64_t)(2 * m - 1) * (2 * m + 1) * (2 * m + 3);
-  if (c->sg_m != m) {
-    int64_t coef[32];
-    for (int i = 0; i <= m; ++i) coef[i] = 3LL * (3LL * m * m + 3LL * m - 1) - 15LL * i * i;
-    CK(cudaMemcpyAsync(sm->sgc, coef, sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, s));
-    CK(cudaStreamSynchronize(s));
-    c->sg_m = m;
-  }
+  if ((rc0 = upload_sg(c, m))) return rc0;
   ColArgs ca;
   ca.hist = reinterpret_cast<const uint32_t *>(c->hist.p);
   ca.T = T;
@@ -525,6 +474,7 @@ void rise_destroy(rise_ctx *c) {
   for (Buf *b : bufs)
     if (b->p) cudaFree(b->p);
   for (auto &kv : c->tables) cudaFree(kv.second.tw);
+  destroy_batch(c);
   if (c->small) cudaFree(c->small);
   if (c->small_h) cudaFreeHost(c->small_h);
   if (c->hbox) cudaFreeHost(c->hbox);
@@ -580,6 +530,8 @@ int rise_set_option(rise_ctx *c, int option, int64_t value) {
     case RISE_OPT_KEEP_POWER: c->keep_power = value != 0; return RISE_OK;
     case RISE_OPT_KEEP_MASKS: c->keep_masks = value != 0; return RISE_OK;
     case RISE_OPT_TIMING: c->timing = value != 0; return RISE_OK;
+    case RISE_OPT_BATCH_GRAPH: c->batch_graph = value != 0; return RISE_OK;
+    case RISE_OPT_AUTOTUNE: c->autotune = value != 0; return RISE_OK;
     case RISE_OPT_RANGE_PATH:
       if (value < 0 || value > 2) return RISE_EINVAL;
       c->range_path = (int)value;
@@ -595,7 +547,23 @@ int rise_stage_times(rise_ctx *c, float *ms, int nstages) {
 }
 
 int rise_debug_export(rise_ctx *c, int what, void *dst, size_t bytes) {
-  if (!c || !dst || !c->last_valid) return RISE_EINVAL;
+  if (!c || !dst) return RISE_EINVAL;
+  if (what == RISE_DBG_LAUNCHES) {
+    if (bytes < sizeof(int64_t)) return RISE_EINVAL;
+    int64_t v = (int64_t)launches_so_far();
+    std::memcpy(dst, &v, sizeof v);
+    return RISE_OK;
+  }
+  if (what == RISE_DBG_BATCH_INFO) {
+    if (bytes < 16 * sizeof(int64_t) || c->batch.last_groups == 0) return RISE_EINVAL;
+    int64_t v[16] = {};
+    v[0] = c->batch.last_groups;
+    v[1] = c->batch.last_graph ? 1 : 0;
+    for (size_t i = 0; i < c->batch.last_params.size() && i + 2 < 16; ++i) v[2 + i] = c->batch.last_params[i];
+    std::memcpy(dst, v, sizeof v);
+    return RISE_OK;
+  }
+  if (!c->last_valid) return RISE_EINVAL;
   CK(cudaSetDevice(c->device));
   const int64_t T = c->last_T;
   const int F = c->last_F;
@@ -621,12 +589,6 @@ int rise_debug_export(rise_ctx *c, int what, void *dst, size_t bytes) {
       return RISE_OK;
     }
     case RISE_DBG_LEVEL_EDGES: src = c->small->edges; need = 257 * sizeof(float); break;
-    case RISE_DBG_LAUNCHES: {
-      if (bytes < sizeof(int64_t)) return RISE_EINVAL;
-      int64_t v = (int64_t)launches_so_far();
-      std::memcpy(dst, &v, sizeof v);
-      return RISE_OK;
-    }
     default: return RISE_EINVAL;
   }
   if (bytes < need || !src) return RISE_EINVAL;

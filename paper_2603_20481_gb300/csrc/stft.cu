@@ -159,6 +159,9 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
 __device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
 }
+__device__ __forceinline__ void mbar_inval(uint64_t *b) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(b)) : "memory");
+}
 __device__ __forceinline__ void mbar_fence_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -246,28 +249,25 @@ struct Smem {
   static constexpr int BLOCKS = (BYTES <= 113 * 1024 && PL::THREADS <= 256) ? 2 : 1;  // per SM
 };
 
+// Frames [f_begin, f_end) of one capture: window, FFT, epilogue.  Returns
+// false (after recording ERR_INDEX) when a staged copy never arrived.
 template <int N, int MODE, bool TMA>
-__global__ void __launch_bounds__(Plan<N>::THREADS, (Smem<N, TMA>::BLOCKS))
-stft_kernel(StftArgs a, int64_t frames_per_block) {
+__device__ __forceinline__ bool stft_frames(const StftArgs &a, int64_t f_begin, int64_t f_end,
+                                            float2 *smem, float *red, uint64_t *bar) {
   using PL = Plan<N>;
   using SM = Smem<N, TMA>;
   constexpr int TPF = PL::TPF, FPB = PL::FPB, SLOT = PL::SLOT, NPASS = PL::NPASS, NXB = SM::NXB;
   constexpr bool DO_MAX = (MODE == STFT_MAX || MODE == STFT_POWER);
   constexpr bool DO_Q = (MODE == STFT_QUANT || MODE == STFT_QUANT_POWER);
   constexpr bool DO_P = (MODE == STFT_POWER || MODE == STFT_QUANT_POWER);
-  extern __shared__ __align__(128) float2 smem[];
   float2 *stage = smem;                                   // [STAGE] (TMA only)
   float2 *xb0 = smem + SM::STAGE;
   float2 *xb1 = xb0 + (NXB == 2 ? SM::XB : 0);
   float2 *twr = xb0 + NXB * SM::XB;
   float *edges = reinterpret_cast<float *>(twr + PL::TW_REST);
-  __shared__ float red[32];
-  __shared__ __align__(8) uint64_t bar;
 
   const int tid = threadIdx.x;
   const int slot = tid / TPF, tau = tid % TPF;
-  const int64_t f_begin = (int64_t)blockIdx.x * frames_per_block;
-  const int64_t f_end = min(a.T, f_begin + frames_per_block);
   const int64_t nsteps = (f_end - f_begin + FPB - 1) / FPB;
 
   auto step_bytes = [&](int64_t st) -> uint32_t {
@@ -280,13 +280,14 @@ stft_kernel(StftArgs a, int64_t frames_per_block) {
   auto issue = [&](int64_t st) {
     const int64_t t0 = f_begin + st * FPB;
     const uint32_t bytes = step_bytes(st);
-    mbar_expect_tx(&bar, bytes);
-    bulk_g2s(stage, a.iq + t0 * (int64_t)a.hop, bytes, &bar);
+    mbar_expect_tx(bar, bytes);
+    bulk_g2s(stage, a.iq + t0 * (int64_t)a.hop, bytes, bar);
   };
   if constexpr (TMA) {
     if (tid == 0) {
-      mbar_init(&bar, 1);
+      mbar_init(bar, 1);
       mbar_fence_init();
+      fence_proxy_async();   // earlier generic reads of the stage come first
       if (nsteps > 0) issue(0);
     }
   }
@@ -315,7 +316,7 @@ stft_kernel(StftArgs a, int64_t frames_per_block) {
     const bool valid = t < f_end;
     float2 v[16];
     if constexpr (TMA) {
-      if (!mbar_wait(&bar, (uint32_t)(st & 1))) failed = true;
+      if (!mbar_wait(bar, (uint32_t)(st & 1))) failed = true;
       const float2 *x = stage + (valid ? slot * a.hop : 0) + tau;
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
@@ -339,9 +340,9 @@ stft_kernel(StftArgs a, int64_t frames_per_block) {
       // a staged copy never arrived: record it, let copies in flight land, leave
       if (tid == 0) {
         atomicOr(a.err, ERR_INDEX);
-        if constexpr (TMA) mbar_wait(&bar, (uint32_t)(st & 1));
+        if constexpr (TMA) mbar_wait(bar, (uint32_t)(st & 1));
       }
-      return;
+      return false;
     }
     if constexpr (TMA) {
       if (tid == 0 && st + 1 < nsteps) {
@@ -394,6 +395,47 @@ stft_kernel(StftArgs a, int64_t frames_per_block) {
       atomicMax(a.max_bits, __float_as_uint(m));   // P >= 0: bit order = value order
     }
   }
+  return true;
+}
+
+template <int N, int MODE, bool TMA>
+__global__ void __launch_bounds__(Plan<N>::THREADS, (Smem<N, TMA>::BLOCKS))
+stft_kernel(StftArgs a, int64_t frames_per_block) {
+  extern __shared__ __align__(128) float2 smem[];
+  __shared__ float red[32];
+  __shared__ __align__(8) uint64_t bar;
+  const int64_t f_begin = (int64_t)blockIdx.x * frames_per_block;
+  const int64_t f_end = min(a.T, f_begin + frames_per_block);
+  stft_frames<N, MODE, TMA>(a, f_begin, f_end, smem, red, &bar);
+}
+
+// Many captures of one FFT size in one launch: a persistent grid whose
+// blocks take (capture, frame range) items from a shared counter until none
+// are left, so uneven captures balance across the SMs.  Items come sorted by
+// size, largest first.
+template <int N, int MODE, bool TMA>
+__global__ void __launch_bounds__(Plan<N>::THREADS, (Smem<N, TMA>::BLOCKS))
+stft_batch_kernel(const StftArgs *segs, const StftItem *items, int n_items, int *counter) {
+  extern __shared__ __align__(128) float2 smem[];
+  __shared__ float red[32];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ StftArgs sa;
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int it = atomicAdd(counter, 1);
+      s_item = it;
+      if (it < n_items) sa = segs[items[it].seg];
+    }
+    __syncthreads();
+    const int it = s_item;
+    if (it >= n_items) return;
+    const StftItem item = items[it];
+    const bool ok = stft_frames<N, MODE, TMA>(sa, item.f0, item.f1, smem, red, &bar);
+    if (!ok) return;   // uniform over the block
+    __syncthreads();   // every wait on the barrier and every read of sa is done
+    if (TMA && threadIdx.x == 0) mbar_inval(&bar);
+  }
 }
 
 template <int N, int MODE, bool TMA>
@@ -428,6 +470,45 @@ cudaError_t launch_mode(const StftArgs &a, StftMode mode, int num_sms, cudaStrea
   return cudaErrorInvalidValue;
 }
 
+template <int N, int MODE, bool TMA>
+cudaError_t launch_batch_n(const StftArgs *segs, const StftItem *items, int n_items, int *counter,
+                           int num_sms, cudaStream_t s) {
+  using PL = Plan<N>;
+  auto kern = stft_batch_kernel<N, MODE, TMA>;
+  const size_t sm = Smem<N, TMA>::BYTES;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, PL::THREADS, sm);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) occ = 1;
+  const int grid = (int)std::min<int64_t>(n_items, (int64_t)num_sms * occ);
+  if (grid < 1) return cudaSuccess;
+  kern<<<grid, PL::THREADS, sm, s>>>(segs, items, n_items, counter);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <int N, bool TMA>
+cudaError_t batch_mode(StftMode mode, const StftArgs *segs, const StftItem *items, int n_items,
+                       int *counter, int num_sms, cudaStream_t s) {
+  switch (mode) {
+    case STFT_MAX: return launch_batch_n<N, STFT_MAX, TMA>(segs, items, n_items, counter, num_sms, s);
+    case STFT_QUANT: return launch_batch_n<N, STFT_QUANT, TMA>(segs, items, n_items, counter, num_sms, s);
+    case STFT_POWER: return launch_batch_n<N, STFT_POWER, TMA>(segs, items, n_items, counter, num_sms, s);
+    case STFT_QUANT_POWER:
+      return launch_batch_n<N, STFT_QUANT_POWER, TMA>(segs, items, n_items, counter, num_sms, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int N>
+cudaError_t batch_size(bool tma, StftMode mode, const StftArgs *segs, const StftItem *items,
+                       int n_items, int *counter, int num_sms, cudaStream_t s) {
+  return tma ? batch_mode<N, true>(mode, segs, items, n_items, counter, num_sms, s)
+             : batch_mode<N, false>(mode, segs, items, n_items, counter, num_sms, s);
+}
+
 template <int N>
 cudaError_t launch_size(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s) {
   // staged input needs every copy 16-byte aligned: an even hop and a 16-byte aligned base
@@ -440,8 +521,9 @@ cudaError_t launch_size(const StftArgs &a, StftMode mode, int num_sms, cudaStrea
 // (FP64, computed on the host), edges[j] is the smallest float not below
 // anchor * ratio[j], so "P >= edges[j]" is the exact comparison for a float
 // P.  edges[0] = 0, edges[256] = +inf.
-__global__ void levels_kernel(const uint32_t *max_bits, double hi_power, int use_fixed,
-                              const double *ratio, double level_db, float *edges, float *qconst) {
+__device__ __forceinline__ void levels_body(const uint32_t *max_bits, double hi_power, int use_fixed,
+                                            const double *ratio, double level_db, float *edges,
+                                            float *qconst) {
   const double M = use_fixed ? hi_power : (double)__uint_as_float(*max_bits);
   const int j = threadIdx.x;
   if (j == 0) {
@@ -455,6 +537,18 @@ __global__ void levels_kernel(const uint32_t *max_bits, double hi_power, int use
     qconst[0] = M > 0.0 ? (float)(1.0 / M) : 0.0f;
     qconst[1] = (float)(3.0102999566398119521 / level_db);   // 10 log10(2) / level_db
   }
+}
+
+__global__ void levels_kernel(const uint32_t *max_bits, double hi_power, int use_fixed,
+                              const double *ratio, double level_db, float *edges, float *qconst) {
+  levels_body(max_bits, hi_power, use_fixed, ratio, level_db, edges, qconst);
+}
+
+// one block per capture of a batch
+__global__ void levels_batch_kernel(CapSmall *cs, double hi_power, int use_fixed, const double *ratio,
+                                    double level_db) {
+  CapSmall &c = cs[blockIdx.x];
+  levels_body(&c.max_bits, hi_power, use_fixed, ratio, level_db, c.edges, c.qconst);
 }
 
 }  // namespace
@@ -513,6 +607,39 @@ cudaError_t launch_stft(const StftArgs &a, StftMode mode, int num_sms, cudaStrea
     case 8192: return launch_size<8192>(a, mode, num_sms, s);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_stft_batch(int N, bool tma, StftMode mode, const StftArgs *segs,
+                              const StftItem *items, int n_items, int *counter, int num_sms,
+                              cudaStream_t s) {
+  switch (N) {
+    case 256: return batch_size<256>(tma, mode, segs, items, n_items, counter, num_sms, s);
+    case 512: return batch_size<512>(tma, mode, segs, items, n_items, counter, num_sms, s);
+    case 1024: return batch_size<1024>(tma, mode, segs, items, n_items, counter, num_sms, s);
+    case 2048: return batch_size<2048>(tma, mode, segs, items, n_items, counter, num_sms, s);
+    case 4096: return batch_size<4096>(tma, mode, segs, items, n_items, counter, num_sms, s);
+    case 8192: return batch_size<8192>(tma, mode, segs, items, n_items, counter, num_sms, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int stft_frames_per_step(int N) {
+  switch (N) {
+    case 256: return Plan<256>::FPB;
+    case 512: return Plan<512>::FPB;
+    case 1024: return Plan<1024>::FPB;
+    case 2048: return Plan<2048>::FPB;
+    case 4096: return Plan<4096>::FPB;
+    case 8192: return Plan<8192>::FPB;
+  }
+  return 1;
+}
+
+cudaError_t launch_levels_batch(CapSmall *cs, int ncap, double hi_power, int use_fixed,
+                                const double *ratio, double level_db, cudaStream_t s) {
+  levels_batch_kernel<<<ncap, 288, 0, s>>>(cs, hi_power, use_fixed, ratio, level_db);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_levels(const uint32_t *max_bits, double hi_power, int use_fixed,

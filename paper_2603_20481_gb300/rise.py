@@ -26,16 +26,19 @@ NOALLOC_MAX_COLS = 4096
 RANGE_AUTO_MAX, RANGE_FIXED = 0, 1
 DBG_POWER_F32, DBG_IMAGE_U8, DBG_HIST, DBG_COLSTATS, DBG_FLOOR = 1, 2, 3, 4, 5
 DBG_MASK0, DBG_MASK1, DBG_MASK2, DBG_MASK3, DBG_MAXPOW, DBG_LEVEL_EDGES = 6, 7, 8, 9, 10, 11
-DBG_LAUNCHES = 12
+DBG_LAUNCHES, DBG_BATCH_INFO = 12, 13
 STAGES = ("spectrum_pass1", "spectrum_pass2", "histogram", "column_stats", "morphology",
           "labelling", "readback", "total")
 OPT_KEEP_POWER, OPT_KEEP_MASKS, OPT_TIMING, OPT_RANGE_PATH = 1, 2, 3, 4
+OPT_BATCH_GRAPH, OPT_AUTOTUNE = 5, 6
+BATCH_MAX_ROWS = 524280
 BOX_COLS = ("t0", "t1", "f0", "f1", "anchor", "area", "sum_q", "energy_fx")
 
 # Functions the header declares; the ABI test checks the library exports them.
 EXPORTS = ("rise_thresholds_default", "rise_create", "rise_destroy", "rise_strerror",
            "rise_detect", "rise_detect_host", "rise_detect_image", "rise_debug_export",
-           "rise_set_option", "rise_stage_times", "rise_column_stats_noalloc")
+           "rise_set_option", "rise_stage_times", "rise_column_stats_noalloc",
+           "rise_detect_batch")
 
 
 class RiseError(RuntimeError):
@@ -53,6 +56,10 @@ class Thresholds(C.Structure):
     _fields_ = [("range_mode", C.c_int), ("hi_db", C.c_double), ("level_db", C.c_double),
                 ("psd_offset_db", C.c_double), ("power_offset_db", C.c_double),
                 ("sg_half_window", C.c_int), ("morph_order", C.c_int)]
+
+
+class Capture(C.Structure):
+    _fields_ = [("iq_dev", C.c_void_p), ("n", C.c_int64), ("fft_size", C.c_int), ("hop", C.c_int)]
 
 
 class Box(C.Structure):
@@ -100,6 +107,8 @@ def lib() -> C.CDLL:
     L.rise_set_option.restype = i32
     L.rise_stage_times.argtypes = [P, P, i32]
     L.rise_stage_times.restype = i32
+    L.rise_detect_batch.argtypes = [P, P, i32, P, P, i64, P]
+    L.rise_detect_batch.restype = i32
     L.rise_column_stats_noalloc.argtypes = [P, i64, i32, P, P]
     L.rise_column_stats_noalloc.restype = i32
     _lib = L
@@ -129,14 +138,20 @@ def boxes_from_raw(raw: np.ndarray, n: int) -> np.ndarray:
 
 
 class Detector:
-    """One library context bound to a device and a CUDA stream."""
+    """One library context bound to a device and a CUDA stream.
+
+    By default the context gets a stream of its own (a torch.cuda.Stream);
+    every call first makes that stream wait for the caller's current torch
+    stream, so inputs produced by torch kernels are complete before the
+    library reads them.
+    """
 
     def __init__(self, device: int = 0, stream=None, mem_budget: int = 0,
                  max_boxes: int = 0, max_samples: int = 0):
         import torch
         self._torch = torch
         if stream is None:
-            stream = torch.cuda.current_stream(device)
+            stream = torch.cuda.Stream(device)
         cfg = Config(device, C.c_void_p(stream.cuda_stream), max_samples, 0, max_boxes, mem_budget)
         h = C.c_void_p()
         rc = lib().rise_create(C.byref(h), C.byref(cfg))
@@ -163,6 +178,11 @@ class Detector:
 
     def __exit__(self, *a):
         self.close()
+
+    def _order(self):
+        cur = self._torch.cuda.current_stream(self.device)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            self.stream.wait_stream(cur)
 
     # -- options ----------------------------------------------------------------
     def set_option(self, option: int, value: int):
@@ -216,6 +236,7 @@ class Detector:
             raise TypeError("iq must be a contiguous 1-D CUDA complex64 tensor")
         args = (self._h, C.c_void_p(iq.data_ptr()), iq.numel(), fft_size, hop,
                 C.byref(thr) if thr is not None else None)
+        self._order()
         return self._run(lib().rise_detect, args, cap)
 
     def detect_host(self, iq, fft_size: int, hop: int, thr: Optional[Thresholds] = None,
@@ -231,6 +252,7 @@ class Detector:
             ptr, n = iq.ctypes.data, iq.shape[0]
         args = (self._h, C.c_void_p(ptr), n, fft_size, hop,
                 C.byref(thr) if thr is not None else None)
+        self._order()
         return self._run(lib().rise_detect_host, args, cap)
 
     def detect_image(self, img, thr: Optional[Thresholds] = None,
@@ -243,7 +265,54 @@ class Detector:
         T, F = img.shape
         args = (self._h, C.c_void_p(img.data_ptr()), T, F,
                 C.byref(thr) if thr is not None else None)
+        self._order()
         return self._run(lib().rise_detect_image, args, cap)
+
+    def detect_batch(self, iqs, fft_sizes, hops, thr: Optional[Thresholds] = None,
+                     cap: Optional[int] = None):
+        """Boxes of many captures in one call (rise_detect_batch).
+
+        `iqs`: list of contiguous 1-D CUDA complex64 tensors; `fft_sizes`,
+        `hops`: one int each, or a list per capture.  Returns (boxes, offsets):
+        boxes (total, 8) as for detect, capture c's rows being
+        boxes[offsets[c]:offsets[c+1]].
+        """
+        t = self._torch
+        k = len(iqs)
+        if isinstance(fft_sizes, int):
+            fft_sizes = [fft_sizes] * k
+        if isinstance(hops, int):
+            hops = [hops] * k
+        caps = (Capture * max(k, 1))()
+        for i, x in enumerate(iqs):
+            if not (isinstance(x, t.Tensor) and x.is_cuda and x.dtype == t.complex64
+                    and x.is_contiguous() and x.dim() == 1):
+                raise TypeError("each capture must be a contiguous 1-D CUDA complex64 tensor")
+            caps[i] = Capture(x.data_ptr(), x.numel(), int(fft_sizes[i]), int(hops[i]))
+        offs = np.zeros(k + 1, np.int64)
+        cap = self.cap if cap is None else int(cap)
+        self._order()
+        while True:
+            raw = self._raw(max(cap, 1))
+            rc = lib().rise_detect_batch(self._h, C.byref(caps), k,
+                                         C.byref(thr) if thr is not None else None,
+                                         raw.ctypes.data if cap > 0 else None, cap,
+                                         offs.ctypes.data)
+            if rc == RISE_ETRUNC and self._auto_grow:
+                cap = int(offs[k])
+                self.cap = max(self.cap, cap)
+                continue
+            if rc not in (RISE_OK, RISE_ETRUNC):
+                raise RiseError(rc, "rise_detect_batch")
+            self.last_status = rc
+            return boxes_from_raw(raw, min(int(offs[k]), cap)), offs
+
+    def batch_info(self) -> np.ndarray:
+        v = np.zeros(16, np.int64)
+        rc = lib().rise_debug_export(self._h, DBG_BATCH_INFO, v.ctypes.data, v.nbytes)
+        if rc != RISE_OK:
+            raise RiseError(rc, "rise_debug_export")
+        return v
 
     # -- introspection ----------------------------------------------------------
     def debug(self, what: int, T: int, F: int) -> np.ndarray:

@@ -1,0 +1,168 @@
+"""rise_detect_batch against one rise_detect call per capture.
+
+A batch shares launches, not results: every capture must come out exactly as
+it does alone (same 8-bit anchor, noise floor, Otsu thresholds, components),
+so the boxes are compared bit for bit, capture by capture.  The single-capture
+path is itself checked against the oracle in test_gpu_parity.py.
+"""
+import numpy as np
+import pytest
+
+from paper_2603_20481_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(count, seed0, n_range=(1 << 13, 1 << 18), sizes=(256, 512, 1024, 2048)):
+    return synth.batched_captures(count, seed0, sizes=sizes, n_range=n_range)
+
+
+def _plain(det, xs, Ns, hops, thr=None):
+    return [det.detect(x, N, h, thr) for x, N, h in zip(xs, Ns, hops)]
+
+
+def _check(boxes, offs, want):
+    assert offs[0] == 0 and len(offs) == len(want) + 1
+    assert offs[-1] == sum(len(w) for w in want) == len(boxes)
+    for c, w in enumerate(want):
+        np.testing.assert_array_equal(boxes[offs[c]:offs[c + 1]], w, err_msg=f"capture {c}")
+
+
+def _to_gpu(caps, ragged=0):
+    import torch
+    xs = []
+    for i, c in enumerate(caps):
+        iq = c.iq
+        if ragged and i % 3 == 1:
+            iq = iq[: max(c.fft_size, iq.shape[0] - ragged - i)]   # ragged tail
+        xs.append(torch.from_numpy(np.ascontiguousarray(iq)).cuda())
+    return xs
+
+
+def test_mixed_sizes_match_single_calls(det):
+    caps = _batch(24, 7000)
+    xs = _to_gpu(caps, ragged=777)
+    Ns = [c.fft_size for c in caps]
+    hops = [c.hop for c in caps]
+    boxes, offs = det.detect_batch(xs, Ns, hops)
+    _check(boxes, offs, _plain(det, xs, Ns, hops))
+    info = det.batch_info()
+    assert info[0] >= 2                                  # several FFT sizes -> several STFT groups
+
+
+def test_odd_hops_and_unaligned_starts(det):
+    # odd hops and a base that is only 8-byte aligned use the non-staged STFT
+    import torch
+    caps = _batch(6, 7100, n_range=(1 << 14, 1 << 16))
+    xs, Ns, hops = [], [], []
+    for i, c in enumerate(caps):
+        t = torch.from_numpy(c.iq).cuda()
+        if i % 2:
+            t = torch.cat([torch.zeros(1, dtype=t.dtype, device=t.device), t])[1:]   # 8-byte offset
+            assert t.data_ptr() % 16 == 8
+        xs.append(t)
+        Ns.append(c.fft_size)
+        hops.append(c.fft_size // 2 + (1 if i % 3 == 0 else 0))
+    boxes, offs = det.detect_batch(xs, Ns, hops)
+    _check(boxes, offs, _plain(det, xs, Ns, hops))
+
+
+def test_fixed_range_and_other_thresholds(det):
+    from paper_2603_20481_gb300 import rise
+    caps = _batch(8, 7200, n_range=(1 << 14, 1 << 17))
+    xs = _to_gpu(caps)
+    Ns = [c.fft_size for c in caps]
+    hops = [c.hop for c in caps]
+    for thr in (rise.default_thresholds(range_mode=rise.RANGE_FIXED, hi_db=75.0),
+                rise.default_thresholds(level_db=0.5, psd_offset_db=1.0, power_offset_db=6.0,
+                                        sg_half_window=3, morph_order=1)):
+        boxes, offs = det.detect_batch(xs, Ns, hops, thr)
+        _check(boxes, offs, _plain(det, xs, Ns, hops, thr))
+
+
+def test_graph_replay_reads_fresh_inputs(det):
+    # same composition twice: the second call replays the captured chain and
+    # must still see the new samples and the new output
+    import torch
+    caps = _batch(10, 7300, n_range=(1 << 14, 1 << 17))
+    Ns = [c.fft_size for c in caps]
+    hops = [c.hop for c in caps]
+    xs = _to_gpu(caps)
+    b1, o1 = det.detect_batch(xs, Ns, hops)
+    _check(b1, o1, _plain(det, xs, Ns, hops))
+    # new contents in the same tensors (same pointers, same shapes)
+    other = _batch(10, 7400, n_range=(1 << 14, 1 << 17))
+    for x, c in zip(xs, other):
+        n = min(x.numel(), c.iq.shape[0])
+        x[:n].copy_(torch.from_numpy(c.iq[:n]))
+    b2, o2 = det.detect_batch(xs, Ns, hops)
+    assert det.batch_info()[1] == 1                       # replayed from the graph
+    _check(b2, o2, _plain(det, xs, Ns, hops))
+    assert not (len(b1) == len(b2) and np.array_equal(b1, b2))
+
+
+def test_switches_give_the_same_boxes(det):
+    from paper_2603_20481_gb300 import rise
+    caps = _batch(12, 7500)
+    xs = _to_gpu(caps)
+    Ns = [c.fft_size for c in caps]
+    hops = [c.hop for c in caps]
+    ref, ro = det.detect_batch(xs, Ns, hops)
+    for graph, tune in ((0, 0), (0, 1), (1, 0)):
+        with rise.Detector(0) as d2:
+            d2.set_option(rise.OPT_BATCH_GRAPH, graph)
+            d2.set_option(rise.OPT_AUTOTUNE, tune)
+            for _ in range(2):
+                b, o = d2.detect_batch(xs, Ns, hops)
+                np.testing.assert_array_equal(o, ro)
+                np.testing.assert_array_equal(b, ref)
+            assert d2.batch_info()[1] == graph
+
+
+def test_truncation_offsets_and_edge_cases(det):
+    import ctypes
+    import torch
+    from paper_2603_20481_gb300 import rise
+    caps = _batch(5, 7600, n_range=(1 << 15, 1 << 17))
+    xs = _to_gpu(caps)
+    Ns = [c.fft_size for c in caps]
+    hops = [c.hop for c in caps]
+    full, fo = det.detect_batch(xs, Ns, hops)
+    assert fo[-1] > 3
+    det._auto_grow = False
+    try:
+        b, o = det.detect_batch(xs, Ns, hops, cap=3)
+        assert det.last_status == rise.RISE_ETRUNC
+        np.testing.assert_array_equal(o, fo)
+        np.testing.assert_array_equal(b, full[:3])
+    finally:
+        det._auto_grow = True
+    # no captures
+    offs = np.zeros(1, np.int64)
+    assert rise.lib().rise_detect_batch(det._h, None, 0, None, None, 0, offs.ctypes.data) == 0
+    assert offs[0] == 0
+    # a capture of exactly one frame, next to normal ones
+    one = torch.from_numpy(caps[0].iq[:Ns[0]].copy()).cuda()
+    b, o = det.detect_batch([one] + xs, [Ns[0]] + Ns, [hops[0]] + hops)
+    _check(b, o, _plain(det, [one] + xs, [Ns[0]] + Ns, [hops[0]] + hops))
+    # rejected before any work: too short, too many frames, bad FFT size
+    bad = [(xs[0], Ns[0] * 4096, hops[0]), (xs[0], Ns[0], 0), (xs[0], 300, 150)]
+    for x, N, h in bad:
+        with pytest.raises(rise.RiseError) as e:
+            det.detect_batch([x], [N], [h])
+        assert e.value.code == rise.RISE_EINVAL
+    long = torch.zeros(rise.BATCH_MAX_ROWS * 256 + 256, dtype=torch.complex64, device="cuda")
+    with pytest.raises(rise.RiseError):
+        det.detect_batch([long], [256], [256])
+    del long
+
+
+@pytest.mark.slow
+def test_many_uneven_captures(det):
+    # 128 captures, 2^14..2^20 samples, every FFT size of the batched workload
+    caps = _batch(128, 1000, n_range=(1 << 14, 1 << 20))
+    xs = _to_gpu(caps)
+    Ns = [c.fft_size for c in caps]
+    hops = [c.hop for c in caps]
+    boxes, offs = det.detect_batch(xs, Ns, hops)
+    _check(boxes, offs, _plain(det, xs, Ns, hops))
