@@ -47,6 +47,7 @@ extern "C" {
 #define RISE_EINTERNAL (-6) /* a kernel's own consistency check failed          */
 #define RISE_ESCRATCH (-7)  /* size beyond the fixed scratch of an allocation-  *
                             * free entry point                                 */
+#define RISE_EAGAIN (-8)    /* server queue full: poll results, then resubmit   */
 
 /* ---- limits ------------------------------------------------------------ */
 #define RISE_MIN_FFT 256
@@ -187,6 +188,95 @@ typedef struct {
  * RISE_EINTERNAL.  rise_debug_export intermediates are not kept for batches. */
 int rise_detect_batch(rise_ctx *ctx, const rise_capture *caps, int ncap,
                       const rise_thresholds *thr, rise_box *out, int64_t cap, int64_t *offsets);
+
+/* ---- serving ------------------------------------------------------------ */
+/* A server takes chunks of IQ from many radio streams as they arrive and
+ * runs them through the path in batches (continuous batching): lane threads,
+ * each with its own context and CUDA stream, take whatever chunks are
+ * pending whenever a batch slot and memory are free, so batches overlap on
+ * the GPU.  A chunk's result is the same whatever else shares its batch.
+ *
+ * Streams are continuous: each keeps on the device the samples its last
+ * chunk left unused (fewer than fft_size), and its next chunk is processed
+ * as those samples followed by the new ones, so every frame t*hop of the
+ * stream is transformed exactly once across chunk boundaries.  A chunk
+ * whose carried + new samples hold no full frame yields no frames and no
+ * boxes and carries everything forward.
+ *
+ * Memory admission: every chunk in flight holds a device slot of
+ * (max_chunk + fft_size) samples; the slot pool and the lanes' scratch are
+ * sized to fit mem_budget, and chunks wait in the queue until a slot frees.
+ * Submitting to a full queue returns RISE_EAGAIN (the chunk is not taken). */
+typedef struct rise_server rise_server;
+
+typedef struct {
+  int device;
+  int fft_size;           /* N of every chunk's STFT                              */
+  int hop;                /* 1..fft_size                                          */
+  int64_t max_chunk;      /* largest chunk, samples                               */
+  int max_streams;        /* stream ids 0 .. max_streams-1                        */
+  int lanes;              /* batches in flight at once (0: 2)                     */
+  int max_batch;          /* chunks per batch (0: 32)                             */
+  int max_pending;        /* queued chunks before RISE_EAGAIN (0: 4096)           */
+  size_t mem_budget;      /* device bytes for slots + lane scratch (0: no cap)    */
+  const rise_thresholds *thr; /* NULL: defaults; copied at create                 */
+} rise_server_config;
+
+typedef struct {
+  int stream;             /* radio stream id                                      */
+  int status;             /* RISE_OK or the error of the chunk's batch            */
+  uint64_t tag;           /* as given to rise_stream_submit                       */
+  int64_t seq;            /* chunk number within its stream, from 0               */
+  int64_t first_frame;    /* stream frame index of the chunk's first frame        */
+  int64_t frames;         /* frames the chunk completed                           */
+  int64_t box_offset;     /* its boxes: arena[box_offset, box_offset + n_boxes)   */
+  int64_t n_boxes;        /* box t0/t1 count frames from first_frame              */
+  int64_t t_submit_ns;    /* steady-clock times: submitted, batch started, done   */
+  int64_t t_start_ns;
+  int64_t t_done_ns;
+} rise_result;
+
+/* Creates a server and starts its lane threads.  Errors: RISE_EINVAL,
+ * RISE_ENOMEM (mem_budget below one slot and one chunk of scratch per lane),
+ * RISE_ECUDA. */
+int rise_server_create(rise_server **out, const rise_server_config *cfg);
+
+/* Queues n samples (complex64, host memory; pinned memory copies fastest)
+ * for stream `stream`.  The buffer must stay valid and unchanged until the
+ * chunk's result has been returned by rise_server_poll.  Chunks of one
+ * stream are processed in submission order.  Errors: RISE_EINVAL (bad
+ * stream, n < 1 or n > max_chunk), RISE_EAGAIN (queue full). */
+int rise_stream_submit(rise_server *s, int stream, const void *iq_host, int64_t n, uint64_t tag);
+
+/* Returns finished chunks, oldest first: up to max_res results into res,
+ * their boxes packed into arena (arena_cap boxes; a result whose boxes do
+ * not fit stays queued, and a lone result larger than the arena comes back
+ * with status RISE_ETRUNC and its first arena_cap boxes).  Waits up to
+ * timeout_ms (0: no wait, < 0: until one result is ready) for the first.
+ * *n_res receives the count.  Errors: RISE_EINVAL. */
+int rise_server_poll(rise_server *s, rise_result *res, int max_res, rise_box *arena,
+                     int64_t arena_cap, int *n_res, int timeout_ms);
+
+/* Waits until no chunk is queued or in flight (timeout_ms < 0: no limit).
+ * Errors: RISE_ETIMEOUT. */
+int rise_server_drain(rise_server *s, int timeout_ms);
+
+/* Copies stream `stream`'s state (its carried samples and counters) to buf,
+ * or, with buf NULL, only reports the size in *need; the stream must have
+ * nothing queued or in flight.  Import restores such a state into a stream
+ * of a server with the same fft_size and hop.  Errors: RISE_EINVAL
+ * (busy stream, small buffer, mismatched server). */
+int rise_stream_export(rise_server *s, int stream, void *buf, size_t bytes, size_t *need);
+int rise_stream_import(rise_server *s, int stream, const void *buf, size_t bytes);
+
+/* Counters: [0] submitted, [1] rejected (RISE_EAGAIN), [2] completed,
+ * [3] batches, [4] largest batch, [5] most chunks in flight, [6] slots,
+ * [7] lanes.  Writes min(n, 8) values. */
+int rise_server_stats(rise_server *s, int64_t *out, int n);
+
+/* Stops the lanes after the chunks in flight and frees everything; queued
+ * chunks that never started are dropped. */
+void rise_server_destroy(rise_server *s);
 
 /* ---- introspection of the last detect call ----------------------------- */
 #define RISE_DBG_POWER_F32 1 /* float [T][F] |X|^2 (needs RISE_OPT_KEEP_POWER)     */

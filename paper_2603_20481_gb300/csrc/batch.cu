@@ -18,7 +18,7 @@ namespace rise {
 namespace host {
 namespace {
 
-constexpr int kMaxGraphs = 8;
+constexpr int kMaxGraphs = 64;
 constexpr int kItemCands[] = {1, 2, 4, 8, 16};      // STFT work item = k x frames per step
 constexpr int kMorphCands[] = {8, 16, 32};          // morphology warps per SM
 constexpr int kNumCands = 5;

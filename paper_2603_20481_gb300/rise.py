@@ -21,7 +21,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "librise.so")
 
 RISE_OK, RISE_EINVAL, RISE_ENOMEM, RISE_ETRUNC = 0, -1, -2, -3
-RISE_ECUDA, RISE_ETIMEOUT, RISE_EINTERNAL, RISE_ESCRATCH = -4, -5, -6, -7
+RISE_ECUDA, RISE_ETIMEOUT, RISE_EINTERNAL, RISE_ESCRATCH, RISE_EAGAIN = -4, -5, -6, -7, -8
 NOALLOC_MAX_COLS = 4096
 RANGE_AUTO_MAX, RANGE_FIXED = 0, 1
 DBG_POWER_F32, DBG_IMAGE_U8, DBG_HIST, DBG_COLSTATS, DBG_FLOOR = 1, 2, 3, 4, 5
@@ -38,7 +38,9 @@ BOX_COLS = ("t0", "t1", "f0", "f1", "anchor", "area", "sum_q", "energy_fx")
 EXPORTS = ("rise_thresholds_default", "rise_create", "rise_destroy", "rise_strerror",
            "rise_detect", "rise_detect_host", "rise_detect_image", "rise_debug_export",
            "rise_set_option", "rise_stage_times", "rise_column_stats_noalloc",
-           "rise_detect_batch")
+           "rise_detect_batch", "rise_server_create", "rise_stream_submit", "rise_server_poll",
+           "rise_server_drain", "rise_stream_export", "rise_stream_import", "rise_server_stats",
+           "rise_server_destroy")
 
 
 class RiseError(RuntimeError):
@@ -60,6 +62,20 @@ class Thresholds(C.Structure):
 
 class Capture(C.Structure):
     _fields_ = [("iq_dev", C.c_void_p), ("n", C.c_int64), ("fft_size", C.c_int), ("hop", C.c_int)]
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("device", C.c_int), ("fft_size", C.c_int), ("hop", C.c_int),
+                ("max_chunk", C.c_int64), ("max_streams", C.c_int), ("lanes", C.c_int),
+                ("max_batch", C.c_int), ("max_pending", C.c_int), ("mem_budget", C.c_size_t),
+                ("thr", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("stream", C.c_int), ("status", C.c_int), ("tag", C.c_uint64), ("seq", C.c_int64),
+                ("first_frame", C.c_int64), ("frames", C.c_int64), ("box_offset", C.c_int64),
+                ("n_boxes", C.c_int64), ("t_submit_ns", C.c_int64), ("t_start_ns", C.c_int64),
+                ("t_done_ns", C.c_int64)]
 
 
 class Box(C.Structure):
@@ -109,6 +125,22 @@ def lib() -> C.CDLL:
     L.rise_stage_times.restype = i32
     L.rise_detect_batch.argtypes = [P, P, i32, P, P, i64, P]
     L.rise_detect_batch.restype = i32
+    L.rise_server_create.argtypes = [C.POINTER(P), P]
+    L.rise_server_create.restype = i32
+    L.rise_stream_submit.argtypes = [P, i32, P, i64, C.c_uint64]
+    L.rise_stream_submit.restype = i32
+    L.rise_server_poll.argtypes = [P, P, i32, P, i64, C.POINTER(i32), i32]
+    L.rise_server_poll.restype = i32
+    L.rise_server_drain.argtypes = [P, i32]
+    L.rise_server_drain.restype = i32
+    L.rise_stream_export.argtypes = [P, i32, P, C.c_size_t, C.POINTER(C.c_size_t)]
+    L.rise_stream_export.restype = i32
+    L.rise_stream_import.argtypes = [P, i32, P, C.c_size_t]
+    L.rise_stream_import.restype = i32
+    L.rise_server_stats.argtypes = [P, P, i32]
+    L.rise_server_stats.restype = i32
+    L.rise_server_destroy.argtypes = [P]
+    L.rise_server_destroy.restype = None
     L.rise_column_stats_noalloc.argtypes = [P, i64, i32, P, P]
     L.rise_column_stats_noalloc.restype = i32
     _lib = L
@@ -356,6 +388,119 @@ def column_stats_noalloc(img, cols, stream=None) -> int:
     return int(lib().rise_column_stats_noalloc(C.c_void_p(img.data_ptr()), img.shape[0],
                                                img.shape[1], C.c_void_p(cols.data_ptr()),
                                                C.c_void_p(stream.cuda_stream)))
+
+
+SERVER_STATS = ("submitted", "rejected", "completed", "batches", "largest_batch",
+                "most_in_flight", "slots", "lanes")
+
+
+class Server:
+    """Continuous-batching server over chunks from many radio streams
+    (rise_server_*).  Host buffers passed to submit are kept referenced here
+    until their result has been polled, as the library requires."""
+
+    def __init__(self, fft_size: int, hop: int, max_chunk: int, max_streams: int,
+                 device: int = 0, lanes: int = 0, max_batch: int = 0, max_pending: int = 0,
+                 mem_budget: int = 0, thr: Optional[Thresholds] = None):
+        self._thr = thr
+        cfg = ServerConfig(device, fft_size, hop, max_chunk, max_streams, lanes, max_batch,
+                           max_pending, mem_budget,
+                           C.cast(C.pointer(thr), C.c_void_p) if thr is not None else None)
+        h = C.c_void_p()
+        rc = lib().rise_server_create(C.byref(h), C.byref(cfg))
+        if rc != RISE_OK:
+            raise RiseError(rc, "rise_server_create")
+        self._h = h
+        self._held = {}                 # (stream, seq) -> host buffer
+        self._seq = [0] * max_streams
+        self._arena = np.empty(1 << 16, BOX_DTYPE)
+        self._res = (Result * 1024)()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rise_server_destroy(self._h)
+            self._h = None
+            self._held.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, stream: int, iq, tag: int = 0) -> bool:
+        """Queues a chunk; False when the queue is full (RISE_EAGAIN)."""
+        import torch
+        if isinstance(iq, torch.Tensor):
+            if iq.is_cuda or iq.dtype != torch.complex64 or not iq.is_contiguous():
+                raise TypeError("iq must be a contiguous host complex64 tensor")
+            ptr, n = iq.data_ptr(), iq.numel()
+        else:
+            if not (isinstance(iq, np.ndarray) and iq.dtype == np.complex64 and iq.flags.c_contiguous):
+                raise TypeError("iq must be a contiguous complex64 array")
+            ptr, n = iq.ctypes.data, iq.shape[0]
+        rc = lib().rise_stream_submit(self._h, stream, C.c_void_p(ptr), n, tag)
+        if rc == RISE_EAGAIN:
+            return False
+        if rc != RISE_OK:
+            raise RiseError(rc, "rise_stream_submit")
+        self._held[(stream, self._seq[stream])] = iq
+        self._seq[stream] += 1
+        return True
+
+    def poll(self, timeout_ms: int = 0, max_results: int = 1024):
+        """Finished chunks: list of (result fields dict, boxes (n, 8) int64)."""
+        n = C.c_int(0)
+        while True:
+            rc = lib().rise_server_poll(self._h, self._res, min(max_results, 1024),
+                                        self._arena.ctypes.data, self._arena.shape[0],
+                                        C.byref(n), timeout_ms)
+            if rc != RISE_OK:
+                raise RiseError(rc, "rise_server_poll")
+            if n.value == 1 and self._res[0].status == RISE_ETRUNC:
+                raise RiseError(RISE_ETRUNC, "rise_server_poll (box arena)")
+            break
+        out = []
+        for i in range(n.value):
+            r = self._res[i]
+            d = {f[0]: getattr(r, f[0]) for f in Result._fields_}
+            b = self._arena[r.box_offset:r.box_offset + r.n_boxes]
+            out.append((d, boxes_from_raw(b, r.n_boxes)))
+            self._held.pop((r.stream, r.seq), None)
+        return out
+
+    def drain(self, timeout_ms: int = -1):
+        rc = lib().rise_server_drain(self._h, timeout_ms)
+        if rc != RISE_OK:
+            raise RiseError(rc, "rise_server_drain")
+
+    def export_stream(self, stream: int) -> bytes:
+        need = C.c_size_t(0)
+        rc = lib().rise_stream_export(self._h, stream, None, 0, C.byref(need))
+        if rc != RISE_OK:
+            raise RiseError(rc, "rise_stream_export")
+        buf = (C.c_char * need.value)()
+        rc = lib().rise_stream_export(self._h, stream, buf, need.value, C.byref(need))
+        if rc != RISE_OK:
+            raise RiseError(rc, "rise_stream_export")
+        return bytes(buf)
+
+    def import_stream(self, stream: int, state: bytes):
+        rc = lib().rise_stream_import(self._h, stream, state, len(state))
+        if rc != RISE_OK:
+            raise RiseError(rc, "rise_stream_import")
+        self._seq[stream] = int(np.frombuffer(state[24:32], np.int64)[0])
+
+    def stats(self) -> dict:
+        v = np.zeros(8, np.int64)
+        lib().rise_server_stats(self._h, v.ctypes.data, 8)
+        return dict(zip(SERVER_STATS, (int(x) for x in v)))
 
 
 def unpack_mask(words: np.ndarray, F: int) -> np.ndarray:

@@ -1,0 +1,140 @@
+"""Serving: continuous batching over chunks from many radio streams.
+
+Each chunk's result must not depend on what shares its batch or lane: the
+same chunks are served one at a time (one lane, batches of one) and all
+interleaved (several lanes, large batches), and every (stream, chunk) result
+must be identical.  Both must also equal rise_detect on the samples the
+stream carries into the chunk followed by the chunk itself, assembled here on
+the host, which checks the carry kept on the device.
+"""
+import numpy as np
+import pytest
+
+from paper_2603_20481_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+N, HOP = 2048, 1024
+
+
+def _chunks(streams, per_stream, n=61440 + 512):
+    # chunk length not a multiple of the hop: the carry length varies
+    return {s: [synth.served_chunk(s, k, n=n).iq for k in range(per_stream)] for s in range(streams)}
+
+
+def _assemble(chunks):
+    """Host restatement of the stream carry: (capture, frames, first_frame) per chunk."""
+    carry = np.zeros(0, np.complex64)
+    out, frame = [], 0
+    for ch in chunks:
+        x = np.concatenate([carry, ch])
+        T = (len(x) - N) // HOP + 1 if len(x) >= N else 0
+        out.append((x, T, frame))
+        frame += T
+        carry = x[T * HOP:]
+    return out
+
+
+def _serve(chunks, order, **kw):
+    import torch
+    from paper_2603_20481_gb300 import rise
+    pinned = {s: [torch.from_numpy(c).pin_memory() for c in cs] for s, cs in chunks.items()}
+    res = {}
+    with rise.Server(N, HOP, max_chunk=max(len(c) for cs in chunks.values() for c in cs),
+                     max_streams=max(chunks) + 1, **kw) as srv:
+        for s, k in order:
+            while not srv.submit(s, pinned[s][k], tag=1000 * s + k):
+                for d, b in srv.poll(timeout_ms=5):
+                    res[(d["stream"], d["seq"])] = (d, b)
+        srv.drain()
+        while len(res) < len(order):
+            for d, b in srv.poll(timeout_ms=100):
+                res[(d["stream"], d["seq"])] = (d, b)
+        stats = srv.stats()
+    return res, stats
+
+
+def test_alone_and_in_the_mix_are_identical(det):
+    chunks = _chunks(6, 4)
+    seq_order = [(s, k) for s in chunks for k in range(4)]            # one stream after another
+    mix_order = [(s, k) for k in range(4) for s in chunks]            # interleaved
+    alone, st_a = _serve(chunks, seq_order, lanes=1, max_batch=1)
+    mixed, st_m = _serve(chunks, mix_order, lanes=3, max_batch=8)
+    assert st_a["largest_batch"] == 1 and st_a["completed"] == 24
+    assert st_m["completed"] == 24
+    import torch
+    for s, cs in chunks.items():
+        for k, (x, T, f0) in enumerate(_assemble(cs)):
+            da, ba = alone[(s, k)]
+            dm, bm = mixed[(s, k)]
+            assert da["status"] == dm["status"] == 0
+            assert da["tag"] == dm["tag"] == 1000 * s + k
+            assert da["frames"] == dm["frames"] == T and da["first_frame"] == dm["first_frame"] == f0
+            np.testing.assert_array_equal(ba, bm, err_msg=f"stream {s} chunk {k}")
+            want = det.detect(torch.from_numpy(x).cuda(), N, HOP)
+            np.testing.assert_array_equal(ba, want, err_msg=f"stream {s} chunk {k} vs rise_detect")
+
+
+def test_export_import_continues_the_stream(det):
+    import torch
+    from paper_2603_20481_gb300 import rise
+    cs = _chunks(1, 3)[0]
+    full, _ = _serve({0: cs}, [(0, 0), (0, 1), (0, 2)], lanes=2, max_batch=4)
+    pinned = [torch.from_numpy(c).pin_memory() for c in cs]
+    with rise.Server(N, HOP, max_chunk=len(cs[0]), max_streams=2) as a:
+        a.submit(0, pinned[0])
+        a.submit(0, pinned[1])
+        a.drain()
+        a.poll(timeout_ms=100)
+        state = a.export_stream(0)
+    with rise.Server(N, HOP, max_chunk=len(cs[0]), max_streams=4) as b:
+        b.import_stream(3, state)
+        assert b.submit(3, pinned[2])
+        b.drain()
+        (d, boxes), = b.poll(timeout_ms=1000)
+    fd, fb = full[(0, 2)]
+    assert d["seq"] == 2 and d["first_frame"] == fd["first_frame"] and d["frames"] == fd["frames"]
+    np.testing.assert_array_equal(boxes, fb)
+    with pytest.raises(rise.RiseError):
+        with rise.Server(4096, 2048, max_chunk=len(cs[0]), max_streams=1) as c:
+            c.import_stream(0, state)                 # another FFT size
+
+
+def test_short_chunks_carry_everything(det):
+    import torch
+    rng = np.random.default_rng(3)
+    long = synth.served_chunk(7, 0, n=40960).iq
+    parts = [long[:500], long[500:1300], long[1300:1400], long[1400:]]   # the first three hold no frame
+    res, _ = _serve({0: parts}, [(0, k) for k in range(4)], lanes=2, max_batch=2)
+    plan = _assemble(parts)
+    for k, (x, T, f0) in enumerate(plan):
+        d, b = res[(0, k)]
+        assert d["frames"] == T and d["first_frame"] == f0
+        if T == 0:
+            assert len(b) == 0
+        else:
+            np.testing.assert_array_equal(b, det.detect(torch.from_numpy(x).cuda(), N, HOP))
+    assert plan[3][0].shape[0] == 40960                     # all earlier samples were carried
+    del rng
+
+
+def test_backpressure_and_bad_arguments():
+    import torch
+    from paper_2603_20481_gb300 import rise
+    x = torch.from_numpy(synth.served_chunk(9, 0, n=8192).iq).pin_memory()
+    with rise.Server(N, HOP, max_chunk=8192, max_streams=2, lanes=1, max_batch=1, max_pending=2) as srv:
+        accepted = sum(srv.submit(i % 2, x) for i in range(300))
+        srv.drain()
+        got = 0
+        while got < accepted:
+            got += len(srv.poll(timeout_ms=100))
+        st = srv.stats()
+        assert st["submitted"] == accepted and st["completed"] == accepted
+        assert st["rejected"] == 300 - accepted > 0
+        with pytest.raises(rise.RiseError):
+            srv.submit(2, x)                                  # no such stream
+        big = torch.zeros(8193, dtype=torch.complex64).pin_memory()
+        with pytest.raises(rise.RiseError):
+            srv.submit(0, big)                                # longer than max_chunk
+    with pytest.raises(rise.RiseError):
+        rise.Server(1000, 500, max_chunk=8192, max_streams=1)   # FFT size not a power of two
