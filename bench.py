@@ -41,6 +41,12 @@ N_FFT, HOP, N_SAMPLES = 4096, 2048, 1 << 26
 WORKLOAD = ("wideband single stream: 2^26 complex64 IQ samples (notional 100 MS/s), "
             "128 emitters (SNR -3..25 dB, 0.1-20 MHz), Hann, FFT 4096, hop 2048 "
             "-> 32767 x 4096 spectrogram; plain method")
+STRESS_WORKLOAD = ("stress: 2^28 complex64 IQ samples, FFT 8192, hop 2048 (75% overlap) "
+                   "-> 131069 x 8192 spectrogram; 1024 emitters at SNR -5..10 dB, half "
+                   "fragmented into 2-20 pieces, 16 narrowband emitters over the whole capture")
+# single-capture workloads: generator, seed, FFT size, hop, samples, description
+SINGLE = {"wideband": ("wideband_capture", 102, 4096, 2048, 1 << 26, WORKLOAD),
+          "stress": ("stress_capture", 105, 8192, 2048, 1 << 28, STRESS_WORKLOAD)}
 HBM_FALLBACK_GBS = 6800.0
 # DRAM bytes (read + write) per launch of the dominant kernel at this workload,
 # from the ncu capture summarised in profiles/stft_power_wideband_2e26_fft4096.md
@@ -122,14 +128,34 @@ def _dist():
     return world, rank, local
 
 
+def _init_dist(local: int, world: int):
+    """One process per GPU (NCCL); gloo where no GPU is visible."""
+    if world <= 1:
+        return
+    import torch
+    import torch.distributed as dist
+    if torch.cuda.is_available():
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist.init_process_group("gloo")
+
+
 def _allreduce_max(x: float, world: int) -> float:
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_throughput(units_per_rank: float, steps: int, t_local: float, world: int):
+    """Replicas: every rank processes its own units; the job's rate is all
+    ranks' units over the slowest rank's time.  Returns (rate, slowest time)."""
+    t_max = _allreduce_max(t_local, world)
+    return world * steps * units_per_rank / t_max, t_max
 
 
 def _barrier(world: int):
@@ -138,12 +164,12 @@ def _barrier(world: int):
         dist.barrier()
 
 
-def cpu_oracle_rate(iq, n_sample: int):
+def cpu_oracle_rate(iq, n_sample: int, N: int, hop: int):
     """FP64 oracle (single-threaded C) on the first n_sample samples."""
     import oracle
     x = iq[:n_sample]
     t0 = time.perf_counter()
-    boxes, _, _ = oracle.detect(x, N_FFT, HOP)
+    boxes, _, _ = oracle.detect(x, N, hop)
     dt = time.perf_counter() - t0
     return n_sample / dt / 1e6, dt, len(boxes)
 
@@ -156,10 +182,9 @@ def run_ours(args):
 
     world, rank, local = _dist()
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    cap = synth.wideband_capture(seed=102 + rank, n=args.samples)
+    _init_dist(local, world)
+    gen, seed, N_FFT, HOP, n_default, workload = SINGLE[args.workload]
+    cap = getattr(synth, gen)(seed=seed + rank, n=args.samples or n_default)
     n = cap.iq.shape[0]
     x = torch.from_numpy(cap.iq).cuda()
     host = torch.from_numpy(cap.iq).pin_memory()
@@ -199,7 +224,7 @@ def run_ours(args):
         clocks["window_s"] = round(w1 - w0, 3)
     _barrier(world)
     t_dev = e0.elapsed_time(e1) / 1e3
-    t_max = _allreduce_max(t_dev, world)
+    rate, t_max = replica_throughput(n, args.steps, t_dev, world)
     stage /= args.steps
     n_boxes = len(boxes)
 
@@ -243,17 +268,18 @@ def run_ours(args):
     achieved = stage_bytes[dom] / (dom_ms / 1e3) / 1e9
     alg_path = 16 * n + 2 * px                      # IQ twice + image write + image read
     result = {
-        "metric": METRIC, "value": round(world * args.steps * n / t_max / 1e6, 1), "unit": UNIT,
+        "metric": METRIC, "value": round(rate / 1e6, 1), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(t_max / args.steps * 1e3, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_samples": n, "fft_size": N_FFT, "hop": HOP,
+        "config": {"workload": workload, "n_samples": n, "fft_size": N_FFT, "hop": HOP,
                    "frames": T, "boxes": n_boxes, "range_path": path,
                    "l2": "inputs larger than L2 (512 MiB capture per step)",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": (TRAFFIC_BYTES.get(path) if dom == "spectrum_pass1" and n == N_SAMPLES
+                                 and args.workload == "wideband"
                                  else None),
                      "peak_source": peak_kind,
                      "alg_bytes_per_launch": stage_bytes[dom], "ms_per_launch": round(dom_ms, 4),
@@ -264,11 +290,12 @@ def run_ours(args):
         "e2e": e2e,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        rate, dt, nb = cpu_oracle_rate(cap.iq, args.cpu_sample)
+        m = min(args.cpu_sample, n)
+        rate, dt, nb = cpu_oracle_rate(cap.iq, m, N_FFT, HOP)
         result["cpu_baseline"] = {
             "value": round(rate, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {args.cpu_sample} samples of the same capture "
-                      f"({(args.cpu_sample - N_FFT) // HOP + 1} frames), one pass, {dt:.1f} s"}
+            "sample": f"first {m} samples of the same capture "
+                      f"({(m - N_FFT) // HOP + 1} frames), one pass, {dt:.1f} s"}
     if rank == 0:
         print(json.dumps(result), flush=True)
     det.close()
@@ -301,9 +328,7 @@ def run_batched(args):
     from paper_2603_20481_gb300 import rise
     world, rank, local = _dist()
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _init_dist(local, world)
     xs = [torch.from_numpy(c.iq).cuda() for c in caps]
     hosts = [torch.from_numpy(c.iq).pin_memory() for c in caps]
     Ns = [c.fft_size for c in caps]
@@ -533,7 +558,7 @@ def run_reference(args):
         return
     from paper_2603_20481_gb300 import synth
     import oracle
-    cap = synth.wideband_capture(seed=102, n=args.samples)
+    cap = synth.wideband_capture(seed=102, n=args.samples or N_SAMPLES)
     m = min(args.ref_sample, cap.iq.shape[0])
     x = cap.iq[:m]
     for _ in range(args.warmup):
@@ -563,7 +588,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--samples", type=int, default=N_SAMPLES)
+    ap.add_argument("--samples", type=int, default=0, help="capture length (0: the workload's)")
     ap.add_argument("--range-path", type=int, default=0, choices=(0, 1, 2))
     ap.add_argument("--cpu-sample", type=int, default=1 << 26)
     ap.add_argument("--ref-sample", type=int, default=1 << 22)
@@ -571,7 +596,8 @@ def main():
     ap.add_argument("--clock-window", type=float, default=1.0,
                     help="seconds of steady load the clock samples span (0: the timed steps only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=("wideband", "batched", "served"), default="wideband")
+    ap.add_argument("--workload", choices=("wideband", "stress", "batched", "served"),
+                    default="wideband")
     ap.add_argument("--lanes", type=int, default=3, help="served: batches in flight")
     ap.add_argument("--max-batch", type=int, default=32, help="served: chunks per batch")
     ap.add_argument("--serve-seconds", type=float, default=1.5, help="served: seconds per load level")
@@ -585,6 +611,9 @@ def main():
         run_batched(args)
     elif args.workload == "served":
         run_served(args)
+    elif args.workload == "stress" and args.cpu_sample == 1 << 26:
+        args.cpu_sample = 1 << 24      # about 20 s of oracle time at FFT 8192, hop 2048
+        run_ours(args)
     else:
         run_ours(args)
 

@@ -176,7 +176,7 @@ typedef struct {
  * together.  The first call with a given composition (the list of n,
  * fft_size, hop and alignment) times a few launch shapes and keeps the
  * fastest (RISE_OPT_AUTOTUNE), and records the chain as a CUDA graph that
- * later calls with the same composition replay (RISE_OPT_BATCH_GRAPH).
+ * later calls with the same composition replay (RISE_OPT_GRAPH).
  *  caps     ncap captures (host array); ncap >= 0.
  *  out      host array of `cap` boxes: the boxes of capture 0 in anchor
  *           order, then those of capture 1, and so on.
@@ -292,6 +292,9 @@ void rise_server_destroy(rise_server *s);
 #define RISE_DBG_LEVEL_EDGES 11 /* float [257]: smallest power of each level          */
 #define RISE_DBG_LAUNCHES 12 /* int64 [1]: kernels launched by this library so far,   *
                               * process-wide (for launch accounting)                */
+#define RISE_DBG_GRAPHS 14   /* int64 [4]: [0] the last rise_detect replayed a     *
+                              * graph, [1] single-capture graphs kept, [2] batch  *
+                              * graphs kept, [3] 0                                */
 #define RISE_DBG_BATCH_INFO 13 /* int64 [16] of the last batch: [0] STFT groups G,   *
                                 * [1] replayed from a graph (0/1), [2..2+G) frames  *
                                 * per STFT item in steps, [2+G] morphology warps    *
@@ -320,7 +323,9 @@ int rise_debug_export(rise_ctx *ctx, int what, void *dst, size_t bytes);
                                 * quantise); 2: FFT once, keep float power,       *
                                 * quantise after                                  */
 
-#define RISE_OPT_BATCH_GRAPH 5 /* 1 (default): batches replay a captured graph   */
+#define RISE_OPT_GRAPH 5       /* 1 (default): a call repeating the previous     *
+                                * call's arguments (a batch: its composition)     *
+                                * replays the launches captured as a CUDA graph   */
 #define RISE_OPT_AUTOTUNE 6    /* 1 (default): tune batch launch shapes once per   *
                                 * composition; 0: fixed defaults                   */
 

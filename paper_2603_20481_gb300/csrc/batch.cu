@@ -498,6 +498,9 @@ int check_capture(const rise_capture &k) {
 void destroy_batch(rise_ctx *c) {
   BatchState &b = c->batch;
   destroy_graphs(b);
+  for (auto &g : c->single_graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  c->single_graphs.clear();
   if (b.tab.p) cudaFree(b.tab.p);
   if (b.small.p) cudaFree(b.small.p);
   if (b.counters.p) cudaFree(b.counters.p);
@@ -546,7 +549,7 @@ int detect_batch(rise_ctx *c, const rise_capture *caps, int ncap, const rise_thr
   if ((rc = fill_tables(c, caps, p, thr))) return rc;
   BatchState &b = c->batch;
   bool launched = false;
-  if (c->batch_graph) {
+  if (c->graphs) {
     const uint64_t key = graph_key(p, thr, cap, c->gen, c->timing);
     BatchState::Graph *gr = nullptr;
     for (auto &g : b.graphs)

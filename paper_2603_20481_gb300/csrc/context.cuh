@@ -69,7 +69,8 @@ struct rise_ctx {
   int num_sms = 1;
   // options
   int keep_power = 0, keep_masks = 0, timing = 0, range_path = 0;
-  int batch_graph = 1, autotune = 1;
+  int graphs = 1, autotune = 1;
+  bool capturing = false;         // enqueueing into a graph capture
   // scratch
   rise::host::Buf iq_stage, power, img, hist, cols, effm1, mask, dbg[3], row_cnt, row_base, run_parent,
       run_sroot, rec, run_out, scan_tmp, boxes, merge;
@@ -91,6 +92,9 @@ struct rise_ctx {
   cudaEvent_t ev[8] = {};
   float stage_ms[8] = {};
   uint64_t gen = 0;              // bumped whenever a scratch buffer moves
+  uint64_t last_key = 0;         // arguments of the last single-capture call
+  bool last_replayed = false;    // the last single-capture call replayed a graph
+  std::vector<rise::host::BatchState::Graph> single_graphs;
   rise::host::BatchState batch;
 };
 

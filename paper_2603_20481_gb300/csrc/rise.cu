@@ -118,7 +118,9 @@ int check_thresholds(const rise_thresholds &t, int F) {
 }
 
 void record(rise_ctx *c, int i) {
-  if (c->timing) cudaEventRecord(c->ev[i], c->stream);
+  // inside a capture the event must become an event-record node
+  if (c->timing)
+    cudaEventRecordWithFlags(c->ev[i], c->stream, c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
 }
 
 // Per-level tables that depend only on level_db: the energy of each level
@@ -158,13 +160,45 @@ using namespace rise::host;
 
 namespace {
 
-// Everything from the 8-bit image on: histogram (unless already built),
-// column statistics, morphology, labelling, boxes back to the host.
-int image_path(rise_ctx *c, const uint8_t *img, int64_t T, int F, const rise_thresholds &thr,
-               bool hist_ready, rise_box *out, int64_t cap, int64_t *n_boxes) {
+CclArgs ccl_args(rise_ctx *c, const uint8_t *img, int64_t T, int F, int64_t cap) {
+  CclArgs la;
+  la.mask = reinterpret_cast<const uint32_t *>(c->mask.p);
+  la.img = img;
+  la.T = T;
+  la.F = F;
+  la.energy = c->small->energy;
+  la.row_base = reinterpret_cast<int64_t *>(c->row_base.p);
+  la.row_cnt = reinterpret_cast<uint32_t *>(c->row_cnt.p);
+  la.status = &c->small->status;
+  la.boxes = c->hbox_dev;   // boxes land directly in mapped pinned host memory
+  la.box_cap = cap;
+  la.run_cap = c->run_cap;
+  la.run_parent = reinterpret_cast<int32_t *>(c->run_parent.p);
+  la.run_sroot = reinterpret_cast<uint8_t *>(c->run_sroot.p);
+  la.rec = reinterpret_cast<rise_box *>(c->rec.p);
+  la.merge = reinterpret_cast<int2 *>(c->merge.p);
+  la.run_out = reinterpret_cast<int64_t *>(c->run_out.p);
+  la.scan_tmp = c->scan_tmp.p;
+  la.scan_tmp_bytes = c->scan_tmp.bytes;
+  return la;
+}
+
+// Host-side set-up of the image part (may allocate or synchronise, so it
+// runs before any launch is enqueued).
+int image_prepare(rise_ctx *c, const rise_thresholds &thr, int64_t cap) {
+  int rc;
+  if ((rc = upload_sg(c, thr.sg_half_window))) return rc;
+  if ((rc = upload_level_tables(c, thr.level_db))) return rc;
+  return ensure_hbox(c, std::max<int64_t>(cap, 1));
+}
+
+// Launches of everything from the 8-bit image on: histogram (unless already
+// built), column statistics, morphology, labelling, status readback.
+// Asynchronous only: it can be captured into a graph.
+int image_enqueue(rise_ctx *c, const uint8_t *img, int64_t T, int F, const rise_thresholds &thr,
+                  bool hist_ready, int64_t cap) {
   Small *sm = c->small;
   cudaStream_t s = c->stream;
-  int rc0;
   if (!hist_ready) {
     if (cluster_hist_accumulates(T))
       CK(cudaMemsetAsync(c->hist.p, 0, (size_t)F * 256 * sizeof(uint32_t), s));
@@ -176,7 +210,6 @@ int image_path(rise_ctx *c, const uint8_t *img, int64_t T, int F, const rise_thr
   // column statistics
   const int m = thr.sg_half_window;
   const int64_t D = (int64_t)(2 * m - 1) * (2 * m + 1) * (2 * m + 3);
-  if ((rc0 = upload_sg(c, m))) return rc0;
   ColArgs ca;
   ca.hist = reinterpret_cast<const uint32_t *>(c->hist.p);
   ca.T = T;
@@ -210,36 +243,22 @@ int image_path(rise_ctx *c, const uint8_t *img, int64_t T, int F, const rise_thr
   CK(launch_morph(ma, s));
   record(c, 5);
   // labelling
-  if ((rc0 = upload_level_tables(c, thr.level_db))) return rc0;
-  int rc;
-  if ((rc = ensure_hbox(c, std::max<int64_t>(cap, 1)))) return rc;
-  CclArgs la;
-  la.mask = ma.mask;
-  la.img = img;
-  la.T = T;
-  la.F = F;
-  la.energy = sm->energy;
-  la.row_base = reinterpret_cast<int64_t *>(c->row_base.p);
-  la.row_cnt = reinterpret_cast<uint32_t *>(c->row_cnt.p);
-  la.status = &sm->status;
-  la.boxes = c->hbox_dev;   // boxes land directly in mapped pinned host memory
-  la.box_cap = cap;
-  auto bind_runs = [&]() {
-    la.run_cap = c->run_cap;
-    la.run_parent = reinterpret_cast<int32_t *>(c->run_parent.p);
-    la.run_sroot = reinterpret_cast<uint8_t *>(c->run_sroot.p);
-    la.rec = reinterpret_cast<rise_box *>(c->rec.p);
-    la.merge = reinterpret_cast<int2 *>(c->merge.p);
-    la.run_out = reinterpret_cast<int64_t *>(c->run_out.p);
-    la.scan_tmp = c->scan_tmp.p;
-    la.scan_tmp_bytes = c->scan_tmp.bytes;
-  };
-  bind_runs();
+  const CclArgs la = ccl_args(c, img, T, F, cap);
   CK(launch_ccl_count(la, c->num_sms, s));
   CK(launch_ccl_label(la, c->num_sms, s));
   record(c, 6);
   CK(cudaMemcpyAsync(&c->small_h->status, &sm->status, sizeof(DeviceStatus), cudaMemcpyDeviceToHost, s));
   record(c, 7);
+  return RISE_OK;
+}
+
+// Waits for the enqueued work, relabels with larger run arrays when they
+// were too small, and copies the boxes out.
+int image_finish(rise_ctx *c, const uint8_t *img, int64_t T, int F, rise_box *out, int64_t cap,
+                 int64_t *n_boxes) {
+  Small *sm = c->small;
+  cudaStream_t s = c->stream;
+  int rc;
   CK(cudaStreamSynchronize(s));
   DeviceStatus h = c->small_h->status;
   if (h.err & ERR_RUN_CAPACITY) {
@@ -252,7 +271,7 @@ int image_path(rise_ctx *c, const uint8_t *img, int64_t T, int F, const rise_thr
     if ((rc = ensure(c, c->run_out, (need + 1) * sizeof(int64_t)))) return rc;
     if ((rc = ensure(c, c->scan_tmp, ccl_scan_tmp_bytes(std::max<int64_t>(need, T + 1))))) return rc;
     c->run_cap = need;
-    bind_runs();
+    const CclArgs la = ccl_args(c, img, T, F, cap);
     CK(cudaMemsetAsync(&sm->status.err, 0, sizeof(uint32_t), s));
     CK(launch_ccl_label(la, c->num_sms, s));
     record(c, 6);
@@ -299,37 +318,22 @@ int prepare_image_buffers(rise_ctx *c, int64_t T, int F) {
   return RISE_OK;
 }
 
-int detect_device(rise_ctx *c, const void *iq, int64_t n, int N, int hop,
-                  const rise_thresholds *thr_in, rise_box *out, int64_t cap, int64_t *n_boxes) {
-  rise_thresholds thr;
-  if (thr_in) thr = *thr_in;
-  else rise_thresholds_default(&thr);
-  if (!c || !iq || !n_boxes || (cap > 0 && !out) || cap < 0) return RISE_EINVAL;
-  if (!pow2(N) || N < RISE_MIN_FFT || N > RISE_MAX_FFT || hop < 1 || hop > N || n < N) return RISE_EINVAL;
-  if ((reinterpret_cast<uintptr_t>(iq) & 7) != 0) return RISE_EINVAL;
-  const int64_t T = (n - N) / hop + 1;
-  if (T > RISE_MAX_ROWS) return RISE_EINVAL;
-  int rc = check_thresholds(thr, N);
-  if (rc) return rc;
-  CK(cudaSetDevice(c->device));
-  const int F = N;
-  const size_t px = (size_t)T * F;
-  if ((rc = prepare_image_buffers(c, T, F))) return rc;
-  if ((rc = ensure(c, c->img, px))) return rc;
-  int path = c->range_path;
-  if (path == 0) {
-    // FFT once keeping float power when that image fits the budget, else twice
-    const size_t need = px * sizeof(float);
-    path = (!c->mem_budget || c->power.bytes >= need ||
-            c->allocated - c->power.bytes + need <= c->mem_budget) ? 2 : 1;
+uint64_t fnv_mix(uint64_t h, const void *p, size_t n) {
+  const unsigned char *b = static_cast<const unsigned char *>(p);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= b[i];
+    h *= 1099511628211ull;
   }
-  const bool want_power = c->keep_power || (path == 2 && thr.range_mode == RISE_RANGE_AUTO_MAX);
-  if (want_power && (rc = ensure(c, c->power, px * sizeof(float)))) return rc;
-  Tables *tb;
-  if ((rc = get_tables(c, N, &tb))) return rc;
-  if ((rc = upload_level_tables(c, thr.level_db))) return rc;
+  return h;
+}
+
+// Launches of one capture's spectrum part, then the image part.
+int enqueue_detect(rise_ctx *c, const void *iq, int64_t n, int N, int hop, int64_t T,
+                   const rise_thresholds &thr, int path, bool want_power, const Tables *tb,
+                   int64_t cap) {
   cudaStream_t s = c->stream;
   Small *sm = c->small;
+  const int F = N;
   CK(cudaMemsetAsync(&sm->status, 0, sizeof(DeviceStatus), s));
   record(c, 0);
   StftArgs a;
@@ -352,7 +356,6 @@ int detect_device(rise_ctx *c, const void *iq, int64_t n, int N, int hop,
     record(c, 1);
     CK(launch_levels(a.max_bits, hp, 1, sm->ratio, thr.level_db, sm->edges, sm->qconst, s));
     CK(launch_stft(a, c->keep_power ? STFT_QUANT_POWER : STFT_QUANT, c->num_sms, s));
-    c->last_anchor = hp;
   } else if (path == 2) {
     CK(launch_stft(a, STFT_POWER, c->num_sms, s));
     record(c, 1);
@@ -370,14 +373,99 @@ int detect_device(rise_ctx *c, const void *iq, int64_t n, int N, int hop,
     CK(launch_stft(a, c->keep_power ? STFT_QUANT_POWER : STFT_QUANT, c->num_sms, s));
   }
   record(c, 2);
+  return image_enqueue(c, a.img, T, F, thr, hist_ready, cap);
+}
+
+int detect_device(rise_ctx *c, const void *iq, int64_t n, int N, int hop,
+                  const rise_thresholds *thr_in, rise_box *out, int64_t cap, int64_t *n_boxes) {
+  rise_thresholds thr;
+  if (thr_in) thr = *thr_in;
+  else rise_thresholds_default(&thr);
+  if (!c || !iq || !n_boxes || (cap > 0 && !out) || cap < 0) return RISE_EINVAL;
+  if (!pow2(N) || N < RISE_MIN_FFT || N > RISE_MAX_FFT || hop < 1 || hop > N || n < N) return RISE_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(iq) & 7) != 0) return RISE_EINVAL;
+  const int64_t T = (n - N) / hop + 1;
+  if (T > RISE_MAX_ROWS) return RISE_EINVAL;
+  int rc = check_thresholds(thr, N);
+  if (rc) return rc;
+  CK(cudaSetDevice(c->device));
+  const int F = N;
+  const size_t px = (size_t)T * F;
+  // host-side set-up: buffers, tables (may allocate or synchronise)
+  if ((rc = prepare_image_buffers(c, T, F))) return rc;
+  if ((rc = ensure(c, c->img, px))) return rc;
+  int path = c->range_path;
+  if (path == 0) {
+    // FFT once keeping float power when that image fits the budget, else twice
+    const size_t need = px * sizeof(float);
+    path = (!c->mem_budget || c->power.bytes >= need ||
+            c->allocated - c->power.bytes + need <= c->mem_budget) ? 2 : 1;
+  }
+  const bool want_power = c->keep_power || (path == 2 && thr.range_mode == RISE_RANGE_AUTO_MAX);
+  if (want_power && (rc = ensure(c, c->power, px * sizeof(float)))) return rc;
+  Tables *tb;
+  if ((rc = get_tables(c, N, &tb))) return rc;
+  if ((rc = image_prepare(c, thr, cap))) return rc;
+  // the launches: replayed from a graph when the same call comes again
+  bool launched = false;
+  if (c->graphs) {
+    uint64_t key = 1469598103934665603ull;
+    const int64_t kv[12] = {(int64_t)reinterpret_cast<uintptr_t>(iq), n, N, hop, cap, path,
+                            c->keep_power, c->keep_masks, c->timing, (int64_t)c->gen,
+                            thr.range_mode, (int64_t)thr.sg_half_window * 2 + thr.morph_order};
+    const double dv[4] = {thr.hi_db, thr.level_db, thr.psd_offset_db, thr.power_offset_db};
+    key = fnv_mix(key, kv, sizeof(kv));
+    key = fnv_mix(key, dv, sizeof(dv));
+    BatchState::Graph *gr = nullptr;
+    for (auto &g : c->single_graphs)
+      if (g.key == key) gr = &g;
+    if (!gr && c->last_key == key) {
+      // the second call with these arguments: capture it
+      cudaGraph_t graph = nullptr;
+      const long long l0 = launches_so_far();
+      if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        c->capturing = true;
+        const int erc = enqueue_detect(c, iq, n, N, hop, T, thr, path, want_power, tb, cap);
+        c->capturing = false;
+        const cudaError_t ee = cudaStreamEndCapture(c->stream, &graph);
+        cudaGraphExec_t exec = nullptr;
+        if (erc == RISE_OK && ee == cudaSuccess && graph &&
+            cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+          if (c->single_graphs.size() >= 8) {
+            cudaGraphExecDestroy(c->single_graphs.front().exec);
+            c->single_graphs.erase(c->single_graphs.begin());
+          }
+          BatchState::Graph g;
+          g.key = key;
+          g.exec = exec;
+          g.launches = (int)(launches_so_far() - l0);
+          c->single_graphs.push_back(g);
+          gr = &c->single_graphs.back();
+        }
+        if (graph) cudaGraphDestroy(graph);
+      }
+      count_launches(-(int)(launches_so_far() - l0));   // counted when the graph runs
+      cudaGetLastError();   // a failed capture falls back to direct launches
+    }
+    c->last_key = key;
+    if (gr) {
+      CK(cudaGraphLaunch(gr->exec, c->stream));
+      count_launches(gr->launches);
+      launched = true;
+    }
+  }
+  c->last_replayed = launched;
+  if (!launched && (rc = enqueue_detect(c, iq, n, N, hop, T, thr, path, want_power, tb, cap))) return rc;
   c->last_T = T;
   c->last_F = F;
-  c->last_img = a.img;
+  c->last_img = reinterpret_cast<uint8_t *>(c->img.p);
   c->last_has_power = want_power;
   c->last_has_masks = c->keep_masks != 0;
   c->last_valid = true;
-  rc = image_path(c, a.img, T, F, thr, hist_ready, out, cap, n_boxes);
-  if (thr.range_mode != RISE_RANGE_FIXED) {
+  rc = image_finish(c, c->last_img, T, F, out, cap, n_boxes);
+  if (thr.range_mode == RISE_RANGE_FIXED) {
+    c->last_anchor = std::pow(10.0, thr.hi_db / 10.0);
+  } else {
     uint32_t bits = c->small_h->status.max_bits;
     float mf;
     std::memcpy(&mf, &bits, 4);
@@ -521,7 +609,9 @@ int rise_detect_image(rise_ctx *c, const uint8_t *img_dev, int64_t T, int F,
   c->last_has_power = false;
   c->last_has_masks = c->keep_masks != 0;
   c->last_valid = true;
-  return image_path(c, img_dev, T, F, thr, false, out, cap, n_boxes);
+  if ((rc = image_prepare(c, thr, cap))) return rc;
+  if ((rc = image_enqueue(c, img_dev, T, F, thr, false, cap))) return rc;
+  return image_finish(c, img_dev, T, F, out, cap, n_boxes);
 }
 
 int rise_set_option(rise_ctx *c, int option, int64_t value) {
@@ -530,7 +620,7 @@ int rise_set_option(rise_ctx *c, int option, int64_t value) {
     case RISE_OPT_KEEP_POWER: c->keep_power = value != 0; return RISE_OK;
     case RISE_OPT_KEEP_MASKS: c->keep_masks = value != 0; return RISE_OK;
     case RISE_OPT_TIMING: c->timing = value != 0; return RISE_OK;
-    case RISE_OPT_BATCH_GRAPH: c->batch_graph = value != 0; return RISE_OK;
+    case RISE_OPT_GRAPH: c->graphs = value != 0; return RISE_OK;
     case RISE_OPT_AUTOTUNE: c->autotune = value != 0; return RISE_OK;
     case RISE_OPT_RANGE_PATH:
       if (value < 0 || value > 2) return RISE_EINVAL;
@@ -552,6 +642,13 @@ int rise_debug_export(rise_ctx *c, int what, void *dst, size_t bytes) {
     if (bytes < sizeof(int64_t)) return RISE_EINVAL;
     int64_t v = (int64_t)launches_so_far();
     std::memcpy(dst, &v, sizeof v);
+    return RISE_OK;
+  }
+  if (what == RISE_DBG_GRAPHS) {
+    if (bytes < 4 * sizeof(int64_t)) return RISE_EINVAL;
+    const int64_t v[4] = {c->last_replayed ? 1 : 0, (int64_t)c->single_graphs.size(),
+                          (int64_t)c->batch.graphs.size(), 0};
+    std::memcpy(dst, v, sizeof v);
     return RISE_OK;
   }
   if (what == RISE_DBG_BATCH_INFO) {

@@ -26,11 +26,12 @@ NOALLOC_MAX_COLS = 4096
 RANGE_AUTO_MAX, RANGE_FIXED = 0, 1
 DBG_POWER_F32, DBG_IMAGE_U8, DBG_HIST, DBG_COLSTATS, DBG_FLOOR = 1, 2, 3, 4, 5
 DBG_MASK0, DBG_MASK1, DBG_MASK2, DBG_MASK3, DBG_MAXPOW, DBG_LEVEL_EDGES = 6, 7, 8, 9, 10, 11
-DBG_LAUNCHES, DBG_BATCH_INFO = 12, 13
+DBG_LAUNCHES, DBG_BATCH_INFO, DBG_GRAPHS = 12, 13, 14
 STAGES = ("spectrum_pass1", "spectrum_pass2", "histogram", "column_stats", "morphology",
           "labelling", "readback", "total")
 OPT_KEEP_POWER, OPT_KEEP_MASKS, OPT_TIMING, OPT_RANGE_PATH = 1, 2, 3, 4
-OPT_BATCH_GRAPH, OPT_AUTOTUNE = 5, 6
+OPT_GRAPH, OPT_AUTOTUNE = 5, 6
+OPT_BATCH_GRAPH = OPT_GRAPH
 BATCH_MAX_ROWS = 524280
 BOX_COLS = ("t0", "t1", "f0", "f1", "anchor", "area", "sum_q", "energy_fx")
 
@@ -338,6 +339,13 @@ class Detector:
                 raise RiseError(rc, "rise_detect_batch")
             self.last_status = rc
             return boxes_from_raw(raw, min(int(offs[k]), cap)), offs
+
+    def graph_info(self) -> np.ndarray:
+        v = np.zeros(4, np.int64)
+        rc = lib().rise_debug_export(self._h, DBG_GRAPHS, v.ctypes.data, v.nbytes)
+        if rc != RISE_OK:
+            raise RiseError(rc, "rise_debug_export")
+        return v
 
     def batch_info(self) -> np.ndarray:
         v = np.zeros(16, np.int64)

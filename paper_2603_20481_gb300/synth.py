@@ -31,17 +31,17 @@ import numpy as np
 try:  # scipy's pocketfft takes complex64 natively and threads
     import scipy.fft as _fft
 
-    def _fwd(x):
-        return _fft.fft(x, workers=-1)
-
     def _inv(x):
         return _fft.ifft(x, workers=-1)
-except Exception:  # pragma: no cover - numpy fallback for the generator only
-    def _fwd(x):
-        return np.fft.fft(x).astype(np.complex64)
 
+    def _fast_len(n):
+        return _fft.next_fast_len(n)
+except Exception:  # pragma: no cover - numpy fallback for the generator only
     def _inv(x):
         return np.fft.ifft(x).astype(np.complex64)
+
+    def _fast_len(n):
+        return 1 << max(0, (n - 1).bit_length())
 
 
 @dataclass
@@ -82,13 +82,19 @@ def _loguniform(rng, lo, hi, size=None):
 
 def _band_noise(rng, length: int, f_lo: float, f_hi: float, fs: float,
                 power: float) -> np.ndarray:
-    """White complex noise confined to [f_lo, f_hi] Hz, scaled to `power`."""
-    w = (rng.standard_normal(length, dtype=np.float32)
-         + 1j * rng.standard_normal(length, dtype=np.float32)).astype(np.complex64)
-    W = _fwd(w)
-    freqs = np.fft.fftfreq(length, d=1.0 / fs)
-    W[(freqs < f_lo) | (freqs > f_hi)] = 0
-    b = _inv(W).astype(np.complex64)
+    """Complex Gaussian noise with a flat spectrum on [f_lo, f_hi] Hz, scaled to
+    `power`: independent Gaussian DFT coefficients on the in-band bins of a
+    transform of fast length L >= length, inverse transform, first `length`
+    samples (the DFT of white Gaussian noise is white Gaussian, so this is
+    band-masked white noise drawn directly in the frequency domain)."""
+    L = _fast_len(max(1, length))
+    k0 = math.ceil(f_lo * L / fs)
+    k1 = max(k0, math.floor(f_hi * L / fs))
+    m = k1 - k0 + 1
+    W = np.zeros(L, np.complex64)
+    coef = rng.standard_normal((m, 2), dtype=np.float32).view(np.complex64).reshape(m)
+    W[np.arange(k0, k1 + 1) % L] = coef
+    b = _inv(W)[:length].astype(np.complex64)
     p = float(np.mean(np.abs(b) ** 2)) if length else 0.0
     if p > 0:
         b *= np.float32(math.sqrt(power / p))

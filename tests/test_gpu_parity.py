@@ -322,3 +322,86 @@ def test_wideband_full_size_sampled(det):
         _check_power(Pg_rows[t:t + 1], oracle.stft_power(cap.iq, N, hop, int(t), 1))
     # from the image on, bit-exact
     assert np.array_equal(boxes_g, oracle.detect_image(qg))
+
+
+@pytest.mark.slow
+def test_stress_full_size_sampled(det):
+    """2^28 samples, FFT 8192, hop 2048 (T = 131069, 1.07 G pixels; 1024
+    emitters, half of them fragmented, 16 running the whole capture): the
+    anchor and sampled frames against the oracle's spectrogram and levels, and
+    boxes bit-exact against the oracle on the GPU's own image."""
+    rise = _rise()
+    cap = synth.stress_capture(105)
+    N, hop = 8192, 2048
+    T = oracle.num_frames(cap.iq.shape[0], N, hop)
+    det.set_option(rise.OPT_KEEP_POWER, 1)
+    det.set_option(rise.OPT_KEEP_MASKS, 0)
+    x = torch.from_numpy(cap.iq).cuda()
+    boxes_g = det.detect(x, N, hop)
+    del x
+    qg = det.debug(rise.DBG_IMAGE_U8, T, N)
+    Pg = det.debug(rise.DBG_POWER_F32, T, N)
+    Mg = float(det.debug(rise.DBG_MAXPOW, T, N)[0])
+    det.set_option(rise.OPT_KEEP_POWER, 0)
+    # the anchor is the largest float power, and the oracle agrees on its value
+    arg = int(np.argmax(Pg))
+    ta, fa = divmod(arg, N)
+    assert Pg.flat[arg] == Mg
+    Pa = oracle.stft_power(cap.iq, N, hop, ta, 1)[0]
+    assert abs(Pa[fa] - Mg) <= 1e-4 * Pa[fa]
+    hi = oracle.hi_db_of(Pa[fa])
+    # sampled frames (the anchor's frame, both ends, random ones): power and levels
+    rng = np.random.default_rng(5)
+    rows = np.unique(np.concatenate([[0, ta, T - 1], rng.integers(0, T, 200)]))
+    px = diff = 0
+    for t in rows:
+        Pr = oracle.stft_power(cap.iq, N, hop, int(t), 1)
+        _check_power(Pg[t:t + 1], Pr)
+        # the GPU's levels are the quantiser on its own float power and anchor
+        assert np.array_equal(qg[t:t + 1], oracle.quantize(Pg[t:t + 1].astype(np.float64),
+                                                           oracle.hi_db_of(Mg)))
+        d = qg[t:t + 1].astype(np.int16) - oracle.quantize(Pr, hi).astype(np.int16)
+        assert np.abs(d).max(initial=0) <= 1
+        px += d.size
+        diff += int(np.count_nonzero(d))
+    assert diff <= math.ceil(1e-5 * px) + 6, f"{diff} of {px} sampled pixels differ"
+    del Pg
+    # from the image on, bit-exact (the oracle labels the whole 1.07 G-pixel image)
+    boxes_r = oracle.detect_image(qg)
+    assert len(boxes_g) > 1000
+    assert np.array_equal(boxes_g, boxes_r)
+
+
+def test_repeated_calls_replay_a_graph(det):
+    """The third identical call replays the captured launches; its boxes and
+    intermediates equal a context with graphs off, and changed arguments
+    (thresholds, another buffer) are not served from the old graph."""
+    rise = _rise()
+    cap = synth.single_capture(104)
+    N, hop = 1024, 512
+    x = torch.from_numpy(cap.iq).cuda()
+    det.set_option(rise.OPT_KEEP_POWER, 0)
+    det.set_option(rise.OPT_KEEP_MASKS, 0)
+    with rise.Detector(0) as d0:
+        d0.set_option(rise.OPT_GRAPH, 0)
+        want = d0.detect(x, N, hop)
+        thr = rise.default_thresholds(power_offset_db=6.0)
+        want6 = d0.detect(x, N, hop, thr)
+        assert d0.graph_info()[0] == 0
+    got = [det.detect(x, N, hop) for _ in range(3)]
+    assert det.graph_info()[0] == 1
+    for g in got:
+        np.testing.assert_array_equal(g, want)
+    g6 = det.detect(x, N, hop, thr)
+    assert det.graph_info()[0] == 0
+    np.testing.assert_array_equal(g6, want6)
+    # same shape, new contents in the same buffer: the replay reads them
+    cap2 = synth.single_capture(105)
+    x.copy_(torch.from_numpy(cap2.iq))
+    with rise.Detector(0) as d0:
+        d0.set_option(rise.OPT_GRAPH, 0)
+        want2 = d0.detect(x, N, hop)
+    for _ in range(3):
+        got2 = det.detect(x, N, hop)
+    assert det.graph_info()[0] == 1
+    np.testing.assert_array_equal(got2, want2)
