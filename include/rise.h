@@ -295,6 +295,8 @@ void rise_server_destroy(rise_server *s);
 #define RISE_DBG_GRAPHS 14   /* int64 [4]: [0] the last rise_detect replayed a     *
                               * graph, [1] single-capture graphs kept, [2] batch  *
                               * graphs kept, [3] 0                                */
+#define RISE_DBG_CCL 15      /* int64 [4] of the last call's labelling: runs,      *
+                              * deferred unions, components, run capacity         */
 #define RISE_DBG_BATCH_INFO 13 /* int64 [16] of the last batch: [0] STFT groups G,   *
                                 * [1] replayed from a graph (0/1), [2..2+G) frames  *
                                 * per STFT item in steps, [2+G] morphology warps    *

@@ -56,7 +56,7 @@ struct Plan {
   int morph_wps = 16;
   // blob layout
   size_t o_stft, o_items, o_hseg, o_hitem, o_col, o_mseg, o_mitem, o_wbase, o_rseg, o_row0, bytes;
-  int n_items = 0, n_hitems = 0, total_warps = 0;
+  int n_items = 0, n_hitems = 0, total_warps = 0, hist_bands = 8;
   uint64_t shape_key = 0;
 };
 
@@ -119,12 +119,15 @@ void size_tables(const rise_ctx *c, const rise_capture *caps, Plan &p) {
   }
   p.n_hitems = 0;
   p.total_warps = 0;
+  int64_t max_T = 1;
+  for (int k = 0; k < p.ncap; ++k) max_T = std::max(max_T, p.T[k]);
   for (int k = 0; k < p.ncap; ++k) {
     p.n_hitems += caps[k].fft_size / 64;
     int nx, rows, w;
     morph_plan(p.T[k], caps[k].fft_size, c->num_sms, p.morph_wps, 32, &nx, &rows, &w);
     p.total_warps += w;
   }
+  p.hist_bands = cluster_hist_bands(!p.fixed, p.n_hitems, max_T);
   size_t o = 0;
   auto take = [&](size_t bytes) {
     const size_t at = o;
@@ -281,7 +284,7 @@ int fill_tables(rise_ctx *c, const rise_capture *caps, const Plan &p, const rise
     ha.src = p.fixed ? static_cast<const void *>(a.img) : static_cast<const void *>(a.power);
     ha.T = T;
     ha.F = F;
-    ha.rows_per_band = cluster_hist_rows_per_band(T);
+    ha.rows_per_band = (T + p.hist_bands - 1) / p.hist_bands;
     ha.edges = cs[k].edges;
     ha.qconst = cs[k].qconst;
     ha.img = a.img;
@@ -382,7 +385,7 @@ int enqueue(rise_ctx *c, const Plan &p, const rise_thresholds &thr, int64_t cap,
   }
   record(c, 1);
   if (!p.fixed) CK(launch_levels_batch(cs, p.ncap, 0.0, 0, sm->ratio, thr.level_db, s));
-  CK(launch_cluster_hist_batch(!p.fixed, hseg, hitem, p.n_hitems, s));
+  CK(launch_cluster_hist_batch(!p.fixed, hseg, hitem, p.n_hitems, p.hist_bands, s));
   record(c, 2);
   record(c, 3);
   CK(launch_floor_batch(col, p.ncap, p.max_F, s));

@@ -219,9 +219,11 @@ struct HistArgs {             // one image for the cluster histogram
 struct HistItem {             // column group cg of capture seg
   int32_t seg, cg;
 };
-int64_t cluster_hist_rows_per_band(int64_t T);   // single cluster of bands
+// Bands per cluster for `groups` column groups (chosen for whole waves, and
+// at least enough that no band exceeds the per-band row limit for max_T).
+int cluster_hist_bands(bool from_power, int groups, int64_t max_T);
 cudaError_t launch_cluster_hist_batch(bool from_power, const HistArgs *segs, const HistItem *items,
-                                      int n_items, cudaStream_t s);
+                                      int n_items, int bands, cudaStream_t s);
 cudaError_t launch_floor_batch(const ColArgs *segs, int ncap, int max_F, cudaStream_t s);
 // S and Otsu threshold of every column of a given [F][256] histogram.
 cudaError_t launch_column_otsu(const uint32_t *hist, int64_t T, int F, rise_colstat *cols,

@@ -5,6 +5,10 @@
 // and one horizontal 1D opening (Eq. 5) on bit-packed tiles.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+#include <map>
+#include <mutex>
+
 #include "common.cuh"
 
 namespace cg = cooperative_groups;
@@ -12,7 +16,7 @@ namespace cg = cooperative_groups;
 namespace rise {
 namespace {
 
-constexpr int HIST_MAX_ROWS = 65535;   // rows per band: 16-bit counters never wrap
+constexpr int HIST_MAX_ROWS = 65535;   // rows per band: 32-bit offsets inside a band suffice
 
 // Level of a stored float |X|^2 (same rule as the STFT epilogue).
 constexpr float kGuardQ = 3.0e-4f;   // the fast level coordinate is off by < 1e-4
@@ -122,40 +126,46 @@ __global__ void otsu_kernel(ColArgs a) {
 // ---------------------------------------------------------------------------
 // Column histogram, cluster version.  A block owns 64 columns of one row
 // band; its 8 warps take interleaved rows.  Lane l reads 2 consecutive
-// columns (2l, 2l+1) per row and counts column 2l+j in shared slot l+32j, so
-// a warp's 32 lanes always hit 32 different banks; counters are 16-bit
-// halves of a word (levels v and v+128) and are bumped with shared-memory
-// atomics whose results are unused, so the adds of many rows are in flight
-// at once.  The 8 blocks of a thread-block cluster cover the same 64 columns
-// over 8 row bands; after counting, each block sums whole columns (8 of them)
-// over the cluster through distributed shared memory, stores their
-// histograms (plain stores: no zeroing, no global atomics) and runs Otsu on
-// them, one warp per column.
+// columns (2l, 2l+1) per row and counts column 2l+j in shared slot l+32j:
+// 32-bit counters, level-major, so a warp's 32 lanes hit 32 banks, bumped
+// with shared-memory reductions whose results are unused.  The main loop
+// takes whole groups of CH_UNROLL rows per warp with no bounds checks and
+// issues the next group's loads before counting the current one; a tail loop
+// takes the remaining rows.  Offsets inside a band are 32-bit (a band holds
+// at most 65535 rows of at most 8192 columns).  The 8 blocks of a
+// thread-block cluster cover the same 64 columns over 8 row bands; after
+// counting, each block sums whole columns (8 of them) over the cluster
+// through distributed shared memory, stores their histograms (plain stores:
+// no zeroing, no global atomics) and runs Otsu on them, one warp per column.
 // FROM_POWER: the input is float |X|^2, quantised here (same level rule as
 // the STFT epilogue) and the 8-bit image is written alongside.
 // ---------------------------------------------------------------------------
 constexpr int CH_WARPS = 8, CH_COLS = 64, CH_BANDS = 8, CH_UNROLL = 8;
 constexpr int CH_PX = CH_COLS / 32;                   // columns per lane
-constexpr int CH_WORDS = 128 * CH_COLS;              // packed counter words per block
+constexpr int CH_WORDS = 256 * CH_COLS;              // 32-bit counters per block
 constexpr int CH_NS = CH_COLS / CH_BANDS;            // columns each block reduces
 
-__device__ __forceinline__ void ch_count(uint32_t *sh, int lane, uint32_t q0, uint32_t q1) {
-  atomicAdd(&sh[(q0 & 127u) * CH_COLS + lane], (q0 & 128u) ? 65536u : 1u);
-  atomicAdd(&sh[(q1 & 127u) * CH_COLS + lane + 32], (q1 & 128u) ? 65536u : 1u);
+__device__ __forceinline__ uint32_t shared_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// one count into the shared counter at byte address `addr`
+__device__ __forceinline__ void ch_red(uint32_t addr) {
+  asm volatile("red.shared::cta.add.u32 [%0], 1;" ::"r"(addr));
 }
 
-// Column group cg, row band `band` of one image (the 8 bands of a column
-// group form one cluster).
+// Column group cgx, row band `band` of one image (the bands of a column group
+// form one cluster; the launch picks how many).
 template <bool FROM_POWER>
 __device__ __forceinline__ void cluster_hist_body(const HistArgs &a, int cgx, int band) {
-  extern __shared__ uint32_t sh[];   // [128 packed levels][64 column slots]
+  extern __shared__ uint4 sh4[];     // [256 levels][64 column slots] u32
+  uint32_t *sh = reinterpret_cast<uint32_t *>(sh4);
   __shared__ float edges[257];
   __shared__ __align__(16) uint32_t hs[CH_NS][256];   // reduced columns
   cg::cluster_group cluster = cg::this_cluster();
   const int64_t T = a.T;
   const int F = a.F;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int i = tid; i < CH_WORDS; i += blockDim.x) sh[i] = 0;
+  for (int i = tid; i < CH_WORDS / 4; i += blockDim.x) sh4[i] = make_uint4(0u, 0u, 0u, 0u);
   float inv_anchor = 0.f, c1 = 0.f;
   if constexpr (FROM_POWER) {
     for (int i = tid; i < 257; i += blockDim.x) edges[i] = a.edges[i];
@@ -166,107 +176,124 @@ __device__ __forceinline__ void cluster_hist_body(const HistArgs &a, int cgx, in
   const int c0 = cgx * CH_COLS + CH_PX * lane;
   const int64_t r0 = (int64_t)band * a.rows_per_band;
   const int64_t r1 = min(T, r0 + a.rows_per_band);
-  const int64_t stride = (int64_t)CH_WARPS * F;          // elements between a warp's rows
-  int64_t r = r0 + warp;
+  const int K = (r1 - r0 > warp) ? (int)((r1 - r0 - warp + CH_WARPS - 1) / CH_WARPS) : 0;
+  const int KF = K / CH_UNROLL * CH_UNROLL;             // rows in whole groups
+  const uint32_t rstep = (uint32_t)CH_WARPS * (uint32_t)F;   // elements between a warp's rows
+  const uint32_t cbase = shared_addr(sh) + 4u * lane;        // slot lane (+128 B: slot lane+32)
+  uint32_t off = (uint32_t)warp * (uint32_t)F;               // this warp's row, from the band start
   if constexpr (FROM_POWER) {
-    const float *p = reinterpret_cast<const float *>(a.src) + r * F + c0;
-    uint8_t *o = a.img + r * F + c0;
-    for (; r < r1; r += CH_UNROLL * CH_WARPS, p += CH_UNROLL * stride, o += CH_UNROLL * stride) {
-      float pv[2 * CH_UNROLL];
+    const float *pb = reinterpret_cast<const float *>(a.src) + r0 * F + c0;
+    uint8_t *ob = a.img + r0 * F + c0;
+    // levels of one row pair of values, the image bytes and the counts
+    auto one_row = [&](float2 x, uint32_t o) {
+      float pv[2] = {x.x, x.y};
+      uint32_t q[2];
+      bool near = false;
 #pragma unroll
-      for (int u = 0; u < CH_UNROLL; ++u) {
-        const float2 x = (r + (int64_t)u * CH_WARPS < r1)
-                             ? __ldg(reinterpret_cast<const float2 *>(p + u * stride))
-                             : make_float2(0.f, 0.f);
-        pv[2 * u] = x.x;
-        pv[2 * u + 1] = x.y;
-      }
-      // fast levels; the exact edge comparison only for values near a level edge
-      uint32_t q[2 * CH_UNROLL];
-      uint32_t near = 0;
-#pragma unroll
-      for (int k = 0; k < 2 * CH_UNROLL; ++k) {
-        const float v = fmaf(__log2f(pv[k] * inv_anchor), c1, 255.5f);
-        q[k] = __float2uint_rd(fminf(v, 255.0f));
-        near |= (fabsf(v - rintf(v)) < kGuardQ ? 1u : 0u) << k;
+      for (int j = 0; j < 2; ++j) {
+        const float v = fmaf(__log2f(pv[j] * inv_anchor), c1, 255.5f);
+        q[j] = min(__float2uint_rd(v), 255u);   // -inf, NaN: 0
+        near |= fabsf(v - rintf(v)) < kGuardQ;
       }
       if (near) {
 #pragma unroll
-        for (int k = 0; k < 2 * CH_UNROLL; ++k)
-          if ((near >> k) & 1u) q[k] = level_of_q(pv[k], inv_anchor, c1, edges);
+        for (int j = 0; j < 2; ++j) q[j] = level_of_q(pv[j], inv_anchor, c1, edges);
       }
+      *reinterpret_cast<uint16_t *>(ob + o) = (uint16_t)(q[0] | (q[1] << 8));
+      ch_red(cbase + (q[0] << 8));
+      ch_red(cbase + 128u + (q[1] << 8));
+    };
+    float2 A[CH_UNROLL], B[CH_UNROLL];
+    auto load = [&](float2 (&X)[CH_UNROLL], uint32_t o) {
 #pragma unroll
-      for (int u = 0; u < CH_UNROLL; ++u) {
-        if (r + (int64_t)u * CH_WARPS < r1) {
-          *reinterpret_cast<uint16_t *>(o + u * stride) = (uint16_t)(q[2 * u] | (q[2 * u + 1] << 8));
-          ch_count(sh, lane, q[2 * u], q[2 * u + 1]);
+      for (int u = 0; u < CH_UNROLL; ++u) X[u] = __ldg(reinterpret_cast<const float2 *>(pb + o + u * rstep));
+    };
+    auto count = [&](const float2 (&X)[CH_UNROLL], uint32_t o) {
+#pragma unroll
+      for (int u = 0; u < CH_UNROLL; ++u) one_row(X[u], o + u * rstep);
+    };
+    const uint32_t gstep = CH_UNROLL * rstep;
+    int k = 0;
+    if (KF > 0) load(A, off);
+    while (k < KF) {
+      if (k + CH_UNROLL < KF) load(B, off + gstep);
+      count(A, off);
+      k += CH_UNROLL;
+      off += gstep;
+      if (k >= KF) break;
+      if (k + CH_UNROLL < KF) load(A, off + gstep);
+      count(B, off);
+      k += CH_UNROLL;
+      off += gstep;
+    }
+    for (; k < K; ++k, off += rstep) one_row(__ldg(reinterpret_cast<const float2 *>(pb + off)), off);
+  } else {
+    const uint8_t *pb = reinterpret_cast<const uint8_t *>(a.src) + r0 * F + c0;
+    auto one_row = [&](uint32_t w) {
+      ch_red(cbase + ((w & 0xffu) << 8));
+      ch_red(cbase + 128u + ((w >> 8) << 8));
+    };
+    constexpr int U2 = 2 * CH_UNROLL;
+    const int KF2 = K / U2 * U2;
+    int k = 0;
+    for (; k < KF2; k += U2, off += U2 * rstep) {
+      uint32_t w[U2];
+#pragma unroll
+      for (int u = 0; u < U2; ++u) w[u] = __ldg(reinterpret_cast<const uint16_t *>(pb + off + u * rstep));
+#pragma unroll
+      for (int u = 0; u < U2; ++u) one_row(w[u]);
+    }
+    for (; k < K; ++k, off += rstep) one_row(__ldg(reinterpret_cast<const uint16_t *>(pb + off)));
+  }
+  cluster.sync();
+  // this block's share of the 64 column slots, summed over the cluster's
+  // bands in chunks of 8 columns, then one warp per column: store its
+  // histogram, then PSD and Otsu threshold
+  const int rank = (int)cluster.block_rank(), nb = (int)cluster.num_blocks();
+  const int s_lo = rank * CH_COLS / nb, s_hi = (rank + 1) * CH_COLS / nb;
+  for (int cs = s_lo; cs < s_hi; cs += CH_NS) {
+    const int nc = min(CH_NS, s_hi - cs);
+    for (int k = tid; k < nc * 256; k += blockDim.x) {
+      const int sl = k % nc, v = k / nc;
+      const int i = v * CH_COLS + cs + sl;
+      uint32_t n = 0;
+      for (int b = 0; b < nb; ++b) n += cluster.map_shared_rank(sh, b)[i];
+      hs[sl][v] = n;
+    }
+    __syncthreads();
+    if (warp < nc) {
+      const int sl = warp;
+      const int slot = cs + sl;
+      const int col = cgx * CH_COLS + CH_PX * (slot & 31) + (slot >> 5);
+      uint32_t *dst = a.hist + (size_t)col * 256;
+      if (a.accumulate) {
+        for (int v = lane; v < 256; v += 32)
+          if (hs[sl][v]) atomicAdd(&dst[v], hs[sl][v]);
+      } else {
+        for (int v = lane; v < 256; v += 32) dst[v] = hs[sl][v];
+        uint64_t S;
+        int th;
+        otsu_warp(&hs[sl][8 * lane], lane, &S, &th);
+        if (lane == 0) {
+          a.cols[col].S = S;
+          a.cols[col].otsu = th;
         }
       }
     }
-  } else {
-    const uint8_t *p = reinterpret_cast<const uint8_t *>(a.src) + r * F + c0;
-    for (; r + (2 * CH_UNROLL - 1) * CH_WARPS < r1; r += 2 * CH_UNROLL * CH_WARPS) {
-      uint32_t w[2 * CH_UNROLL];
-#pragma unroll
-      for (int u = 0; u < 2 * CH_UNROLL; ++u) w[u] = __ldg(reinterpret_cast<const uint16_t *>(p + u * stride));
-#pragma unroll
-      for (int u = 0; u < 2 * CH_UNROLL; ++u) ch_count(sh, lane, w[u] & 0xffu, w[u] >> 8);
-      p += 2 * CH_UNROLL * stride;
-    }
-    for (; r < r1; r += CH_WARPS, p += stride) {
-      const uint32_t w = __ldg(reinterpret_cast<const uint16_t *>(p));
-      ch_count(sh, lane, w & 0xffu, w >> 8);
-    }
-  }
-  cluster.sync();
-  // this block's column slots: sum every level over the cluster's 8 bands
-  const unsigned rank = cluster.block_rank();
-  for (int k = tid; k < CH_NS * 128; k += blockDim.x) {
-    const int sl = k % CH_NS, vm = k / CH_NS;
-    const int i = vm * CH_COLS + rank * CH_NS + sl;
-    uint32_t l = 0, h = 0;
-#pragma unroll
-    for (int b = 0; b < CH_BANDS; ++b) {
-      const uint32_t w = cluster.map_shared_rank(sh, b)[i];
-      l += w & 0xffffu;
-      h += w >> 16;
-    }
-    hs[sl][vm] = l;
-    hs[sl][vm + 128] = h;
+    __syncthreads();   // hs is refilled by the next chunk
   }
   cluster.sync();   // remote reads finished before any block leaves
-  // one warp per column: store its histogram, then PSD and Otsu threshold
-  if (warp < CH_NS) {
-    const int sl = warp;
-    const int slot = rank * CH_NS + sl;
-    const int col = cgx * CH_COLS + CH_PX * (slot & 31) + (slot >> 5);
-    uint32_t *dst = a.hist + (size_t)col * 256;
-    if (a.accumulate) {
-      for (int v = lane; v < 256; v += 32)
-        if (hs[sl][v]) atomicAdd(&dst[v], hs[sl][v]);
-    } else {
-      for (int v = lane; v < 256; v += 32) dst[v] = hs[sl][v];
-      uint64_t S;
-      int th;
-      otsu_warp(&hs[sl][8 * lane], lane, &S, &th);
-      if (lane == 0) {
-        a.cols[col].S = S;
-        a.cols[col].otsu = th;
-      }
-    }
-  }
 }
 
 template <bool FROM_POWER>
-__global__ void __cluster_dims__(1, CH_BANDS, 1) __launch_bounds__(32 * CH_WARPS, 4)
-cluster_hist_kernel(HistArgs a) {
+__global__ void __launch_bounds__(32 * CH_WARPS, 3) cluster_hist_kernel(HistArgs a) {
   cluster_hist_body<FROM_POWER>(a, blockIdx.x, blockIdx.y);
 }
 
 // Batch: blockIdx.x indexes (capture, column group) items; the arguments of
 // the item's capture are copied to shared memory first.
 template <bool FROM_POWER>
-__global__ void __cluster_dims__(1, CH_BANDS, 1) __launch_bounds__(32 * CH_WARPS, 4)
+__global__ void __launch_bounds__(32 * CH_WARPS, 3)
 cluster_hist_batch_kernel(const HistArgs *segs, const HistItem *items) {
   __shared__ HistArgs sa;
   const HistItem it = items[blockIdx.x];
@@ -553,6 +580,76 @@ morph_batch_kernel(const MorphArgs *segs, const MorphItem *mi, const int *warp_b
   const MorphItem it = mi[lo];
   morph_body<ORDER>(sa[wib], it.nx, it.rows, gwarp - __ldg(&warp_base[lo]));
 }
+// Bands per cluster.  Grid: (column groups) x (bands); the clusters that fit
+// at once come from the occupancy API, and the band count minimises
+// waves / bands (time ~ waves x rows per band), so that the last wave is not
+// mostly idle.  At least ceil(T / HIST_MAX_ROWS) bands for a single cluster.
+template <bool FP>
+int bands_for(int groups, int64_t max_T) {
+  static std::mutex mu;
+  static std::map<int, int> cache;
+  const int need = (int)std::min<int64_t>(CH_BANDS, (max_T + HIST_MAX_ROWS - 1) / HIST_MAX_ROWS);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(groups);
+    if (it != cache.end()) return std::max(it->second, need);
+  }
+  const size_t sm = (size_t)CH_WORDS * sizeof(uint32_t);
+  cudaFuncSetAttribute(cluster_hist_kernel<FP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  int best = CH_BANDS;
+  double best_cost = 1e30;
+  for (int B = 1; B <= CH_BANDS; ++B) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)groups, (unsigned)B);
+    cfg.blockDim = dim3(32 * CH_WARPS);
+    cfg.dynamicSmemBytes = sm;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1;
+    at[0].val.clusterDim.y = (unsigned)B;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, cluster_hist_kernel<FP>, &cfg) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    const double cost = (double)((groups + n - 1) / n) / B;
+    if (cost <= best_cost) {
+      best_cost = cost;
+      best = B;
+    }
+  }
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    cache[groups] = best;
+  }
+  return std::max(best, need);
+}
+
+template <typename K, typename... Args>
+cudaError_t launch_clustered(K kernel, dim3 grid, int B, cudaStream_t s, Args... args) {
+  const size_t sm = (size_t)CH_WORDS * sizeof(uint32_t);
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(32 * CH_WARPS);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 1;
+  at[0].val.clusterDim.y = (unsigned)B;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, kernel, args...);
+  count_launches(1);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 }  // namespace
 
 // Cluster histogram (optionally quantising float power on the way).  The
@@ -560,53 +657,38 @@ morph_batch_kernel(const MorphArgs *segs, const MorphItem *mi, const int *warp_b
 // cluster of bands, in which case the caller's zeroed histogram is accumulated.
 bool cluster_hist_accumulates(int64_t T) { return T > (int64_t)CH_BANDS * HIST_MAX_ROWS; }
 
+int cluster_hist_bands(bool from_power, int groups, int64_t max_T) {
+  return from_power ? bands_for<true>(groups, max_T) : bands_for<false>(groups, max_T);
+}
+
 cudaError_t launch_cluster_hist(const void *src, bool from_power, int64_t T, int F,
                                 const float *edges, const float *qconst, uint8_t *img,
                                 uint32_t *hist, rise_colstat *cols, bool *needs_zero,
                                 cudaStream_t s) {
-  int64_t groups = 1;
-  while ((T + groups * CH_BANDS - 1) / (groups * CH_BANDS) > HIST_MAX_ROWS) ++groups;
-  const int64_t rows = (T + groups * CH_BANDS - 1) / (groups * CH_BANDS);
-  const int accumulate = groups > 1;
-  if (needs_zero) *needs_zero = accumulate;
-  dim3 grid(F / CH_COLS, (unsigned)(groups * CH_BANDS));
-  const size_t sm = (size_t)CH_WORDS * sizeof(uint32_t);
   static_assert(CH_WARPS >= CH_NS, "one warp per reduced column");
-  HistArgs ha{src, T, F, rows, edges, qconst, img, hist, cols, accumulate};
-  cudaError_t e;
-  if (from_power) {
-    e = cudaFuncSetAttribute(cluster_hist_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    cluster_hist_kernel<true><<<grid, 32 * CH_WARPS, sm, s>>>(ha);
-    count_launches(1);
+  const int groups_x = F / CH_COLS;
+  int B = CH_BANDS;
+  int64_t G = 1;
+  if (cluster_hist_accumulates(T)) {
+    while ((T + G * CH_BANDS - 1) / (G * CH_BANDS) > HIST_MAX_ROWS) ++G;
   } else {
-    e = cudaFuncSetAttribute(cluster_hist_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    cluster_hist_kernel<false><<<grid, 32 * CH_WARPS, sm, s>>>(ha);
-    count_launches(1);
+    B = cluster_hist_bands(from_power, groups_x, T);
   }
-  return cudaGetLastError();
+  const int64_t rows = (T + G * B - 1) / (G * B);
+  const int accumulate = G > 1;
+  if (needs_zero) *needs_zero = accumulate;
+  HistArgs ha{src, T, F, rows, edges, qconst, img, hist, cols, accumulate};
+  const dim3 grid((unsigned)groups_x, (unsigned)(G * B));
+  return from_power ? launch_clustered(cluster_hist_kernel<true>, grid, B, s, ha)
+                    : launch_clustered(cluster_hist_kernel<false>, grid, B, s, ha);
 }
 
-int64_t cluster_hist_rows_per_band(int64_t T) { return (T + CH_BANDS - 1) / CH_BANDS; }
-
 cudaError_t launch_cluster_hist_batch(bool from_power, const HistArgs *segs, const HistItem *items,
-                                      int n_items, cudaStream_t s) {
+                                      int n_items, int bands, cudaStream_t s) {
   if (n_items < 1) return cudaSuccess;
-  dim3 grid((unsigned)n_items, CH_BANDS);
-  const size_t sm = (size_t)CH_WORDS * sizeof(uint32_t);
-  cudaError_t e;
-  if (from_power) {
-    e = cudaFuncSetAttribute(cluster_hist_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    cluster_hist_batch_kernel<true><<<grid, 32 * CH_WARPS, sm, s>>>(segs, items);
-  } else {
-    e = cudaFuncSetAttribute(cluster_hist_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    cluster_hist_batch_kernel<false><<<grid, 32 * CH_WARPS, sm, s>>>(segs, items);
-  }
-  count_launches(1);
-  return cudaGetLastError();
+  const dim3 grid((unsigned)n_items, (unsigned)bands);
+  return from_power ? launch_clustered(cluster_hist_batch_kernel<true>, grid, bands, s, segs, items)
+                    : launch_clustered(cluster_hist_batch_kernel<false>, grid, bands, s, segs, items);
 }
 
 cudaError_t launch_floor_batch(const ColArgs *segs, int ncap, int max_F, cudaStream_t s) {

@@ -644,6 +644,13 @@ int rise_debug_export(rise_ctx *c, int what, void *dst, size_t bytes) {
     std::memcpy(dst, &v, sizeof v);
     return RISE_OK;
   }
+  if (what == RISE_DBG_CCL) {
+    if (bytes < 4 * sizeof(int64_t)) return RISE_EINVAL;
+    const DeviceStatus &h = c->small_h->status;
+    const int64_t v[4] = {h.n_runs, h.n_merge, h.n_boxes, c->run_cap};
+    std::memcpy(dst, v, sizeof v);
+    return RISE_OK;
+  }
   if (what == RISE_DBG_GRAPHS) {
     if (bytes < 4 * sizeof(int64_t)) return RISE_EINVAL;
     const int64_t v[4] = {c->last_replayed ? 1 : 0, (int64_t)c->single_graphs.size(),

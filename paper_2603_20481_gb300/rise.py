@@ -26,7 +26,7 @@ NOALLOC_MAX_COLS = 4096
 RANGE_AUTO_MAX, RANGE_FIXED = 0, 1
 DBG_POWER_F32, DBG_IMAGE_U8, DBG_HIST, DBG_COLSTATS, DBG_FLOOR = 1, 2, 3, 4, 5
 DBG_MASK0, DBG_MASK1, DBG_MASK2, DBG_MASK3, DBG_MAXPOW, DBG_LEVEL_EDGES = 6, 7, 8, 9, 10, 11
-DBG_LAUNCHES, DBG_BATCH_INFO, DBG_GRAPHS = 12, 13, 14
+DBG_LAUNCHES, DBG_BATCH_INFO, DBG_GRAPHS, DBG_CCL = 12, 13, 14, 15
 STAGES = ("spectrum_pass1", "spectrum_pass2", "histogram", "column_stats", "morphology",
           "labelling", "readback", "total")
 OPT_KEEP_POWER, OPT_KEEP_MASKS, OPT_TIMING, OPT_RANGE_PATH = 1, 2, 3, 4
