@@ -405,9 +405,13 @@ __global__ void zero_if_over_kernel(DeviceStatus *st, int64_t run_cap) {
   if (st->n_runs > run_cap) st->n_boxes = 0;
 }
 
-int grid_for(int64_t n, int threads, int num_sms) {
+// Grid of the run-indexed kernels (grid-stride loops), sized on the run
+// capacity and capped at `per_sm` blocks per SM: one image's runs are
+// usually a small fraction of the capacity (idle blocks still cost), a
+// batch's are many (more threads shorten the union-find walks).
+int grid_for(int64_t n, int threads, int num_sms, int per_sm) {
   int64_t g = (n + threads - 1) / threads;
-  g = std::min<int64_t>(g, (int64_t)num_sms * 16);
+  g = std::min<int64_t>(g, (int64_t)num_sms * per_sm);
   return (int)std::max<int64_t>(1, g);
 }
 
@@ -425,7 +429,7 @@ cudaError_t launch_ccl_count(const CclArgs &a, int num_sms, cudaStream_t s) {
 namespace {
 cudaError_t label_common(const CclArgs &a, const RowSeg *segs, const int64_t *row0, int ncap,
                          int64_t *offs, int num_sms, cudaStream_t s) {
-  const int g = grid_for(a.run_cap, 256, num_sms);
+  const int g = grid_for(a.run_cap, 256, num_sms, segs ? 16 : 4);
   runs_init_kernel<<<g, 256, 0, s>>>(a);
   count_launches(1);
   const unsigned row_blocks = (unsigned)((a.T + ROW_WARPS - 1) / ROW_WARPS);

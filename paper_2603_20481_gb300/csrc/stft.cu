@@ -202,7 +202,7 @@ __device__ __forceinline__ void fft_pass(float2 (&v)[16], const float2 *src, flo
                                          const float2 (&tw0)[15], const float2 *twr) {
   using PL = Plan<N>;
   constexpr int R = PL::radix(I);
-  constexpr int MI = PL::mi(I), MP = PL::mp(I), NR = N / R;
+  constexpr int MI = PL::mi(I), MP = PL::mp(I);
   constexpr bool LAST = (I == PL::NPASS - 1);
   if constexpr (!FIRST) {
 #pragma unroll
