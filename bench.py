@@ -194,7 +194,10 @@ def run_ours(args):
     det.set_option(rise.OPT_TIMING, 1)
     stream = det.stream          # the stream the library launches on
     for _ in range(args.warmup):
-        boxes = det.detect(x, N_FFT, HOP)
+        det.submit(x, N_FFT, HOP)
+        det.submit(x, N_FFT, HOP)
+        det.collect()
+        boxes = det.collect()
     torch.cuda.synchronize()
     _barrier(world)
     torch.cuda.synchronize()
@@ -207,8 +210,11 @@ def run_ours(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     w0 = time.time()
     e0.record(stream)
-    for _ in range(args.steps):
-        boxes = det.detect(x, N_FFT, HOP)
+    det.submit(x, N_FFT, HOP)            # two calls in flight: the next one is queued
+    for i in range(args.steps):          # while the current one runs
+        if i + 1 < args.steps:
+            det.submit(x, N_FFT, HOP)
+        boxes = det.collect()
         stage += det.stage_times()
     e1.record(stream)
     torch.cuda.synchronize()
@@ -236,8 +242,11 @@ def run_ours(args):
         torch.cuda.synchronize()
         _barrier(world)
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            bh = det.detect_host(host, N_FFT, HOP)
+        det.submit(host, N_FFT, HOP)     # the next capture's copy overlaps this one's detection
+        for i in range(args.steps):
+            if i + 1 < args.steps:
+                det.submit(host, N_FFT, HOP)
+            bh = det.collect()
         torch.cuda.synchronize()
         t_e2e = _allreduce_max(time.perf_counter() - t0, world)
         e2e = {"value": round(world * args.steps * n / t_e2e / 1e6, 1), "unit": UNIT,

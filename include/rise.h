@@ -146,6 +146,24 @@ int rise_detect_host(rise_ctx *ctx, const void *iq_host, int64_t n, int fft_size
                      const rise_thresholds *thr, rise_box *out, int64_t cap,
                      int64_t *n_boxes);
 
+/* Asynchronous form of rise_detect / rise_detect_host: rise_submit queues
+ * one capture's detection and returns; rise_collect waits for the oldest
+ * queued call and returns its boxes exactly as the synchronous call would.
+ * At most two calls are queued (RISE_EAGAIN beyond).  Queued calls run one
+ * after the other on the context's stream; a host capture (iq_on_host != 0)
+ * is copied into one of two device buffers on a second stream, so the copy
+ * of the next capture overlaps the detection of the current one.  The
+ * caller's samples must stay valid and unchanged until the call has been
+ * collected.  `cap` at submit bounds the boxes the call keeps; rise_collect
+ * returns at most min(its cap, that cap) of them (RISE_ETRUNC beyond, with
+ * *n_boxes the full count).  While calls are queued, rise_detect,
+ * rise_detect_host, rise_detect_image and rise_detect_batch return
+ * RISE_EINVAL.  Errors: those of rise_detect; rise_collect with nothing
+ * queued: RISE_EINVAL. */
+int rise_submit(rise_ctx *ctx, const void *iq, int iq_on_host, int64_t n, int fft_size, int hop,
+                const rise_thresholds *thr, int64_t cap);
+int rise_collect(rise_ctx *ctx, rise_box *out, int64_t cap, int64_t *n_boxes);
+
 /* Runs the image part of the path (column histogram onwards, Sec. IV-B) on
  * a given 8-bit image: img_dev device pointer to T*F bytes, layout above,
  * F a power of two in [RISE_MIN_FFT, RISE_MAX_FFT], 1 <= T <= RISE_MAX_ROWS.
@@ -330,6 +348,9 @@ int rise_debug_export(rise_ctx *ctx, int what, void *dst, size_t bytes);
                                 * replays the launches captured as a CUDA graph   */
 #define RISE_OPT_AUTOTUNE 6    /* 1 (default): tune batch launch shapes once per   *
                                 * composition; 0: fixed defaults                   */
+#define RISE_OPT_RUN_CAPACITY 7 /* runs the labelling arrays hold at the next call *
+                                 * (>= 1024; they still grow when a mask needs    *
+                                 * more)                                          */
 
 /* Sets an option; errors: RISE_EINVAL. */
 int rise_set_option(rise_ctx *ctx, int option, int64_t value);

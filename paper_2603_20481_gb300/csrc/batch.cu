@@ -348,7 +348,7 @@ int enqueue(rise_ctx *c, const Plan &p, const rise_thresholds &thr, int64_t cap,
   // inside a capture, timing events must become event-record nodes
   auto record = [&](rise_ctx *cc, int i) {
     if (cc->timing)
-      cudaEventRecordWithFlags(cc->ev[i], s, capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+      cudaEventRecordWithFlags(cc->cs().ev[i], s, capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
   };
   BatchState &b = c->batch;
   const long long l0 = launches_so_far();
@@ -411,13 +411,13 @@ int enqueue(rise_ctx *c, const Plan &p, const rise_thresholds &thr, int64_t cap,
   la.run_out = static_cast<int64_t *>(c->run_out.p);
   la.scan_tmp = c->scan_tmp.p;
   la.scan_tmp_bytes = c->scan_tmp.bytes;
-  la.boxes = c->hbox_dev;
+  la.boxes = c->cs().hbox_dev;
   la.box_cap = cap;
   la.status = &sm->status;
   CK(launch_ccl_count(la, c->num_sms, s));
   CK(launch_ccl_label_batch(la, rseg, row0, p.ncap, b.offs_dev, c->num_sms, s));
   record(c, 6);
-  CK(cudaMemcpyAsync(&c->small_h->status, &sm->status, sizeof(DeviceStatus), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->cs().st_h, &sm->status, sizeof(DeviceStatus), cudaMemcpyDeviceToHost, s));
   record(c, 7);
   if (launches) *launches = (int)(launches_so_far() - l0);
   return RISE_OK;
@@ -517,7 +517,9 @@ int detect_batch(rise_ctx *c, const rise_capture *caps, int ncap, const rise_thr
   rise_thresholds thr;
   if (thr_in) thr = *thr_in;
   else rise_thresholds_default(&thr);
-  if (!c || !offsets || ncap < 0 || cap < 0 || (cap > 0 && !out) || (ncap > 0 && !caps)) return RISE_EINVAL;
+  if (!c || !offsets || ncap < 0 || cap < 0 || (cap > 0 && !out) || (ncap > 0 && !caps) || c->npend)
+    return RISE_EINVAL;
+  c->cur = 0;
   if (ncap == 0) {
     offsets[0] = 0;
     return RISE_OK;
@@ -587,7 +589,7 @@ int detect_batch(rise_ctx *c, const rise_capture *caps, int ncap, const rise_thr
   }
   if (!launched && (rc = enqueue(c, p, thr, cap, nullptr, nullptr, false))) return rc;
   CK(cudaStreamSynchronize(c->stream));
-  DeviceStatus h = c->small_h->status;
+  DeviceStatus h = (*c->cs().st_h);
   if (h.err & ERR_RUN_CAPACITY) {
     // more runs than the run arrays hold: grow them and run the chain again
     const int64_t need = h.n_runs + h.n_runs / 4 + 1024;
@@ -602,17 +604,18 @@ int detect_batch(rise_ctx *c, const rise_capture *caps, int ncap, const rise_thr
     if ((rc = fill_tables(c, caps, p, thr))) return rc;
     if ((rc = enqueue(c, p, thr, cap, nullptr, nullptr, false))) return rc;
     CK(cudaStreamSynchronize(c->stream));
-    h = c->small_h->status;
+    h = (*c->cs().st_h);
   }
+  c->last_status = c->cs().st_h;
   if (h.err & ERR_UNION_LIMIT) return RISE_ETIMEOUT;
   if (h.err) return RISE_EINTERNAL;
   std::memcpy(offsets, b.offs_h, sizeof(int64_t) * (ncap + 1));
   const int64_t total = h.n_boxes;
   const int64_t ncopy = std::min<int64_t>(total, cap);
-  if (ncopy > 0) std::memcpy(out, c->hbox, (size_t)ncopy * sizeof(rise_box));
+  if (ncopy > 0) std::memcpy(out, c->cs().hbox, (size_t)ncopy * sizeof(rise_box));
   if (c->timing) {
-    for (int i = 0; i < 7; ++i) cudaEventElapsedTime(&c->stage_ms[i], c->ev[i], c->ev[i + 1]);
-    cudaEventElapsedTime(&c->stage_ms[7], c->ev[0], c->ev[7]);
+    for (int i = 0; i < 7; ++i) cudaEventElapsedTime(&c->stage_ms[i], c->cs().ev[i], c->cs().ev[i + 1]);
+    cudaEventElapsedTime(&c->stage_ms[7], c->cs().ev[0], c->cs().ev[7]);
   }
   b.last_groups = (int)p.groups.size();
   b.last_params.assign(p.item_mult.begin(), p.item_mult.end());

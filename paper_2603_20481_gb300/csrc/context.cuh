@@ -57,6 +57,27 @@ struct BatchState {
   bool last_graph = false;
 };
 
+// One call in flight: where its boxes, status and stage events land, and
+// (for a host capture) the device copy of its samples.  Two slots let the
+// next call be queued, and its samples copied in, while this one runs.
+struct CallSlot {
+  rise_box *hbox = nullptr;      // mapped pinned host buffer the compaction writes into
+  rise_box *hbox_dev = nullptr;  // its device address
+  int64_t hbox_cap = 0;
+  DeviceStatus *st_h = nullptr;  // pinned status readback
+  cudaEvent_t ev[8] = {};        // stage events
+  cudaEvent_t done = nullptr;    // the call's work has finished
+  cudaEvent_t copied = nullptr;  // its host samples are on the device
+  Buf iq;                        // device copy of a host capture
+  bool pending = false;
+  // the queued call, kept to run it again if its run arrays overflow
+  const void *src = nullptr;
+  int64_t n = 0, T = 0, cap = 0;
+  int N = 0, hop = 0, path = 0;
+  bool want_power = false;
+  rise_thresholds thr{};
+};
+
 }  // namespace host
 }  // namespace rise
 
@@ -72,14 +93,19 @@ struct rise_ctx {
   int graphs = 1, autotune = 1;
   bool capturing = false;         // enqueueing into a graph capture
   // scratch
-  rise::host::Buf iq_stage, power, img, hist, cols, effm1, mask, dbg[3], row_cnt, row_base, run_parent,
+  rise::host::Buf power, img, hist, cols, effm1, mask, dbg[3], row_cnt, row_base, run_parent,
       run_sroot, rec, run_out, scan_tmp, boxes, merge;
   int64_t run_cap = 0;
+  int64_t run_cap_req = 0;             // capacity asked for by RISE_OPT_RUN_CAPACITY
   rise::host::Small *small = nullptr;   // device
-  rise::host::Small *small_h = nullptr; // pinned host mirror for readback
-  rise_box *hbox = nullptr;     // mapped pinned host buffer the compaction writes into
-  rise_box *hbox_dev = nullptr; // its device address
-  int64_t hbox_cap = 0;
+  // calls in flight: slots, queue order, the stream host captures are copied on
+  rise::host::CallSlot slot[2];
+  int cur = 0;                          // slot of the call being enqueued or finished
+  int pend[2] = {0, 0};
+  int npend = 0, next_slot = 0;
+  cudaStream_t copy_stream = nullptr;
+  rise::host::CallSlot &cs() { return slot[cur]; }
+  const rise::DeviceStatus *last_status = nullptr;   // status of the last finished call
   std::map<int, rise::host::Tables> tables;
   double energy_level_db = NAN;
   int sg_m = -1;
@@ -89,10 +115,9 @@ struct rise_ctx {
   const uint8_t *last_img = nullptr;
   bool last_has_power = false, last_has_masks = false, last_valid = false;
   double last_anchor = 0.0;
-  cudaEvent_t ev[8] = {};
   float stage_ms[8] = {};
   uint64_t gen = 0;              // bumped whenever a scratch buffer moves
-  uint64_t last_key = 0;         // arguments of the last single-capture call
+  uint64_t last_key[2] = {0, 0}; // arguments of the last call in each slot
   bool last_replayed = false;    // the last single-capture call replayed a graph
   std::vector<rise::host::BatchState::Graph> single_graphs;
   rise::host::BatchState batch;
@@ -113,7 +138,7 @@ inline int cuda_fail(cudaError_t e) {
 
 // Grows b to at least `bytes` (with 1/8 headroom), within the memory budget.
 int ensure(rise_ctx *c, Buf &b, size_t bytes);
-// Mapped pinned host buffer for the boxes (grown to at least `cap` entries).
+// Mapped pinned host buffer for the current slot's boxes (at least `cap`).
 int ensure_hbox(rise_ctx *c, int64_t cap);
 // Twiddle and window tables of FFT size N (built once per context).
 int get_tables(rise_ctx *c, int N, Tables **out);

@@ -314,22 +314,24 @@ __device__ __forceinline__ int64_t floor_div_d(int64_t a, int64_t b) {
 }
 
 __device__ __forceinline__ void floor_body(const ColArgs &a) {
-  extern __shared__ int64_t S[];   // [F] column PSD, then [F] D-scaled smoothing
-  int64_t *Sh = S + a.F;
+  // [F] D-scaled smoothing (int64), then [F] column PSD: S_f <= 255 T < 2^31
+  // and |c_i| < 2^12, so each tap is one 32 x 32 -> 64-bit product
+  extern __shared__ int64_t Sh[];
+  int32_t *S = reinterpret_cast<int32_t *>(Sh + a.F);
   __shared__ int64_t red_min[32], red_g[32];
   __shared__ int red_found[32];
-  __shared__ int64_t c[64];
+  __shared__ int32_t c[64];
   __shared__ int64_t s_N0, s_Pq;
   const int F = a.F, m = a.m, tid = threadIdx.x;
-  for (int i = tid; i <= m; i += blockDim.x) c[i] = a.sg_c[i];
-  for (int f = tid; f < F; f += blockDim.x) S[f] = (int64_t)a.cols[f].S;
+  for (int i = tid; i <= m; i += blockDim.x) c[i] = (int32_t)a.sg_c[i];
+  for (int f = tid; f < F; f += blockDim.x) S[f] = (int32_t)a.cols[f].S;
   __syncthreads();
   // Savitzky-Golay (D-scaled) on the interior, 0 elsewhere
   for (int f = tid; f < F; f += blockDim.x) {
     int64_t acc = 0;
     if (f >= m && f <= F - 1 - m) {
-      acc = c[0] * S[f];
-      for (int i = 1; i <= m; ++i) acc += c[i] * (S[f - i] + S[f + i]);
+      acc = (int64_t)c[0] * S[f];
+      for (int i = 1; i <= m; ++i) acc += (int64_t)c[i] * (int64_t)(S[f - i] + S[f + i]);
     }
     Sh[f] = acc;
     a.cols[f].Shat = acc;
@@ -379,7 +381,7 @@ __device__ __forceinline__ void floor_body(const ColArgs &a) {
   __syncthreads();
   const int64_t N0 = s_N0, Pq = s_Pq;
   for (int f = tid; f < F; f += blockDim.x) {
-    const int keep = a.psd_on ? (a.D * S[f] >= N0 + a.delta_psd) : 1;
+    const int keep = a.psd_on ? (a.D * (int64_t)S[f] >= N0 + a.delta_psd) : 1;
     const int th = a.cols[f].otsu;
     int eff = 256;
     if (keep && th >= 0) eff = max(th + 1, (int)Pq);

@@ -50,13 +50,13 @@ int ensure(rise_ctx *c, Buf &b, size_t bytes) {
 
 // Mapped pinned host buffer for the boxes (grown to at least `cap` entries).
 int ensure_hbox(rise_ctx *c, int64_t cap) {
-  if (c->hbox_cap >= cap) return RISE_OK;
-  if (c->hbox) {
+  if (c->cs().hbox_cap >= cap) return RISE_OK;
+  if (c->cs().hbox) {
     CK(cudaStreamSynchronize(c->stream));
-    cudaFreeHost(c->hbox);
-    c->hbox = nullptr;
-    c->hbox_dev = nullptr;
-    c->hbox_cap = 0;
+    cudaFreeHost(c->cs().hbox);
+    c->cs().hbox = nullptr;
+    c->cs().hbox_dev = nullptr;
+    c->cs().hbox_cap = 0;
   }
   const int64_t want = std::max<int64_t>(cap, 4096);
   void *h = nullptr;
@@ -70,9 +70,9 @@ int ensure_hbox(rise_ctx *c, int64_t cap) {
     cudaFreeHost(h);
     return RISE_ECUDA;
   }
-  c->hbox = reinterpret_cast<rise_box *>(h);
-  c->hbox_dev = reinterpret_cast<rise_box *>(d);
-  c->hbox_cap = want;
+  c->cs().hbox = reinterpret_cast<rise_box *>(h);
+  c->cs().hbox_dev = reinterpret_cast<rise_box *>(d);
+  c->cs().hbox_cap = want;
   ++c->gen;
   return RISE_OK;
 }
@@ -120,7 +120,7 @@ int check_thresholds(const rise_thresholds &t, int F) {
 void record(rise_ctx *c, int i) {
   // inside a capture the event must become an event-record node
   if (c->timing)
-    cudaEventRecordWithFlags(c->ev[i], c->stream, c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+    cudaEventRecordWithFlags(c->cs().ev[i], c->stream, c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
 }
 
 // Per-level tables that depend only on level_db: the energy of each level
@@ -170,7 +170,7 @@ CclArgs ccl_args(rise_ctx *c, const uint8_t *img, int64_t T, int F, int64_t cap)
   la.row_base = reinterpret_cast<int64_t *>(c->row_base.p);
   la.row_cnt = reinterpret_cast<uint32_t *>(c->row_cnt.p);
   la.status = &c->small->status;
-  la.boxes = c->hbox_dev;   // boxes land directly in mapped pinned host memory
+  la.boxes = c->cs().hbox_dev;   // boxes land directly in mapped pinned host memory
   la.box_cap = cap;
   la.run_cap = c->run_cap;
   la.run_parent = reinterpret_cast<int32_t *>(c->run_parent.p);
@@ -247,7 +247,7 @@ int image_enqueue(rise_ctx *c, const uint8_t *img, int64_t T, int F, const rise_
   CK(launch_ccl_count(la, c->num_sms, s));
   CK(launch_ccl_label(la, c->num_sms, s));
   record(c, 6);
-  CK(cudaMemcpyAsync(&c->small_h->status, &sm->status, sizeof(DeviceStatus), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->cs().st_h, &sm->status, sizeof(DeviceStatus), cudaMemcpyDeviceToHost, s));
   record(c, 7);
   return RISE_OK;
 }
@@ -260,7 +260,7 @@ int image_finish(rise_ctx *c, const uint8_t *img, int64_t T, int F, rise_box *ou
   cudaStream_t s = c->stream;
   int rc;
   CK(cudaStreamSynchronize(s));
-  DeviceStatus h = c->small_h->status;
+  DeviceStatus h = (*c->cs().st_h);
   if (h.err & ERR_RUN_CAPACITY) {
     // the run arrays were too small for this mask: grow to fit and relabel
     int64_t need = h.n_runs + h.n_runs / 4 + 1024;
@@ -275,19 +275,20 @@ int image_finish(rise_ctx *c, const uint8_t *img, int64_t T, int F, rise_box *ou
     CK(cudaMemsetAsync(&sm->status.err, 0, sizeof(uint32_t), s));
     CK(launch_ccl_label(la, c->num_sms, s));
     record(c, 6);
-    CK(cudaMemcpyAsync(&c->small_h->status, &sm->status, sizeof(DeviceStatus), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->cs().st_h, &sm->status, sizeof(DeviceStatus), cudaMemcpyDeviceToHost, s));
     record(c, 7);
     CK(cudaStreamSynchronize(s));
-    h = c->small_h->status;
+    h = (*c->cs().st_h);
   }
+  c->last_status = c->cs().st_h;
   if (h.err & ERR_UNION_LIMIT) return RISE_ETIMEOUT;
   if (h.err) return RISE_EINTERNAL;
   *n_boxes = h.n_boxes;
   const int64_t ncopy = std::min<int64_t>(h.n_boxes, cap);
-  if (ncopy > 0 && out) std::memcpy(out, c->hbox, (size_t)ncopy * sizeof(rise_box));
+  if (ncopy > 0 && out) std::memcpy(out, c->cs().hbox, (size_t)ncopy * sizeof(rise_box));
   if (c->timing) {
-    for (int i = 0; i < 7; ++i) cudaEventElapsedTime(&c->stage_ms[i], c->ev[i], c->ev[i + 1]);
-    cudaEventElapsedTime(&c->stage_ms[7], c->ev[0], c->ev[7]);
+    for (int i = 0; i < 7; ++i) cudaEventElapsedTime(&c->stage_ms[i], c->cs().ev[i], c->cs().ev[i + 1]);
+    cudaEventElapsedTime(&c->stage_ms[7], c->cs().ev[0], c->cs().ev[7]);
   }
   return h.n_boxes > cap ? RISE_ETRUNC : RISE_OK;
 }
@@ -304,6 +305,17 @@ int prepare_image_buffers(rise_ctx *c, int64_t T, int F) {
       if ((rc = ensure(c, d, px / 8))) return rc;
   if ((rc = ensure(c, c->row_cnt, (size_t)T * sizeof(uint32_t)))) return rc;
   if ((rc = ensure(c, c->row_base, (size_t)(T + 1) * sizeof(int64_t)))) return rc;
+  if (c->run_cap_req) {
+    // a capacity asked for by the caller, once (the arrays still grow on overflow)
+    const int64_t want = c->run_cap_req;
+    c->run_cap_req = 0;
+    if ((rc = ensure(c, c->run_parent, want * sizeof(int32_t)))) return rc;
+    if ((rc = ensure(c, c->run_sroot, want))) return rc;
+    if ((rc = ensure(c, c->rec, want * sizeof(rise_box)))) return rc;
+    if ((rc = ensure(c, c->merge, want * sizeof(int2)))) return rc;
+    if ((rc = ensure(c, c->run_out, (want + 1) * sizeof(int64_t)))) return rc;
+    c->run_cap = want;
+  }
   if (c->run_cap == 0) {
     int64_t cap0 = std::max<int64_t>(1 << 20, (int64_t)(px / 256));
     if ((rc = ensure(c, c->run_parent, cap0 * sizeof(int32_t)))) return rc;
@@ -376,19 +388,26 @@ int enqueue_detect(rise_ctx *c, const void *iq, int64_t n, int N, int hop, int64
   return image_enqueue(c, a.img, T, F, thr, hist_ready, cap);
 }
 
-int detect_device(rise_ctx *c, const void *iq, int64_t n, int N, int hop,
-                  const rise_thresholds *thr_in, rise_box *out, int64_t cap, int64_t *n_boxes) {
+// Queues one capture's detection in slot c->next_slot: validation and
+// host-side set-up, then (for a host capture) its copy on the copy stream,
+// then the launches on the context's stream, replayed from a graph when the
+// same call comes again.  The result is taken by finish_call.
+int submit_call(rise_ctx *c, const void *iq, bool on_host, int64_t n, int N, int hop,
+                const rise_thresholds *thr_in, int64_t cap) {
   rise_thresholds thr;
   if (thr_in) thr = *thr_in;
   else rise_thresholds_default(&thr);
-  if (!c || !iq || !n_boxes || (cap > 0 && !out) || cap < 0) return RISE_EINVAL;
+  if (!c || !iq || cap < 0) return RISE_EINVAL;
   if (!pow2(N) || N < RISE_MIN_FFT || N > RISE_MAX_FFT || hop < 1 || hop > N || n < N) return RISE_EINVAL;
-  if ((reinterpret_cast<uintptr_t>(iq) & 7) != 0) return RISE_EINVAL;
+  if (!on_host && (reinterpret_cast<uintptr_t>(iq) & 7) != 0) return RISE_EINVAL;
   const int64_t T = (n - N) / hop + 1;
   if (T > RISE_MAX_ROWS) return RISE_EINVAL;
   int rc = check_thresholds(thr, N);
   if (rc) return rc;
+  if (c->npend >= 2) return RISE_EAGAIN;
   CK(cudaSetDevice(c->device));
+  c->cur = c->next_slot;
+  CallSlot &sl = c->cs();
   const int F = N;
   const size_t px = (size_t)T * F;
   // host-side set-up: buffers, tables (may allocate or synchronise)
@@ -406,26 +425,37 @@ int detect_device(rise_ctx *c, const void *iq, int64_t n, int N, int hop,
   Tables *tb;
   if ((rc = get_tables(c, N, &tb))) return rc;
   if ((rc = image_prepare(c, thr, cap))) return rc;
+  const void *src = iq;
+  if (on_host) {
+    // the samples go to this slot's device copy on the copy stream; the
+    // launches wait for that copy only
+    if ((rc = ensure(c, sl.iq, (size_t)n * sizeof(float2)))) return rc;
+    CK(cudaMemcpyAsync(sl.iq.p, iq, (size_t)n * sizeof(float2), cudaMemcpyHostToDevice, c->copy_stream));
+    CK(cudaEventRecord(sl.copied, c->copy_stream));
+    CK(cudaStreamWaitEvent(c->stream, sl.copied, 0));
+    src = sl.iq.p;
+  }
   // the launches: replayed from a graph when the same call comes again
   bool launched = false;
   if (c->graphs) {
     uint64_t key = 1469598103934665603ull;
-    const int64_t kv[12] = {(int64_t)reinterpret_cast<uintptr_t>(iq), n, N, hop, cap, path,
+    const int64_t kv[13] = {(int64_t)reinterpret_cast<uintptr_t>(src), n, N, hop, cap, path,
                             c->keep_power, c->keep_masks, c->timing, (int64_t)c->gen,
-                            thr.range_mode, (int64_t)thr.sg_half_window * 2 + thr.morph_order};
+                            thr.range_mode, (int64_t)thr.sg_half_window * 2 + thr.morph_order,
+                            c->cur};
     const double dv[4] = {thr.hi_db, thr.level_db, thr.psd_offset_db, thr.power_offset_db};
     key = fnv_mix(key, kv, sizeof(kv));
     key = fnv_mix(key, dv, sizeof(dv));
     BatchState::Graph *gr = nullptr;
     for (auto &g : c->single_graphs)
       if (g.key == key) gr = &g;
-    if (!gr && c->last_key == key) {
-      // the second call with these arguments: capture it
+    if (!gr && c->last_key[c->cur] == key) {
+      // the second call with these arguments in this slot: capture it
       cudaGraph_t graph = nullptr;
       const long long l0 = launches_so_far();
       if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
         c->capturing = true;
-        const int erc = enqueue_detect(c, iq, n, N, hop, T, thr, path, want_power, tb, cap);
+        const int erc = enqueue_detect(c, src, n, N, hop, T, thr, path, want_power, tb, cap);
         c->capturing = false;
         const cudaError_t ee = cudaStreamEndCapture(c->stream, &graph);
         cudaGraphExec_t exec = nullptr;
@@ -447,7 +477,7 @@ int detect_device(rise_ctx *c, const void *iq, int64_t n, int N, int hop,
       count_launches(-(int)(launches_so_far() - l0));   // counted when the graph runs
       cudaGetLastError();   // a failed capture falls back to direct launches
     }
-    c->last_key = key;
+    c->last_key[c->cur] = key;
     if (gr) {
       CK(cudaGraphLaunch(gr->exec, c->stream));
       count_launches(gr->launches);
@@ -455,23 +485,86 @@ int detect_device(rise_ctx *c, const void *iq, int64_t n, int N, int hop,
     }
   }
   c->last_replayed = launched;
-  if (!launched && (rc = enqueue_detect(c, iq, n, N, hop, T, thr, path, want_power, tb, cap))) return rc;
+  if (!launched && (rc = enqueue_detect(c, src, n, N, hop, T, thr, path, want_power, tb, cap))) return rc;
+  CK(cudaEventRecord(sl.done, c->stream));
+  sl.pending = true;
+  sl.src = src;
+  sl.n = n;
+  sl.T = T;
+  sl.cap = cap;
+  sl.N = N;
+  sl.hop = hop;
+  sl.path = path;
+  sl.want_power = want_power;
+  sl.thr = thr;
+  c->pend[c->npend++] = c->cur;
+  c->next_slot ^= 1;
   c->last_T = T;
   c->last_F = F;
   c->last_img = reinterpret_cast<uint8_t *>(c->img.p);
   c->last_has_power = want_power;
   c->last_has_masks = c->keep_masks != 0;
   c->last_valid = true;
-  rc = image_finish(c, c->last_img, T, F, out, cap, n_boxes);
-  if (thr.range_mode == RISE_RANGE_FIXED) {
-    c->last_anchor = std::pow(10.0, thr.hi_db / 10.0);
+  return RISE_OK;
+}
+
+// Waits for the oldest queued call and returns its boxes.  If its run arrays
+// overflowed, everything queued is waited for, the arrays grow, and the call
+// runs again from its samples (still valid: a slot is reused only after it
+// has been collected).
+int finish_call(rise_ctx *c, rise_box *out, int64_t cap, int64_t *n_boxes) {
+  if (!c || !n_boxes || cap < 0 || (cap > 0 && !out)) return RISE_EINVAL;
+  if (c->npend == 0) return RISE_EINVAL;
+  CK(cudaSetDevice(c->device));
+  c->cur = c->pend[0];
+  c->pend[0] = c->pend[1];
+  c->npend -= 1;
+  CallSlot &sl = c->cs();
+  sl.pending = false;
+  int rc;
+  CK(cudaEventSynchronize(sl.done));
+  DeviceStatus h = *sl.st_h;
+  if (h.err & ERR_RUN_CAPACITY) {
+    CK(cudaStreamSynchronize(c->stream));
+    const int64_t need = h.n_runs + h.n_runs / 4 + 1024;
+    if ((rc = ensure(c, c->run_parent, need * sizeof(int32_t)))) return rc;
+    if ((rc = ensure(c, c->run_sroot, need))) return rc;
+    if ((rc = ensure(c, c->rec, need * sizeof(rise_box)))) return rc;
+    if ((rc = ensure(c, c->merge, need * sizeof(int2)))) return rc;
+    if ((rc = ensure(c, c->run_out, (need + 1) * sizeof(int64_t)))) return rc;
+    if ((rc = ensure(c, c->scan_tmp, ccl_scan_tmp_bytes(std::max<int64_t>(need, sl.T + 1))))) return rc;
+    c->run_cap = need;
+    Tables *tb;
+    if ((rc = get_tables(c, sl.N, &tb))) return rc;
+    if ((rc = enqueue_detect(c, sl.src, sl.n, sl.N, sl.hop, sl.T, sl.thr, sl.path, sl.want_power, tb,
+                             sl.cap)))
+      return rc;
+    CK(cudaStreamSynchronize(c->stream));
+    h = *sl.st_h;
+    c->last_T = sl.T;
+    c->last_F = sl.N;
+    c->last_img = reinterpret_cast<uint8_t *>(c->img.p);
+    c->last_has_power = sl.want_power;
+  }
+  c->last_status = sl.st_h;
+  if (sl.thr.range_mode == RISE_RANGE_FIXED) {
+    c->last_anchor = std::pow(10.0, sl.thr.hi_db / 10.0);
   } else {
-    uint32_t bits = c->small_h->status.max_bits;
     float mf;
-    std::memcpy(&mf, &bits, 4);
+    std::memcpy(&mf, &h.max_bits, 4);
     c->last_anchor = mf;
   }
-  return rc;
+  if (h.err & ERR_UNION_LIMIT) return RISE_ETIMEOUT;
+  if (h.err) return RISE_EINTERNAL;
+  *n_boxes = h.n_boxes;
+  const int64_t lim = std::min(cap, sl.cap);
+  const int64_t ncopy = std::min<int64_t>(h.n_boxes, lim);
+  if (ncopy > 0) std::memcpy(out, sl.hbox, (size_t)ncopy * sizeof(rise_box));
+  if (c->timing) {
+    for (int i = 0; i < 7; ++i) cudaEventElapsedTime(&c->stage_ms[i], sl.ev[i], sl.ev[i + 1]);
+    cudaEventElapsedTime(&c->stage_ms[7], sl.ev[0], sl.ev[7]);
+  }
+  return h.n_boxes > lim ? RISE_ETRUNC : RISE_OK;
 }
 
 }  // namespace
@@ -527,10 +620,20 @@ int rise_create(rise_ctx **out, const rise_config *cfg) {
       c->own_stream = true;
     }
     if (cudaMalloc(&c->small, sizeof(Small)) != cudaSuccess) { rc = RISE_ENOMEM; break; }
-    if (cudaMallocHost(&c->small_h, sizeof(Small)) != cudaSuccess) { rc = RISE_ENOMEM; break; }
     cudaMemset(c->small, 0, sizeof(Small));
-    for (auto &e : c->ev)
-      if (cudaEventCreate(&e) != cudaSuccess) { rc = RISE_ECUDA; break; }
+    if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess) { rc = RISE_ECUDA; break; }
+    for (auto &sl : c->slot) {
+      void *p = nullptr;
+      if (cudaMallocHost(&p, sizeof(DeviceStatus)) != cudaSuccess) { rc = RISE_ENOMEM; break; }
+      sl.st_h = static_cast<DeviceStatus *>(p);
+      std::memset(sl.st_h, 0, sizeof(DeviceStatus));
+      for (auto &e : sl.ev)
+        if (cudaEventCreate(&e) != cudaSuccess) rc = RISE_ECUDA;
+      if (cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) rc = RISE_ECUDA;
+      if (cudaEventCreateWithFlags(&sl.copied, cudaEventDisableTiming) != cudaSuccess) rc = RISE_ECUDA;
+      if (rc) break;
+    }
+    c->last_status = c->slot[0].st_h;
     if (rc) break;
     if (cfg->max_fft && (cfg->max_fft < RISE_MIN_FFT || cfg->max_fft > RISE_MAX_FFT || !pow2(cfg->max_fft))) {
       rc = RISE_EINVAL;
@@ -541,7 +644,14 @@ int rise_create(rise_ctx **out, const rise_config *cfg) {
       // the 8-bit image of a capture with hop >= F/2 has at most 2 pixels per sample
       if ((rc = ensure(c, c->img, (size_t)cfg->max_samples * 2))) break;
     }
-    if (cfg->max_boxes > 0 && (rc = ensure_hbox(c, cfg->max_boxes))) break;
+    if (cfg->max_boxes > 0) {
+      for (int k = 0; k < 2 && rc == RISE_OK; ++k) {
+        c->cur = k;
+        rc = ensure_hbox(c, cfg->max_boxes);
+      }
+      c->cur = 0;
+      if (rc) break;
+    }
   } while (0);
   if (rc) {
     cudaGetLastError();
@@ -556,7 +666,7 @@ void rise_destroy(rise_ctx *c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
-  Buf *bufs[] = {&c->iq_stage, &c->power, &c->img, &c->hist, &c->cols, &c->effm1, &c->mask,
+  Buf *bufs[] = {&c->power, &c->img, &c->hist, &c->cols, &c->effm1, &c->mask,
                  &c->dbg[0], &c->dbg[1], &c->dbg[2], &c->row_cnt, &c->row_base,
                  &c->run_parent, &c->run_sroot, &c->rec, &c->run_out, &c->scan_tmp, &c->boxes, &c->merge};
   for (Buf *b : bufs)
@@ -564,27 +674,41 @@ void rise_destroy(rise_ctx *c) {
   for (auto &kv : c->tables) cudaFree(kv.second.tw);
   destroy_batch(c);
   if (c->small) cudaFree(c->small);
-  if (c->small_h) cudaFreeHost(c->small_h);
-  if (c->hbox) cudaFreeHost(c->hbox);
-  for (auto &e : c->ev)
-    if (e) cudaEventDestroy(e);
+  for (auto &sl : c->slot) {
+    if (sl.hbox) cudaFreeHost(sl.hbox);
+    if (sl.st_h) cudaFreeHost(sl.st_h);
+    if (sl.iq.p) cudaFree(sl.iq.p);
+    for (auto &e : sl.ev)
+      if (e) cudaEventDestroy(e);
+    if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.copied) cudaEventDestroy(sl.copied);
+  }
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
 
 int rise_detect(rise_ctx *c, const void *iq_dev, int64_t n, int fft_size, int hop,
                 const rise_thresholds *thr, rise_box *out, int64_t cap, int64_t *n_boxes) {
-  return detect_device(c, iq_dev, n, fft_size, hop, thr, out, cap, n_boxes);
+  if (!c || !n_boxes || (cap > 0 && !out) || c->npend) return RISE_EINVAL;
+  const int rc = submit_call(c, iq_dev, false, n, fft_size, hop, thr, cap);
+  return rc ? rc : finish_call(c, out, cap, n_boxes);
 }
 
 int rise_detect_host(rise_ctx *c, const void *iq_host, int64_t n, int fft_size, int hop,
                      const rise_thresholds *thr, rise_box *out, int64_t cap, int64_t *n_boxes) {
-  if (!c || !iq_host || n <= 0) return RISE_EINVAL;
-  CK(cudaSetDevice(c->device));
-  int rc = ensure(c, c->iq_stage, (size_t)n * 8);
-  if (rc) return rc;
-  CK(cudaMemcpyAsync(c->iq_stage.p, iq_host, (size_t)n * 8, cudaMemcpyHostToDevice, c->stream));
-  return detect_device(c, c->iq_stage.p, n, fft_size, hop, thr, out, cap, n_boxes);
+  if (!c || !n_boxes || (cap > 0 && !out) || c->npend) return RISE_EINVAL;
+  const int rc = submit_call(c, iq_host, true, n, fft_size, hop, thr, cap);
+  return rc ? rc : finish_call(c, out, cap, n_boxes);
+}
+
+int rise_submit(rise_ctx *c, const void *iq, int iq_on_host, int64_t n, int fft_size, int hop,
+                const rise_thresholds *thr, int64_t cap) {
+  return submit_call(c, iq, iq_on_host != 0, n, fft_size, hop, thr, cap);
+}
+
+int rise_collect(rise_ctx *c, rise_box *out, int64_t cap, int64_t *n_boxes) {
+  return finish_call(c, out, cap, n_boxes);
 }
 
 int rise_detect_image(rise_ctx *c, const uint8_t *img_dev, int64_t T, int F,
@@ -592,7 +716,8 @@ int rise_detect_image(rise_ctx *c, const uint8_t *img_dev, int64_t T, int F,
   rise_thresholds thr;
   if (thr_in) thr = *thr_in;
   else rise_thresholds_default(&thr);
-  if (!c || !img_dev || !n_boxes || (cap > 0 && !out) || cap < 0) return RISE_EINVAL;
+  if (!c || !img_dev || !n_boxes || (cap > 0 && !out) || cap < 0 || c->npend) return RISE_EINVAL;
+  c->cur = 0;
   if (!pow2(F) || F < RISE_MIN_FFT || F > RISE_MAX_FFT || T < 1 || T > RISE_MAX_ROWS) return RISE_EINVAL;
   if ((reinterpret_cast<uintptr_t>(img_dev) & 31) != 0) return RISE_EINVAL;
   int rc = check_thresholds(thr, F);
@@ -622,6 +747,10 @@ int rise_set_option(rise_ctx *c, int option, int64_t value) {
     case RISE_OPT_TIMING: c->timing = value != 0; return RISE_OK;
     case RISE_OPT_GRAPH: c->graphs = value != 0; return RISE_OK;
     case RISE_OPT_AUTOTUNE: c->autotune = value != 0; return RISE_OK;
+    case RISE_OPT_RUN_CAPACITY:
+      if (value < 1024 || value > (int64_t)1 << 31) return RISE_EINVAL;
+      c->run_cap_req = value;
+      return RISE_OK;
     case RISE_OPT_RANGE_PATH:
       if (value < 0 || value > 2) return RISE_EINVAL;
       c->range_path = (int)value;
@@ -646,7 +775,7 @@ int rise_debug_export(rise_ctx *c, int what, void *dst, size_t bytes) {
   }
   if (what == RISE_DBG_CCL) {
     if (bytes < 4 * sizeof(int64_t)) return RISE_EINVAL;
-    const DeviceStatus &h = c->small_h->status;
+    const DeviceStatus &h = *c->last_status;
     const int64_t v[4] = {h.n_runs, h.n_merge, h.n_boxes, c->run_cap};
     std::memcpy(dst, v, sizeof v);
     return RISE_OK;

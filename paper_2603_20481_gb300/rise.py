@@ -30,7 +30,7 @@ DBG_LAUNCHES, DBG_BATCH_INFO, DBG_GRAPHS, DBG_CCL = 12, 13, 14, 15
 STAGES = ("spectrum_pass1", "spectrum_pass2", "histogram", "column_stats", "morphology",
           "labelling", "readback", "total")
 OPT_KEEP_POWER, OPT_KEEP_MASKS, OPT_TIMING, OPT_RANGE_PATH = 1, 2, 3, 4
-OPT_GRAPH, OPT_AUTOTUNE = 5, 6
+OPT_GRAPH, OPT_AUTOTUNE, OPT_RUN_CAPACITY = 5, 6, 7
 OPT_BATCH_GRAPH = OPT_GRAPH
 BATCH_MAX_ROWS = 524280
 BOX_COLS = ("t0", "t1", "f0", "f1", "anchor", "area", "sum_q", "energy_fx")
@@ -39,7 +39,7 @@ BOX_COLS = ("t0", "t1", "f0", "f1", "anchor", "area", "sum_q", "energy_fx")
 EXPORTS = ("rise_thresholds_default", "rise_create", "rise_destroy", "rise_strerror",
            "rise_detect", "rise_detect_host", "rise_detect_image", "rise_debug_export",
            "rise_set_option", "rise_stage_times", "rise_column_stats_noalloc",
-           "rise_detect_batch", "rise_server_create", "rise_stream_submit", "rise_server_poll",
+           "rise_detect_batch", "rise_submit", "rise_collect", "rise_server_create", "rise_stream_submit", "rise_server_poll",
            "rise_server_drain", "rise_stream_export", "rise_stream_import", "rise_server_stats",
            "rise_server_destroy")
 
@@ -124,6 +124,10 @@ def lib() -> C.CDLL:
     L.rise_set_option.restype = i32
     L.rise_stage_times.argtypes = [P, P, i32]
     L.rise_stage_times.restype = i32
+    L.rise_submit.argtypes = [P, P, i32, i64, i32, i32, P, i64]
+    L.rise_submit.restype = i32
+    L.rise_collect.argtypes = [P, P, i64, C.POINTER(i64)]
+    L.rise_collect.restype = i32
     L.rise_detect_batch.argtypes = [P, P, i32, P, P, i64, P]
     L.rise_detect_batch.restype = i32
     L.rise_server_create.argtypes = [C.POINTER(P), P]
@@ -164,9 +168,12 @@ def default_thresholds(**overrides) -> Thresholds:
 
 
 def boxes_from_raw(raw: np.ndarray, n: int) -> np.ndarray:
+    """rise_box[n] -> int64 (n, 8): the four int32 fields, then the four 64-bit ones
+    (sum_q and energy_fx stay below 2^63)."""
     out = np.empty((n, 8), np.int64)
-    for j, name in enumerate(BOX_COLS):
-        out[:, j] = raw[name][:n].astype(np.int64)
+    if n:
+        out[:, :4] = raw.view(np.int32).reshape(-1, 12)[:n, :4]
+        out[:, 4:] = raw.view(np.int64).reshape(-1, 6)[:n, 2:]
     return out
 
 
@@ -193,6 +200,7 @@ class Detector:
         self._h = h
         self.device = device
         self.stream = stream
+        self._ev = torch.cuda.Event()
         self.cap = 1 << 16
 
     def close(self):
@@ -215,7 +223,8 @@ class Detector:
     def _order(self):
         cur = self._torch.cuda.current_stream(self.device)
         if cur.cuda_stream != self.stream.cuda_stream:
-            self.stream.wait_stream(cur)
+            self._ev.record(cur)
+            self.stream.wait_event(self._ev)
 
     # -- options ----------------------------------------------------------------
     def set_option(self, option: int, value: int):
@@ -287,6 +296,39 @@ class Detector:
                 C.byref(thr) if thr is not None else None)
         self._order()
         return self._run(lib().rise_detect_host, args, cap)
+
+    # -- asynchronous calls ---------------------------------------------------
+    def submit(self, iq, fft_size: int, hop: int, thr: Optional[Thresholds] = None,
+               cap: Optional[int] = None):
+        """Queues a capture (rise_submit): a CUDA complex64 tensor, or a host one
+        (pinned tensor or numpy array), kept referenced until collected."""
+        t = self._torch
+        if isinstance(iq, t.Tensor):
+            if iq.dtype != t.complex64 or not iq.is_contiguous() or iq.dim() != 1:
+                raise TypeError("iq must be a contiguous 1-D complex64 tensor")
+            ptr, n, host = iq.data_ptr(), iq.numel(), not iq.is_cuda
+        else:
+            iq = np.ascontiguousarray(iq, dtype=np.complex64)
+            ptr, n, host = iq.ctypes.data, iq.shape[0], True
+        cap = self.cap if cap is None else int(cap)
+        self._order()
+        rc = lib().rise_submit(self._h, C.c_void_p(ptr), int(host), n, fft_size, hop,
+                               C.byref(thr) if thr is not None else None, cap)
+        if rc != RISE_OK:
+            raise RiseError(rc, "rise_submit")
+        self._queued = getattr(self, "_queued", []) + [(iq, cap)]
+
+    def collect(self) -> np.ndarray:
+        """Boxes of the oldest queued call (rise_collect)."""
+        _, cap = self._queued[0]
+        raw = self._raw(max(cap, 1))
+        n = C.c_int64(0)
+        rc = lib().rise_collect(self._h, raw.ctypes.data, cap, C.byref(n))
+        self._queued = self._queued[1:]
+        if rc not in (RISE_OK, RISE_ETRUNC):
+            raise RiseError(rc, "rise_collect")
+        self.last_status = rc
+        return boxes_from_raw(raw, min(int(n.value), cap))
 
     def detect_image(self, img, thr: Optional[Thresholds] = None,
                      cap: Optional[int] = None) -> np.ndarray:
