@@ -149,9 +149,13 @@ int rise_detect_host(rise_ctx *ctx, const void *iq_host, int64_t n, int fft_size
 /* Asynchronous form of rise_detect / rise_detect_host: rise_submit queues
  * one capture's detection and returns; rise_collect waits for the oldest
  * queued call and returns its boxes exactly as the synchronous call would.
- * At most two calls are queued (RISE_EAGAIN beyond).  Queued calls run one
- * after the other on the context's stream; a host capture (iq_on_host != 0)
- * is copied into one of two device buffers on a second stream, so the copy
+ * iq_flags: RISE_IQ_HOST when iq is host memory (else device memory), and
+ * RISE_IQ_SC16 when the samples are 16-bit integer I/Q (interleaved int16
+ * I, Q, 4-byte aligned; sample = (I + iQ) * 2^-15, exact in float, so the
+ * results equal those of the same samples given as complex64) instead of
+ * complex64.  At most two calls are queued (RISE_EAGAIN beyond).  Queued
+ * calls run one after the other on the context's stream; a host capture is
+ * copied into one of two device buffers on a second stream, so the copy
  * of the next capture overlaps the detection of the current one.  The
  * caller's samples must stay valid and unchanged until the call has been
  * collected.  `cap` at submit bounds the boxes the call keeps; rise_collect
@@ -160,7 +164,9 @@ int rise_detect_host(rise_ctx *ctx, const void *iq_host, int64_t n, int fft_size
  * rise_detect_host, rise_detect_image and rise_detect_batch return
  * RISE_EINVAL.  Errors: those of rise_detect; rise_collect with nothing
  * queued: RISE_EINVAL. */
-int rise_submit(rise_ctx *ctx, const void *iq, int iq_on_host, int64_t n, int fft_size, int hop,
+#define RISE_IQ_HOST 1
+#define RISE_IQ_SC16 2
+int rise_submit(rise_ctx *ctx, const void *iq, int iq_flags, int64_t n, int fft_size, int hop,
                 const rise_thresholds *thr, int64_t cap);
 int rise_collect(rise_ctx *ctx, rise_box *out, int64_t cap, int64_t *n_boxes);
 

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "librise.so")
-SOURCES = ["stft.cu", "image.cu", "ccl.cu", "rise.cu", "batch.cu", "server.cu", "noalloc.cu"]
+SOURCES = ["stft.cu", "stft_sc16.cu", "image.cu", "ccl.cu", "rise.cu", "batch.cu", "server.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]
@@ -31,6 +31,7 @@ def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
     deps = [src, os.path.join(CSRC, "common.cuh"), os.path.join(CSRC, "context.cuh"),
+            os.path.join(CSRC, "stft_impl.cuh"),
             os.path.join(os.path.dirname(HERE), "include", "rise.h")]
     return any(os.path.getmtime(d) > os.path.getmtime(obj) for d in deps)
 

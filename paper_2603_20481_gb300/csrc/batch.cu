@@ -258,7 +258,8 @@ int fill_tables(rise_ctx *c, const rise_capture *caps, const Plan &p, const rise
     int rc = get_tables(c, F, &tb);
     if (rc) return rc;
     StftArgs &a = stft[k];
-    a.iq = static_cast<const float2 *>(cp.iq_dev);
+    a.iq = cp.iq_dev;
+    a.fmt = IQ_FC32;
     a.n = cp.n;
     a.N = F;
     a.hop = cp.hop;

@@ -126,8 +126,10 @@ namespace rise {
 void count_launches(int k);
 long long launches_so_far();
 
+enum IqFormat { IQ_FC32 = 0, IQ_SC16 = 1 };
+
 struct StftArgs {
-  const float2 *iq;       // device, n complex samples
+  const void *iq;         // device, n complex samples (float2, or short2 for sc16)
   int64_t n;
   int N;                  // FFT size
   int hop;
@@ -140,9 +142,11 @@ struct StftArgs {
   const float2 *tw;       // per-N twiddle tables (device)
   const float *win;       // per-N Hann window (device)
   uint32_t *err;          // device error word (ERR_* bits)
+  int fmt;                // IqFormat
 };
 
 enum StftMode { STFT_MAX = 0, STFT_QUANT = 1, STFT_POWER = 2, STFT_QUANT_POWER = 3 };
+cudaError_t launch_stft_sc16(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Batches: one launch per stage covers many captures; each block or warp

@@ -73,7 +73,7 @@ struct CallSlot {
   // the queued call, kept to run it again if its run arrays overflow
   const void *src = nullptr;
   int64_t n = 0, T = 0, cap = 0;
-  int N = 0, hop = 0, path = 0;
+  int N = 0, hop = 0, path = 0, fmt = 0;
   bool want_power = false;
   rise_thresholds thr{};
 };

@@ -340,7 +340,7 @@ uint64_t fnv_mix(uint64_t h, const void *p, size_t n) {
 }
 
 // Launches of one capture's spectrum part, then the image part.
-int enqueue_detect(rise_ctx *c, const void *iq, int64_t n, int N, int hop, int64_t T,
+int enqueue_detect(rise_ctx *c, const void *iq, int fmt, int64_t n, int N, int hop, int64_t T,
                    const rise_thresholds &thr, int path, bool want_power, const Tables *tb,
                    int64_t cap) {
   cudaStream_t s = c->stream;
@@ -349,7 +349,8 @@ int enqueue_detect(rise_ctx *c, const void *iq, int64_t n, int N, int hop, int64
   CK(cudaMemsetAsync(&sm->status, 0, sizeof(DeviceStatus), s));
   record(c, 0);
   StftArgs a;
-  a.iq = reinterpret_cast<const float2 *>(iq);
+  a.iq = iq;
+  a.fmt = fmt;
   a.n = n;
   a.N = N;
   a.hop = hop;
@@ -392,14 +393,18 @@ int enqueue_detect(rise_ctx *c, const void *iq, int64_t n, int N, int hop, int64
 // host-side set-up, then (for a host capture) its copy on the copy stream,
 // then the launches on the context's stream, replayed from a graph when the
 // same call comes again.  The result is taken by finish_call.
-int submit_call(rise_ctx *c, const void *iq, bool on_host, int64_t n, int N, int hop,
+int submit_call(rise_ctx *c, const void *iq, int flags, int64_t n, int N, int hop,
                 const rise_thresholds *thr_in, int64_t cap) {
+  const bool on_host = (flags & RISE_IQ_HOST) != 0;
+  const int fmt = (flags & RISE_IQ_SC16) ? IQ_SC16 : IQ_FC32;
+  const size_t bps = fmt == IQ_SC16 ? 4 : 8;   // bytes per sample
   rise_thresholds thr;
   if (thr_in) thr = *thr_in;
   else rise_thresholds_default(&thr);
   if (!c || !iq || cap < 0) return RISE_EINVAL;
   if (!pow2(N) || N < RISE_MIN_FFT || N > RISE_MAX_FFT || hop < 1 || hop > N || n < N) return RISE_EINVAL;
-  if (!on_host && (reinterpret_cast<uintptr_t>(iq) & 7) != 0) return RISE_EINVAL;
+  if (flags & ~(RISE_IQ_HOST | RISE_IQ_SC16)) return RISE_EINVAL;
+  if (!on_host && (reinterpret_cast<uintptr_t>(iq) & (bps - 1)) != 0) return RISE_EINVAL;
   const int64_t T = (n - N) / hop + 1;
   if (T > RISE_MAX_ROWS) return RISE_EINVAL;
   int rc = check_thresholds(thr, N);
@@ -429,8 +434,8 @@ int submit_call(rise_ctx *c, const void *iq, bool on_host, int64_t n, int N, int
   if (on_host) {
     // the samples go to this slot's device copy on the copy stream; the
     // launches wait for that copy only
-    if ((rc = ensure(c, sl.iq, (size_t)n * sizeof(float2)))) return rc;
-    CK(cudaMemcpyAsync(sl.iq.p, iq, (size_t)n * sizeof(float2), cudaMemcpyHostToDevice, c->copy_stream));
+    if ((rc = ensure(c, sl.iq, (size_t)n * bps))) return rc;
+    CK(cudaMemcpyAsync(sl.iq.p, iq, (size_t)n * bps, cudaMemcpyHostToDevice, c->copy_stream));
     CK(cudaEventRecord(sl.copied, c->copy_stream));
     CK(cudaStreamWaitEvent(c->stream, sl.copied, 0));
     src = sl.iq.p;
@@ -439,10 +444,10 @@ int submit_call(rise_ctx *c, const void *iq, bool on_host, int64_t n, int N, int
   bool launched = false;
   if (c->graphs) {
     uint64_t key = 1469598103934665603ull;
-    const int64_t kv[13] = {(int64_t)reinterpret_cast<uintptr_t>(src), n, N, hop, cap, path,
+    const int64_t kv[14] = {(int64_t)reinterpret_cast<uintptr_t>(src), n, N, hop, cap, path,
                             c->keep_power, c->keep_masks, c->timing, (int64_t)c->gen,
                             thr.range_mode, (int64_t)thr.sg_half_window * 2 + thr.morph_order,
-                            c->cur};
+                            c->cur, fmt};
     const double dv[4] = {thr.hi_db, thr.level_db, thr.psd_offset_db, thr.power_offset_db};
     key = fnv_mix(key, kv, sizeof(kv));
     key = fnv_mix(key, dv, sizeof(dv));
@@ -455,7 +460,7 @@ int submit_call(rise_ctx *c, const void *iq, bool on_host, int64_t n, int N, int
       const long long l0 = launches_so_far();
       if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
         c->capturing = true;
-        const int erc = enqueue_detect(c, src, n, N, hop, T, thr, path, want_power, tb, cap);
+        const int erc = enqueue_detect(c, src, fmt, n, N, hop, T, thr, path, want_power, tb, cap);
         c->capturing = false;
         const cudaError_t ee = cudaStreamEndCapture(c->stream, &graph);
         cudaGraphExec_t exec = nullptr;
@@ -485,10 +490,11 @@ int submit_call(rise_ctx *c, const void *iq, bool on_host, int64_t n, int N, int
     }
   }
   c->last_replayed = launched;
-  if (!launched && (rc = enqueue_detect(c, src, n, N, hop, T, thr, path, want_power, tb, cap))) return rc;
+  if (!launched && (rc = enqueue_detect(c, src, fmt, n, N, hop, T, thr, path, want_power, tb, cap))) return rc;
   CK(cudaEventRecord(sl.done, c->stream));
   sl.pending = true;
   sl.src = src;
+  sl.fmt = fmt;
   sl.n = n;
   sl.T = T;
   sl.cap = cap;
@@ -536,8 +542,8 @@ int finish_call(rise_ctx *c, rise_box *out, int64_t cap, int64_t *n_boxes) {
     c->run_cap = need;
     Tables *tb;
     if ((rc = get_tables(c, sl.N, &tb))) return rc;
-    if ((rc = enqueue_detect(c, sl.src, sl.n, sl.N, sl.hop, sl.T, sl.thr, sl.path, sl.want_power, tb,
-                             sl.cap)))
+    if ((rc = enqueue_detect(c, sl.src, sl.fmt, sl.n, sl.N, sl.hop, sl.T, sl.thr, sl.path,
+                             sl.want_power, tb, sl.cap)))
       return rc;
     CK(cudaStreamSynchronize(c->stream));
     h = *sl.st_h;
@@ -691,20 +697,20 @@ void rise_destroy(rise_ctx *c) {
 int rise_detect(rise_ctx *c, const void *iq_dev, int64_t n, int fft_size, int hop,
                 const rise_thresholds *thr, rise_box *out, int64_t cap, int64_t *n_boxes) {
   if (!c || !n_boxes || (cap > 0 && !out) || c->npend) return RISE_EINVAL;
-  const int rc = submit_call(c, iq_dev, false, n, fft_size, hop, thr, cap);
+  const int rc = submit_call(c, iq_dev, 0, n, fft_size, hop, thr, cap);
   return rc ? rc : finish_call(c, out, cap, n_boxes);
 }
 
 int rise_detect_host(rise_ctx *c, const void *iq_host, int64_t n, int fft_size, int hop,
                      const rise_thresholds *thr, rise_box *out, int64_t cap, int64_t *n_boxes) {
   if (!c || !n_boxes || (cap > 0 && !out) || c->npend) return RISE_EINVAL;
-  const int rc = submit_call(c, iq_host, true, n, fft_size, hop, thr, cap);
+  const int rc = submit_call(c, iq_host, RISE_IQ_HOST, n, fft_size, hop, thr, cap);
   return rc ? rc : finish_call(c, out, cap, n_boxes);
 }
 
-int rise_submit(rise_ctx *c, const void *iq, int iq_on_host, int64_t n, int fft_size, int hop,
+int rise_submit(rise_ctx *c, const void *iq, int iq_flags, int64_t n, int fft_size, int hop,
                 const rise_thresholds *thr, int64_t cap) {
-  return submit_call(c, iq, iq_on_host != 0, n, fft_size, hop, thr, cap);
+  return submit_call(c, iq, iq_flags, n, fft_size, hop, thr, cap);
 }
 
 int rise_collect(rise_ctx *c, rise_box *out, int64_t cap, int64_t *n_boxes) {

@@ -15,506 +15,10 @@
 // Epilogues: MAX (running max of |X|^2 for the anchor), QUANT (8-bit level
 // per bin, stored with DC in column N/2), POWER (float |X|^2 stored plus the
 // running max) and QUANT_POWER (both).
-#include <cmath>
-#include <vector>
-
-#include "common.cuh"
+#include "stft_impl.cuh"
 
 namespace rise {
 namespace {
-
-constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
-
-template <int N>
-struct Plan {
-  static constexpr int LOG2N = ilog2c(N);
-  static constexpr int NP16 = LOG2N / 4;
-  static constexpr int RLAST = 1 << (LOG2N % 4);
-  static constexpr int NPASS = NP16 + (RLAST > 1 ? 1 : 0);
-  static constexpr int TPF = N / 16;                       // threads per frame
-  static constexpr int FPB = TPF >= 256 ? 1 : 256 / TPF;   // frames per block step
-  static constexpr int THREADS = TPF * FPB;
-  static constexpr int SLOT = N + N / 16;                  // padded complex per frame
-  static constexpr int radix(int i) { return i < NP16 ? 16 : RLAST; }
-  static constexpr int lprev(int i) { return i == 0 ? 1 : lprev(i - 1) * radix(i - 1); }
-  static constexpr int mi(int i) { return N / lprev(i); }
-  static constexpr int mp(int i) { return mi(i) / radix(i); }
-  // twiddle tables: pass 0 [15][N/16] kept in registers, passes 1..NPASS-2 in smem
-  static constexpr int tw_off(int i) { return i == 0 ? 0 : tw_off(i - 1) + 15 * mp(i - 1); }
-  static constexpr int TW_TOTAL = tw_off(NPASS - 1);
-  static constexpr int TW_REST = TW_TOTAL - 15 * (N / 16);
-};
-
-__device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
-
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 cmul(float2 a, float2 w) {
-  return make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
-}
-__device__ __forceinline__ float2 mul_negi(float2 a) { return make_float2(a.y, -a.x); }  // a * (-i)
-
-constexpr float kR = 0.70710678118654752440f;   // cos(pi/4)
-constexpr float kC = 0.92387953251128675613f;   // cos(pi/8)
-constexpr float kS = 0.38268343236508977173f;   // sin(pi/8)
-
-// a * (r - i r)  (W_8^1 = W_16^2)
-__device__ __forceinline__ float2 mul_w8_1(float2 a) { return make_float2(kR * (a.x + a.y), kR * (a.y - a.x)); }
-// a * (-r - i r)  (W_8^3 = W_16^6)
-__device__ __forceinline__ float2 mul_w8_3(float2 a) { return make_float2(kR * (a.y - a.x), -kR * (a.x + a.y)); }
-
-// forward DFTs in place, natural order, X[k] = sum_n x[n] e^{-2 pi i n k / R}
-__device__ __forceinline__ void dft2(float2 &a, float2 &b) {
-  float2 t = a;
-  a = cadd(t, b);
-  b = csub(t, b);
-}
-// Packed (f32x2) complex add / subtract: one instruction each, the same
-// rounding as two scalar adds (a - b is computed as b * -1 + a, exact product).
-__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 psub(float2 a, float2 b) {
-  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
-}
-__device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3) {
-  const float2 t0 = padd(a0, a2), t1 = psub(a0, a2), t2 = padd(a1, a3);
-  // (a1 - a3) with its components swapped, so that multiplying by -i becomes a
-  // lane-wise sign: -i (x + i y) = y - i x
-  const float2 ts = make_float2(a1.y - a3.y, a1.x - a3.x);
-  a0 = padd(t0, t2);
-  a2 = psub(t0, t2);
-  a1 = __ffma2_rn(ts, make_float2(1.0f, -1.0f), t1);
-  a3 = __ffma2_rn(ts, make_float2(-1.0f, 1.0f), t1);
-}
-__device__ __forceinline__ void dft8(float2 *v) {
-  // n = 2 n1 + n2, k = k1 + 4 k2
-  dft4(v[0], v[2], v[4], v[6]);
-  dft4(v[1], v[3], v[5], v[7]);
-  float2 b1 = mul_w8_1(v[3]), b2 = mul_negi(v[5]), b3 = mul_w8_3(v[7]);
-  float2 x0 = cadd(v[0], v[1]), x4 = csub(v[0], v[1]);
-  float2 x1 = cadd(v[2], b1), x5 = csub(v[2], b1);
-  float2 x2 = cadd(v[4], b2), x6 = csub(v[4], b2);
-  float2 x3 = cadd(v[6], b3), x7 = csub(v[6], b3);
-  v[0] = x0; v[1] = x1; v[2] = x2; v[3] = x3; v[4] = x4; v[5] = x5; v[6] = x6; v[7] = x7;
-}
-__device__ __forceinline__ void dft16(float2 *v) {
-  // n = 4 n1 + n2, k = k1 + 4 k2: DFT4 over n1, twiddle W16^(n2 k1), DFT4 over n2
-  dft4(v[0], v[4], v[8], v[12]);
-  dft4(v[1], v[5], v[9], v[13]);
-  dft4(v[2], v[6], v[10], v[14]);
-  dft4(v[3], v[7], v[11], v[15]);
-  // y[n2][k1] sits at v[4 k1 + n2]
-  v[5] = cmul(v[5], make_float2(kC, -kS));    // n2=1,k1=1: W^1
-  v[9] = mul_w8_1(v[9]);                      // n2=1,k1=2: W^2
-  v[13] = cmul(v[13], make_float2(kS, -kC));  // n2=1,k1=3: W^3
-  v[6] = mul_w8_1(v[6]);                      // n2=2,k1=1: W^2
-  v[10] = mul_negi(v[10]);                    // n2=2,k1=2: W^4
-  v[14] = mul_w8_3(v[14]);                    // n2=2,k1=3: W^6
-  v[7] = cmul(v[7], make_float2(kS, -kC));    // n2=3,k1=1: W^3
-  v[11] = mul_w8_3(v[11]);                    // n2=3,k1=2: W^6
-  v[15] = cmul(v[15], make_float2(-kC, kS));  // n2=3,k1=3: W^9
-  dft4(v[0], v[1], v[2], v[3]);
-  dft4(v[4], v[5], v[6], v[7]);
-  dft4(v[8], v[9], v[10], v[11]);
-  dft4(v[12], v[13], v[14], v[15]);
-  // X[k1 + 4 k2] is at v[4 k1 + k2]: transpose 4x4 to natural order
-  float2 t;
-  t = v[1]; v[1] = v[4]; v[4] = t;
-  t = v[2]; v[2] = v[8]; v[8] = t;
-  t = v[3]; v[3] = v[12]; v[12] = t;
-  t = v[6]; v[6] = v[9]; v[9] = t;
-  t = v[7]; v[7] = v[13]; v[13] = t;
-  t = v[11]; v[11] = v[14]; v[14] = t;
-}
-
-template <int R>
-__device__ __forceinline__ void dft_r(float2 *v) {
-  if constexpr (R == 16) dft16(v);
-  else if constexpr (R == 8) dft8(v);
-  else if constexpr (R == 4) dft4(v[0], v[1], v[2], v[3]);
-  else dft2(v[0], v[1]);
-}
-
-constexpr float kGuard = 3.0e-4f;   // |fast level coordinate error| is below 1e-4
-
-// 8-bit level of power P: the count of edges[1..255] that P reaches.  A fast
-// estimate from log2(P / anchor) is trusted away from level edges (the float
-// to unsigned conversion floors and clamps to 0..255, NaN and -inf give 0);
-// within kGuard of an edge the power is compared against the exact edge table.
-__device__ __forceinline__ uint32_t level_of(float P, float inv_anchor, float c1, const float *edges) {
-  const float v = fmaf(__log2f(P * inv_anchor), c1, 255.5f);
-  uint32_t q = __float2uint_rd(fminf(v, 255.0f));
-  if (fabsf(v - rintf(v)) < kGuard) {
-    int qi = (int)q;
-    for (int it = 0; it < 256 && qi < 255 && P >= edges[qi + 1]; ++it) ++qi;
-    for (int it = 0; it < 256 && qi > 0 && P < edges[qi]; ++it) --qi;
-    q = (uint32_t)qi;
-  }
-  return q;
-}
-
-// ---- TMA bulk copies and mbarriers (inline PTX) ---------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_inval(uint64_t *b) {
-  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(b)) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
-               : "memory");
-}
-// 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16)
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *b) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(b))
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait: try_wait suspends for a hardware-defined interval per call
-constexpr int kWaitLimit = 1 << 22;
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
-  for (int i = 0; i < kWaitLimit; ++i)
-    if (mbar_test(b, parity)) return true;
-  return false;
-}
-
-template <int N, int I, bool FIRST>
-__device__ __forceinline__ void fft_pass(float2 (&v)[16], const float2 *src, float2 *dst, int tau,
-                                         const float2 (&tw0)[15], const float2 *twr) {
-  using PL = Plan<N>;
-  constexpr int R = PL::radix(I);
-  constexpr int MI = PL::mi(I), MP = PL::mp(I);
-  constexpr bool LAST = (I == PL::NPASS - 1);
-  if constexpr (!FIRST) {
-#pragma unroll
-    for (int s = 0; s < 16 / R; ++s) {
-      const int d = tau + (N / 16) * s;
-      const int P = d / MP, j = d % MP;
-#pragma unroll
-      for (int a = 0; a < R; ++a) v[s * R + a] = src[padi(P * MI + a * MP + j)];
-    }
-  }
-#pragma unroll
-  for (int s = 0; s < 16 / R; ++s) dft_r<R>(&v[s * R]);
-  if constexpr (!LAST) {
-    static_assert(R == 16, "only the last pass may have a radix below 16");
-    if constexpr (I == 0) {
-#pragma unroll
-      for (int p = 1; p < 16; ++p) v[p] = cmul(v[p], tw0[p - 1]);
-    } else {
-      const int j = tau % MP;
-      const float2 *t = twr + (PL::tw_off(I) - 15 * (N / 16));
-#pragma unroll
-      for (int p = 1; p < 16; ++p) v[p] = cmul(v[p], t[(p - 1) * MP + j]);
-    }
-  }
-}
-
-template <int N, int I>
-__device__ __forceinline__ void store_pass(const float2 (&v)[16], float2 *dst, int tau) {
-  constexpr int NR = N / 16;
-#pragma unroll
-  for (int p = 0; p < 16; ++p) dst[padi(tau + p * NR)] = v[p];
-}
-
-// Exchange buffers: two (ping-pong, one barrier per pass) unless they would
-// not fit next to the input stages, then one (two barriers per pass).
-template <int N, bool TMA>
-struct Smem {
-  using PL = Plan<N>;
-  static constexpr size_t STAGE = TMA ? (size_t)PL::FPB * N : 0;   // complex in the input stage
-  static constexpr size_t XB = (size_t)PL::FPB * PL::SLOT;         // complex per exchange buffer
-  static constexpr size_t FIXED = (size_t)PL::TW_REST * 8 + 260 * 4;
-  static constexpr int NXB = (STAGE * 8 + 2 * XB * 8 + FIXED <= 113 * 1024) ? 2 : 1;
-  static constexpr size_t BYTES = STAGE * 8 + NXB * XB * 8 + FIXED;
-  static constexpr int BLOCKS = (BYTES <= 113 * 1024 && PL::THREADS <= 256) ? 2 : 1;  // per SM
-};
-
-// Frames [f_begin, f_end) of one capture: window, FFT, epilogue.  Returns
-// false (after recording ERR_INDEX) when a staged copy never arrived.
-template <int N, int MODE, bool TMA>
-__device__ __forceinline__ bool stft_frames(const StftArgs &a, int64_t f_begin, int64_t f_end,
-                                            float2 *smem, float *red, uint64_t *bar) {
-  using PL = Plan<N>;
-  using SM = Smem<N, TMA>;
-  constexpr int TPF = PL::TPF, FPB = PL::FPB, SLOT = PL::SLOT, NPASS = PL::NPASS, NXB = SM::NXB;
-  constexpr bool DO_MAX = (MODE == STFT_MAX || MODE == STFT_POWER);
-  constexpr bool DO_Q = (MODE == STFT_QUANT || MODE == STFT_QUANT_POWER);
-  constexpr bool DO_P = (MODE == STFT_POWER || MODE == STFT_QUANT_POWER);
-  float2 *stage = smem;                                   // [STAGE] (TMA only)
-  float2 *xb0 = smem + SM::STAGE;
-  float2 *xb1 = xb0 + (NXB == 2 ? SM::XB : 0);
-  float2 *twr = xb0 + NXB * SM::XB;
-  float *edges = reinterpret_cast<float *>(twr + PL::TW_REST);
-
-  const int tid = threadIdx.x;
-  const int slot = tid / TPF, tau = tid % TPF;
-  const int64_t nsteps = (f_end - f_begin + FPB - 1) / FPB;
-
-  auto step_bytes = [&](int64_t st) -> uint32_t {
-    const int64_t t0 = f_begin + st * FPB;
-    const int64_t nfr = (f_end - t0 < FPB) ? (f_end - t0) : (int64_t)FPB;
-    return (uint32_t)(((nfr - 1) * a.hop + N) * sizeof(float2));
-  };
-  // one input stage: the copy for step st+1 is issued as soon as every thread
-  // has its step-st samples in registers, and lands while step st computes
-  auto issue = [&](int64_t st) {
-    const int64_t t0 = f_begin + st * FPB;
-    const uint32_t bytes = step_bytes(st);
-    mbar_expect_tx(bar, bytes);
-    bulk_g2s(stage, a.iq + t0 * (int64_t)a.hop, bytes, bar);
-  };
-  if constexpr (TMA) {
-    if (tid == 0) {
-      mbar_init(bar, 1);
-      mbar_fence_init();
-      fence_proxy_async();   // earlier generic reads of the stage come first
-      if (nsteps > 0) issue(0);
-    }
-  }
-
-  float win[16];
-  float2 tw0[15];
-#pragma unroll
-  for (int i = 0; i < 16; ++i) win[i] = __ldg(&a.win[i * (N / 16) + tau]);
-#pragma unroll
-  for (int p = 1; p < 16; ++p) tw0[p - 1] = __ldg(&a.tw[(p - 1) * (N / 16) + tau]);
-  for (int i = tid; i < PL::TW_REST; i += PL::THREADS) twr[i] = a.tw[15 * (N / 16) + i];
-  float inv_anchor = 0.f, c1 = 0.f;
-  if constexpr (DO_Q) {
-    for (int i = tid; i < 257; i += PL::THREADS) edges[i] = a.edges[i];
-    inv_anchor = a.qconst[0];
-    c1 = a.qconst[1];
-  }
-  __syncthreads();
-
-  float run_max = 0.0f;
-  int parity = 0;
-  bool failed = false;
-  for (int64_t st = 0; st < nsteps; ++st, parity ^= (NXB == 2 && (NPASS & 1) == 0)) {
-    const int64_t t0 = f_begin + st * FPB;
-    const int64_t t = t0 + slot;
-    const bool valid = t < f_end;
-    float2 v[16];
-    if constexpr (TMA) {
-      if (!mbar_wait(bar, (uint32_t)(st & 1))) failed = true;
-      const float2 *x = stage + (valid ? slot * a.hop : 0) + tau;
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const float2 s = valid ? x[i * (N / 16)] : make_float2(0.f, 0.f);
-        v[i] = make_float2(s.x * win[i], s.y * win[i]);
-      }
-    } else {
-      const float2 *x = a.iq + (valid ? t * (int64_t)a.hop : 0) + tau;
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const float2 s = valid ? __ldg(x + i * (N / 16)) : make_float2(0.f, 0.f);
-        v[i] = make_float2(s.x * win[i], s.y * win[i]);
-      }
-    }
-    float2 *b0 = (parity ? xb1 : xb0) + slot * SLOT;
-    float2 *b1 = (parity ? xb0 : xb1) + slot * SLOT;
-    if constexpr (NXB == 1) __syncthreads();   // previous frame's last reads done
-    fft_pass<N, 0, true>(v, nullptr, b0, tau, tw0, twr);
-    store_pass<N, 0>(v, b0, tau);
-    if (__syncthreads_or(failed)) {
-      // a staged copy never arrived: record it, let copies in flight land, leave
-      if (tid == 0) {
-        atomicOr(a.err, ERR_INDEX);
-        if constexpr (TMA) mbar_wait(bar, (uint32_t)(st & 1));
-      }
-      return false;
-    }
-    if constexpr (TMA) {
-      if (tid == 0 && st + 1 < nsteps) {
-        fence_proxy_async();   // generic reads of the stage are ordered before the async write
-        issue(st + 1);
-      }
-    }
-    if constexpr (NPASS >= 2) {
-      fft_pass<N, 1, false>(v, b0, b1, tau, tw0, twr);
-      if constexpr (NPASS >= 3) {
-        if constexpr (NXB == 1) __syncthreads();
-        store_pass<N, 1>(v, b1, tau);
-        __syncthreads();
-        fft_pass<N, 2, false>(v, b1, b0, tau, tw0, twr);
-        if constexpr (NPASS >= 4) {
-          if constexpr (NXB == 1) __syncthreads();
-          store_pass<N, 2>(v, b0, tau);
-          __syncthreads();
-          fft_pass<N, 3, false>(v, b0, b1, tau, tw0, twr);
-        }
-      }
-    }
-    if (valid) {
-      constexpr int R = PL::radix(NPASS - 1);
-      uint8_t *qrow = DO_Q ? a.img + t * (int64_t)N : nullptr;
-      float *prow = DO_P ? a.power + t * (int64_t)N : nullptr;
-#pragma unroll
-      for (int s = 0; s < 16 / R; ++s) {
-#pragma unroll
-        for (int p = 0; p < R; ++p) {
-          const int k = tau + (N / 16) * s + (N / R) * p;
-          const int f = (k + N / 2) & (N - 1);
-          const float2 z = v[s * R + p];
-          const float P = fmaf(z.x, z.x, z.y * z.y);
-          if constexpr (DO_MAX) run_max = fmaxf(run_max, P);
-          if constexpr (DO_P) prow[f] = P;
-          if constexpr (DO_Q) qrow[f] = (uint8_t)level_of(P, inv_anchor, c1, edges);
-        }
-      }
-    }
-  }
-  if constexpr (DO_MAX) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) run_max = fmaxf(run_max, __shfl_xor_sync(0xffffffffu, run_max, o));
-    if ((tid & 31) == 0) red[tid >> 5] = run_max;
-    __syncthreads();
-    if (tid == 0) {
-      float m = 0.f;
-      for (int w = 0; w < PL::THREADS / 32; ++w) m = fmaxf(m, red[w]);
-      atomicMax(a.max_bits, __float_as_uint(m));   // P >= 0: bit order = value order
-    }
-  }
-  return true;
-}
-
-template <int N, int MODE, bool TMA>
-__global__ void __launch_bounds__(Plan<N>::THREADS, (Smem<N, TMA>::BLOCKS))
-stft_kernel(StftArgs a, int64_t frames_per_block) {
-  extern __shared__ __align__(128) float2 smem[];
-  __shared__ float red[32];
-  __shared__ __align__(8) uint64_t bar;
-  const int64_t f_begin = (int64_t)blockIdx.x * frames_per_block;
-  const int64_t f_end = min(a.T, f_begin + frames_per_block);
-  stft_frames<N, MODE, TMA>(a, f_begin, f_end, smem, red, &bar);
-}
-
-// Many captures of one FFT size in one launch: a persistent grid whose
-// blocks take (capture, frame range) items from a shared counter until none
-// are left, so uneven captures balance across the SMs.  Items come sorted by
-// size, largest first.
-template <int N, int MODE, bool TMA>
-__global__ void __launch_bounds__(Plan<N>::THREADS, (Smem<N, TMA>::BLOCKS))
-stft_batch_kernel(const StftArgs *segs, const StftItem *items, int n_items, int *counter) {
-  extern __shared__ __align__(128) float2 smem[];
-  __shared__ float red[32];
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ StftArgs sa;
-  __shared__ int s_item;
-  for (;;) {
-    if (threadIdx.x == 0) {
-      const int it = atomicAdd(counter, 1);
-      s_item = it;
-      if (it < n_items) sa = segs[items[it].seg];
-    }
-    __syncthreads();
-    const int it = s_item;
-    if (it >= n_items) return;
-    const StftItem item = items[it];
-    const bool ok = stft_frames<N, MODE, TMA>(sa, item.f0, item.f1, smem, red, &bar);
-    if (!ok) return;   // uniform over the block
-    __syncthreads();   // every wait on the barrier and every read of sa is done
-    if (TMA && threadIdx.x == 0) mbar_inval(&bar);
-  }
-}
-
-template <int N, int MODE, bool TMA>
-cudaError_t launch_n(const StftArgs &a, int num_sms, cudaStream_t s) {
-  using PL = Plan<N>;
-  auto kern = stft_kernel<N, MODE, TMA>;
-  const size_t sm = Smem<N, TMA>::BYTES;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, PL::THREADS, sm);
-  if (e != cudaSuccess) return e;
-  if (occ < 1) occ = 1;
-  const int64_t steps = (a.T + PL::FPB - 1) / PL::FPB;
-  int64_t grid = std::min<int64_t>(steps, (int64_t)num_sms * occ);
-  if (grid < 1) grid = 1;
-  int64_t per = (steps + grid - 1) / grid * PL::FPB;
-  grid = (a.T + per - 1) / per;
-  kern<<<(unsigned)grid, PL::THREADS, sm, s>>>(a, per);
-  count_launches(1);
-  return cudaGetLastError();
-}
-
-template <int N, bool TMA>
-cudaError_t launch_mode(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s) {
-  switch (mode) {
-    case STFT_MAX: return launch_n<N, STFT_MAX, TMA>(a, num_sms, s);
-    case STFT_QUANT: return launch_n<N, STFT_QUANT, TMA>(a, num_sms, s);
-    case STFT_POWER: return launch_n<N, STFT_POWER, TMA>(a, num_sms, s);
-    case STFT_QUANT_POWER: return launch_n<N, STFT_QUANT_POWER, TMA>(a, num_sms, s);
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <int N, int MODE, bool TMA>
-cudaError_t launch_batch_n(const StftArgs *segs, const StftItem *items, int n_items, int *counter,
-                           int num_sms, cudaStream_t s) {
-  using PL = Plan<N>;
-  auto kern = stft_batch_kernel<N, MODE, TMA>;
-  const size_t sm = Smem<N, TMA>::BYTES;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, PL::THREADS, sm);
-  if (e != cudaSuccess) return e;
-  if (occ < 1) occ = 1;
-  const int grid = (int)std::min<int64_t>(n_items, (int64_t)num_sms * occ);
-  if (grid < 1) return cudaSuccess;
-  kern<<<grid, PL::THREADS, sm, s>>>(segs, items, n_items, counter);
-  count_launches(1);
-  return cudaGetLastError();
-}
-
-template <int N, bool TMA>
-cudaError_t batch_mode(StftMode mode, const StftArgs *segs, const StftItem *items, int n_items,
-                       int *counter, int num_sms, cudaStream_t s) {
-  switch (mode) {
-    case STFT_MAX: return launch_batch_n<N, STFT_MAX, TMA>(segs, items, n_items, counter, num_sms, s);
-    case STFT_QUANT: return launch_batch_n<N, STFT_QUANT, TMA>(segs, items, n_items, counter, num_sms, s);
-    case STFT_POWER: return launch_batch_n<N, STFT_POWER, TMA>(segs, items, n_items, counter, num_sms, s);
-    case STFT_QUANT_POWER:
-      return launch_batch_n<N, STFT_QUANT_POWER, TMA>(segs, items, n_items, counter, num_sms, s);
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <int N>
-cudaError_t batch_size(bool tma, StftMode mode, const StftArgs *segs, const StftItem *items,
-                       int n_items, int *counter, int num_sms, cudaStream_t s) {
-  return tma ? batch_mode<N, true>(mode, segs, items, n_items, counter, num_sms, s)
-             : batch_mode<N, false>(mode, segs, items, n_items, counter, num_sms, s);
-}
-
-template <int N>
-cudaError_t launch_size(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s) {
-  // staged input needs every copy 16-byte aligned: an even hop and a 16-byte aligned base
-  const bool tma = (a.hop % 2 == 0) && ((reinterpret_cast<uintptr_t>(a.iq) & 15) == 0);
-  return tma ? launch_mode<N, true>(a, mode, num_sms, s) : launch_mode<N, false>(a, mode, num_sms, s);
-}
 
 // Edges of the 8-bit levels: level j >= 1 is reached at power
 // anchor * 10^((j - 255.5) * level_db / 10); ratio[j] holds the power of ten
@@ -598,15 +102,8 @@ void stft_fill_tables(int N, float2 *tw, float *win) {
 }
 
 cudaError_t launch_stft(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s) {
-  switch (a.N) {
-    case 256: return launch_size<256>(a, mode, num_sms, s);
-    case 512: return launch_size<512>(a, mode, num_sms, s);
-    case 1024: return launch_size<1024>(a, mode, num_sms, s);
-    case 2048: return launch_size<2048>(a, mode, num_sms, s);
-    case 4096: return launch_size<4096>(a, mode, num_sms, s);
-    case 8192: return launch_size<8192>(a, mode, num_sms, s);
-  }
-  return cudaErrorInvalidValue;
+  return a.fmt == IQ_SC16 ? launch_stft_sc16(a, mode, num_sms, s)
+                          : launch_stft_in<float2>(a, mode, num_sms, s);
 }
 
 cudaError_t launch_stft_batch(int N, bool tma, StftMode mode, const StftArgs *segs,

@@ -1,0 +1,11 @@
+// STFT launches for 16-bit integer I/Q (sc16) input, in a translation unit of
+// their own so that the two input types compile in parallel.
+#include "stft_impl.cuh"
+
+namespace rise {
+
+cudaError_t launch_stft_sc16(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s) {
+  return launch_stft_in<short2>(a, mode, num_sms, s);
+}
+
+}  // namespace rise

@@ -31,6 +31,7 @@ STAGES = ("spectrum_pass1", "spectrum_pass2", "histogram", "column_stats", "morp
           "labelling", "readback", "total")
 OPT_KEEP_POWER, OPT_KEEP_MASKS, OPT_TIMING, OPT_RANGE_PATH = 1, 2, 3, 4
 OPT_GRAPH, OPT_AUTOTUNE, OPT_RUN_CAPACITY = 5, 6, 7
+IQ_HOST, IQ_SC16 = 1, 2
 OPT_BATCH_GRAPH = OPT_GRAPH
 BATCH_MAX_ROWS = 524280
 BOX_COLS = ("t0", "t1", "f0", "f1", "anchor", "area", "sum_q", "energy_fx")
@@ -300,19 +301,36 @@ class Detector:
     # -- asynchronous calls ---------------------------------------------------
     def submit(self, iq, fft_size: int, hop: int, thr: Optional[Thresholds] = None,
                cap: Optional[int] = None):
-        """Queues a capture (rise_submit): a CUDA complex64 tensor, or a host one
-        (pinned tensor or numpy array), kept referenced until collected."""
+        """Queues a capture (rise_submit), kept referenced until collected: a
+        complex64 tensor or array (1-D), or 16-bit integer I/Q (sc16) as an
+        int16 tensor or array of shape (n, 2); CUDA tensors are read in place,
+        host ones (pinned tensors copy fastest) are copied in."""
         t = self._torch
+        flags = 0
         if isinstance(iq, t.Tensor):
-            if iq.dtype != t.complex64 or not iq.is_contiguous() or iq.dim() != 1:
-                raise TypeError("iq must be a contiguous 1-D complex64 tensor")
-            ptr, n, host = iq.data_ptr(), iq.numel(), not iq.is_cuda
+            if not iq.is_contiguous():
+                raise TypeError("iq must be contiguous")
+            if iq.dtype == t.int16 and iq.dim() == 2 and iq.shape[1] == 2:
+                flags |= IQ_SC16
+                n = iq.shape[0]
+            elif iq.dtype == t.complex64 and iq.dim() == 1:
+                n = iq.numel()
+            else:
+                raise TypeError("iq must be complex64 [n] or int16 [n, 2]")
+            ptr = iq.data_ptr()
+            if not iq.is_cuda:
+                flags |= IQ_HOST
         else:
-            iq = np.ascontiguousarray(iq, dtype=np.complex64)
-            ptr, n, host = iq.ctypes.data, iq.shape[0], True
+            iq = np.ascontiguousarray(iq)
+            if iq.dtype == np.int16 and iq.ndim == 2 and iq.shape[1] == 2:
+                flags |= IQ_SC16
+            elif iq.dtype != np.complex64 or iq.ndim != 1:
+                iq = np.ascontiguousarray(iq, dtype=np.complex64)
+            ptr, n = iq.ctypes.data, iq.shape[0]
+            flags |= IQ_HOST
         cap = self.cap if cap is None else int(cap)
         self._order()
-        rc = lib().rise_submit(self._h, C.c_void_p(ptr), int(host), n, fft_size, hop,
+        rc = lib().rise_submit(self._h, C.c_void_p(ptr), flags, n, fft_size, hop,
                                C.byref(thr) if thr is not None else None, cap)
         if rc != RISE_OK:
             raise RiseError(rc, "rise_submit")
