@@ -227,6 +227,16 @@ int rise_detect_batch(rise_ctx *ctx, const rise_capture *caps, int ncap,
  * whose carried + new samples hold no full frame yields no frames and no
  * boxes and carries everything forward.
  *
+ * Window mode (window_frames = W > 0) follows the real-time design of
+ * Sec. IV-D: the stream's frames are cut into consecutive TF plots of W
+ * frames (plot w = frames [w W, (w + 1) W), samples [w W hop, w W hop +
+ * (W - 1) hop + fft_size)), and every plot is detected as soon as the chunk
+ * that completes it arrives; chunks may have any length.  Results are one
+ * per plot: seq = plot number, first_frame = w W, frames = W, tag and
+ * t_submit_ns those of the completing chunk (its latency against the plot
+ * deadline W hop / fs is t_done_ns - t_submit_ns); a chunk that completes
+ * no plot gives no result.
+ *
  * Memory admission: every chunk in flight holds a device slot of
  * (max_chunk + fft_size) samples; the slot pool and the lanes' scratch are
  * sized to fit mem_budget, and chunks wait in the queue until a slot frees.
@@ -244,6 +254,8 @@ typedef struct {
   int max_pending;        /* queued chunks before RISE_EAGAIN (0: 4096)           */
   size_t mem_budget;      /* device bytes for slots + lane scratch (0: no cap)    */
   const rise_thresholds *thr; /* NULL: defaults; copied at create                 */
+  int64_t window_frames;  /* 0: detect each chunk (its complete frames); W > 0:   *
+                           * window mode, detect TF plots of W frames             */
 } rise_server_config;
 
 typedef struct {
@@ -267,7 +279,8 @@ int rise_server_create(rise_server **out, const rise_server_config *cfg);
 
 /* Queues n samples (complex64, host memory; pinned memory copies fastest)
  * for stream `stream`.  The buffer must stay valid and unchanged until the
- * chunk's result has been returned by rise_server_poll.  Chunks of one
+ * chunk's result has been returned by rise_server_poll (window mode, where a
+ * chunk may complete no plot: until rise_server_drain has returned).  Chunks of one
  * stream are processed in submission order.  Errors: RISE_EINVAL (bad
  * stream, n < 1 or n > max_chunk), RISE_EAGAIN (queue full). */
 int rise_stream_submit(rise_server *s, int stream, const void *iq_host, int64_t n, uint64_t tag);

@@ -8,7 +8,14 @@
 //
 // Streams are continuous across chunks: the samples a chunk leaves unused
 // (from its last frame start on, fewer than N) stay on the device in the
-// stream's carry buffer and are put in front of the next chunk.  The carry
+// stream's carry buffer and are put in front of the next chunk.
+//
+// Window mode (window_frames = W > 0) detects fixed TF plots of W frames, as
+// the real-time design of Sec. IV-D does with its T-row ping-pong buffer:
+// the samples of a stream accumulate across chunks, every W consecutive
+// frames form one plot, and each complete plot is detected (its STFT
+// included) as soon as the chunk that completes it arrives; what is left
+// (fewer than W frames) is carried.  Results are then one per plot.  The carry
 // update of one chunk and the carry read of the next are ordered by an event
 // when they run on different lanes; the dispatch of chunks (slot
 // assignment, copies, carry update) happens under the server lock, so the
@@ -43,10 +50,11 @@ struct Chunk {
 };
 
 struct StreamState {
-  float2 *carry = nullptr;      // device, N samples
+  float2 *carry = nullptr;      // device: N samples, or a plot's span in window mode
   int64_t carry_len = 0;
   int64_t next_seq = 0;
   int64_t next_frame = 0;
+  int64_t next_window = 0;      // window mode: number of the next plot
   int64_t busy = 0;             // chunks queued or in flight
   cudaEvent_t ready = nullptr;  // the last carry update
   bool has_event = false;
@@ -65,8 +73,8 @@ struct Lane {
 constexpr uint32_t kStateMagic = 0x52534531u;   // stream state blob, version 1
 struct StateHeader {
   uint32_t magic;
-  int32_t fft_size, hop, pad;
-  int64_t carry_len, next_seq, next_frame;
+  int32_t fft_size, hop, window;
+  int64_t carry_len, next_seq, next_frame, next_window;
 };
 
 }  // namespace
@@ -76,6 +84,9 @@ struct rise_server {
   int N = 0, hop = 0;
   int64_t max_chunk = 0;
   int max_batch = 32, max_pending = 4096;
+  int64_t window = 0;     // frames per plot in window mode, else 0
+  int64_t span = 0;       // samples of one plot: (window - 1) * hop + N
+  int64_t carry_cap = 0;  // samples a stream's carry buffer holds
   rise_thresholds thr;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -101,7 +112,9 @@ void lane_main(rise_server *s, int li) {
     Chunk ch;
     int slot;
     int64_t first_frame, frames;
-    int cap_index;      // index in caps, -1 when the chunk holds no frame
+    int cap_index;      // index in caps, -1 when the chunk holds no frame (no plot)
+    int64_t n_windows;  // window mode: plots the chunk completes
+    int64_t first_window;
   };
   std::vector<Item> items;
   std::vector<rise_capture> caps;
@@ -127,21 +140,39 @@ void lane_main(rise_server *s, int li) {
         cudaMemcpyAsync(dst, st.carry, st.carry_len * sizeof(float2), cudaMemcpyDeviceToDevice, cs);
       cudaMemcpyAsync(dst + st.carry_len, it.ch.host, it.ch.n * sizeof(float2), cudaMemcpyHostToDevice, cs);
       const int64_t len = st.carry_len + it.ch.n;
-      const int64_t T = len >= s->N ? (len - s->N) / s->hop + 1 : 0;
-      const int64_t keep = len - T * s->hop;   // from the next frame start on: < N samples
+      it.cap_index = -1;
+      it.n_windows = 0;
+      it.first_window = st.next_window;
+      int64_t used;   // samples before the first one the next unit needs
+      if (s->window == 0) {
+        const int64_t T = len >= s->N ? (len - s->N) / s->hop + 1 : 0;
+        used = T * s->hop;   // the rest, from the next frame start on, is < N samples
+        it.first_frame = st.next_frame;
+        it.frames = T;
+        st.next_frame += T;
+        if (T > 0) {
+          it.cap_index = (int)caps.size();
+          caps.push_back(rise_capture{dst, len, s->N, s->hop});
+        }
+      } else {
+        // every complete plot of W frames: samples [j W hop, j W hop + span)
+        const int64_t step = s->window * s->hop;
+        const int64_t k = len >= s->span ? 1 + (len - s->span) / step : 0;
+        used = k * step;     // the rest holds fewer than W frames: < span samples
+        it.first_frame = st.next_frame;
+        it.frames = k * s->window;
+        st.next_frame += k * s->window;
+        it.n_windows = k;
+        st.next_window += k;
+        if (k > 0) it.cap_index = (int)caps.size();
+        for (int64_t j = 0; j < k; ++j) caps.push_back(rise_capture{dst + j * step, s->span, s->N, s->hop});
+      }
+      const int64_t keep = len - used;
       if (keep)
-        cudaMemcpyAsync(st.carry, dst + T * s->hop, keep * sizeof(float2), cudaMemcpyDeviceToDevice, cs);
+        cudaMemcpyAsync(st.carry, dst + used, keep * sizeof(float2), cudaMemcpyDeviceToDevice, cs);
       cudaEventRecord(st.ready, cs);
       st.has_event = true;
       st.carry_len = keep;
-      it.first_frame = st.next_frame;
-      it.frames = T;
-      st.next_frame += T;
-      it.cap_index = -1;
-      if (T > 0) {
-        it.cap_index = (int)caps.size();
-        caps.push_back(rise_capture{dst, len, s->N, s->hop});
-      }
       items.push_back(it);
     }
     s->running += (int64_t)items.size();
@@ -169,23 +200,27 @@ void lane_main(rise_server *s, int li) {
 
     lk.lock();
     for (const Item &it : items) {
-      Done d;
-      std::memset(&d.r, 0, sizeof(d.r));
-      d.r.stream = it.ch.stream;
-      d.r.status = rc;
-      d.r.tag = it.ch.tag;
-      d.r.seq = it.ch.seq;
-      d.r.first_frame = it.first_frame;
-      d.r.frames = it.frames;
-      d.r.t_submit_ns = it.ch.t_submit;
-      d.r.t_start_ns = t_start;
-      d.r.t_done_ns = t_done;
-      if (rc == RISE_OK && it.cap_index >= 0) {
-        const int64_t b0 = offs[it.cap_index], b1 = offs[it.cap_index + 1];
-        d.boxes.assign(boxes.begin() + b0, boxes.begin() + b1);
+      // chunk mode: one result per chunk; window mode: one per completed plot
+      const int64_t nres = s->window == 0 ? 1 : it.n_windows;
+      for (int64_t j = 0; j < nres; ++j) {
+        Done d;
+        std::memset(&d.r, 0, sizeof(d.r));
+        d.r.stream = it.ch.stream;
+        d.r.status = rc;
+        d.r.tag = it.ch.tag;
+        d.r.seq = s->window == 0 ? it.ch.seq : it.first_window + j;
+        d.r.first_frame = s->window == 0 ? it.first_frame : it.first_frame + j * s->window;
+        d.r.frames = s->window == 0 ? it.frames : s->window;
+        d.r.t_submit_ns = it.ch.t_submit;
+        d.r.t_start_ns = t_start;
+        d.r.t_done_ns = t_done;
+        if (rc == RISE_OK && it.cap_index >= 0) {
+          const int64_t b0 = offs[it.cap_index + j], b1 = offs[it.cap_index + j + 1];
+          d.boxes.assign(boxes.begin() + b0, boxes.begin() + b1);
+        }
+        d.r.n_boxes = (int64_t)d.boxes.size();
+        s->done.push_back(std::move(d));
       }
-      d.r.n_boxes = (int64_t)d.boxes.size();
-      s->done.push_back(std::move(d));
       s->free_slots.push_back(it.slot);
       s->streams[it.ch.stream].busy -= 1;
     }
@@ -224,8 +259,12 @@ int rise_server_create(rise_server **out, const rise_server_config *cfg) {
   const int lanes = cfg->lanes > 0 ? cfg->lanes : 2;
   const int max_batch = cfg->max_batch > 0 ? cfg->max_batch : 32;
   if (lanes > 64 || max_batch > 4096) return RISE_EINVAL;
-  const int64_t max_len = cfg->max_chunk + N;           // carried + new samples
-  if ((max_len - N) / hop + 1 > RISE_BATCH_MAX_ROWS) return RISE_EINVAL;
+  const int64_t window = cfg->window_frames;
+  if (window < 0 || window > RISE_BATCH_MAX_ROWS) return RISE_EINVAL;
+  const int64_t span = window ? (window - 1) * (int64_t)hop + N : 0;
+  const int64_t carry_cap = window ? span : N;           // the carry is always shorter
+  const int64_t max_len = cfg->max_chunk + carry_cap;    // carried + new samples
+  if ((max_len - N) / hop + 1 > RISE_BATCH_MAX_ROWS && window == 0) return RISE_EINVAL;
   rise_thresholds thr;
   if (cfg->thr) thr = *cfg->thr;
   else rise_thresholds_default(&thr);
@@ -253,13 +292,16 @@ int rise_server_create(rise_server **out, const rise_server_config *cfg) {
   s->N = N;
   s->hop = hop;
   s->max_chunk = cfg->max_chunk;
+  s->window = window;
+  s->span = span;
+  s->carry_cap = carry_cap;
   s->max_batch = max_batch;
   s->max_pending = cfg->max_pending > 0 ? cfg->max_pending : 4096;
   s->thr = thr;
   int rc = RISE_OK;
   s->streams.resize(cfg->max_streams);
   for (auto &st : s->streams) {
-    if (cudaMalloc(&st.carry, (size_t)N * sizeof(float2)) != cudaSuccess) { rc = RISE_ENOMEM; break; }
+    if (cudaMalloc(&st.carry, (size_t)carry_cap * sizeof(float2)) != cudaSuccess) { rc = RISE_ENOMEM; break; }
     if (cudaEventCreateWithFlags(&st.ready, cudaEventDisableTiming) != cudaSuccess) { rc = RISE_ECUDA; break; }
   }
   for (int64_t k = 0; k < slots && rc == RISE_OK; ++k) {
@@ -352,7 +394,8 @@ int rise_stream_export(rise_server *s, int stream, void *buf, size_t bytes, size
   if (need) *need = total;
   if (!buf) return RISE_OK;
   if (st.busy != 0 || bytes < total) return RISE_EINVAL;
-  StateHeader h{kStateMagic, s->N, s->hop, 0, st.carry_len, st.next_seq, st.next_frame};
+  StateHeader h{kStateMagic, s->N, s->hop, (int32_t)s->window, st.carry_len, st.next_seq,
+                st.next_frame, st.next_window};
   std::memcpy(buf, &h, sizeof h);
   cudaSetDevice(s->device);
   if (st.has_event && cudaEventSynchronize(st.ready) != cudaSuccess) return RISE_ECUDA;
@@ -368,8 +411,9 @@ int rise_stream_import(rise_server *s, int stream, const void *buf, size_t bytes
     return RISE_EINVAL;
   StateHeader h;
   std::memcpy(&h, buf, sizeof h);
-  if (h.magic != kStateMagic || h.fft_size != s->N || h.hop != s->hop || h.carry_len < 0 ||
-      h.carry_len >= s->N || bytes < sizeof h + (size_t)h.carry_len * sizeof(float2))
+  if (h.magic != kStateMagic || h.fft_size != s->N || h.hop != s->hop || h.window != s->window ||
+      h.carry_len < 0 || h.carry_len >= s->carry_cap ||
+      bytes < sizeof h + (size_t)h.carry_len * sizeof(float2))
     return RISE_EINVAL;
   std::lock_guard<std::mutex> lk(s->mu);
   StreamState &st = s->streams[stream];
@@ -383,6 +427,7 @@ int rise_stream_import(rise_server *s, int stream, const void *buf, size_t bytes
   st.carry_len = h.carry_len;
   st.next_seq = h.next_seq;
   st.next_frame = h.next_frame;
+  st.next_window = h.next_window;
   st.has_event = false;
   return RISE_OK;
 }

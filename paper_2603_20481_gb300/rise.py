@@ -70,7 +70,7 @@ class ServerConfig(C.Structure):
     _fields_ = [("device", C.c_int), ("fft_size", C.c_int), ("hop", C.c_int),
                 ("max_chunk", C.c_int64), ("max_streams", C.c_int), ("lanes", C.c_int),
                 ("max_batch", C.c_int), ("max_pending", C.c_int), ("mem_budget", C.c_size_t),
-                ("thr", C.c_void_p)]
+                ("thr", C.c_void_p), ("window_frames", C.c_int64)]
 
 
 class Result(C.Structure):
@@ -469,11 +469,13 @@ class Server:
 
     def __init__(self, fft_size: int, hop: int, max_chunk: int, max_streams: int,
                  device: int = 0, lanes: int = 0, max_batch: int = 0, max_pending: int = 0,
-                 mem_budget: int = 0, thr: Optional[Thresholds] = None):
+                 mem_budget: int = 0, thr: Optional[Thresholds] = None, window_frames: int = 0):
         self._thr = thr
+        self.window = window_frames
         cfg = ServerConfig(device, fft_size, hop, max_chunk, max_streams, lanes, max_batch,
                            max_pending, mem_budget,
-                           C.cast(C.pointer(thr), C.c_void_p) if thr is not None else None)
+                           C.cast(C.pointer(thr), C.c_void_p) if thr is not None else None,
+                           window_frames)
         h = C.c_void_p()
         rc = lib().rise_server_create(C.byref(h), C.byref(cfg))
         if rc != RISE_OK:
@@ -540,13 +542,16 @@ class Server:
             d = {f[0]: getattr(r, f[0]) for f in Result._fields_}
             b = self._arena[r.box_offset:r.box_offset + r.n_boxes]
             out.append((d, boxes_from_raw(b, r.n_boxes)))
-            self._held.pop((r.stream, r.seq), None)
+            if not self.window:   # window mode: results are per plot; buffers go at drain()
+                self._held.pop((r.stream, r.seq), None)
         return out
 
     def drain(self, timeout_ms: int = -1):
         rc = lib().rise_server_drain(self._h, timeout_ms)
         if rc != RISE_OK:
             raise RiseError(rc, "rise_server_drain")
+        if self.window:
+            self._held.clear()
 
     def export_stream(self, stream: int) -> bytes:
         need = C.c_size_t(0)

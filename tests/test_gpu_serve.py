@@ -138,3 +138,46 @@ def test_backpressure_and_bad_arguments():
             srv.submit(0, big)                                # longer than max_chunk
     with pytest.raises(rise.RiseError):
         rise.Server(1000, 500, max_chunk=8192, max_streams=1)   # FFT size not a power of two
+
+
+def _serve_windows(chunks, order, W, **kw):
+    import torch
+    from paper_2603_20481_gb300 import rise
+    pinned = {s: [torch.from_numpy(c).pin_memory() for c in cs] for s, cs in chunks.items()}
+    res = {}
+    with rise.Server(N, HOP, max_chunk=max(len(c) for cs in chunks.values() for c in cs),
+                     max_streams=max(chunks) + 1, window_frames=W, **kw) as srv:
+        for s, k in order:
+            assert srv.submit(s, pinned[s][k], tag=1000 * s + k)
+        srv.drain()
+        for d, b in srv.poll(timeout_ms=100):
+            res[(d["stream"], d["seq"])] = (d, b)
+    return res
+
+
+def test_window_mode_plots_match_rise_detect(det):
+    """Plots of W frames cut across chunks of uneven length: plot w is
+    exactly rise_detect on samples [w W hop, w W hop + (W - 1) hop + N) of
+    the stream, alone or served interleaved with other streams."""
+    import torch
+    W = 37
+    rng = np.random.default_rng(11)
+    chunks = {}
+    for s in range(3):
+        full = synth.served_chunk(20 + s, 0, n=180000).iq
+        cuts = np.sort(rng.choice(np.arange(1, full.shape[0]), size=6, replace=False))
+        chunks[s] = np.split(full, cuts)                       # 7 chunks, uneven
+    span = (W - 1) * HOP + N
+    for order, kw in (([(s, k) for s in chunks for k in range(7)], dict(lanes=1, max_batch=1)),
+                      ([(s, k) for k in range(7) for s in chunks], dict(lanes=3, max_batch=8))):
+        res = _serve_windows(chunks, order, W, **kw)
+        for s, cs in chunks.items():
+            full = np.concatenate(cs)
+            n_plots = (full.shape[0] - span) // (W * HOP) + 1
+            assert sum(1 for key in res if key[0] == s) == n_plots
+            for w in range(n_plots):
+                d, b = res[(s, w)]
+                assert d["first_frame"] == w * W and d["frames"] == W
+                x = full[w * W * HOP: w * W * HOP + span]
+                np.testing.assert_array_equal(b, det.detect(torch.from_numpy(x).cuda(), N, HOP),
+                                              err_msg=f"stream {s} plot {w}")
