@@ -67,6 +67,7 @@ def lib():
             "ro_ccl_boxes": (i32, [P, P, i64, i32, dbl, P, i64, P]),
             "ro_detect_image": (i32, [P, i64, i32, P, P, i64, P, P, P, P, P]),
             "ro_detect": (i32, [P, i64, i32, i32, P, P, i64, P, P, P]),
+            "ro_match": (i32, [P, i64, P, i64, P, i32, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -283,3 +284,21 @@ def detect(iq: np.ndarray, N: int, hop: int, prm: Optional[Params] = None):
 def hi_db_of(max_power: float) -> float:
     """Anchor of the 8-bit range for a capture whose largest |X|^2 is max_power."""
     return 10.0 * math.log10(max_power) if max_power > 0 else -math.inf
+
+
+def match(gt: np.ndarray, det: np.ndarray, thetas) -> Dict:
+    """Detection quality (Sec. III-A-2, Eqs. 2-3) of detections against ground
+    truth: boxes as (t0, t1, f0, f1) inclusive rows (extra columns ignored).
+    Returns n_t, n_f per threshold, P_d = n_t / N_gt, P_fa = n_f / N_d, and the
+    best (intersection, union) pair of every box."""
+    g = np.ascontiguousarray(np.asarray(gt)[:, :4], dtype=np.int32).reshape(-1, 4)
+    d = np.ascontiguousarray(np.asarray(det)[:, :4], dtype=np.int32).reshape(-1, 4)
+    th = np.ascontiguousarray(np.asarray(thetas, dtype=np.float64).reshape(-1))
+    nt = np.zeros(th.shape[0], np.int64)
+    nf = np.zeros(th.shape[0], np.int64)
+    gb = np.zeros((g.shape[0], 2), np.int64)
+    db = np.zeros((d.shape[0], 2), np.int64)
+    _check(lib().ro_match(_p(g), g.shape[0], _p(d), d.shape[0], _p(th), th.shape[0], _p(nt), _p(nf),
+                          _p(gb), _p(db)), "match")
+    return {"n_t": nt, "n_f": nf, "gt_best": gb, "det_best": db,
+            "p_d": nt / max(1, g.shape[0]), "p_fa": nf / max(1, d.shape[0])}

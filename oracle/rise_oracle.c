@@ -507,3 +507,70 @@ int ro_detect(const float *iq, int64_t n, int N, int hop, const ro_params *p, ro
   free(row);
   return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Detection quality (Sec. III-A-2, Eqs. 2 and 3): IoU of two boxes over TF  */
+/* cells; every ground-truth box's best IoU over the detections and every   */
+/* detection's best IoU over the ground truth, by exhaustive pairs; N_t =    */
+/* boxes of the ground truth whose best IoU exceeds theta, N_f = detections  */
+/* whose best IoU is below theta (IoU equal to theta counts as neither).     */
+/* ------------------------------------------------------------------------ */
+
+/* Boxes are int32 quadruples (t0, t1, f0, f1), inclusive cell ranges. */
+static int64_t ro_area(const int32_t *b) {
+  return ((int64_t)b[1] - b[0] + 1) * ((int64_t)b[3] - b[2] + 1);
+}
+
+static int64_t ro_overlap(const int32_t *a, const int32_t *b) {
+  int64_t t = (int64_t)(a[1] < b[1] ? a[1] : b[1]) - (a[0] > b[0] ? a[0] : b[0]) + 1;
+  int64_t f = (int64_t)(a[3] < b[3] ? a[3] : b[3]) - (a[2] > b[2] ? a[2] : b[2]) + 1;
+  return (t > 0 && f > 0) ? t * f : 0;
+}
+
+/* best[2 i], best[2 i + 1] = (intersection, union) of box i of A with the
+ * box of B of largest IoU (exact comparison of the fractions); (0, 1) when B
+ * is empty. */
+static void ro_best(const int32_t *A, int64_t na, const int32_t *B, int64_t nb, int64_t *best) {
+  for (int64_t i = 0; i < na; i++) {
+    int64_t bi = 0, bu = 1;
+    const int64_t aa = ro_area(A + 4 * i);
+    for (int64_t j = 0; j < nb; j++) {
+      const int64_t in = ro_overlap(A + 4 * i, B + 4 * j);
+      const int64_t un = aa + ro_area(B + 4 * j) - in;
+      if ((__int128)in * bu > (__int128)bi * un) {
+        bi = in;
+        bu = un;
+      }
+    }
+    best[2 * i] = bi;
+    best[2 * i + 1] = bu;
+  }
+}
+
+/* n_t[k], n_f[k] for the IoU thresholds theta[k] (Eq. 2); gt_best and
+ * det_best (optional) receive the best (intersection, union) pairs.  The
+ * decisions compare the intersection with theta * union in double. */
+int ro_match(const int32_t *gt, int64_t ng, const int32_t *det, int64_t nd, const double *theta,
+             int nth, int64_t *n_t, int64_t *n_f, int64_t *gt_best, int64_t *det_best) {
+  int64_t *gb = gt_best ? gt_best : malloc(sizeof(int64_t) * 2 * (ng > 0 ? ng : 1));
+  int64_t *db = det_best ? det_best : malloc(sizeof(int64_t) * 2 * (nd > 0 ? nd : 1));
+  if (!gb || !db) {
+    if (!gt_best) free(gb);
+    if (!det_best) free(db);
+    return RO_ENOMEM;
+  }
+  ro_best(gt, ng, det, nd, gb);
+  ro_best(det, nd, gt, ng, db);
+  for (int k = 0; k < nth; k++) {
+    int64_t t = 0, f = 0;
+    for (int64_t i = 0; i < ng; i++)
+      if ((double)gb[2 * i] > theta[k] * (double)gb[2 * i + 1]) t++;
+    for (int64_t j = 0; j < nd; j++)
+      if ((double)db[2 * j] < theta[k] * (double)db[2 * j + 1]) f++;
+    n_t[k] = t;
+    n_f[k] = f;
+  }
+  if (!gt_best) free(gb);
+  if (!det_best) free(db);
+  return RO_OK;
+}
