@@ -213,6 +213,29 @@ typedef struct {
 int rise_detect_batch(rise_ctx *ctx, const rise_capture *caps, int ncap,
                       const rise_thresholds *thr, rise_box *out, int64_t cap, int64_t *offsets);
 
+/* ---- detection quality ---------------------------------------------------- */
+/* Scores detections against ground truth as the paper does (Sec. III-A-2):
+ * the IoU of two boxes is |B n B'| / |B u B'| over TF cells; ground-truth box
+ * i is detected at threshold theta when its best IoU over the detections
+ * exceeds theta, detection j is false when its best IoU over the ground
+ * truth is below theta (Eq. 2; IoU equal to theta is neither), and
+ * P_d = n_t / n_gt, P_fa = n_f / n_det (Eq. 3).  Runs on the GPU: the best
+ * IoU of every box is computed exactly, as an (intersection, union) pair
+ * compared by 128-bit cross products; a box with nothing on the other side
+ * has (0, 1).  The decisions compare the intersection with theta * union in
+ * double.
+ *  gt       host int32 [n_gt][4] = t0, t1, f0, f1 (inclusive cell ranges)
+ *  det      host rise_box [n_det] (only t0, t1, f0, f1 are read)
+ *  thetas   host double [n_theta], each in [0, 1]; n_theta <= 65535
+ *  n_t, n_f host int64 [n_theta] outputs
+ *  gt_best, det_best  host int64 [n][2] (intersection, union) outputs, or NULL
+ * Synchronous, on the context's stream.  Errors: RISE_EINVAL (bad sizes,
+ * empty boxes, thresholds outside [0, 1], calls queued), RISE_ENOMEM,
+ * RISE_ECUDA. */
+int rise_match_boxes(rise_ctx *ctx, const int32_t *gt, int64_t n_gt, const rise_box *det,
+                     int64_t n_det, const double *thetas, int n_theta, int64_t *n_t, int64_t *n_f,
+                     int64_t *gt_best, int64_t *det_best);
+
 /* ---- serving ------------------------------------------------------------ */
 /* A server takes chunks of IQ from many radio streams as they arrive and
  * runs them through the path in batches (continuous batching): lane threads,

@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "librise.so")
-SOURCES = ["stft.cu", "stft_sc16.cu", "image.cu", "ccl.cu", "rise.cu", "batch.cu", "server.cu", "noalloc.cu"]
+SOURCES = ["stft.cu", "stft_sc16.cu", "image.cu", "ccl.cu", "rise.cu", "batch.cu", "server.cu",
+           "match.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

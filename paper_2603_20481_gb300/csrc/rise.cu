@@ -674,7 +674,8 @@ void rise_destroy(rise_ctx *c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   Buf *bufs[] = {&c->power, &c->img, &c->hist, &c->cols, &c->effm1, &c->mask,
                  &c->dbg[0], &c->dbg[1], &c->dbg[2], &c->row_cnt, &c->row_base,
-                 &c->run_parent, &c->run_sroot, &c->rec, &c->run_out, &c->scan_tmp, &c->boxes, &c->merge};
+                 &c->run_parent, &c->run_sroot, &c->rec, &c->run_out, &c->scan_tmp, &c->boxes, &c->merge,
+                 &c->match_boxes, &c->match_best, &c->match_misc};
   for (Buf *b : bufs)
     if (b->p) cudaFree(b->p);
   for (auto &kv : c->tables) cudaFree(kv.second.tw);

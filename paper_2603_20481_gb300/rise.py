@@ -40,7 +40,8 @@ BOX_COLS = ("t0", "t1", "f0", "f1", "anchor", "area", "sum_q", "energy_fx")
 EXPORTS = ("rise_thresholds_default", "rise_create", "rise_destroy", "rise_strerror",
            "rise_detect", "rise_detect_host", "rise_detect_image", "rise_debug_export",
            "rise_set_option", "rise_stage_times", "rise_column_stats_noalloc",
-           "rise_detect_batch", "rise_submit", "rise_collect", "rise_server_create", "rise_stream_submit", "rise_server_poll",
+           "rise_detect_batch", "rise_submit", "rise_collect", "rise_match_boxes",
+           "rise_server_create", "rise_stream_submit", "rise_server_poll",
            "rise_server_drain", "rise_stream_export", "rise_stream_import", "rise_server_stats",
            "rise_server_destroy")
 
@@ -129,6 +130,8 @@ def lib() -> C.CDLL:
     L.rise_submit.restype = i32
     L.rise_collect.argtypes = [P, P, i64, C.POINTER(i64)]
     L.rise_collect.restype = i32
+    L.rise_match_boxes.argtypes = [P, P, i64, P, i64, P, i32, P, P, P, P]
+    L.rise_match_boxes.restype = i32
     L.rise_detect_batch.argtypes = [P, P, i32, P, P, i64, P]
     L.rise_detect_batch.restype = i32
     L.rise_server_create.argtypes = [C.POINTER(P), P]
@@ -297,6 +300,29 @@ class Detector:
                 C.byref(thr) if thr is not None else None)
         self._order()
         return self._run(lib().rise_detect_host, args, cap)
+
+    def match(self, gt, det, thetas):
+        """Detection quality on the GPU (rise_match_boxes): gt and det are
+        arrays whose first four columns are t0, t1, f0, f1 (e.g. detect's
+        output).  Returns n_t, n_f, p_d, p_fa per threshold and the best
+        (intersection, union) pair of every box."""
+        g = np.ascontiguousarray(np.asarray(gt)[:, :4], dtype=np.int32).reshape(-1, 4)
+        d4 = np.asarray(det)[:, :4].reshape(-1, 4)
+        d = np.zeros(d4.shape[0], BOX_DTYPE)
+        for j, name in enumerate(("t0", "t1", "f0", "f1")):
+            d[name] = d4[:, j]
+        th = np.ascontiguousarray(np.asarray(thetas, dtype=np.float64).reshape(-1))
+        nt = np.zeros(th.shape[0], np.int64)
+        nf = np.zeros(th.shape[0], np.int64)
+        gb = np.zeros((g.shape[0], 2), np.int64)
+        db = np.zeros((d.shape[0], 2), np.int64)
+        rc = lib().rise_match_boxes(self._h, g.ctypes.data, g.shape[0], d.ctypes.data, d.shape[0],
+                                    th.ctypes.data, th.shape[0], nt.ctypes.data, nf.ctypes.data,
+                                    gb.ctypes.data, db.ctypes.data)
+        if rc != RISE_OK:
+            raise RiseError(rc, "rise_match_boxes")
+        return {"n_t": nt, "n_f": nf, "gt_best": gb, "det_best": db,
+                "p_d": nt / max(1, g.shape[0]), "p_fa": nf / max(1, d.shape[0])}
 
     # -- asynchronous calls ---------------------------------------------------
     def submit(self, iq, fft_size: int, hop: int, thr: Optional[Thresholds] = None,
