@@ -68,6 +68,9 @@ def lib():
             "ro_detect_image": (i32, [P, i64, i32, P, P, i64, P, P, P, P, P]),
             "ro_detect": (i32, [P, i64, i32, i32, P, P, i64, P, P, P]),
             "ro_match": (i32, [P, i64, P, i64, P, i32, P, P, P, P]),
+            "ro_label": (i32, [P, i64, i32, P]),
+            "ro_component_runs": (i32, [P, i64, i32, P, i64, P]),
+            "ro_boundary": (None, [P, i64, i32, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -302,3 +305,32 @@ def match(gt: np.ndarray, det: np.ndarray, thetas) -> Dict:
                           _p(gb), _p(db)), "match")
     return {"n_t": nt, "n_f": nf, "gt_best": gb, "det_best": db,
             "p_d": nt / max(1, g.shape[0]), "p_fa": nf / max(1, d.shape[0])}
+
+
+def label(mask: np.ndarray) -> np.ndarray:
+    """Component of every pixel (box order), -1 for background."""
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    T, F = m.shape
+    out = np.empty((T, F), np.int64)
+    _check(lib().ro_label(_p(m), T, F, _p(out)), "label")
+    return out
+
+
+def component_runs(mask: np.ndarray) -> np.ndarray:
+    """Foreground runs in raster order: int32 (n, 4) = component, row, first, last column."""
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    T, F = m.shape
+    cap = (T * F + 1) // 2 + 1
+    runs = np.empty((cap, 4), np.int32)
+    n = np.zeros(1, np.int64)
+    _check(lib().ro_component_runs(_p(m), T, F, _p(runs), cap, _p(n)), "component_runs")
+    return runs[: int(n[0])].copy()
+
+
+def boundary(mask: np.ndarray) -> np.ndarray:
+    """Foreground pixels with a background 4-neighbour (outside counts as background)."""
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    T, F = m.shape
+    out = np.empty((T, F), np.uint8)
+    lib().ro_boundary(_p(m), T, F, _p(out))
+    return out

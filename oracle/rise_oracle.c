@@ -574,3 +574,95 @@ int ro_match(const int32_t *gt, int64_t ng, const int32_t *det, int64_t nd, cons
   if (!det_best) free(db);
   return RO_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Block shapes (Sec. IV-B, bounding-box paragraph: the labelling stage can  */
+/* also give the blocks' boundaries): every foreground run with its         */
+/* component, and the boundary pixels.                                       */
+/* ------------------------------------------------------------------------ */
+
+/* label[p] = component of pixel p, numbered by first pixel in raster order
+ * (the box order), -1 for background; BFS flood fill with 4-neighbours. */
+int ro_label(const uint8_t *mask, int64_t T, int F, int64_t *label) {
+  const int64_t npx = T * (int64_t)F;
+  int64_t qcap = 1024, *queue = malloc(sizeof(int64_t) * qcap);
+  if (!queue) return RO_ENOMEM;
+  for (int64_t i = 0; i < npx; i++) label[i] = -1;
+  int64_t comp = 0;
+  for (int64_t i = 0; i < npx; i++) {
+    if (!mask[i] || label[i] >= 0) continue;
+    int64_t head = 0, tail = 0;
+    queue[tail++] = i;
+    label[i] = comp;
+    while (head < tail) {
+      const int64_t p = queue[head++];
+      const int64_t t = p / F, f = p % F;
+      int64_t nb[4];
+      int nn = 0;
+      if (t > 0) nb[nn++] = p - F;
+      if (t < T - 1) nb[nn++] = p + F;
+      if (f > 0) nb[nn++] = p - 1;
+      if (f < F - 1) nb[nn++] = p + 1;
+      for (int k = 0; k < nn; k++) {
+        if (!mask[nb[k]] || label[nb[k]] >= 0) continue;
+        label[nb[k]] = comp;
+        if (tail == qcap) {
+          memmove(queue, queue + head, sizeof(int64_t) * (tail - head));
+          tail -= head;
+          head = 0;
+          if (tail == qcap) {
+            int64_t *nq = realloc(queue, sizeof(int64_t) * qcap * 2);
+            if (!nq) { free(queue); return RO_ENOMEM; }
+            queue = nq;
+            qcap *= 2;
+          }
+        }
+        queue[tail++] = nb[k];
+      }
+    }
+    comp++;
+  }
+  free(queue);
+  return RO_OK;
+}
+
+/* Every maximal horizontal run of foreground, in raster order of its first
+ * pixel: runs[4 k .. 4 k + 3] = component, row t, first and last column. */
+int ro_component_runs(const uint8_t *mask, int64_t T, int F, int32_t *runs, int64_t cap,
+                      int64_t *n_out) {
+  int64_t *label = malloc(sizeof(int64_t) * (size_t)(T * F > 0 ? T * F : 1));
+  if (!label) return RO_ENOMEM;
+  int rc = ro_label(mask, T, F, label);
+  if (rc) { free(label); return rc; }
+  int64_t n = 0;
+  for (int64_t t = 0; t < T; t++) {
+    for (int f = 0; f < F; f++) {
+      if (!mask[t * F + f] || (f > 0 && mask[t * F + f - 1])) continue;
+      int g = f;
+      while (g + 1 < F && mask[t * F + g + 1]) g++;
+      if (n < cap) {
+        runs[4 * n] = (int32_t)label[t * F + f];
+        runs[4 * n + 1] = (int32_t)t;
+        runs[4 * n + 2] = f;
+        runs[4 * n + 3] = g;
+      }
+      n++;
+    }
+  }
+  free(label);
+  *n_out = n;
+  return n > cap ? RO_ETRUNC : RO_OK;
+}
+
+/* out[p] = 1 for a foreground pixel with a background 4-neighbour, pixels
+ * outside the image counting as background. */
+void ro_boundary(const uint8_t *mask, int64_t T, int F, uint8_t *out) {
+  for (int64_t t = 0; t < T; t++)
+    for (int f = 0; f < F; f++) {
+      const int64_t p = t * F + f;
+      if (!mask[p]) { out[p] = 0; continue; }
+      const int up = t > 0 && mask[p - F], dn = t < T - 1 && mask[p + F];
+      const int lf = f > 0 && mask[p - 1], rt = f < F - 1 && mask[p + 1];
+      out[p] = (uint8_t)!(up && dn && lf && rt);
+    }
+}

@@ -180,3 +180,34 @@ def test_ccl_hand_images():
     assert oracle.ccl_boxes(np.zeros((4, 4), np.uint8), np.zeros((4, 4), np.uint8)).shape[0] == 0
     full = oracle.ccl_boxes(np.ones((4, 6), np.uint8), np.full((4, 6), 255, np.uint8))
     assert full.tolist() == [[0, 3, 0, 5, 0, 24, 24 * 255, 24 << 32]]
+
+
+def test_component_runs_and_boundary_against_scipy():
+    """Runs rebuild the mask, their components are scipy's 4-connected labels
+    numbered by first pixel (the box order), and the boundary is the mask
+    minus its erosion by the 4-neighbour cross with a background border."""
+    from scipy import ndimage
+    rng = np.random.default_rng(21)
+    cross = ndimage.generate_binary_structure(2, 1)
+    for _ in range(25):
+        T, F = int(rng.integers(1, 40)), int(rng.integers(1, 60))
+        M = (rng.random((T, F)) < rng.uniform(0.2, 0.8)).astype(np.uint8)
+        runs = oracle.component_runs(M)
+        back = np.zeros_like(M)
+        for c, t, f0, f1 in runs:
+            assert np.all(back[t, f0:f1 + 1] == 0)
+            back[t, f0:f1 + 1] = 1
+        assert np.array_equal(back, M)
+        lab, n = ndimage.label(M, structure=cross)
+        # scipy numbers components by first pixel in raster order too
+        mine = oracle.label(M)
+        assert np.array_equal(mine + 1, lab)
+        for c, t, f0, f1 in runs:
+            assert np.all(lab[t, f0:f1 + 1] == c + 1)
+        er = ndimage.binary_erosion(M, structure=cross, border_value=0)
+        assert np.array_equal(oracle.boundary(M), (M.astype(bool) & ~er).astype(np.uint8))
+        # the boxes of the CCL are the runs' extents per component
+        boxes = oracle.ccl_boxes(M, np.zeros_like(M))
+        for k, b in enumerate(boxes):
+            rk = runs[runs[:, 0] == k]
+            assert (b[0], b[1], b[2], b[3]) == (rk[:, 1].min(), rk[:, 1].max(), rk[:, 2].min(), rk[:, 3].max())
