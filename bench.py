@@ -617,27 +617,39 @@ def run_windows(args):
                       lanes=args.lanes, max_batch=args.max_batch, max_pending=1 << 14,
                       window_frames=WIN_T)
 
+    worst = []
+
     def drive(times, limit_s):
         """Chunk j of the schedule goes to radio j % radios at times[j]
         (None: as fast as possible); returns plot latencies (ms), plots,
         elapsed seconds."""
-        lat, nxt = [], [0] * radios
+        lat, nxt, rec = [], [0] * radios, []
+
+        def take(res):
+            for d, _ in res:
+                lat.append((d["t_done_ns"] - d["t_submit_ns"]) / 1e6)
+                rec.append((d["t_submit_ns"], d["t_start_ns"], d["t_done_ns"]))
         t0 = time.perf_counter()
         for j, t in enumerate(times):
             if t is not None:
                 while time.perf_counter() - t0 < t:
-                    for d, _ in srv.poll(timeout_ms=0):
-                        lat.append((d["t_done_ns"] - d["t_submit_ns"]) / 1e6)
+                    take(srv.poll(timeout_ms=0))
             r = j % radios
             while not srv.submit(r, pinned[r][nxt[r] % per]):
-                for d, _ in srv.poll(timeout_ms=1):
-                    lat.append((d["t_done_ns"] - d["t_submit_ns"]) / 1e6)
+                take(srv.poll(timeout_ms=1))
             nxt[r] += 1
             if time.perf_counter() - t0 > limit_s:
                 break
         srv.drain()
-        for d, _ in srv.poll(timeout_ms=0):
-            lat.append((d["t_done_ns"] - d["t_submit_ns"]) / 1e6)
+        while True:   # a poll returns at most 1024 results: empty the queue
+            res = srv.poll(timeout_ms=0)
+            if not res:
+                break
+            take(res)
+        if rec:   # the slowest plots: (submitted, waited in queue, ran), ms from the first
+            s0 = min(x[0] for x in rec)
+            worst[:] = [(round((a - s0) / 1e6, 2), round((b - a) / 1e6, 3), round((c - b) / 1e6, 3))
+                        for a, b, c in sorted(rec, key=lambda x: x[2] - x[0])[-5:]]
         return np.array(lat), len(lat), time.perf_counter() - t0
 
     # warm-up: closed loop, then paced like the real-time run (small batches,
@@ -670,7 +682,8 @@ def run_windows(args):
                       "max_ms": round(float(lat_rt.max()), 3) if plots_rt else None,
                       "deadline_ms": deadline_ms,
                       "deadline_miss_frac": round(float((lat_rt > deadline_ms).mean()), 4)
-                      if plots_rt else None},
+                      if plots_rt else None,
+                      "slowest": worst},
         "stats": stats,
         "e2e": {"value": round(sat_ms_s, 1), "unit": UNIT, "h2d_bytes_per_step": WIN_T * WIN_N * 8,
                 "d2h_bytes_per_step": None,

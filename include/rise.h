@@ -213,6 +213,20 @@ typedef struct {
 int rise_detect_batch(rise_ctx *ctx, const rise_capture *caps, int ncap,
                       const rise_thresholds *thr, rise_box *out, int64_t cap, int64_t *offsets);
 
+/* ---- block shapes ------------------------------------------------------------ */
+/* The shapes of the last call's energy blocks (the labelling stage can also
+ * give the blocks' boundaries, Sec. IV-B): every foreground run of the final
+ * mask, in raster order of its first pixel, as runs[k] = {box index, row t,
+ * first column, last column} (int32 x 4; the box index is the run's
+ * component in the order boxes are returned), and, if `boundary` is not
+ * NULL, the boundary mask: uint32 [T][F/32], bit f%32 of word f/32 set for a
+ * foreground pixel with a background 4-neighbour (pixels outside the image
+ * count as background).  For the last rise_detect, rise_detect_host,
+ * rise_detect_image or collected call, with nothing queued (not after a
+ * batch).  *n_runs receives the number of runs; at most cap are written
+ * (RISE_ETRUNC beyond).  Errors: RISE_EINVAL, RISE_ETRUNC, RISE_ECUDA. */
+int rise_contours(rise_ctx *ctx, int32_t *runs, int64_t cap, int64_t *n_runs, uint32_t *boundary);
+
 /* ---- detection quality ---------------------------------------------------- */
 /* Scores detections against ground truth as the paper does (Sec. III-A-2):
  * the IoU of two boxes is |B n B'| / |B u B'| over TF cells; ground-truth box

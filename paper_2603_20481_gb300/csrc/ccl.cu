@@ -401,6 +401,59 @@ __global__ void ccl_compact_kernel(CclArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Block shapes after labelling: every run's component (its box index) and
+// span, and the boundary pixels of the final mask.
+// ---------------------------------------------------------------------------
+// A non-root run keeps its own record; a root's record became its
+// component's box, so its own span is taken from its anchor and the mask.
+__global__ void runs_export_kernel(CclArgs a, int4 *out, int64_t cap) {
+  DeviceStatus *st = a.status;
+  const int64_t n = st->n_runs;
+  if (n > a.run_cap) return;
+  const int Wd = a.F / 32;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < min(n, cap);
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int r = uf_find(a.run_parent, (int)g, st);
+    const rise_box &b = a.rec[g];
+    int t, f0, f1;
+    if (r != (int)g) {
+      t = b.t0;
+      f0 = b.f0;
+      f1 = b.f1;
+    } else {
+      t = (int)(b.anchor / a.F);
+      f0 = (int)(b.anchor % a.F);
+      const uint32_t *row = a.mask + (int64_t)t * Wd;
+      f1 = a.F - 1;
+      for (int w = f0 >> 5; w < Wd; ++w) {   // first background bit after f0
+        const uint32_t z = ~row[w] & (w == (f0 >> 5) ? (~0u << (f0 & 31)) : ~0u);
+        if (z) {
+          f1 = 32 * w + __ffs(z) - 2;
+          break;
+        }
+      }
+    }
+    out[g] = make_int4((int)a.run_out[r], t, f0, f1);
+  }
+}
+
+// boundary = foreground with a background 4-neighbour (outside is background)
+__global__ void boundary_kernel(const uint32_t *mask, int64_t T, int F, uint32_t *out) {
+  const int Wd = F / 32;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < T * Wd;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = i / Wd;
+    const int w = (int)(i % Wd);
+    const uint32_t m = mask[i];
+    const uint32_t up = t > 0 ? mask[i - Wd] : 0u, dn = t + 1 < T ? mask[i + Wd] : 0u;
+    const uint32_t prev = w > 0 ? mask[i - 1] : 0u, next = w + 1 < Wd ? mask[i + 1] : 0u;
+    const uint32_t left = (m << 1) | (prev >> 31);    // bit f: pixel f - 1
+    const uint32_t right = (m >> 1) | (next << 31);   // bit f: pixel f + 1
+    out[i] = m & ~(up & dn & left & right);
+  }
+}
+
 __global__ void zero_if_over_kernel(DeviceStatus *st, int64_t run_cap) {
   if (st->n_runs > run_cap) st->n_boxes = 0;
 }
@@ -462,6 +515,21 @@ cudaError_t label_common(const CclArgs &a, const RowSeg *segs, const int64_t *ro
   return cudaGetLastError();
 }
 }  // namespace
+
+cudaError_t launch_runs_export(const CclArgs &a, int4 *out, int64_t cap, int num_sms, cudaStream_t s) {
+  const int g = grid_for(std::max<int64_t>(cap, 1), 256, num_sms, 8);
+  runs_export_kernel<<<g, 256, 0, s>>>(a, out, cap);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_boundary(const uint32_t *mask, int64_t T, int F, uint32_t *out, int num_sms,
+                            cudaStream_t s) {
+  const int g = grid_for(T * (F / 32), 256, num_sms, 8);
+  boundary_kernel<<<g, 256, 0, s>>>(mask, T, F, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_ccl_label(const CclArgs &a, int num_sms, cudaStream_t s) {
   return label_common(a, nullptr, nullptr, 0, nullptr, num_sms, s);

@@ -285,6 +285,11 @@ struct RowSeg {               // one capture's image in a batch
   int64_t T;
   int F, pad;
 };
+// After labelling one image: run g -> (box index, row, first, last column)
+// for g < min(runs, cap); and the boundary bits of a [T][F/32] mask.
+cudaError_t launch_runs_export(const CclArgs &a, int4 *out, int64_t cap, int num_sms, cudaStream_t s);
+cudaError_t launch_boundary(const uint32_t *mask, int64_t T, int F, uint32_t *out, int num_sms,
+                            cudaStream_t s);
 // Batch labelling: a.T = rows of all captures; boxes come out ordered by
 // capture then anchor, offs[c] (device, ncap + 1) = first box of capture c.
 cudaError_t launch_ccl_label_batch(const CclArgs &a, const RowSeg *segs, const int64_t *row0,

@@ -94,7 +94,8 @@ struct rise_ctx {
   bool capturing = false;         // enqueueing into a graph capture
   // scratch
   rise::host::Buf power, img, hist, cols, effm1, mask, dbg[3], row_cnt, row_base, run_parent,
-      run_sroot, rec, run_out, scan_tmp, boxes, merge, match_boxes, match_best, match_misc;
+      run_sroot, rec, run_out, scan_tmp, boxes, merge, match_boxes, match_best, match_misc,
+      contour;
   int64_t run_cap = 0;
   int64_t run_cap_req = 0;             // capacity asked for by RISE_OPT_RUN_CAPACITY
   rise::host::Small *small = nullptr;   // device

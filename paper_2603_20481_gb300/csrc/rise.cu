@@ -517,7 +517,7 @@ int submit_call(rise_ctx *c, const void *iq, int flags, int64_t n, int N, int ho
 // Waits for the oldest queued call and returns its boxes.  If its run arrays
 // overflowed, everything queued is waited for, the arrays grow, and the call
 // runs again from its samples (still valid: a slot is reused only after it
-// has been collected).
+// has been collected), followed by the call queued behind it, if any.
 int finish_call(rise_ctx *c, rise_box *out, int64_t cap, int64_t *n_boxes) {
   if (!c || !n_boxes || cap < 0 || (cap > 0 && !out)) return RISE_EINVAL;
   if (c->npend == 0) return RISE_EINVAL;
@@ -547,10 +547,25 @@ int finish_call(rise_ctx *c, rise_box *out, int64_t cap, int64_t *n_boxes) {
       return rc;
     CK(cudaStreamSynchronize(c->stream));
     h = *sl.st_h;
-    c->last_T = sl.T;
-    c->last_F = sl.N;
-    c->last_img = reinterpret_cast<uint8_t *>(c->img.p);
-    c->last_has_power = sl.want_power;
+    if (c->npend) {
+      // the call queued behind it ran before this re-run: run it again too,
+      // so the image, masks and runs on the device are the latest call's
+      const int me = c->cur;
+      c->cur = c->pend[0];
+      CallSlot &nx = c->cs();
+      Tables *tb2;
+      if ((rc = get_tables(c, nx.N, &tb2))) return rc;
+      rc = enqueue_detect(c, nx.src, nx.fmt, nx.n, nx.N, nx.hop, nx.T, nx.thr, nx.path, nx.want_power,
+                          tb2, nx.cap);
+      c->cur = me;
+      if (rc) return rc;
+      CK(cudaEventRecord(nx.done, c->stream));
+    } else {
+      c->last_T = sl.T;
+      c->last_F = sl.N;
+      c->last_img = reinterpret_cast<uint8_t *>(c->img.p);
+      c->last_has_power = sl.want_power;
+    }
   }
   c->last_status = sl.st_h;
   if (sl.thr.range_mode == RISE_RANGE_FIXED) {
@@ -675,7 +690,7 @@ void rise_destroy(rise_ctx *c) {
   Buf *bufs[] = {&c->power, &c->img, &c->hist, &c->cols, &c->effm1, &c->mask,
                  &c->dbg[0], &c->dbg[1], &c->dbg[2], &c->row_cnt, &c->row_base,
                  &c->run_parent, &c->run_sroot, &c->rec, &c->run_out, &c->scan_tmp, &c->boxes, &c->merge,
-                 &c->match_boxes, &c->match_best, &c->match_misc};
+                 &c->match_boxes, &c->match_best, &c->match_misc, &c->contour};
   for (Buf *b : bufs)
     if (b->p) cudaFree(b->p);
   for (auto &kv : c->tables) cudaFree(kv.second.tw);
@@ -744,6 +759,35 @@ int rise_detect_image(rise_ctx *c, const uint8_t *img_dev, int64_t T, int F,
   if ((rc = image_prepare(c, thr, cap))) return rc;
   if ((rc = image_enqueue(c, img_dev, T, F, thr, false, cap))) return rc;
   return image_finish(c, img_dev, T, F, out, cap, n_boxes);
+}
+
+int rise_contours(rise_ctx *c, int32_t *runs, int64_t cap, int64_t *n_runs, uint32_t *boundary) {
+  if (!c || !n_runs || cap < 0 || (cap > 0 && !runs) || c->npend || !c->last_valid || !c->last_status)
+    return RISE_EINVAL;
+  CK(cudaSetDevice(c->device));
+  const int64_t T = c->last_T;
+  const int F = c->last_F;
+  const int64_t n = c->last_status->n_runs;
+  if (n > c->run_cap) return RISE_EINTERNAL;
+  *n_runs = n;
+  const int64_t k = std::min(n, cap);
+  const size_t bb = boundary ? (size_t)T * (F / 32) * sizeof(uint32_t) : 0;
+  int rc;
+  if ((rc = ensure(c, c->contour, std::max<size_t>((size_t)k * sizeof(int4), bb)))) return rc;
+  cudaStream_t s = c->stream;
+  if (k > 0) {
+    const CclArgs la = ccl_args(c, c->last_img, T, F, 0);
+    CK(launch_runs_export(la, static_cast<int4 *>(c->contour.p), k, c->num_sms, s));
+    CK(cudaMemcpyAsync(runs, c->contour.p, (size_t)k * sizeof(int4), cudaMemcpyDeviceToHost, s));
+  }
+  if (boundary) {
+    CK(cudaStreamSynchronize(s));   // the export above is done with the buffer
+    CK(launch_boundary(static_cast<const uint32_t *>(c->mask.p), T, F, static_cast<uint32_t *>(c->contour.p),
+                       c->num_sms, s));
+    CK(cudaMemcpyAsync(boundary, c->contour.p, bb, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  return n > cap ? RISE_ETRUNC : RISE_OK;
 }
 
 int rise_set_option(rise_ctx *c, int option, int64_t value) {

@@ -40,7 +40,7 @@ BOX_COLS = ("t0", "t1", "f0", "f1", "anchor", "area", "sum_q", "energy_fx")
 EXPORTS = ("rise_thresholds_default", "rise_create", "rise_destroy", "rise_strerror",
            "rise_detect", "rise_detect_host", "rise_detect_image", "rise_debug_export",
            "rise_set_option", "rise_stage_times", "rise_column_stats_noalloc",
-           "rise_detect_batch", "rise_submit", "rise_collect", "rise_match_boxes",
+           "rise_detect_batch", "rise_submit", "rise_collect", "rise_match_boxes", "rise_contours",
            "rise_server_create", "rise_stream_submit", "rise_server_poll",
            "rise_server_drain", "rise_stream_export", "rise_stream_import", "rise_server_stats",
            "rise_server_destroy")
@@ -130,6 +130,8 @@ def lib() -> C.CDLL:
     L.rise_submit.restype = i32
     L.rise_collect.argtypes = [P, P, i64, C.POINTER(i64)]
     L.rise_collect.restype = i32
+    L.rise_contours.argtypes = [P, P, i64, C.POINTER(i64), P]
+    L.rise_contours.restype = i32
     L.rise_match_boxes.argtypes = [P, P, i64, P, i64, P, i32, P, P, P, P]
     L.rise_match_boxes.restype = i32
     L.rise_detect_batch.argtypes = [P, P, i32, P, P, i64, P]
@@ -300,6 +302,22 @@ class Detector:
                 C.byref(thr) if thr is not None else None)
         self._order()
         return self._run(lib().rise_detect_host, args, cap)
+
+    def contours(self, T: int, F: int, boundary: bool = True):
+        """Shapes of the last call's blocks (rise_contours): runs int32 (n, 4) =
+        box index, row, first, last column, in raster order; and the boundary
+        mask unpacked to uint8 [T, F] (or None)."""
+        n = C.c_int64(0)
+        rc = lib().rise_contours(self._h, None, 0, C.byref(n), None)
+        if rc not in (RISE_OK, RISE_ETRUNC):
+            raise RiseError(rc, "rise_contours")
+        runs = np.zeros((max(int(n.value), 1), 4), np.int32)
+        words = np.zeros((T, F // 32), np.uint32) if boundary else None
+        rc = lib().rise_contours(self._h, runs.ctypes.data, runs.shape[0], C.byref(n),
+                                 words.ctypes.data if boundary else None)
+        if rc != RISE_OK:
+            raise RiseError(rc, "rise_contours")
+        return runs[: int(n.value)], (unpack_mask(words, F) if boundary else None)
 
     def match(self, gt, det, thetas):
         """Detection quality on the GPU (rise_match_boxes): gt and det are
