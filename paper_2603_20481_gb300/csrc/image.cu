@@ -127,11 +127,13 @@ __global__ void otsu_kernel(ColArgs a) {
 // Column histogram, cluster version.  A block owns 64 columns of one row
 // band; its 8 warps take interleaved rows.  Lane l reads 2 consecutive
 // columns (2l, 2l+1) per row and counts column 2l+j in shared slot l+32j:
-// 32-bit counters, level-major, so a warp's 32 lanes hit 32 banks, bumped
-// with shared-memory reductions whose results are unused.  The main loop
-// takes whole groups of CH_UNROLL rows per warp with no bounds checks and
-// issues the next group's loads before counting the current one; a tail loop
-// takes the remaining rows.  Offsets inside a band are 32-bit (a band holds
+// 16-bit counters (a band holds at most 65535 rows), the two of lane l in
+// one 32-bit word, level-major, so a warp's 32 lanes hit 32 banks, bumped
+// with shared-memory reductions whose results are unused (32 KB of counters
+// per block: three blocks fit an SM by registers).  The main loop takes
+// whole groups of CH_UNROLL rows per warp with no bounds checks and issues
+// the next group's loads before counting the current one; a tail loop takes
+// the remaining rows.  Offsets inside a band are 32-bit (a band holds
 // at most 65535 rows of at most 8192 columns).  The 8 blocks of a
 // thread-block cluster cover the same 64 columns over 8 row bands; after
 // counting, each block sums whole columns (8 of them) over the cluster
@@ -142,22 +144,24 @@ __global__ void otsu_kernel(ColArgs a) {
 // ---------------------------------------------------------------------------
 constexpr int CH_WARPS = 8, CH_COLS = 64, CH_BANDS = 8, CH_UNROLL = 8;
 constexpr int CH_PX = CH_COLS / 32;                   // columns per lane
-constexpr int CH_WORDS = 256 * CH_COLS;              // 32-bit counters per block
+constexpr int CH_WORDS = 256 * CH_COLS / 2;          // 32-bit words of 16-bit counters per block
+constexpr size_t ch_smem() { return (size_t)CH_WORDS * sizeof(uint32_t); }
 constexpr int CH_NS = CH_COLS / CH_BANDS;            // columns each block reduces
 
 __device__ __forceinline__ uint32_t shared_addr(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-// one count into the shared counter at byte address `addr`
-__device__ __forceinline__ void ch_red(uint32_t addr) {
-  asm volatile("red.shared::cta.add.u32 [%0], 1;" ::"r"(addr));
+// one count into the shared counter word at byte address `addr`: inc is 1
+// for the low 16-bit counter, 1 << 16 for the high one
+__device__ __forceinline__ void ch_red(uint32_t addr, uint32_t inc) {
+  asm volatile("red.shared::cta.add.u32 [%0], %1;" ::"r"(addr), "r"(inc));
 }
 
 // Column group cgx, row band `band` of one image (the bands of a column group
 // form one cluster; the launch picks how many).
 template <bool FROM_POWER>
 __device__ __forceinline__ void cluster_hist_body(const HistArgs &a, int cgx, int band) {
-  extern __shared__ uint4 sh4[];     // [256 levels][64 column slots] u32
+  extern __shared__ uint4 sh4[];     // [256 levels][32 lanes] u32 = two u16 column counters
   uint32_t *sh = reinterpret_cast<uint32_t *>(sh4);
   __shared__ float edges[257];
   __shared__ __align__(16) uint32_t hs[CH_NS][256];   // reduced columns
@@ -177,9 +181,8 @@ __device__ __forceinline__ void cluster_hist_body(const HistArgs &a, int cgx, in
   const int64_t r0 = (int64_t)band * a.rows_per_band;
   const int64_t r1 = min(T, r0 + a.rows_per_band);
   const int K = (r1 - r0 > warp) ? (int)((r1 - r0 - warp + CH_WARPS - 1) / CH_WARPS) : 0;
-  const int KF = K / CH_UNROLL * CH_UNROLL;             // rows in whole groups
   const uint32_t rstep = (uint32_t)CH_WARPS * (uint32_t)F;   // elements between a warp's rows
-  const uint32_t cbase = shared_addr(sh) + 4u * lane;        // slot lane (+128 B: slot lane+32)
+  const uint32_t cbase = shared_addr(sh) + 4u * lane;        // slots lane (low half), lane+32 (high)
   uint32_t off = (uint32_t)warp * (uint32_t)F;               // this warp's row, from the band start
   if constexpr (FROM_POWER) {
     const float *pb = reinterpret_cast<const float *>(a.src) + r0 * F + c0;
@@ -200,9 +203,10 @@ __device__ __forceinline__ void cluster_hist_body(const HistArgs &a, int cgx, in
         for (int j = 0; j < 2; ++j) q[j] = level_of_q(pv[j], inv_anchor, c1, edges);
       }
       *reinterpret_cast<uint16_t *>(ob + o) = (uint16_t)(q[0] | (q[1] << 8));
-      ch_red(cbase + (q[0] << 8));
-      ch_red(cbase + 128u + (q[1] << 8));
+      ch_red(cbase + (q[0] << 7), 1u);
+      ch_red(cbase + (q[1] << 7), 1u << 16);
     };
+    const int KF = K / CH_UNROLL * CH_UNROLL;
     float2 A[CH_UNROLL], B[CH_UNROLL];
     auto load = [&](float2 (&X)[CH_UNROLL], uint32_t o) {
 #pragma unroll
@@ -230,8 +234,8 @@ __device__ __forceinline__ void cluster_hist_body(const HistArgs &a, int cgx, in
   } else {
     const uint8_t *pb = reinterpret_cast<const uint8_t *>(a.src) + r0 * F + c0;
     auto one_row = [&](uint32_t w) {
-      ch_red(cbase + ((w & 0xffu) << 8));
-      ch_red(cbase + 128u + ((w >> 8) << 8));
+      ch_red(cbase + ((w & 0xffu) << 7), 1u);
+      ch_red(cbase + ((w >> 8) << 7), 1u << 16);
     };
     constexpr int U2 = 2 * CH_UNROLL;
     const int KF2 = K / U2 * U2;
@@ -255,9 +259,9 @@ __device__ __forceinline__ void cluster_hist_body(const HistArgs &a, int cgx, in
     const int nc = min(CH_NS, s_hi - cs);
     for (int k = tid; k < nc * 256; k += blockDim.x) {
       const int sl = k % nc, v = k / nc;
-      const int i = v * CH_COLS + cs + sl;
+      const int slot = cs + sl, i = v * 32 + (slot & 31), sh16 = 16 * (slot >> 5);
       uint32_t n = 0;
-      for (int b = 0; b < nb; ++b) n += cluster.map_shared_rank(sh, b)[i];
+      for (int b = 0; b < nb; ++b) n += (cluster.map_shared_rank(sh, b)[i] >> sh16) & 0xffffu;
       hs[sl][v] = n;
     }
     __syncthreads();
@@ -596,7 +600,7 @@ int bands_for(int groups, int64_t max_T) {
     auto it = cache.find(groups);
     if (it != cache.end()) return std::max(it->second, need);
   }
-  const size_t sm = (size_t)CH_WORDS * sizeof(uint32_t);
+  const size_t sm = ch_smem();
   cudaFuncSetAttribute(cluster_hist_kernel<FP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   int best = CH_BANDS;
   double best_cost = 1e30;
@@ -631,8 +635,7 @@ int bands_for(int groups, int64_t max_T) {
 }
 
 template <typename K, typename... Args>
-cudaError_t launch_clustered(K kernel, dim3 grid, int B, cudaStream_t s, Args... args) {
-  const size_t sm = (size_t)CH_WORDS * sizeof(uint32_t);
+cudaError_t launch_clustered(K kernel, size_t sm, dim3 grid, int B, cudaStream_t s, Args... args) {
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -681,16 +684,17 @@ cudaError_t launch_cluster_hist(const void *src, bool from_power, int64_t T, int
   if (needs_zero) *needs_zero = accumulate;
   HistArgs ha{src, T, F, rows, edges, qconst, img, hist, cols, accumulate};
   const dim3 grid((unsigned)groups_x, (unsigned)(G * B));
-  return from_power ? launch_clustered(cluster_hist_kernel<true>, grid, B, s, ha)
-                    : launch_clustered(cluster_hist_kernel<false>, grid, B, s, ha);
+  return from_power ? launch_clustered(cluster_hist_kernel<true>, ch_smem(), grid, B, s, ha)
+                    : launch_clustered(cluster_hist_kernel<false>, ch_smem(), grid, B, s, ha);
 }
 
 cudaError_t launch_cluster_hist_batch(bool from_power, const HistArgs *segs, const HistItem *items,
                                       int n_items, int bands, cudaStream_t s) {
   if (n_items < 1) return cudaSuccess;
   const dim3 grid((unsigned)n_items, (unsigned)bands);
-  return from_power ? launch_clustered(cluster_hist_batch_kernel<true>, grid, bands, s, segs, items)
-                    : launch_clustered(cluster_hist_batch_kernel<false>, grid, bands, s, segs, items);
+  return from_power
+             ? launch_clustered(cluster_hist_batch_kernel<true>, ch_smem(), grid, bands, s, segs, items)
+             : launch_clustered(cluster_hist_batch_kernel<false>, ch_smem(), grid, bands, s, segs, items);
 }
 
 cudaError_t launch_floor_batch(const ColArgs *segs, int ncap, int max_F, cudaStream_t s) {
