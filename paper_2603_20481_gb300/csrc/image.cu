@@ -9,6 +9,8 @@
 #include <map>
 #include <mutex>
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace cg = cooperative_groups;
@@ -432,8 +434,8 @@ struct MorphOp {
     if (!in) x = ERODE ? 0xffffffffu : 0u;
     const uint32_t l = __shfl_up_sync(0xffffffffu, x, 1);
     const uint32_t r = __shfl_down_sync(0xffffffffu, x, 1);
-    const uint32_t xl = (x << 1) | (l >> 31);    // pixel f-1 moved to f
-    const uint32_t xr = (x >> 1) | (r << 31);    // pixel f+1 moved to f
+    const uint32_t xl = __funnelshift_l(l, x, 1);   // (x << 1) | (l >> 31): pixel f-1 moved to f
+    const uint32_t xr = __funnelshift_r(x, r, 1);   // (x >> 1) | (r << 31): pixel f+1 moved to f
     const uint32_t h = ERODE ? (x & xl & xr) : (x | xl | xr);
     if constexpr (!VERT) return h;
     const uint32_t o = ERODE ? (a & b & h) : (a | b | h);   // output row = input row - 1
@@ -443,9 +445,17 @@ struct MorphOp {
   }
 };
 
-__device__ __forceinline__ uint32_t gather4(uint32_t m) {
-  // bit j of the result = bit 0 of byte j (each byte of m is 0x00 or 0xff)
-  return (((m & 0x01010101u) * 0x01020408u) >> 24) & 0xfu;
+// Threshold of 4 pixels: the levels q (4 bytes) against the columns' eff-1
+// (4 bytes); bit j of the result = [q_j > e_j] (unsigned bytes).  SWAR:
+// t = (e | 0x80..) - (q & 0x7f..) never borrows across bytes and its bit 7 is
+// [e mod 128 >= q mod 128]; q > e iff (q_7 and not e_7) or (q_7 == e_7 and
+// not t_7).  The four bit-7 flags are gathered by one multiply: the factor
+// 2^21 + 2^14 + 2^7 + 1 moves bits 7, 15, 23, 31 to 28..31, every other
+// partial product landing below bit 28 on a distinct bit (no carries).
+__device__ __forceinline__ uint32_t gt4(uint32_t q, uint32_t e) {
+  const uint32_t t = (e | 0x80808080u) - (q & 0x7f7f7f7fu);
+  const uint32_t g = ((q & ~e) | (~(q ^ e) & ~t)) & 0x80808080u;
+  return (g * 0x00204081u) >> 28;
 }
 
 __device__ __forceinline__ uint32_t threshold32(const uint4 &q0, const uint4 &q1, const uint4 &e0,
@@ -454,7 +464,7 @@ __device__ __forceinline__ uint32_t threshold32(const uint4 &q0, const uint4 &q1
   const uint32_t es[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
   uint32_t bits = 0;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) bits |= gather4(__vcmpgtu4(qs[k], es[k])) << (4 * k);
+  for (int k = 0; k < 8; ++k) bits = __funnelshift_r(bits, gt4(qs[k], es[k]), 4);   // nibble k -> bits 4k..
   return bits;   // foreground where q > eff-1
 }
 
@@ -508,51 +518,70 @@ __device__ __forceinline__ void morph_body(const MorphArgs &a, int nx, int rows_
     }
   }
   uint32_t p0 = 0, p1 = 0, p2 = 0, p3 = 0, p4 = 0, p5 = 0;   // previous-step stage outputs
-  auto in_img = [&](int row) { return lane_in && (unsigned)row < (unsigned)T; };
-  for (int s0 = 0; s0 < nsteps; s0 += MS_PF) {
+  // Every row an operation takes in lies inside the image unless the band is
+  // within LAG + 4 rows of the top or 9 rows of the bottom: then only the
+  // lane's column decides whether an operation sees a pixel.
+  const bool edge_band = tb0 < LAG + 4 || tb1 + 9 > T;
+  const bool dbg = a.dbg0 || a.dbg1 || a.dbg2;
+  auto run = [&](auto checked, auto with_dbg) {
+    constexpr bool CHECK = decltype(checked)::value, DBG = decltype(with_dbg)::value;
+    auto in_img = [&](int row) { return CHECK ? lane_in && (unsigned)row < (unsigned)T : lane_in; };
+    for (int s0 = 0; s0 < nsteps; s0 += MS_PF) {
 #pragma unroll
-    for (int k = 0; k < MS_PF; ++k) {
-      const int s = s0 + k;
-      if (s < nsteps) {   // warp-uniform
-        const int i = first + s;
-        uint32_t x0 = 0;
-        if (in_img(i) && i <= tb1 + 3) x0 = threshold32(ring[k][0], ring[k][1], e0, e1);
-        const int ip = i + MS_PF;   // prefetch
-        if (in_img(ip) && ip <= tb1 + 3) {
-          const uint4 *p = reinterpret_cast<const uint4 *>(base + (int64_t)ip * a.F);
-          ring[k][0] = __ldg(p);
-          ring[k][1] = __ldg(p + 1);
-        }
-        const uint32_t x1 = op1.step(p0, in_img(i - IN1));
-        const uint32_t x2 = op2.step(p1, in_img(i - IN2));
-        const uint32_t x3 = op3.step(p2, in_img(i - IN3));
-        const uint32_t x4 = op4.step(p3, in_img(i - IN4));
-        const uint32_t x5 = op5.step(p4, in_img(i - IN5));
-        const uint32_t x6 = op6.step(p5, in_img(i - IN6));
-        p0 = x0; p1 = x1; p2 = x2; p3 = x3; p4 = x4; p5 = x5;
-        if (a.dbg0 && out_lane && i >= tb0 && i < tb1) a.dbg0[(int64_t)i * Wd + gw] = x0;
-        if (a.dbg1) {
-          const int r = i - DBG1;
-          if (out_lane && r >= tb0 && r < tb1) a.dbg1[(int64_t)r * Wd + gw] = x2;
-        }
-        if (a.dbg2) {
-          const int r = i - DBG2;
-          if (out_lane && r >= tb0 && r < tb1) a.dbg2[(int64_t)r * Wd + gw] = x4;
-        }
-        const int r = i - LAG;   // the final row of this step
-        if (r >= tb0 && r < tb1) {   // warp-uniform
-          // runs starting in this word: its bit 31 neighbour is the left lane's
-          // word (exact on the halo lane too), or nothing at the image's left edge
-          const uint32_t left = __shfl_up_sync(0xffffffffu, x6, 1);
-          if (out_lane) {
-            a.mask[(int64_t)r * Wd + gw] = x6;
-            const uint32_t lft = gw > 0 ? left : 0u;
-            const uint32_t n = __popc(x6 & ~((x6 << 1) | (lft >> 31)));
-            if (n) atomicAdd(&a.row_cnt[r], n);
+      for (int k = 0; k < MS_PF; ++k) {
+        const int s = s0 + k;
+        if (s < nsteps) {   // warp-uniform
+          const int i = first + s;
+          uint32_t x0 = 0;
+          if (in_img(i) && i <= tb1 + 3) x0 = threshold32(ring[k][0], ring[k][1], e0, e1);
+          const int ip = i + MS_PF;   // prefetch
+          if (in_img(ip) && ip <= tb1 + 3) {
+            const uint4 *p = reinterpret_cast<const uint4 *>(base + (int64_t)ip * a.F);
+            ring[k][0] = __ldg(p);
+            ring[k][1] = __ldg(p + 1);
+          }
+          const uint32_t x1 = op1.step(p0, in_img(i - IN1));
+          const uint32_t x2 = op2.step(p1, in_img(i - IN2));
+          const uint32_t x3 = op3.step(p2, in_img(i - IN3));
+          const uint32_t x4 = op4.step(p3, in_img(i - IN4));
+          const uint32_t x5 = op5.step(p4, in_img(i - IN5));
+          const uint32_t x6 = op6.step(p5, in_img(i - IN6));
+          p0 = x0; p1 = x1; p2 = x2; p3 = x3; p4 = x4; p5 = x5;
+          if constexpr (DBG) {
+            if (a.dbg0 && out_lane && i >= tb0 && i < tb1) a.dbg0[(int64_t)i * Wd + gw] = x0;
+            if (a.dbg1) {
+              const int r = i - DBG1;
+              if (out_lane && r >= tb0 && r < tb1) a.dbg1[(int64_t)r * Wd + gw] = x2;
+            }
+            if (a.dbg2) {
+              const int r = i - DBG2;
+              if (out_lane && r >= tb0 && r < tb1) a.dbg2[(int64_t)r * Wd + gw] = x4;
+            }
+          }
+          const int r = i - LAG;   // the final row of this step
+          if (r >= tb0 && r < tb1) {   // warp-uniform
+            // runs starting in this word: its bit 31 neighbour is the left lane's
+            // word (exact on the halo lane too), or nothing at the image's left edge
+            const uint32_t left = __shfl_up_sync(0xffffffffu, x6, 1);
+            if (out_lane) {
+              a.mask[(int64_t)r * Wd + gw] = x6;
+              const uint32_t lft = gw > 0 ? left : 0u;
+              const uint32_t n = __popc(x6 & ~((x6 << 1) | (lft >> 31)));
+              if (n) atomicAdd(&a.row_cnt[r], n);
+            }
           }
         }
       }
     }
+  };
+  using T_ = std::true_type;
+  using F_ = std::false_type;
+  if (dbg) {
+    if (edge_band) run(T_{}, T_{});
+    else run(F_{}, T_{});
+  } else {
+    if (edge_band) run(T_{}, F_{});
+    else run(F_{}, F_{});
   }
 }
 
