@@ -24,6 +24,7 @@ from __future__ import annotations
 import argparse
 import datetime
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -319,6 +320,19 @@ def run_ours(args):
         "clocks": clocks,
         "e2e": e2e,
     }
+    if dom == "spectrum_pass1":
+        # the same kernel against the FP32 pipe: FFT flops by the 5 N log2 N
+        # convention over the peak of 128 FP32 lanes x 2 flops per SM clock
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = float(clocks.get("sm_max_mhz") or 2070.0)
+        fp32_peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+        flops = T * 5 * N_FFT * int(math.log2(N_FFT))
+        fp32_ach = flops / (dom_ms / 1e3) / 1e12
+        result["roofline"]["fp32"] = {
+            "achieved": round(fp32_ach, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
+            "frac": round(fp32_ach / fp32_peak, 4), "flops_per_launch": flops,
+            "convention": "5 N log2 N per frame",
+            "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz"}
     if rank == 0 and not args.no_cpu_baseline:
         m = min(args.cpu_sample, n)
         rate, dt, nb = cpu_oracle_rate(cap.iq, m, N_FFT, HOP)
