@@ -608,7 +608,7 @@ int detect_batch(rise_ctx *c, const rise_capture *caps, int ncap, const rise_thr
     h = (*c->cs().st_h);
   }
   c->last_status = c->cs().st_h;
-  if (h.err & ERR_UNION_LIMIT) return RISE_ETIMEOUT;
+  if (h.err & (ERR_UNION_LIMIT | ERR_SCAN)) return RISE_ETIMEOUT;
   if (h.err) return RISE_EINTERNAL;
   std::memcpy(offsets, b.offs_h, sizeof(int64_t) * (ncap + 1));
   const int64_t total = h.n_boxes;

@@ -10,14 +10,15 @@
 // links by smaller number, hence every root is the anchor run and the final
 // roots, taken in run order, are the boxes in anchor order.
 //
-//   1. the morphology kernel counts the runs of each row; an exclusive scan
-//      gives row_base[t], the number of the first run of row t.
+//   1. the morphology kernel counts the runs of each row; a single-pass
+//      exclusive scan gives row_base[t], the number of the first run of row t.
 //   2. init: every run is its own tree, with zeroed sums.
 //   3. rows: one warp per row records each run's extent, area, level sum and
 //      energy, and unites it with the runs of the next row that share a
 //      column (4-connectivity), on a global lock-free union-find.
 //   4. reduce: every run adds its record into its root's (warp-aggregated).
-//   5. compact: roots -> exclusive scan -> boxes in run order.
+//   5. compact: a single-pass scan of the root flags gives each root its box
+//      slot (boxes in run order) and writes its record there.
 // Every stage touches only rows that hold runs: the foreground of a spectrum
 // mask is sparse, so the work follows the runs, not the pixels.
 #include "common.cuh"
@@ -25,106 +26,135 @@
 namespace rise {
 namespace {
 
-constexpr int CCL_THREADS = 256;
 constexpr int SCAN_THREADS = 256, SCAN_ITEMS = 8, SCAN_BLOCK = SCAN_THREADS * SCAN_ITEMS;
 
 // ---------------------------------------------------------------------------
-// Generic exclusive scan of counts (uint32 or uint8) into int64 offsets.
-// The item count may live on the device (n_dev); the grid covers n_host.
+// Single-pass exclusive scans (decoupled look-back).  A block takes the next
+// tile of SCAN_BLOCK items by ticket, so every tile it waits for belongs to a
+// block that started earlier and is running or done.  It publishes its tile
+// sum at once, then walks back over its predecessors' published sums until
+// one carries a full prefix, and publishes its own.  Published words hold a
+// state in the top two bits and the value below.  The state words and the
+// ticket live in the scan scratch and are zeroed before each scan; every
+// wait is bounded (ERR_SCAN).
 // ---------------------------------------------------------------------------
-template <typename In>
-__global__ void __launch_bounds__(SCAN_THREADS)
-scan_reduce_kernel(const In *in, const int64_t *n_dev, int64_t n_host, int64_t *partial) {
-  const int64_t n = n_dev ? min(*n_dev, n_host) : n_host;
-  const int64_t base = (int64_t)blockIdx.x * SCAN_BLOCK;
-  int64_t s = 0;
-  for (int i = threadIdx.x; i < SCAN_BLOCK; i += SCAN_THREADS) {
-    const int64_t k = base + i;
-    if (k < n) s += (int64_t)in[k];
-  }
-  __shared__ int64_t scratch[32];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) scratch[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int64_t t = 0;
-    for (int w = 0; w < SCAN_THREADS / 32; ++w) t += scratch[w];
-    partial[blockIdx.x] = t;
-  }
+constexpr uint64_t LB_AGG = 1ull << 62, LB_INC = 2ull << 62, LB_VAL = (1ull << 62) - 1;
+constexpr int LB_SPIN_LIMIT = 1 << 20;   // with 32 ns sleeps: about a second
+
+__device__ __forceinline__ uint64_t ld_acquire(const uint64_t *p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(uint64_t *p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-__global__ void __launch_bounds__(1024) scan_partials_kernel(int64_t *partial, int64_t nblocks) {
-  __shared__ int64_t scratch[32];
-  int64_t carry = 0;
-  for (int64_t c0 = 0; c0 < nblocks; c0 += 1024) {
-    const int64_t k = c0 + threadIdx.x;
-    const int64_t v = k < nblocks ? partial[k] : 0;
-    int64_t tot;
-    const int64_t ex = block_exclusive_scan<int64_t>(v, scratch, &tot);
-    if (k < nblocks) partial[k] = carry + ex;
-    carry += tot;
+// Thread 0 of tile `tile` (sum `agg`): the sum of all earlier tiles.
+__device__ int64_t lookback(uint64_t *stat, int64_t tile, int64_t agg, DeviceStatus *st) {
+  if (tile == 0) {
+    st_release(&stat[0], LB_INC | (uint64_t)agg);
+    return 0;
   }
+  st_release(&stat[tile], LB_AGG | (uint64_t)agg);
+  int64_t excl = 0;
+  for (int64_t k = tile - 1; k >= 0; --k) {
+    uint64_t w = ld_acquire(&stat[k]);
+    for (int spins = 0; (w >> 62) == 0; ++spins) {
+      if (spins >= LB_SPIN_LIMIT) {
+        set_err(st, ERR_SCAN);
+        return excl;
+      }
+      __nanosleep(32);
+      w = ld_acquire(&stat[k]);
+    }
+    excl += (int64_t)(w & LB_VAL);
+    if ((w >> 62) == 2) break;
+  }
+  st_release(&stat[tile], LB_INC | (uint64_t)(excl + agg));
+  return excl;
 }
 
+// Scan scratch: [0] ticket of the row scan, [1] ticket of the root scan,
+// [2, 2 + tiles) row-scan tile words, then root-scan tile words.
+struct ScanState {
+  uint64_t *ticket_rows, *ticket_roots, *rows, *roots;
+};
+__host__ __device__ inline int64_t scan_tiles(int64_t n) { return n / SCAN_BLOCK + 1; }
+inline ScanState scan_state(void *tmp, int64_t row_tiles) {
+  uint64_t *w = static_cast<uint64_t *>(tmp);
+  return ScanState{w, w + 1, w + 2, w + 2 + row_tiles};
+}
+
+// A tile's items, their exclusive offsets within the whole scan and (for the
+// last tile) the total.  `ex` receives each item's offset; returns the tile's
+// first offset.
 template <typename In>
-__global__ void __launch_bounds__(SCAN_THREADS)
-scan_apply_kernel(const In *in, const int64_t *n_dev, int64_t n_host, const int64_t *partial,
-                  int64_t *out, int64_t *total_out) {
-  const int64_t n = n_dev ? min(*n_dev, n_host) : n_host;
-  const int64_t base = (int64_t)blockIdx.x * SCAN_BLOCK + (int64_t)threadIdx.x * SCAN_ITEMS;
-  int64_t v[SCAN_ITEMS];
-  int64_t s = 0;
+__device__ __forceinline__ void tile_scan(const In *in, int64_t n, int64_t tile, uint64_t *stat,
+                                          DeviceStatus *st, int64_t (&v)[SCAN_ITEMS],
+                                          int64_t (&ex)[SCAN_ITEMS]) {
+  __shared__ int64_t scratch[32];
+  __shared__ int64_t s_prefix;
+  const int64_t base = tile * SCAN_BLOCK + (int64_t)threadIdx.x * SCAN_ITEMS;
+  int64_t sum = 0;
 #pragma unroll
   for (int i = 0; i < SCAN_ITEMS; ++i) {
     const int64_t k = base + i;
     v[i] = k < n ? (int64_t)in[k] : 0;
-    s += v[i];
+    sum += v[i];
   }
-  __shared__ int64_t scratch[32];
   int64_t tot;
-  int64_t run = block_exclusive_scan<int64_t>(s, scratch, &tot) + partial[blockIdx.x];
+  const int64_t mine = block_exclusive_scan<int64_t>(sum, scratch, &tot);
+  if (threadIdx.x == 0) s_prefix = lookback(stat, tile, tot, st);
+  __syncthreads();
+  int64_t run = s_prefix + mine;
 #pragma unroll
   for (int i = 0; i < SCAN_ITEMS; ++i) {
-    const int64_t k = base + i;
-    if (k < n) out[k] = run;
-    if (k == n - 1) {
-      out[n] = run + v[i];
-      if (total_out) *total_out = run + v[i];
-    }
+    ex[i] = run;
     run += v[i];
-  }
-  if (n == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
-    out[0] = 0;
-    if (total_out) *total_out = 0;
   }
 }
 
-template <typename In>
-cudaError_t device_scan(const In *in, const int64_t *n_dev, int64_t n_host, int64_t *out,
-                        int64_t *total_out, int64_t *partial, cudaStream_t s) {
-  const int64_t nb = std::max<int64_t>(1, (n_host + SCAN_BLOCK - 1) / SCAN_BLOCK);
-  scan_reduce_kernel<In><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n_dev, n_host, partial);
-  count_launches(1);
-  scan_partials_kernel<<<1, 1024, 0, s>>>(partial, nb);
-  count_launches(1);
-  scan_apply_kernel<In><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n_dev, n_host, partial, out,
-                                                               total_out);
-  count_launches(1);
-  return cudaGetLastError();
+// Row offsets of the runs: row_base[t] = runs in rows before t, row_base[T]
+// and n_runs = all runs.
+__global__ void __launch_bounds__(SCAN_THREADS)
+row_scan_kernel(const uint32_t *cnt, int64_t T, int64_t *row_base, DeviceStatus *st, ScanState ss) {
+  __shared__ int64_t s_tile;
+  if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(reinterpret_cast<unsigned long long *>(ss.ticket_rows), 1ull);
+  __syncthreads();
+  const int64_t tile = s_tile;
+  if (tile >= scan_tiles(T)) return;
+  int64_t v[SCAN_ITEMS], ex[SCAN_ITEMS];
+  tile_scan<uint32_t>(cnt, T, tile, ss.rows, st, v, ex);
+  const int64_t base = tile * SCAN_BLOCK + (int64_t)threadIdx.x * SCAN_ITEMS;
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    const int64_t k = base + i;
+    if (k < T) row_base[k] = ex[i];
+    if (k == T) {   // one past the last row: the total
+      row_base[T] = ex[i];
+      st->n_runs = ex[i];
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
 // 2. per-run initialisation: every run is its own tree and record
 // ---------------------------------------------------------------------------
-__global__ void runs_init_kernel(CclArgs a) {
+__global__ void runs_init_kernel(CclArgs a, ScanState ss, int64_t root_tiles) {
   DeviceStatus *st = a.status;
   const int64_t n = st->n_runs;
   if (n > a.run_cap) {
     if (blockIdx.x == 0 && threadIdx.x == 0) set_err(st, ERR_RUN_CAPACITY);
     return;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) st->n_merge = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->n_merge = 0;
+    *ss.ticket_roots = 0;   // the root scan's state (this chain may run again on a relabel)
+  }
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < root_tiles;
+       k += (int64_t)gridDim.x * blockDim.x)
+    ss.roots[k] = 0;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
        g += (int64_t)gridDim.x * blockDim.x) {
     a.run_parent[g] = (int)g;
@@ -387,17 +417,36 @@ __global__ void ccl_reduce_kernel(CclArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// 5. compaction of global roots (run_sroot now flags exactly them)
+// 5. box slots of the global roots (run_sroot flags exactly them): one
+//    single-pass scan that also writes each root's record to its slot; with
+//    too many runs for the arrays, no boxes
 // ---------------------------------------------------------------------------
-__global__ void ccl_compact_kernel(CclArgs a) {
+__global__ void __launch_bounds__(SCAN_THREADS) root_scan_kernel(CclArgs a, ScanState ss) {
   DeviceStatus *st = a.status;
   const int64_t n = st->n_runs;
-  if (n > a.run_cap) return;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
-       g += (int64_t)gridDim.x * blockDim.x) {
-    if (!a.run_sroot[g]) continue;
-    const int64_t idx = a.run_out[g];
-    if (idx < a.box_cap) a.boxes[idx] = a.rec[g];
+  __shared__ int64_t s_tile;
+  if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(reinterpret_cast<unsigned long long *>(ss.ticket_roots), 1ull);
+  __syncthreads();
+  const int64_t tile = s_tile;
+  if (n > a.run_cap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->n_boxes = 0;
+    return;
+  }
+  if (tile >= scan_tiles(n)) return;
+  int64_t v[SCAN_ITEMS], ex[SCAN_ITEMS];
+  tile_scan<uint8_t>(a.run_sroot, n, tile, ss.roots, st, v, ex);
+  const int64_t base = tile * SCAN_BLOCK + (int64_t)threadIdx.x * SCAN_ITEMS;
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    const int64_t k = base + i;
+    if (k < n) {
+      a.run_out[k] = ex[i];
+      if (v[i] && ex[i] < a.box_cap) a.boxes[ex[i]] = a.rec[k];
+    }
+    if (k == n) {
+      a.run_out[n] = ex[i];
+      st->n_boxes = ex[i];
+    }
   }
 }
 
@@ -454,10 +503,6 @@ __global__ void boundary_kernel(const uint32_t *mask, int64_t T, int F, uint32_t
   }
 }
 
-__global__ void zero_if_over_kernel(DeviceStatus *st, int64_t run_cap) {
-  if (st->n_runs > run_cap) st->n_boxes = 0;
-}
-
 // Grid of the run-indexed kernels (grid-stride loops), sized on the run
 // capacity and capped at `per_sm` blocks per SM: one image's runs are
 // usually a small fraction of the capacity (idle blocks still cost), a
@@ -471,19 +516,31 @@ int grid_for(int64_t n, int threads, int num_sms, int per_sm) {
 }  // namespace
 
 size_t ccl_scan_tmp_bytes(int64_t max_items) {
-  return (size_t)(max_items / SCAN_BLOCK + 2) * sizeof(int64_t);
+  return (size_t)(2 + 2 * scan_tiles(max_items)) * sizeof(uint64_t);
 }
 
 cudaError_t launch_ccl_count(const CclArgs &a, int num_sms, cudaStream_t s) {
-  return device_scan<uint32_t>(a.row_cnt, nullptr, a.T, a.row_base, &a.status->n_runs,
-                               reinterpret_cast<int64_t *>(a.scan_tmp), s);
+  (void)num_sms;
+  const int64_t tiles = scan_tiles(a.T);
+  if ((size_t)(2 + tiles + scan_tiles(a.run_cap)) * sizeof(uint64_t) > a.scan_tmp_bytes)
+    return cudaErrorInvalidValue;
+  const ScanState ss = scan_state(a.scan_tmp, tiles);
+  cudaError_t e = cudaMemsetAsync(a.scan_tmp, 0, (size_t)(2 + tiles) * sizeof(uint64_t), s);
+  if (e != cudaSuccess) return e;
+  row_scan_kernel<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(a.row_cnt, a.T, a.row_base, a.status, ss);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 namespace {
 cudaError_t label_common(const CclArgs &a, const RowSeg *segs, const int64_t *row0, int ncap,
                          int64_t *offs, int num_sms, cudaStream_t s) {
   const int g = grid_for(a.run_cap, 256, num_sms, segs ? 16 : 4);
-  runs_init_kernel<<<g, 256, 0, s>>>(a);
+  const int64_t root_tiles = scan_tiles(a.run_cap);
+  if ((size_t)(2 + scan_tiles(a.T) + root_tiles) * sizeof(uint64_t) > a.scan_tmp_bytes)
+    return cudaErrorInvalidValue;
+  const ScanState ss = scan_state(a.scan_tmp, scan_tiles(a.T));
+  runs_init_kernel<<<g, 256, 0, s>>>(a, ss, root_tiles);
   count_launches(1);
   const unsigned row_blocks = (unsigned)((a.T + ROW_WARPS - 1) / ROW_WARPS);
   if (segs)
@@ -501,12 +558,7 @@ cudaError_t label_common(const CclArgs &a, const RowSeg *segs, const int64_t *ro
   count_launches(1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = device_scan<uint8_t>(a.run_sroot, &a.status->n_runs, a.run_cap, a.run_out,
-                           &a.status->n_boxes, reinterpret_cast<int64_t *>(a.scan_tmp), s);
-  if (e != cudaSuccess) return e;
-  ccl_compact_kernel<<<g, 256, 0, s>>>(a);
-  count_launches(1);
-  zero_if_over_kernel<<<1, 1, 0, s>>>(a.status, a.run_cap);
+  root_scan_kernel<<<(unsigned)root_tiles, SCAN_THREADS, 0, s>>>(a, ss);
   count_launches(1);
   if (segs) {
     ccl_offsets_kernel<<<(ncap + 1 + 255) / 256, 256, 0, s>>>(a, row0, ncap, offs);

@@ -18,6 +18,7 @@ enum : uint32_t {
   ERR_UNION_LIMIT = 1u << 1,    // a union/find loop hit its iteration limit
   ERR_ROW_RUNS = 1u << 2,       // a row holds more runs than the morphology allows
   ERR_INDEX = 1u << 3,          // an index check failed
+  ERR_SCAN = 1u << 4,           // a single-pass scan waited too long for a predecessor tile
 };
 
 struct DeviceStatus {

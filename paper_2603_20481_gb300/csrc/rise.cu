@@ -281,7 +281,7 @@ int image_finish(rise_ctx *c, const uint8_t *img, int64_t T, int F, rise_box *ou
     h = (*c->cs().st_h);
   }
   c->last_status = c->cs().st_h;
-  if (h.err & ERR_UNION_LIMIT) return RISE_ETIMEOUT;
+  if (h.err & (ERR_UNION_LIMIT | ERR_SCAN)) return RISE_ETIMEOUT;
   if (h.err) return RISE_EINTERNAL;
   *n_boxes = h.n_boxes;
   const int64_t ncopy = std::min<int64_t>(h.n_boxes, cap);
@@ -575,7 +575,7 @@ int finish_call(rise_ctx *c, rise_box *out, int64_t cap, int64_t *n_boxes) {
     std::memcpy(&mf, &h.max_bits, 4);
     c->last_anchor = mf;
   }
-  if (h.err & ERR_UNION_LIMIT) return RISE_ETIMEOUT;
+  if (h.err & (ERR_UNION_LIMIT | ERR_SCAN)) return RISE_ETIMEOUT;
   if (h.err) return RISE_EINTERNAL;
   *n_boxes = h.n_boxes;
   const int64_t lim = std::min(cap, sl.cap);
