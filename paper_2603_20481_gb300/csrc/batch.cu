@@ -400,7 +400,7 @@ int enqueue(rise_ctx *c, const Plan &p, const rise_thresholds &thr, int64_t cap,
   la.mask = static_cast<const uint32_t *>(c->mask.p);
   la.img = static_cast<const uint8_t *>(c->img.p);
   la.T = p.total_rows;
-  la.F = 0;
+  la.F = p.max_F;   // the widest capture: sizes the row pass's staging
   la.energy = sm->energy;
   la.row_base = static_cast<int64_t *>(c->row_base.p);
   la.row_cnt = static_cast<uint32_t *>(c->row_cnt.p);

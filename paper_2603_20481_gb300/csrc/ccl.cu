@@ -185,34 +185,77 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane, int *total) {
   return x - v;
 }
 
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Row t (of T) of an image of width F whose mask and levels start at
 // mask0 / img0; tg is the row's index in the run-count arrays (the same as t
 // for a single image).  Rows without runs are skipped by the callers.
-__device__ __forceinline__ void runs_row_body(const CclArgs &a, const unsigned long long *Es,
-                                              uint8_t *myq, int64_t tg, int64_t t, int64_t T, int F,
+// The row is latency-bound, so every load it needs is issued first: the
+// next row's run count, both rows' run offsets and mask words (MAXC chunks
+// of 32 words, in registers), then this lane's levels of its foreground
+// words (asynchronous copies into `lq`, MAXC x 32 bytes of shared memory).
+// Extents and unions are done while the levels are in flight; the level and
+// energy sums come last.
+template <int MAXC>
+__device__ __forceinline__ void runs_row_body(const CclArgs &a, const unsigned long long *Es, uint8_t *lq,
+                                              int64_t tg, int64_t t, int64_t T, int F,
                                               const uint32_t *mask0, const uint8_t *img0) {
   DeviceStatus *st = a.status;
   const int lane = threadIdx.x & 31;
   const int Wd = F / 32;
+  const int nch = (Wd + 31) / 32;   // <= MAXC
+  const bool next_in = t + 1 < T;
   const uint32_t *m = mask0 + t * Wd;
-  const bool has_next = t + 1 < T && a.row_cnt[tg + 1] != 0;
-  const uint32_t *m2 = has_next ? mask0 + (t + 1) * Wd : nullptr;
-  const int64_t base = a.row_base[tg], base2 = has_next ? a.row_base[tg + 1] : 0;
+  const uint32_t *m2 = mask0 + (next_in ? t + 1 : t) * Wd;
+  const uint32_t cnt2 = next_in ? a.row_cnt[tg + 1] : 0u;
+  const int64_t base = a.row_base[tg];
+  const int64_t base2 = next_in ? a.row_base[tg + 1] : 0;
+  uint32_t X[MAXC], Y[MAXC];
+#pragma unroll
+  for (int c = 0; c < MAXC; ++c) {
+    const int w = 32 * c + lane;
+    const bool in = c < nch && w < Wd;
+    X[c] = in ? m[w] : 0u;
+    Y[c] = in && next_in ? m2[w] : 0u;
+  }
+  const uint32_t lq_s = static_cast<uint32_t>(__cvta_generic_to_shared(lq));
+  const uint8_t *qrow = img0 + t * F;
+#pragma unroll
+  for (int c = 0; c < MAXC; ++c) {
+    if (X[c]) {   // a foreground word: c < nch and w < Wd
+      const uint8_t *src = qrow + 32 * (32 * c + lane);
+      cp_async16(lq_s + 32 * c, src);
+      cp_async16(lq_s + 32 * c + 16, src + 16);
+    }
+  }
+  const bool has_next = cnt2 != 0;
+  uint32_t SX[MAXC];
+  int BS[MAXC];
   uint32_t cx = 0, cy = 0;       // previous chunk's last words
   int nst = 0, nen = 0, nsy = 0; // runs started / ended before this chunk
-  for (int w0 = 0; w0 < Wd; w0 += 32) {
-    const int w = w0 + lane;
-    const uint32_t x = w < Wd ? m[w] : 0u;
-    const uint32_t y = (has_next && w < Wd) ? m2[w] : 0u;
+#pragma unroll
+  for (int c = 0; c < MAXC; ++c) {
+    SX[c] = 0;
+    BS[c] = 0;
+    if (c >= nch) continue;   // warp-uniform
+    const int w = 32 * c + lane;
+    const uint32_t x = X[c];
+    const uint32_t y = has_next ? Y[c] : 0u;
     uint32_t px = __shfl_up_sync(0xffffffffu, x, 1), py = __shfl_up_sync(0xffffffffu, y, 1);
     if (lane == 0) { px = cx; py = cy; }
     uint32_t nx = __shfl_down_sync(0xffffffffu, x, 1);
-    if (lane == 31) nx = (w + 1 < Wd) ? m[w + 1] : 0u;
+    const uint32_t nx0 = __shfl_sync(0xffffffffu, c + 1 < MAXC ? X[c + 1 < MAXC ? c + 1 : c] : 0u, 0);
+    if (lane == 31) nx = (c + 1 < nch) ? nx0 : 0u;
     const uint32_t sx = run_starts(x, px), ex = run_ends(x, nx), sy = run_starts(y, py);
     int tot_s, tot_e, tot_y;
     const int bs = nst + warp_excl_scan(__popc(sx), lane, &tot_s);
     const int be = nen + warp_excl_scan(__popc(ex), lane, &tot_e);
     const int by = nsy + warp_excl_scan(__popc(sy), lane, &tot_y);
+    SX[c] = sx;
+    BS[c] = bs;
     if (x) {
       // extent: the start lane owns t0, t1, f0, anchor; the end lane owns f1
       uint32_t ss = sx;
@@ -233,38 +276,16 @@ __device__ __forceinline__ void runs_row_body(const CclArgs &a, const unsigned l
         ee &= ee - 1;
         a.rec[base + id++].f1 = 32 * w + b;
       }
-      // area, level and energy sums of each segment of set bits in the word
-      const uint4 *qv = reinterpret_cast<const uint4 *>(img0 + t * F + 32 * w);
-      reinterpret_cast<uint4 *>(myq)[0] = __ldg(qv);
-      reinterpret_cast<uint4 *>(myq)[1] = __ldg(qv + 1);   // read back by this lane only
-      uint32_t mm = x;
-      while (mm) {
-        const int b0 = __ffs(mm) - 1;
-        const uint32_t inv = ~(mm >> b0);
-        const int len = inv ? __ffs(inv) - 1 : 32 - b0;
-        uint32_t sq = 0;
-        unsigned long long se = 0;
-        for (int b = b0; b < b0 + len; ++b) {
-          const uint32_t q = myq[b];
-          sq += q;
-          se += Es[q];
-        }
-        rise_box *rc = &a.rec[base + bs + __popc(sx & mask_upto(b0)) - 1];
-        atomicAdd(reinterpret_cast<unsigned long long *>(&rc->area), (unsigned long long)len);
-        atomicAdd(reinterpret_cast<unsigned long long *>(&rc->sum_q), (unsigned long long)sq);
-        atomicAdd(reinterpret_cast<unsigned long long *>(&rc->energy_fx), se);
-        mm &= (len + b0 >= 32) ? 0u : ~0u << (b0 + len);
-      }
     }
     // union with the runs of the next row that share a column
     const uint32_t ov = x & y;
     if (ov) {
       uint32_t os = ov & ~((ov << 1) | ((px & py) >> 31));
       while (os) {
-        const int c = __ffs(os) - 1;
+        const int cc = __ffs(os) - 1;
         os &= os - 1;
-        const int ia = (int)(base + bs + __popc(sx & mask_upto(c)) - 1);
-        const int ib = (int)(base2 + by + __popc(sy & mask_upto(c)) - 1);
+        const int ia = (int)(base + bs + __popc(sx & mask_upto(cc)) - 1);
+        const int ib = (int)(base2 + by + __popc(sy & mask_upto(cc)) - 1);
         // a lower run touched by one upper run (the common case) hangs under
         // it with one CAS: ib is still a root and ia < ib, so this is a union.
         // A failed CAS means ib already hangs elsewhere (it touches a second
@@ -283,12 +304,42 @@ __device__ __forceinline__ void runs_row_body(const CclArgs &a, const unsigned l
     cx = __shfl_sync(0xffffffffu, x, 31);
     cy = __shfl_sync(0xffffffffu, y, 31);
   }
+  // area, level and energy sums of each segment of set bits in a word
+  cp_async_wait_all();
+#pragma unroll
+  for (int c = 0; c < MAXC; ++c) {
+    uint32_t mm = X[c];
+    const uint8_t *myq = lq + 32 * c;
+    while (mm) {
+      const int b0 = __ffs(mm) - 1;
+      const uint32_t inv = ~(mm >> b0);
+      const int len = inv ? __ffs(inv) - 1 : 32 - b0;
+      uint32_t sq = 0;
+      unsigned long long se = 0;
+      for (int b = b0; b < b0 + len; ++b) {
+        const uint32_t q = myq[b];
+        sq += q;
+        se += Es[q];
+      }
+      rise_box *rc = &a.rec[base + BS[c] + __popc(SX[c] & mask_upto(b0)) - 1];
+      atomicAdd(reinterpret_cast<unsigned long long *>(&rc->area), (unsigned long long)len);
+      atomicAdd(reinterpret_cast<unsigned long long *>(&rc->sum_q), (unsigned long long)sq);
+      atomicAdd(reinterpret_cast<unsigned long long *>(&rc->energy_fx), se);
+      mm &= (len + b0 >= 32) ? 0u : ~0u << (b0 + len);
+    }
+  }
 }
 
-__global__ void __launch_bounds__(32 * ROW_WARPS, 4)
+// levels staged per lane: MAXC chunks x 32 bytes, lanes 16 bytes apart more
+// than that (fewer bank conflicts on the byte reads; copies stay 16-aligned)
+constexpr int row_lane_bytes(int maxc) { return maxc * 32 + 16; }
+constexpr size_t row_smem(int maxc) { return (size_t)ROW_WARPS * 32 * row_lane_bytes(maxc); }
+
+template <int MAXC>
+__global__ void __launch_bounds__(32 * ROW_WARPS, MAXC >= 8 ? 3 : 4)
 runs_row_kernel(CclArgs a) {
   __shared__ unsigned long long Es[256];
-  __shared__ __align__(16) uint8_t qs[ROW_WARPS][32][32];   // each lane's 32 levels
+  extern __shared__ __align__(16) uint8_t lqs[];   // [ROW_WARPS][32 lanes][row_lane_bytes]
   for (int i = threadIdx.x; i < 256; i += blockDim.x) Es[i] = a.energy[i];
   __syncthreads();
   if (a.status->n_runs > a.run_cap) return;
@@ -296,16 +347,17 @@ runs_row_kernel(CclArgs a) {
   const int64_t t = (int64_t)blockIdx.x * ROW_WARPS + wib;
   if (t >= a.T) return;
   if (a.row_cnt[t] == 0) return;   // no runs in this row: nothing to label or unite
-  runs_row_body(a, Es, qs[wib][lane], t, t, a.T, a.F, a.mask, a.img);
+  runs_row_body<MAXC>(a, Es, lqs + (wib * 32 + lane) * row_lane_bytes(MAXC), t, t, a.T, a.F, a.mask, a.img);
 }
 
 // Batch: rows of all captures, concatenated (a.T = total rows); row0[c] is
 // the first row of capture c (ncap + 1 entries).  Rows of different
 // captures are never united: has_next stops at the capture's last row.
-__global__ void __launch_bounds__(32 * ROW_WARPS, 4)
+template <int MAXC>
+__global__ void __launch_bounds__(32 * ROW_WARPS, MAXC >= 8 ? 3 : 4)
 runs_row_batch_kernel(CclArgs a, const RowSeg *segs, const int64_t *row0, int ncap) {
   __shared__ unsigned long long Es[256];
-  __shared__ __align__(16) uint8_t qs[ROW_WARPS][32][32];
+  extern __shared__ __align__(16) uint8_t lqs[];
   for (int i = threadIdx.x; i < 256; i += blockDim.x) Es[i] = a.energy[i];
   __syncthreads();
   if (a.status->n_runs > a.run_cap) return;
@@ -320,7 +372,26 @@ runs_row_batch_kernel(CclArgs a, const RowSeg *segs, const int64_t *row0, int nc
     else hi = mid - 1;
   }
   const RowSeg rs = segs[lo];
-  runs_row_body(a, Es, qs[wib][lane], tg, tg - __ldg(&row0[lo]), rs.T, rs.F, rs.mask, rs.img);
+  runs_row_body<MAXC>(a, Es, lqs + (wib * 32 + lane) * row_lane_bytes(MAXC), tg, tg - __ldg(&row0[lo]), rs.T, rs.F,
+                      rs.mask, rs.img);
+}
+
+template <int MAXC>
+cudaError_t launch_rows(const CclArgs &a, const RowSeg *segs, const int64_t *row0, int ncap, cudaStream_t s) {
+  const unsigned row_blocks = (unsigned)((a.T + ROW_WARPS - 1) / ROW_WARPS);
+  const size_t sm = row_smem(MAXC);
+  cudaError_t e;
+  if (segs) {
+    e = cudaFuncSetAttribute(runs_row_batch_kernel<MAXC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    runs_row_batch_kernel<MAXC><<<row_blocks, 32 * ROW_WARPS, sm, s>>>(a, segs, row0, ncap);
+  } else {
+    e = cudaFuncSetAttribute(runs_row_kernel<MAXC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    runs_row_kernel<MAXC><<<row_blocks, 32 * ROW_WARPS, sm, s>>>(a);
+  }
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 // Batch: offs[c] = index of capture c's first box in the output (boxes of a
@@ -542,12 +613,13 @@ cudaError_t label_common(const CclArgs &a, const RowSeg *segs, const int64_t *ro
   const ScanState ss = scan_state(a.scan_tmp, scan_tiles(a.T));
   runs_init_kernel<<<g, 256, 0, s>>>(a, ss, root_tiles);
   count_launches(1);
-  const unsigned row_blocks = (unsigned)((a.T + ROW_WARPS - 1) / ROW_WARPS);
-  if (segs)
-    runs_row_batch_kernel<<<row_blocks, 32 * ROW_WARPS, 0, s>>>(a, segs, row0, ncap);
-  else
-    runs_row_kernel<<<row_blocks, 32 * ROW_WARPS, 0, s>>>(a);
-  count_launches(1);
+  // widest image of the launch (a.F; for a batch, the largest F)
+  const int nch = (a.F / 32 + 31) / 32;
+  cudaError_t er = nch <= 1 ? launch_rows<1>(a, segs, row0, ncap, s)
+                   : nch <= 2 ? launch_rows<2>(a, segs, row0, ncap, s)
+                   : nch <= 4 ? launch_rows<4>(a, segs, row0, ncap, s)
+                              : launch_rows<8>(a, segs, row0, ncap, s);
+  if (er != cudaSuccess) return er;
   ccl_flatten_kernel<<<g, 256, 0, s>>>(a);
   count_launches(1);
   ccl_merge_kernel<<<g, 256, 0, s>>>(a);
