@@ -320,19 +320,28 @@ __device__ __forceinline__ int64_t floor_div_d(int64_t a, int64_t b) {
 }
 
 __device__ __forceinline__ void floor_body(const ColArgs &a) {
-  // [F] D-scaled smoothing (int64), then [F] column PSD: S_f <= 255 T < 2^31
-  // and |c_i| < 2^12, so each tap is one 32 x 32 -> 64-bit product
+  // [F] D-scaled smoothing (int64), then [F] column PSD and [F] Otsu
+  // thresholds (int32 each): S_f <= 255 T < 2^31 and |c_i| < 2^12, so each
+  // tap is one 32 x 32 -> 64-bit product
   extern __shared__ int64_t Sh[];
   int32_t *S = reinterpret_cast<int32_t *>(Sh + a.F);
+  int32_t *TH = S + a.F;
   __shared__ int64_t red_min[32], red_g[32];
   __shared__ int red_found[32];
   __shared__ int32_t c[64];
   __shared__ int64_t s_N0, s_Pq;
   const int F = a.F, m = a.m, tid = threadIdx.x;
   for (int i = tid; i <= m; i += blockDim.x) c[i] = (int32_t)a.sg_c[i];
-  for (int f = tid; f < F; f += blockDim.x) S[f] = (int32_t)a.cols[f].S;
+  // one pass over the column records (the loads of a thread are independent)
+#pragma unroll 4
+  for (int f = tid; f < F; f += blockDim.x) {
+    const rise_colstat cs = a.cols[f];
+    S[f] = (int32_t)cs.S;
+    TH[f] = cs.otsu;
+  }
   __syncthreads();
   // Savitzky-Golay (D-scaled) on the interior, 0 elsewhere
+#pragma unroll 4
   for (int f = tid; f < F; f += blockDim.x) {
     int64_t acc = 0;
     if (f >= m && f <= F - 1 - m) {
@@ -354,7 +363,7 @@ __device__ __forceinline__ void floor_body(const ColArgs &a) {
       best = min(best, v);
     }
   }
-  const int lane = tid & 31, w = tid >> 5;
+  const int lane = tid & 31, w = tid >> 5, nw = (int)(blockDim.x >> 5);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
@@ -363,32 +372,37 @@ __device__ __forceinline__ void floor_body(const ColArgs &a) {
   }
   if (lane == 0) { red_min[w] = best; red_g[w] = gmin; red_found[w] = found; }
   __syncthreads();
-  if (tid == 0) {
-    int64_t bb = INT64_MAX, gg = INT64_MAX;
-    int ff = 0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-      bb = min(bb, red_min[i]);
-      gg = min(gg, red_g[i]);
-      ff |= red_found[i];
+  if (w == 0) {   // the warps' results, reduced by one warp
+    int64_t bb = lane < nw ? red_min[lane] : INT64_MAX;
+    int64_t gg = lane < nw ? red_g[lane] : INT64_MAX;
+    int ff = lane < nw ? red_found[lane] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      bb = min(bb, __shfl_xor_sync(0xffffffffu, bb, o));
+      gg = min(gg, __shfl_xor_sync(0xffffffffu, gg, o));
+      ff |= __shfl_xor_sync(0xffffffffu, ff, o);
     }
-    const int64_t N0 = ff ? bb : gg;
-    const int64_t DT = a.D * a.T;
-    int64_t Pq = 0;
-    if (a.pow_on) {
-      Pq = -floor_div_d(-(N0 + a.delta_pow), DT);   // ceil((N0 + delta_pow) / DT)
-      Pq = Pq < 0 ? 0 : (Pq > 256 ? 256 : Pq);
+    if (lane == 0) {
+      const int64_t N0 = ff ? bb : gg;
+      const int64_t DT = a.D * a.T;
+      int64_t Pq = 0;
+      if (a.pow_on) {
+        Pq = -floor_div_d(-(N0 + a.delta_pow), DT);   // ceil((N0 + delta_pow) / DT)
+        Pq = Pq < 0 ? 0 : (Pq > 256 ? 256 : Pq);
+      }
+      s_N0 = N0;
+      s_Pq = Pq;
+      int64_t *fo = a.floor_out;
+      fo[0] = N0; fo[1] = a.delta_psd; fo[2] = a.delta_pow; fo[3] = Pq;
+      fo[4] = a.D; fo[5] = a.T; fo[6] = F; fo[7] = 0;
     }
-    s_N0 = N0;
-    s_Pq = Pq;
-    int64_t *fo = a.floor_out;
-    fo[0] = N0; fo[1] = a.delta_psd; fo[2] = a.delta_pow; fo[3] = Pq;
-    fo[4] = a.D; fo[5] = a.T; fo[6] = F; fo[7] = 0;
   }
   __syncthreads();
   const int64_t N0 = s_N0, Pq = s_Pq;
+#pragma unroll 4
   for (int f = tid; f < F; f += blockDim.x) {
     const int keep = a.psd_on ? (a.D * (int64_t)S[f] >= N0 + a.delta_psd) : 1;
-    const int th = a.cols[f].otsu;
+    const int th = TH[f];
     int eff = 256;
     if (keep && th >= 0) eff = max(th + 1, (int)Pq);
     a.cols[f].keep = keep;
