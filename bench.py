@@ -324,7 +324,7 @@ def run_ours(args):
         # the same kernel against the FP32 pipe: FFT flops by the 5 N log2 N
         # convention over the peak of 128 FP32 lanes x 2 flops per SM clock
         sms = torch.cuda.get_device_properties(local).multi_processor_count
-        mhz = float(clocks.get("sm_max_mhz") or 2070.0)
+        mhz = float((clocks or {}).get("sm_max_mhz") or 2070.0)
         fp32_peak = sms * 128 * 2 * mhz * 1e6 / 1e12
         flops = T * 5 * N_FFT * int(math.log2(N_FFT))
         fp32_ach = flops / (dom_ms / 1e3) / 1e12
