@@ -50,28 +50,47 @@ __device__ __forceinline__ void st_release(uint64_t *p, uint64_t v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Thread 0 of tile `tile` (sum `agg`): the sum of all earlier tiles.
+// Warp 0 of tile `tile` (sum `agg`): the sum of all earlier tiles, returned
+// to every lane.  The warp reads 32 predecessors at once (lane l: tile
+// hi - l), waits until each has published, and adds the values up to and
+// including the nearest full prefix; without one in the window it moves 32
+// tiles back.  Tiles before 0 read as a full prefix of 0.
 __device__ int64_t lookback(uint64_t *stat, int64_t tile, int64_t agg, DeviceStatus *st) {
+  const int lane = threadIdx.x & 31;
   if (tile == 0) {
-    st_release(&stat[0], LB_INC | (uint64_t)agg);
+    if (lane == 0) st_release(&stat[0], LB_INC | (uint64_t)agg);
     return 0;
   }
-  st_release(&stat[tile], LB_AGG | (uint64_t)agg);
+  if (lane == 0) st_release(&stat[tile], LB_AGG | (uint64_t)agg);
   int64_t excl = 0;
-  for (int64_t k = tile - 1; k >= 0; --k) {
-    uint64_t w = ld_acquire(&stat[k]);
-    for (int spins = 0; (w >> 62) == 0; ++spins) {
-      if (spins >= LB_SPIN_LIMIT) {
-        set_err(st, ERR_SCAN);
-        return excl;
-      }
-      __nanosleep(32);
+  for (int64_t hi = tile - 1;; hi -= 32) {
+    const int64_t k = hi - lane;
+    uint64_t w = LB_INC;
+    bool late = false;
+    if (k >= 0) {
       w = ld_acquire(&stat[k]);
+      for (int spins = 0; (w >> 62) == 0; ++spins) {
+        if (spins >= LB_SPIN_LIMIT) {
+          late = true;
+          break;
+        }
+        __nanosleep(32);
+        w = ld_acquire(&stat[k]);
+      }
     }
-    excl += (int64_t)(w & LB_VAL);
-    if ((w >> 62) == 2) break;
+    if (__any_sync(0xffffffffu, late)) {
+      if (lane == 0) set_err(st, ERR_SCAN);
+      return excl;
+    }
+    const unsigned inc = __ballot_sync(0xffffffffu, (w >> 62) == 2);
+    const int first = inc ? __ffs(inc) - 1 : 31;   // the nearest full prefix
+    int64_t v = lane <= first ? (int64_t)(w & LB_VAL) : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    excl += v;
+    if (inc) break;
   }
-  st_release(&stat[tile], LB_INC | (uint64_t)(excl + agg));
+  if (lane == 0) st_release(&stat[tile], LB_INC | (uint64_t)(excl + agg));
   return excl;
 }
 
@@ -105,7 +124,10 @@ __device__ __forceinline__ void tile_scan(const In *in, int64_t n, int64_t tile,
   }
   int64_t tot;
   const int64_t mine = block_exclusive_scan<int64_t>(sum, scratch, &tot);
-  if (threadIdx.x == 0) s_prefix = lookback(stat, tile, tot, st);
+  if (threadIdx.x < 32) {
+    const int64_t e = lookback(stat, tile, tot, st);
+    if (threadIdx.x == 0) s_prefix = e;
+  }
   __syncthreads();
   int64_t run = s_prefix + mine;
 #pragma unroll
