@@ -437,22 +437,28 @@ __global__ void ccl_offsets_kernel(CclArgs a, const int64_t *row0, int ncap, int
 
 // ---------------------------------------------------------------------------
 // 3b. point every run straight at its root (the row pass leaves chains as
-//     tall as the component), then apply the deferred unions on flat trees.
+//     tall as the component), then apply the deferred unions.
 // ---------------------------------------------------------------------------
-__global__ void ccl_flatten_kernel(CclArgs a) {
+// FLATTEN: every thread points its runs at their roots; MERGE: it applies
+// its share of the deferred unions.  With both in one launch (one image:
+// few runs, the launch costs more than the overlap) the phases of different
+// threads overlap, which the lock-free union-find allows: a path-halving
+// store always writes an ancestor, and a union links one root under a
+// smaller root with a CAS that fails if the root has moved.  Batches (many
+// runs, tall chains) run the phases as two launches.
+template <bool FLATTEN, bool MERGE>
+__global__ void ccl_flatten_merge_kernel(CclArgs a) {
   DeviceStatus *st = a.status;
   const int64_t n = st->n_runs;
   if (n > a.run_cap) return;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
-       g += (int64_t)gridDim.x * blockDim.x) {
-    const int r = uf_find(a.run_parent, (int)g, st);
-    if (r != (int)g) *(volatile int *)&a.run_parent[g] = r;   // an ancestor: still valid
+  if (FLATTEN) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
+         g += (int64_t)gridDim.x * blockDim.x) {
+      const int r = uf_find(a.run_parent, (int)g, st);
+      if (r != (int)g) *(volatile int *)&a.run_parent[g] = r;   // an ancestor: still valid
+    }
   }
-}
-
-__global__ void ccl_merge_kernel(CclArgs a) {
-  DeviceStatus *st = a.status;
-  if (st->n_runs > a.run_cap) return;
+  if (!MERGE) return;
   const int64_t m = min(st->n_merge, a.run_cap);
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
        k += (int64_t)gridDim.x * blockDim.x) {
@@ -517,29 +523,34 @@ __global__ void ccl_reduce_kernel(CclArgs a) {
 __global__ void __launch_bounds__(SCAN_THREADS) root_scan_kernel(CclArgs a, ScanState ss) {
   DeviceStatus *st = a.status;
   const int64_t n = st->n_runs;
-  __shared__ int64_t s_tile;
-  if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(reinterpret_cast<unsigned long long *>(ss.ticket_roots), 1ull);
-  __syncthreads();
-  const int64_t tile = s_tile;
   if (n > a.run_cap) {
     if (blockIdx.x == 0 && threadIdx.x == 0) st->n_boxes = 0;
     return;
   }
-  if (tile >= scan_tiles(n)) return;
-  int64_t v[SCAN_ITEMS], ex[SCAN_ITEMS];
-  tile_scan<uint8_t>(a.run_sroot, n, tile, ss.roots, st, v, ex);
-  const int64_t base = tile * SCAN_BLOCK + (int64_t)threadIdx.x * SCAN_ITEMS;
+  // persistent: the grid is sized on the capacity, the tiles on the runs
+  const int64_t tiles = scan_tiles(n);
+  __shared__ int64_t s_tile;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(reinterpret_cast<unsigned long long *>(ss.ticket_roots), 1ull);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    if (tile >= tiles) return;
+    int64_t v[SCAN_ITEMS], ex[SCAN_ITEMS];
+    tile_scan<uint8_t>(a.run_sroot, n, tile, ss.roots, st, v, ex);
+    const int64_t base = tile * SCAN_BLOCK + (int64_t)threadIdx.x * SCAN_ITEMS;
 #pragma unroll
-  for (int i = 0; i < SCAN_ITEMS; ++i) {
-    const int64_t k = base + i;
-    if (k < n) {
-      a.run_out[k] = ex[i];
-      if (v[i] && ex[i] < a.box_cap) a.boxes[ex[i]] = a.rec[k];
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+      const int64_t k = base + i;
+      if (k < n) {
+        a.run_out[k] = ex[i];
+        if (v[i] && ex[i] < a.box_cap) a.boxes[ex[i]] = a.rec[k];
+      }
+      if (k == n) {
+        a.run_out[n] = ex[i];
+        st->n_boxes = ex[i];
+      }
     }
-    if (k == n) {
-      a.run_out[n] = ex[i];
-      st->n_boxes = ex[i];
-    }
+    __syncthreads();   // s_tile and the scan's shared words are reused
   }
 }
 
@@ -642,17 +653,22 @@ cudaError_t label_common(const CclArgs &a, const RowSeg *segs, const int64_t *ro
                    : nch <= 4 ? launch_rows<4>(a, segs, row0, ncap, s)
                               : launch_rows<8>(a, segs, row0, ncap, s);
   if (er != cudaSuccess) return er;
-  ccl_flatten_kernel<<<g, 256, 0, s>>>(a);
-  count_launches(1);
-  ccl_merge_kernel<<<g, 256, 0, s>>>(a);
-  count_launches(1);
+  if (segs) {
+    ccl_flatten_merge_kernel<true, false><<<g, 256, 0, s>>>(a);
+    ccl_flatten_merge_kernel<false, true><<<g, 256, 0, s>>>(a);
+    count_launches(2);
+  } else {
+    ccl_flatten_merge_kernel<true, true><<<g, 256, 0, s>>>(a);
+    count_launches(1);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   ccl_reduce_kernel<<<g, 256, 0, s>>>(a);
   count_launches(1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  root_scan_kernel<<<(unsigned)root_tiles, SCAN_THREADS, 0, s>>>(a, ss);
+  root_scan_kernel<<<(unsigned)std::min<int64_t>(root_tiles, (int64_t)num_sms * (segs ? 4 : 1)), SCAN_THREADS,
+                     0, s>>>(a, ss);
   count_launches(1);
   if (segs) {
     ccl_offsets_kernel<<<(ncap + 1 + 255) / 256, 256, 0, s>>>(a, row0, ncap, offs);
