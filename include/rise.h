@@ -121,6 +121,11 @@ void rise_destroy(rise_ctx *ctx);
 /* Static description of a status code. */
 const char *rise_strerror(int code);
 
+/* Host-side layout helper for bindings: boxes[i] -> out[8 i .. 8 i + 7] =
+ * t0, t1, f0, f1, anchor, area, sum_q, energy_fx as int64 (sum_q and
+ * energy_fx stay below 2^63).  in and out are host memory; n >= 0. */
+void rise_boxes_widen(const rise_box *in, int64_t n, int64_t *out);
+
 /* Detects energy blocks in one capture (Sec. III-A-1 formulation).
  *  iq_dev    device pointer to n complex64 samples, interleaved (re, im),
  *            8-byte aligned.

@@ -603,6 +603,21 @@ void rise_thresholds_default(rise_thresholds *t) {
   t->morph_order = 0;
 }
 
+void rise_boxes_widen(const rise_box *in, int64_t n, int64_t *out) {
+  for (int64_t i = 0; i < n; ++i) {
+    const rise_box &b = in[i];
+    int64_t *o = out + 8 * i;
+    o[0] = b.t0;
+    o[1] = b.t1;
+    o[2] = b.f0;
+    o[3] = b.f1;
+    o[4] = b.anchor;
+    o[5] = b.area;
+    o[6] = (int64_t)b.sum_q;
+    o[7] = (int64_t)b.energy_fx;
+  }
+}
+
 const char *rise_strerror(int code) {
   switch (code) {
     case RISE_OK: return "ok";
