@@ -38,6 +38,8 @@ bool tma_ok(const rise_capture &k) {
   return k.hop % 2 == 0 && (reinterpret_cast<uintptr_t>(k.iq_dev) & 15) == 0;
 }
 
+constexpr int64_t kHistSplitRows = 8192;
+
 struct Plan {
   int ncap = 0;
   bool fixed = false;
@@ -57,6 +59,10 @@ struct Plan {
   // blob layout
   size_t o_stft, o_items, o_hseg, o_hitem, o_col, o_mseg, o_mitem, o_wbase, o_rseg, o_row0, bytes;
   int n_items = 0, n_hitems = 0, total_warps = 0, hist_bands = 8;
+  // histogram items of captures taller than kHistSplitRows come first and
+  // run in clusters of hist_bands row bands; the rest run one block per
+  // column group (hist_bands_small), which costs the least block time
+  int n_hbig = 0, hist_bands_small = 1;
   uint64_t shape_key = 0;
 };
 
@@ -118,16 +124,25 @@ void size_tables(const rise_ctx *c, const rise_capture *caps, Plan &p) {
     p.n_items += cnt;
   }
   p.n_hitems = 0;
+  p.n_hbig = 0;
   p.total_warps = 0;
-  int64_t max_T = 1;
-  for (int k = 0; k < p.ncap; ++k) max_T = std::max(max_T, p.T[k]);
+  int64_t max_T = 1, max_T_small = 1;
+  for (int k = 0; k < p.ncap; ++k) {
+    if (p.T[k] > kHistSplitRows) {
+      max_T = std::max(max_T, p.T[k]);
+      p.n_hbig += caps[k].fft_size / 64;
+    } else {
+      max_T_small = std::max(max_T_small, p.T[k]);
+    }
+  }
   for (int k = 0; k < p.ncap; ++k) {
     p.n_hitems += caps[k].fft_size / 64;
     int nx, rows, w;
     morph_plan(p.T[k], caps[k].fft_size, c->num_sms, p.morph_wps, 32, &nx, &rows, &w);
     p.total_warps += w;
   }
-  p.hist_bands = cluster_hist_bands(!p.fixed, p.n_hitems, max_T);
+  p.hist_bands = p.n_hbig ? cluster_hist_bands(!p.fixed, p.n_hbig, max_T) : 1;
+  p.hist_bands_small = (int)((max_T_small + 65534) / 65535);   // 1: a band holds up to 65535 rows
   size_t o = 0;
   auto take = [&](size_t bytes) {
     const size_t at = o;
@@ -249,7 +264,7 @@ int fill_tables(rise_ctx *c, const rise_capture *caps, const Plan &p, const rise
   const bool pow_on = !(std::isinf(thr.power_offset_db) && thr.power_offset_db < 0);
   std::vector<int> next_item(p.groups.size());
   for (size_t g = 0; g < p.groups.size(); ++g) next_item[g] = p.groups[g].item0;
-  int hi = 0, warps = 0;
+  int hi = 0, hs = p.n_hbig, warps = 0;   // histogram items: tall captures, then short ones
   for (int k = 0; k < p.ncap; ++k) {
     const rise_capture &cp = caps[k];
     const int F = cp.fft_size;
@@ -285,14 +300,16 @@ int fill_tables(rise_ctx *c, const rise_capture *caps, const Plan &p, const rise
     ha.src = p.fixed ? static_cast<const void *>(a.img) : static_cast<const void *>(a.power);
     ha.T = T;
     ha.F = F;
-    ha.rows_per_band = (T + p.hist_bands - 1) / p.hist_bands;
+    const bool big = T > kHistSplitRows;
+    const int bands = big ? p.hist_bands : p.hist_bands_small;
+    ha.rows_per_band = (T + bands - 1) / bands;
     ha.edges = cs[k].edges;
     ha.qconst = cs[k].qconst;
     ha.img = a.img;
     ha.hist = hist + p.col_off[k] * 256;
     ha.cols = cols + p.col_off[k];
     ha.accumulate = 0;
-    for (int cg = 0; cg < F / 64; ++cg) hitem[hi++] = HistItem{k, cg};
+    for (int cg = 0; cg < F / 64; ++cg) hitem[big ? hi++ : hs++] = HistItem{k, cg};
     ColArgs &ca = col[k];
     ca.hist = ha.hist;
     ca.T = T;
@@ -386,7 +403,9 @@ int enqueue(rise_ctx *c, const Plan &p, const rise_thresholds &thr, int64_t cap,
   }
   record(c, 1);
   if (!p.fixed) CK(launch_levels_batch(cs, p.ncap, 0.0, 0, sm->ratio, thr.level_db, s));
-  CK(launch_cluster_hist_batch(!p.fixed, hseg, hitem, p.n_hitems, p.hist_bands, s));
+  if (p.n_hbig) CK(launch_cluster_hist_batch(!p.fixed, hseg, hitem, p.n_hbig, p.hist_bands, s));
+  if (p.n_hitems > p.n_hbig)
+    CK(launch_cluster_hist_batch(!p.fixed, hseg, hitem + p.n_hbig, p.n_hitems - p.n_hbig, p.hist_bands_small, s));
   record(c, 2);
   record(c, 3);
   CK(launch_floor_batch(col, p.ncap, p.max_F, s));
