@@ -409,6 +409,7 @@ def run_batched(args):
     t_batch, l_batch, st_batch, (boxes, offs) = timed(batched)
     same = all(np.array_equal(boxes[offs[c]:offs[c + 1]], res_plain[c]) for c in range(len(xs)))
     info = det.batch_info()
+    ccl = det.debug(rise.DBG_CCL, 0, 0)   # runs, deferred unions, boxes, run capacity
     t_plain = _allreduce_max(t_plain, world)
     t_batch = _allreduce_max(t_batch, world)
     # end to end: pinned host captures copied in, then the batch call
@@ -448,6 +449,8 @@ def run_batched(args):
                   "gpu_launches": int(l_plain)},
         "batched_over_plain": round(t_plain / t_batch, 3),
         "boxes_identical": bool(same), "boxes": int(offs[-1]),
+        "runs": int(ccl[0]) if ccl is not None else None,
+        "deferred_unions": int(ccl[1]) if ccl is not None else None,
         "roofline": {"bound": "hbm", "kernel": "spectrum (all STFT launches of the batch)",
                      "achieved": round(alg / (stft_ms / 1e3) / 1e9, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(alg / (stft_ms / 1e3) / 1e9 / peak, 4), "traffic": None,

@@ -12,7 +12,7 @@
 //
 //   1. the morphology kernel counts the runs of each row; a single-pass
 //      exclusive scan gives row_base[t], the number of the first run of row t.
-//   2. init: every run is its own tree, with zeroed sums.
+//   2. init: every run is its own tree.
 //   3. rows: one warp per row records each run's extent, area, level sum and
 //      energy, and unites it with the runs of the next row that share a
 //      column (4-connectivity), on a global lock-free union-find.
@@ -161,7 +161,7 @@ row_scan_kernel(const uint32_t *cnt, int64_t T, int64_t *row_base, DeviceStatus 
 }
 
 // ---------------------------------------------------------------------------
-// 2. per-run initialisation: every run is its own tree and record
+// 2. per-run initialisation: every run is its own tree
 // ---------------------------------------------------------------------------
 __global__ void runs_init_kernel(CclArgs a, ScanState ss, int64_t root_tiles) {
   DeviceStatus *st = a.status;
@@ -180,10 +180,6 @@ __global__ void runs_init_kernel(CclArgs a, ScanState ss, int64_t root_tiles) {
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
        g += (int64_t)gridDim.x * blockDim.x) {
     a.run_parent[g] = (int)g;
-    a.run_sroot[g] = 1;
-    a.rec[g].area = 0;
-    a.rec[g].sum_q = 0;
-    a.rec[g].energy_fx = 0;
   }
 }
 
@@ -326,12 +322,17 @@ __device__ __forceinline__ void runs_row_body(const CclArgs &a, const unsigned l
     cx = __shfl_sync(0xffffffffu, x, 31);
     cy = __shfl_sync(0xffffffffu, y, 31);
   }
-  // area, level and energy sums of each segment of set bits in a word
+  // area, level and energy sums of each segment of set bits in a word: a
+  // run's first segment is stored (no zeroed record needed), the segment
+  // continuing a run from an earlier word (at most one per word) is added
+  // once every first segment of the chunk is stored
   cp_async_wait_all();
 #pragma unroll
   for (int c = 0; c < MAXC; ++c) {
     uint32_t mm = X[c];
     const uint8_t *myq = lq + 32 * c;
+    rise_box *cont = nullptr;
+    unsigned long long c_area = 0, c_sq = 0, c_se = 0;
     while (mm) {
       const int b0 = __ffs(mm) - 1;
       const uint32_t inv = ~(mm >> b0);
@@ -344,10 +345,23 @@ __device__ __forceinline__ void runs_row_body(const CclArgs &a, const unsigned l
         se += Es[q];
       }
       rise_box *rc = &a.rec[base + BS[c] + __popc(SX[c] & mask_upto(b0)) - 1];
-      atomicAdd(reinterpret_cast<unsigned long long *>(&rc->area), (unsigned long long)len);
-      atomicAdd(reinterpret_cast<unsigned long long *>(&rc->sum_q), (unsigned long long)sq);
-      atomicAdd(reinterpret_cast<unsigned long long *>(&rc->energy_fx), se);
+      if ((SX[c] >> b0) & 1u) {
+        rc->area = len;
+        rc->sum_q = sq;
+        rc->energy_fx = se;
+      } else {
+        cont = rc;
+        c_area = (unsigned long long)len;
+        c_sq = sq;
+        c_se = se;
+      }
       mm &= (len + b0 >= 32) ? 0u : ~0u << (b0 + len);
+    }
+    __syncwarp();   // orders the chunk's first-segment stores before the adds
+    if (cont) {
+      atomicAdd(reinterpret_cast<unsigned long long *>(&cont->area), c_area);
+      atomicAdd(reinterpret_cast<unsigned long long *>(&cont->sum_q), c_sq);
+      atomicAdd(reinterpret_cast<unsigned long long *>(&cont->energy_fx), c_se);
     }
   }
 }
@@ -469,7 +483,7 @@ __global__ void ccl_flatten_merge_kernel(CclArgs a) {
 
 // ---------------------------------------------------------------------------
 // 4. every run that is not its component's root adds its record into the
-//    root's; run_sroot keeps 1 exactly for the roots.  Lanes of a warp with
+//    root's; run_sroot is set to 1 exactly for the roots.  Lanes of a warp with
 //    the same root combine first, so a tall component costs one atomic per
 //    field per warp rather than per run.
 // ---------------------------------------------------------------------------
@@ -483,7 +497,7 @@ __global__ void ccl_reduce_kernel(CclArgs a) {
     const bool live = g < n;
     int r = live ? uf_find(a.run_parent, (int)g, st) : -1;
     const bool contrib = live && r != (int)g;
-    if (live && contrib) a.run_sroot[g] = 0;
+    if (live) a.run_sroot[g] = contrib ? 0 : 1;
     rise_box src;
     if (contrib) src = a.rec[g];
     const unsigned grp = __match_any_sync(0xffffffffu, contrib ? r : -1);

@@ -472,7 +472,7 @@ class Detector:
     def debug(self, what: int, T: int, F: int) -> np.ndarray:
         shapes = {
             DBG_POWER_F32: ((T, F), np.float32), DBG_IMAGE_U8: ((T, F), np.uint8),
-            DBG_HIST: ((F, 256), np.uint32), DBG_FLOOR: ((8,), np.int64),
+            DBG_HIST: ((F, 256), np.uint32), DBG_FLOOR: ((8,), np.int64), DBG_CCL: ((4,), np.int64),
             DBG_MASK0: ((T, F // 32), np.uint32), DBG_MASK1: ((T, F // 32), np.uint32),
             DBG_MASK2: ((T, F // 32), np.uint32), DBG_MASK3: ((T, F // 32), np.uint32),
             DBG_MAXPOW: ((1,), np.float32), DBG_LEVEL_EDGES: ((257,), np.float32),
