@@ -18,6 +18,12 @@ namespace rise {
 namespace host {
 namespace {
 
+// dst[i] = src[i] for i < n (src: pinned host memory, read over the bus)
+__global__ void copy16_kernel(uint4 *dst, const uint4 *src, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
 constexpr int kMaxGraphs = 64;
 constexpr int kItemCands[] = {1, 2, 4, 8, 16};      // STFT work item = k x frames per step
 constexpr int kMorphCands[] = {8, 16, 32};          // morphology warps per SM
@@ -388,7 +394,15 @@ int enqueue(rise_ctx *c, const Plan &p, const rise_thresholds &thr, int64_t cap,
     if (ev) cudaEventRecord(ev->e[ev->n++], s);
   };
   record(c, 0);
-  CK(cudaMemcpyAsync(b.tab.p, b.tab_h, p.bytes, cudaMemcpyHostToDevice, s));
+  // the tables come over with SM loads from the pinned staging blob, not a
+  // copy engine: H2D copies the caller queues (e.g. the next batch's
+  // samples) would hold a copy-engine upload back
+  {
+    const int64_t n16 = (int64_t)(p.bytes / 16);
+    const int g = (int)std::min<int64_t>(std::max<int64_t>((n16 + 255) / 256, 1), (int64_t)c->num_sms * 4);
+    copy16_kernel<<<g, 256, 0, s>>>(static_cast<uint4 *>(b.tab.p), static_cast<const uint4 *>(b.tab_h), n16);
+    count_launches(1);
+  }
   CK(cudaMemsetAsync(&sm->status, 0, sizeof(DeviceStatus), s));
   CK(cudaMemsetAsync(cs, 0, sizeof(CapSmall) * p.ncap, s));
   CK(cudaMemsetAsync(counters, 0, sizeof(int) * p.groups.size(), s));

@@ -209,7 +209,7 @@ class Detector:
         self.stream = stream
         self._ev = torch.cuda.Event()
         self.cap = 1 << 16
-        self._batch_key, self._batch_caps = None, None
+        self._batch_caps = {}   # capture tables of recent batch calls, by their tensors
 
     def close(self):
         if getattr(self, "_h", None):
@@ -422,20 +422,21 @@ class Detector:
             fft_sizes = [fft_sizes] * k
         if isinstance(hops, int):
             hops = [hops] * k
-        # the capture table of the previous call is reused when the same
-        # tensors (same objects, storage, size and type) come again
+        # a recent call's capture table is reused when the same tensors (same
+        # objects, storage, size and type) come again
         key = (tuple((id(x), x.data_ptr(), x.numel(), x.dtype) for x in iqs),
                tuple(fft_sizes), tuple(hops))
-        if key == self._batch_key:
-            caps = self._batch_caps
-        else:
+        caps = self._batch_caps.get(key)
+        if caps is None:
             caps = (Capture * max(k, 1))()
             for i, x in enumerate(iqs):
                 if not (isinstance(x, t.Tensor) and x.is_cuda and x.dtype == t.complex64
                         and x.is_contiguous() and x.dim() == 1):
                     raise TypeError("each capture must be a contiguous 1-D CUDA complex64 tensor")
                 caps[i] = Capture(x.data_ptr(), x.numel(), int(fft_sizes[i]), int(hops[i]))
-            self._batch_key, self._batch_caps = key, caps
+            if len(self._batch_caps) >= 4:
+                self._batch_caps.pop(next(iter(self._batch_caps)))
+            self._batch_caps[key] = caps
         offs = np.zeros(k + 1, np.int64)
         cap = self.cap if cap is None else int(cap)
         self._order()
