@@ -448,6 +448,7 @@ int enqueue(rise_ctx *c, const Plan &p, const rise_thresholds &thr, int64_t cap,
   la.boxes = c->cs().hbox_dev;
   la.box_cap = cap;
   la.status = &sm->status;
+  la.status_out = nullptr;   // the offsets kernel runs after the labelling: a copy node reads the status
   CK(launch_ccl_count(la, c->num_sms, s));
   CK(launch_ccl_label_batch(la, rseg, row0, p.ncap, b.offs_dev, c->num_sms, s));
   record(c, 6);

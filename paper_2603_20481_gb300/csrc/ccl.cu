@@ -95,14 +95,15 @@ __device__ int64_t lookback(uint64_t *stat, int64_t tile, int64_t agg, DeviceSta
 }
 
 // Scan scratch: [0] ticket of the row scan, [1] ticket of the root scan,
-// [2, 2 + tiles) row-scan tile words, then root-scan tile words.
+// [2] blocks of the root scan done, [3, 3 + tiles) row-scan tile words, then
+// root-scan tile words.
 struct ScanState {
-  uint64_t *ticket_rows, *ticket_roots, *rows, *roots;
+  uint64_t *ticket_rows, *ticket_roots, *done_roots, *rows, *roots;
 };
 __host__ __device__ inline int64_t scan_tiles(int64_t n) { return n / SCAN_BLOCK + 1; }
 inline ScanState scan_state(void *tmp, int64_t row_tiles) {
   uint64_t *w = static_cast<uint64_t *>(tmp);
-  return ScanState{w, w + 1, w + 2, w + 2 + row_tiles};
+  return ScanState{w, w + 1, w + 2, w + 3, w + 3 + row_tiles};
 }
 
 // A tile's items, their exclusive offsets within the whole scan and (for the
@@ -166,14 +167,15 @@ row_scan_kernel(const uint32_t *cnt, int64_t T, int64_t *row_base, DeviceStatus 
 __global__ void runs_init_kernel(CclArgs a, ScanState ss, int64_t root_tiles) {
   DeviceStatus *st = a.status;
   const int64_t n = st->n_runs;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *ss.ticket_roots = 0;   // the root scan's state (this chain may run again on a relabel)
+    *ss.done_roots = 0;
+  }
   if (n > a.run_cap) {
     if (blockIdx.x == 0 && threadIdx.x == 0) set_err(st, ERR_RUN_CAPACITY);
     return;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    st->n_merge = 0;
-    *ss.ticket_roots = 0;   // the root scan's state (this chain may run again on a relabel)
-  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->n_merge = 0;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < root_tiles;
        k += (int64_t)gridDim.x * blockDim.x)
     ss.roots[k] = 0;
@@ -534,7 +536,7 @@ __global__ void ccl_reduce_kernel(CclArgs a) {
 //    single-pass scan that also writes each root's record to its slot; with
 //    too many runs for the arrays, no boxes
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(SCAN_THREADS) root_scan_kernel(CclArgs a, ScanState ss) {
+__device__ __forceinline__ void root_scan_body(const CclArgs &a, const ScanState &ss) {
   DeviceStatus *st = a.status;
   const int64_t n = st->n_runs;
   if (n > a.run_cap) {
@@ -565,6 +567,26 @@ __global__ void __launch_bounds__(SCAN_THREADS) root_scan_kernel(CclArgs a, Scan
       }
     }
     __syncthreads();   // s_tile and the scan's shared words are reused
+  }
+}
+
+// The last kernel of a single image's chain: after the scan, the last block
+// to finish copies the status to the caller's mapped host copy (no copy
+// node after the kernel).
+__global__ void __launch_bounds__(SCAN_THREADS) root_scan_kernel(CclArgs a, ScanState ss) {
+  root_scan_body(a, ss);
+  if (!a.status_out) return;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long d = atomicAdd(reinterpret_cast<unsigned long long *>(ss.done_roots), 1ull);
+    if (d == gridDim.x - 1) {   // every other block has finished its status writes
+      __threadfence();
+      const volatile uint32_t *src = reinterpret_cast<const volatile uint32_t *>(a.status);
+      volatile uint32_t *dst = reinterpret_cast<volatile uint32_t *>(a.status_out);
+      for (int i = 0; i < (int)(sizeof(DeviceStatus) / 4); ++i) dst[i] = src[i];
+      __threadfence_system();
+    }
   }
 }
 
@@ -634,16 +656,16 @@ int grid_for(int64_t n, int threads, int num_sms, int per_sm) {
 }  // namespace
 
 size_t ccl_scan_tmp_bytes(int64_t max_items) {
-  return (size_t)(2 + 2 * scan_tiles(max_items)) * sizeof(uint64_t);
+  return (size_t)(3 + 2 * scan_tiles(max_items)) * sizeof(uint64_t);
 }
 
 cudaError_t launch_ccl_count(const CclArgs &a, int num_sms, cudaStream_t s) {
   (void)num_sms;
   const int64_t tiles = scan_tiles(a.T);
-  if ((size_t)(2 + tiles + scan_tiles(a.run_cap)) * sizeof(uint64_t) > a.scan_tmp_bytes)
+  if ((size_t)(3 + tiles + scan_tiles(a.run_cap)) * sizeof(uint64_t) > a.scan_tmp_bytes)
     return cudaErrorInvalidValue;
   const ScanState ss = scan_state(a.scan_tmp, tiles);
-  cudaError_t e = cudaMemsetAsync(a.scan_tmp, 0, (size_t)(2 + tiles) * sizeof(uint64_t), s);
+  cudaError_t e = cudaMemsetAsync(a.scan_tmp, 0, (size_t)(3 + tiles) * sizeof(uint64_t), s);
   if (e != cudaSuccess) return e;
   row_scan_kernel<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(a.row_cnt, a.T, a.row_base, a.status, ss);
   count_launches(1);
@@ -655,7 +677,7 @@ cudaError_t label_common(const CclArgs &a, const RowSeg *segs, const int64_t *ro
                          int64_t *offs, int num_sms, cudaStream_t s) {
   const int g = grid_for(a.run_cap, 256, num_sms, segs ? 16 : 4);
   const int64_t root_tiles = scan_tiles(a.run_cap);
-  if ((size_t)(2 + scan_tiles(a.T) + root_tiles) * sizeof(uint64_t) > a.scan_tmp_bytes)
+  if ((size_t)(3 + scan_tiles(a.T) + root_tiles) * sizeof(uint64_t) > a.scan_tmp_bytes)
     return cudaErrorInvalidValue;
   const ScanState ss = scan_state(a.scan_tmp, scan_tiles(a.T));
   runs_init_kernel<<<g, 256, 0, s>>>(a, ss, root_tiles);

@@ -272,6 +272,7 @@ struct CclArgs {
   rise_box *boxes;        // [box_cap] output
   int64_t box_cap;
   DeviceStatus *status;
+  DeviceStatus *status_out;   // mapped host copy written by the last kernel, or NULL
 };
 size_t ccl_scan_tmp_bytes(int64_t max_items);
 // Scan of the per-row run counts: fills row_base and status->n_runs.

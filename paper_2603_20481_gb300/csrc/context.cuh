@@ -64,7 +64,8 @@ struct CallSlot {
   rise_box *hbox = nullptr;      // mapped pinned host buffer the compaction writes into
   rise_box *hbox_dev = nullptr;  // its device address
   int64_t hbox_cap = 0;
-  DeviceStatus *st_h = nullptr;  // pinned status readback
+  DeviceStatus *st_h = nullptr;  // pinned, mapped status readback
+  DeviceStatus *st_d = nullptr;  // its device address
   cudaEvent_t ev[8] = {};        // stage events
   cudaEvent_t done = nullptr;    // the call's work has finished
   cudaEvent_t copied = nullptr;  // its host samples are on the device

@@ -170,6 +170,7 @@ CclArgs ccl_args(rise_ctx *c, const uint8_t *img, int64_t T, int F, int64_t cap)
   la.row_base = reinterpret_cast<int64_t *>(c->row_base.p);
   la.row_cnt = reinterpret_cast<uint32_t *>(c->row_cnt.p);
   la.status = &c->small->status;
+  la.status_out = c->cs().st_d;   // the status lands in mapped pinned host memory too
   la.boxes = c->cs().hbox_dev;   // boxes land directly in mapped pinned host memory
   la.box_cap = cap;
   la.run_cap = c->run_cap;
@@ -245,9 +246,8 @@ int image_enqueue(rise_ctx *c, const uint8_t *img, int64_t T, int F, const rise_
   // labelling
   const CclArgs la = ccl_args(c, img, T, F, cap);
   CK(launch_ccl_count(la, c->num_sms, s));
-  CK(launch_ccl_label(la, c->num_sms, s));
+  CK(launch_ccl_label(la, c->num_sms, s));   // its last kernel hands the status to the host
   record(c, 6);
-  CK(cudaMemcpyAsync(c->cs().st_h, &sm->status, sizeof(DeviceStatus), cudaMemcpyDeviceToHost, s));
   record(c, 7);
   return RISE_OK;
 }
@@ -275,7 +275,6 @@ int image_finish(rise_ctx *c, const uint8_t *img, int64_t T, int F, rise_box *ou
     CK(cudaMemsetAsync(&sm->status.err, 0, sizeof(uint32_t), s));
     CK(launch_ccl_label(la, c->num_sms, s));
     record(c, 6);
-    CK(cudaMemcpyAsync(c->cs().st_h, &sm->status, sizeof(DeviceStatus), cudaMemcpyDeviceToHost, s));
     record(c, 7);
     CK(cudaStreamSynchronize(s));
     h = (*c->cs().st_h);
@@ -660,8 +659,11 @@ int rise_create(rise_ctx **out, const rise_config *cfg) {
     if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess) { rc = RISE_ECUDA; break; }
     for (auto &sl : c->slot) {
       void *p = nullptr;
-      if (cudaMallocHost(&p, sizeof(DeviceStatus)) != cudaSuccess) { rc = RISE_ENOMEM; break; }
+      if (cudaHostAlloc(&p, sizeof(DeviceStatus), cudaHostAllocMapped) != cudaSuccess) { rc = RISE_ENOMEM; break; }
       sl.st_h = static_cast<DeviceStatus *>(p);
+      void *pd = nullptr;
+      if (cudaHostGetDevicePointer(&pd, p, 0) != cudaSuccess) { rc = RISE_ECUDA; break; }
+      sl.st_d = static_cast<DeviceStatus *>(pd);
       std::memset(sl.st_h, 0, sizeof(DeviceStatus));
       for (auto &e : sl.ev)
         if (cudaEventCreate(&e) != cudaSuccess) rc = RISE_ECUDA;
