@@ -303,6 +303,7 @@ int fill_tables(rise_ctx *c, const rise_capture *caps, const Plan &p, const rise
       it.f1 = std::min<int64_t>(T, f0 + frames);
     }
     HistArgs &ha = hseg[k];
+    ha = HistArgs{};   // edges come from the levels kernel of the batch
     ha.src = p.fixed ? static_cast<const void *>(a.img) : static_cast<const void *>(a.power);
     ha.T = T;
     ha.F = F;

@@ -188,7 +188,8 @@ cudaError_t launch_levels(const uint32_t *max_bits, double hi_power, int use_fix
 cudaError_t launch_cluster_hist(const void *src, bool from_power, int64_t T, int F,
                                 const float *edges, const float *qconst, uint8_t *img,
                                 uint32_t *hist, rise_colstat *cols, bool *needs_zero,
-                                cudaStream_t s);
+                                cudaStream_t s, const uint32_t *max_bits = nullptr,
+                                const double *ratio = nullptr, double level_db = 0.0);
 // True when T needs more than one cluster of row bands: then hist must be
 // zeroed before launch_cluster_hist, which accumulates into it.
 bool cluster_hist_accumulates(int64_t T);
@@ -220,6 +221,14 @@ struct HistArgs {             // one image for the cluster histogram
   uint32_t *hist;             // [F][256]
   rise_colstat *cols;         // [F] S and Otsu threshold
   int accumulate;             // add into a zeroed hist (no Otsu) instead of storing
+  // float source, levels built in the kernel from the capture's maximum
+  // (max_bits != NULL; the same rule as the levels kernel): the FP64 ratio
+  // table and level step, and where block (0, 0) leaves the edges and
+  // constants for later readers; else edges / qconst are read as given
+  const uint32_t *max_bits;
+  const double *ratio;
+  double level_db;
+  float *edges_out, *qconst_out;
 };
 struct HistItem {             // column group cg of capture seg
   int32_t seg, cg;

@@ -174,9 +174,30 @@ __device__ __forceinline__ void cluster_hist_body(const HistArgs &a, int cgx, in
   for (int i = tid; i < CH_WORDS / 4; i += blockDim.x) sh4[i] = make_uint4(0u, 0u, 0u, 0u);
   float inv_anchor = 0.f, c1 = 0.f;
   if constexpr (FROM_POWER) {
-    for (int i = tid; i < 257; i += blockDim.x) edges[i] = a.edges[i];
-    inv_anchor = a.qconst[0];
-    c1 = a.qconst[1];
+    if (a.max_bits) {
+      // level j >= 1 is reached at M 10^((j - 255.5) level_db / 10): the
+      // smallest float not below M ratio[j] (ratio in FP64)
+      const double M = (double)__uint_as_float(*a.max_bits);
+      const bool first = blockIdx.x == 0 && blockIdx.y == 0;
+      for (int i = tid; i < 257; i += blockDim.x) {
+        float e;
+        if (i == 0) e = 0.0f;
+        else if (i == 256 || !(M > 0.0)) e = __int_as_float(0x7f800000);
+        else e = __double2float_ru(M * a.ratio[i]);
+        edges[i] = e;
+        if (first && a.edges_out) a.edges_out[i] = e;
+      }
+      inv_anchor = M > 0.0 ? (float)(1.0 / M) : 0.0f;
+      c1 = (float)(3.0102999566398119521 / a.level_db);   // 10 log10(2) / level_db
+      if (first && tid == 0 && a.qconst_out) {
+        a.qconst_out[0] = inv_anchor;
+        a.qconst_out[1] = c1;
+      }
+    } else {
+      for (int i = tid; i < 257; i += blockDim.x) edges[i] = a.edges[i];
+      inv_anchor = a.qconst[0];
+      c1 = a.qconst[1];
+    }
   }
   __syncthreads();
   const int c0 = cgx * CH_COLS + CH_PX * lane;
@@ -712,7 +733,8 @@ int cluster_hist_bands(bool from_power, int groups, int64_t max_T) {
 cudaError_t launch_cluster_hist(const void *src, bool from_power, int64_t T, int F,
                                 const float *edges, const float *qconst, uint8_t *img,
                                 uint32_t *hist, rise_colstat *cols, bool *needs_zero,
-                                cudaStream_t s) {
+                                cudaStream_t s, const uint32_t *max_bits, const double *ratio,
+                                double level_db) {
   static_assert(CH_WARPS >= CH_NS, "one warp per reduced column");
   const int groups_x = F / CH_COLS;
   int B = CH_BANDS;
@@ -726,6 +748,13 @@ cudaError_t launch_cluster_hist(const void *src, bool from_power, int64_t T, int
   const int accumulate = G > 1;
   if (needs_zero) *needs_zero = accumulate;
   HistArgs ha{src, T, F, rows, edges, qconst, img, hist, cols, accumulate};
+  if (max_bits) {   // the levels are built in the kernel; edges / qconst receive them
+    ha.max_bits = max_bits;
+    ha.ratio = ratio;
+    ha.level_db = level_db;
+    ha.edges_out = const_cast<float *>(edges);
+    ha.qconst_out = const_cast<float *>(qconst);
+  }
   const dim3 grid((unsigned)groups_x, (unsigned)(G * B));
   return from_power ? launch_clustered(cluster_hist_kernel<true>, ch_smem(), grid, B, s, ha)
                     : launch_clustered(cluster_hist_kernel<false>, ch_smem(), grid, B, s, ha);

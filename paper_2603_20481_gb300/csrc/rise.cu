@@ -371,12 +371,13 @@ int enqueue_detect(rise_ctx *c, const void *iq, int fmt, int64_t n, int N, int h
   } else if (path == 2) {
     CK(launch_stft(a, STFT_POWER, c->num_sms, s));
     record(c, 1);
-    CK(launch_levels(a.max_bits, 0.0, 0, sm->ratio, thr.level_db, sm->edges, sm->qconst, s));
     if (cluster_hist_accumulates(T))
       CK(cudaMemsetAsync(c->hist.p, 0, (size_t)F * 256 * sizeof(uint32_t), s));
+    // the level edges are built by the histogram kernel itself (no levels launch)
     CK(launch_cluster_hist(a.power, true, T, F, sm->edges, sm->qconst, a.img,
                            reinterpret_cast<uint32_t *>(c->hist.p),
-                           reinterpret_cast<rise_colstat *>(c->cols.p), nullptr, s));
+                           reinterpret_cast<rise_colstat *>(c->cols.p), nullptr, s, a.max_bits, sm->ratio,
+                           thr.level_db));
     hist_ready = true;
   } else {
     CK(launch_stft(a, STFT_MAX, c->num_sms, s));
