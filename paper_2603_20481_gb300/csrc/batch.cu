@@ -318,6 +318,7 @@ int fill_tables(rise_ctx *c, const rise_capture *caps, const Plan &p, const rise
     ha.accumulate = 0;
     for (int cg = 0; cg < F / 64; ++cg) hitem[big ? hi++ : hs++] = HistItem{k, cg};
     ColArgs &ca = col[k];
+    ca = ColArgs{};
     ca.hist = ha.hist;
     ca.T = T;
     ca.F = F;

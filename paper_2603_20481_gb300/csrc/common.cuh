@@ -29,6 +29,13 @@ struct DeviceStatus {
   uint32_t max_bits;   // float bits of the anchor power
   uint32_t pad2;
   int64_t n_merge;     // deferred unions recorded by the labelling row pass
+  // noise floor of one image, gathered by the column blocks: order-reversed
+  // keys of the lowest local minimum and of the lowest smoothed PSD (0: none
+  // yet, so a zeroed status is the empty state), and whether a local
+  // minimum exists
+  unsigned long long floor_best, floor_gmin;
+  uint32_t floor_found;
+  uint32_t pad3;
 };
 
 __device__ __forceinline__ void set_err(DeviceStatus *st, uint32_t bit) {
@@ -207,6 +214,7 @@ struct ColArgs {
   rise_colstat *cols;     // [F]
   uint8_t *effm1;         // [F] eff-1 clamped to 0..255 (q > effm1 is foreground)
   int64_t *floor_out;     // [8]
+  DeviceStatus *st;       // one image: the floor's gathering words (zeroed)
 };
 cudaError_t launch_colstats(const ColArgs &a, bool need_otsu, cudaStream_t s);
 

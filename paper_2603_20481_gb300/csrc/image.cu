@@ -435,6 +435,106 @@ __device__ __forceinline__ void floor_body(const ColArgs &a) {
 
 __global__ void __launch_bounds__(FLOOR_THREADS) floor_kernel(ColArgs a) { floor_body(a); }
 
+// One image, column-parallel: the same floor in two launches of F/256
+// blocks.  Keys map int64 order to reversed uint64 order, so that an
+// atomicMax over keys is a minimum over values and the zeroed word is empty.
+__device__ __forceinline__ unsigned long long min_key(int64_t v) {
+  return ~((unsigned long long)v ^ 0x8000000000000000ull);
+}
+__device__ __forceinline__ int64_t key_value(unsigned long long k) {
+  return (int64_t)(~k ^ 0x8000000000000000ull);
+}
+constexpr int FP_COLS = 256;
+
+// Part 1: each block smooths its columns (with the neighbours it needs) and
+// offers its lowest local minimum and lowest smoothed value.
+__global__ void __launch_bounds__(FP_COLS) floor_part_kernel(ColArgs a) {
+  __shared__ int32_t S[FP_COLS + 2 * 64];
+  __shared__ int64_t Sh[FP_COLS + 2];
+  __shared__ int32_t c[64];
+  __shared__ unsigned long long r_best[FP_COLS / 32], r_gmin[FP_COLS / 32];
+  __shared__ int r_found[FP_COLS / 32];
+  const int F = a.F, m = a.m, tid = threadIdx.x;
+  const int f0 = blockIdx.x * FP_COLS;
+  const int lo = f0 - 1 - m;                // S[j] holds column lo + j
+  for (int i = tid; i <= m; i += blockDim.x) c[i] = (int32_t)a.sg_c[i];
+  for (int j = tid; j < FP_COLS + 2 + 2 * m; j += blockDim.x) {
+    const int f = lo + j;
+    S[j] = (f >= 0 && f < F) ? (int32_t)a.cols[f].S : 0;
+  }
+  __syncthreads();
+  // Sh[1 + i] = smoothed column f0 + i, for i = -1 .. FP_COLS (0 off the interior)
+  for (int i = tid - 1; i <= FP_COLS; i += blockDim.x) {
+    const int f = f0 + i;
+    int64_t acc = 0;
+    if (f >= m && f <= F - 1 - m) {
+      const int j = f - lo;
+      acc = (int64_t)c[0] * S[j];
+      for (int t = 1; t <= m; ++t) acc += (int64_t)c[t] * (int64_t)(S[j - t] + S[j + t]);
+    }
+    Sh[1 + i] = acc;
+    if (i >= 0 && i < FP_COLS && f < F) a.cols[f].Shat = acc;
+  }
+  __syncthreads();
+  const int f = f0 + tid;
+  unsigned long long best = 0, gmin = 0;
+  int found = 0;
+  if (f >= m && f <= F - 1 - m) {
+    const int64_t v = Sh[1 + tid];
+    gmin = min_key(v);
+    if (f >= m + 1 && f <= F - 2 - m && v < Sh[tid] && v <= Sh[2 + tid]) {
+      found = 1;
+      best = min_key(v);
+    }
+  }
+  const int lane = tid & 31, w = tid >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    gmin = max(gmin, __shfl_xor_sync(0xffffffffu, gmin, o));
+    found |= __shfl_xor_sync(0xffffffffu, found, o);
+  }
+  if (lane == 0) { r_best[w] = best; r_gmin[w] = gmin; r_found[w] = found; }
+  __syncthreads();
+  if (tid == 0) {
+    for (int k = 1; k < FP_COLS / 32; ++k) {
+      best = max(best, r_best[k]);
+      gmin = max(gmin, r_gmin[k]);
+      found |= r_found[k];
+    }
+    if (best) atomicMax(&a.st->floor_best, best);
+    if (gmin) atomicMax(&a.st->floor_gmin, gmin);
+    if (found) atomicOr(&a.st->floor_found, 1u);
+  }
+}
+
+// Part 2: N0, P_q and every column's keep / eff (one thread per column).
+__global__ void __launch_bounds__(FP_COLS) floor_eff_kernel(ColArgs a) {
+  const DeviceStatus *st = a.st;
+  const int64_t N0 = key_value(st->floor_found ? st->floor_best : st->floor_gmin);
+  const int64_t DT = a.D * a.T;
+  int64_t Pq = 0;
+  if (a.pow_on) {
+    Pq = -floor_div_d(-(N0 + a.delta_pow), DT);   // ceil((N0 + delta_pow) / DT)
+    Pq = Pq < 0 ? 0 : (Pq > 256 ? 256 : Pq);
+  }
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f == 0) {
+    int64_t *fo = a.floor_out;
+    fo[0] = N0; fo[1] = a.delta_psd; fo[2] = a.delta_pow; fo[3] = Pq;
+    fo[4] = a.D; fo[5] = a.T; fo[6] = a.F; fo[7] = 0;
+  }
+  if (f >= a.F) return;
+  const rise_colstat cs = a.cols[f];
+  const int keep = a.psd_on ? (a.D * (int64_t)(int32_t)cs.S >= N0 + a.delta_psd) : 1;
+  int eff = 256;
+  if (keep && cs.otsu >= 0) eff = max(cs.otsu + 1, (int)Pq);
+  a.cols[f].keep = keep;
+  a.cols[f].eff = eff;
+  a.cols[f].pad = 0;
+  a.effm1[f] = (uint8_t)min(255, max(0, eff - 1));
+}
+
 // Batch: one block per capture.
 __global__ void __launch_bounds__(FLOOR_THREADS) floor_batch_kernel(const ColArgs *segs) {
   __shared__ ColArgs sa;
@@ -812,6 +912,13 @@ cudaError_t launch_colstats(const ColArgs &a, bool need_otsu, cudaStream_t s) {
     count_launches(1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+  }
+  if (a.st && a.m < 64) {   // column-parallel: two launches of F/256 blocks
+    const unsigned g = (unsigned)((a.F + FP_COLS - 1) / FP_COLS);
+    floor_part_kernel<<<g, FP_COLS, 0, s>>>(a);
+    floor_eff_kernel<<<g, FP_COLS, 0, s>>>(a);
+    count_launches(2);
+    return cudaGetLastError();
   }
   const size_t sm = 2 * (size_t)a.F * sizeof(int64_t);
   e = cudaFuncSetAttribute(floor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -226,6 +226,7 @@ int image_enqueue(rise_ctx *c, const uint8_t *img, int64_t T, int F, const rise_
   ca.cols = reinterpret_cast<rise_colstat *>(c->cols.p);
   ca.effm1 = reinterpret_cast<uint8_t *>(c->effm1.p);
   ca.floor_out = sm->floor_out;
+  ca.st = &sm->status;   // zeroed at the start of the call
   CK(launch_colstats(ca, cluster_hist_accumulates(T), s));
   record(c, 4);
   // mask + morphology
