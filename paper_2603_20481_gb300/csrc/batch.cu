@@ -168,9 +168,16 @@ void size_tables(const rise_ctx *c, const rise_capture *caps, Plan &p) {
   p.bytes = o;
 }
 
-int ensure_pinned(BatchState &b, size_t bytes) {
+// The pinned staging blob of the tables (grown to at least `bytes`).  A
+// captured graph reads the blob through its address, so a new blob is a new
+// buffer generation: graphs captured with the old one are never replayed.
+int ensure_pinned(rise_ctx *c, size_t bytes) {
+  BatchState &b = c->batch;
   if (b.tab_h_bytes >= bytes) return RISE_OK;
-  if (b.tab_h) cudaFreeHost(b.tab_h);
+  if (b.tab_h) {
+    CK(cudaStreamSynchronize(c->stream));
+    cudaFreeHost(b.tab_h);
+  }
   b.tab_h = nullptr;
   b.tab_h_bytes = 0;
   const size_t want = bytes + bytes / 4 + 4096;
@@ -179,6 +186,7 @@ int ensure_pinned(BatchState &b, size_t bytes) {
     return RISE_ENOMEM;
   }
   b.tab_h_bytes = want;
+  ++c->gen;
   return RISE_OK;
 }
 
@@ -237,7 +245,7 @@ int ensure_buffers(rise_ctx *c, const Plan &p, int64_t cap) {
   if ((rc = ensure(c, b.small, sizeof(CapSmall) * p.ncap))) return rc;
   if ((rc = ensure(c, b.counters, sizeof(int) * 64))) return rc;
   if ((rc = ensure(c, b.tab, p.bytes))) return rc;
-  if ((rc = ensure_pinned(b, p.bytes))) return rc;
+  if ((rc = ensure_pinned(c, p.bytes))) return rc;
   if ((rc = ensure_offs(c, p.ncap + 1))) return rc;
   if ((rc = ensure_hbox(c, std::max<int64_t>(cap, 1)))) return rc;
   return RISE_OK;

@@ -166,3 +166,24 @@ def test_many_uneven_captures(det):
     hops = [c.hop for c in caps]
     boxes, offs = det.detect_batch(xs, Ns, hops)
     _check(boxes, offs, _plain(det, xs, Ns, hops))
+
+
+def test_replay_after_the_tables_grew():
+    """A small composition, a larger one (its tables outgrow the staging
+    blob, which moves), then the small one again: the small batch's graph
+    must not be replayed with the old blob's address; every call equals the
+    per-capture calls."""
+    from paper_2603_20481_gb300 import rise
+    caps_s = _batch(2, 3100)
+    caps_b = _batch(96, 3200, n_range=(1 << 12, 1 << 14))
+    small, big = _to_gpu(caps_s), _to_gpu(caps_b)
+    args_s = ([c.fft_size for c in caps_s], [c.hop for c in caps_s])
+    args_b = ([c.fft_size for c in caps_b], [c.hop for c in caps_b])
+    with rise.Detector(0) as d:
+        d.set_option(rise.OPT_AUTOTUNE, 0)
+        want_s = _plain(d, small, *args_s)
+        want_b = _plain(d, big, *args_b)
+        for xs, args, want in ((small, args_s, want_s), (small, args_s, want_s), (big, args_b, want_b),
+                               (big, args_b, want_b), (small, args_s, want_s), (small, args_s, want_s)):
+            boxes, offs = d.detect_batch(xs, *args)
+            _check(boxes, offs, want)
