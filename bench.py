@@ -525,6 +525,8 @@ def _serve_run(srv, pinned, arrivals, limit_s):
             nbox += len(bx)
             done += 1
             outstanding -= 1
+            if d["status"] != 0:
+                _serve_run.failed += 1
         if i >= n and outstanding == 0:
             break
         if time.perf_counter() - t0 > limit_s:
@@ -532,6 +534,9 @@ def _serve_run(srv, pinned, arrivals, limit_s):
         time.sleep(0.0002)
     _serve_run.boxes = nbox
     return np.array(lat), done, rejected, time.perf_counter() - t0
+
+
+_serve_run.failed = 0   # results whose status was not RISE_OK (must stay 0)
 
 
 def run_served(args):
@@ -602,7 +607,7 @@ def run_served(args):
                    "radios": SERVE_RADIOS, "chunk_samples": SERVE_CHUNK,
                    "step": "one chunk (steps = chunks completed; ms_per_step = 1 / saturation rate)",
                    "parallelism": "replicas x1"},
-        "served": served, "plain": plain,
+        "served": served, "plain": plain, "failed_results": int(_serve_run.failed),
         "p99_ms_at_saturation": at1["p99_ms"],
         "e2e": {"value": served["saturation_ms_s"], "unit": UNIT,
                 "h2d_bytes_per_step": SERVE_CHUNK * 8,
@@ -649,6 +654,7 @@ def run_windows(args):
                       window_frames=WIN_T)
 
     worst = []
+    failed = [0]   # plots whose status was not RISE_OK (must stay 0)
 
     def drive(times, limit_s):
         """Chunk j of the schedule goes to radio j % radios at times[j]
@@ -658,6 +664,8 @@ def run_windows(args):
 
         def take(res):
             for d, _ in res:
+                if d["status"] != 0:
+                    failed[0] += 1
                 lat.append((d["t_done_ns"] - d["t_submit_ns"]) / 1e6)
                 rec.append((d["t_submit_ns"], d["t_start_ns"], d["t_done_ns"]))
         t0 = time.perf_counter()
@@ -715,7 +723,7 @@ def run_windows(args):
                       "deadline_miss_frac": round(float((lat_rt > deadline_ms).mean()), 4)
                       if plots_rt else None,
                       "slowest": worst},
-        "stats": stats,
+        "stats": stats, "failed_results": int(failed[0]),
         "e2e": {"value": round(sat_ms_s, 1), "unit": UNIT, "h2d_bytes_per_step": WIN_T * WIN_N * 8,
                 "d2h_bytes_per_step": None,
                 "note": "window mode numbers are end to end: pinned host chunks in, boxes out"},
