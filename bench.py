@@ -559,10 +559,20 @@ def run_served(args):
     def measure(lanes, max_batch):
         srv = rise.Server(SERVE_N, SERVE_HOP, max_chunk=SERVE_CHUNK, max_streams=SERVE_RADIOS,
                           device=local, lanes=lanes, max_batch=max_batch, max_pending=1 << 14)
-        # warm-up: every batch size the lanes will meet, closed loop
+        # warm-up: every batch size the lanes will meet (largest first, so the
+        # tables' staging is sized once), each a few times so that every lane
+        # has captured its launch chain; then a closed loop
+        for k in range(max_batch, 0, -1):
+            for _ in range(4):
+                for j in range(k):
+                    srv.submit(j % SERVE_RADIOS, pinned[j % SERVE_RADIOS][0])
+                srv.drain()
+                while srv.poll(timeout_ms=0):
+                    pass
         _serve_run(srv, pinned, [(None, j % SERVE_RADIOS) for j in range(96 * 3)], 60)
         srv.drain()
-        srv.poll(timeout_ms=0)
+        while srv.poll(timeout_ms=0):
+            pass
         # saturation: closed loop for about 1.5 s
         k_sat = 4000
         lat, done, rej, dt = _serve_run(srv, pinned, [(None, j % SERVE_RADIOS) for j in range(k_sat)],

@@ -180,13 +180,13 @@ int ensure_pinned(rise_ctx *c, size_t bytes) {
   }
   b.tab_h = nullptr;
   b.tab_h_bytes = 0;
-  const size_t want = bytes + bytes / 4 + 4096;
+  const size_t want = std::max<size_t>(2 * bytes, 256 * 1024);   // few moves: each drops the graphs
   if (cudaMallocHost(&b.tab_h, want) != cudaSuccess) {
     cudaGetLastError();
     return RISE_ENOMEM;
   }
   b.tab_h_bytes = want;
-  ++c->gen;
+  new_generation(c);
   return RISE_OK;
 }
 
@@ -215,7 +215,7 @@ int ensure_offs(rise_ctx *c, int64_t n) {
   b.offs_h = static_cast<int64_t *>(h);
   b.offs_dev = static_cast<int64_t *>(d);
   b.offs_cap = want;
-  ++c->gen;
+  new_generation(c);
   return RISE_OK;
 }
 

@@ -138,6 +138,10 @@ inline int cuda_fail(cudaError_t e) {
     if (_e != cudaSuccess) return rise::host::cuda_fail(_e); \
   } while (0)
 
+// A scratch buffer moved: bumps the buffer generation and drops every
+// captured graph (each holds old addresses and can never be replayed),
+// after the context's stream is idle.
+void new_generation(rise_ctx *c);
 // Grows b to at least `bytes` (with 1/8 headroom), within the memory budget.
 int ensure(rise_ctx *c, Buf &b, size_t bytes);
 // Mapped pinned host buffer for the current slot's boxes (at least `cap`).

@@ -44,8 +44,20 @@ int ensure(rise_ctx *c, Buf &b, size_t bytes) {
   b.p = p;
   b.bytes = grow;
   c->allocated += grow;
-  ++c->gen;
+  new_generation(c);
   return RISE_OK;
+}
+
+void new_generation(rise_ctx *c) {
+  ++c->gen;
+  cudaStreamSynchronize(c->stream);
+  for (auto &g : c->single_graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  c->single_graphs.clear();
+  c->last_key[0] = c->last_key[1] = 0;
+  for (auto &g : c->batch.graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  c->batch.graphs.clear();
 }
 
 // Mapped pinned host buffer for the boxes (grown to at least `cap` entries).
@@ -73,7 +85,7 @@ int ensure_hbox(rise_ctx *c, int64_t cap) {
   c->cs().hbox = reinterpret_cast<rise_box *>(h);
   c->cs().hbox_dev = reinterpret_cast<rise_box *>(d);
   c->cs().hbox_cap = want;
-  ++c->gen;
+  new_generation(c);
   return RISE_OK;
 }
 
