@@ -710,6 +710,7 @@ def run_windows(args):
     lat, plots, dt = drive([None] * n_sat, 120)
     sat_ms_s = n_sat * WIN_CHUNK / dt / 1e6           # samples consumed per second
     # real time: every radio sends a chunk every 10 ms, staggered
+    stats_before = srv.stats()
     rounds = int(max(20, args.serve_seconds / period))
     times = [k * period + (r / radios) * period for k in range(rounds) for r in range(radios)]
     lat_rt, plots_rt, dt_rt = drive(times, times[-1] + 30)
@@ -733,7 +734,7 @@ def run_windows(args):
                       "deadline_miss_frac": round(float((lat_rt > deadline_ms).mean()), 4)
                       if plots_rt else None,
                       "slowest": worst},
-        "stats": stats, "failed_results": int(failed[0]),
+        "stats": stats, "stats_before_real_time": stats_before, "failed_results": int(failed[0]),
         "e2e": {"value": round(sat_ms_s, 1), "unit": UNIT, "h2d_bytes_per_step": WIN_T * WIN_N * 8,
                 "d2h_bytes_per_step": None,
                 "note": "window mode numbers are end to end: pinned host chunks in, boxes out"},

@@ -619,6 +619,7 @@ int detect_batch(rise_ctx *c, const rise_capture *caps, int ncap, const rise_thr
             b.graphs.erase(b.graphs.begin());
           }
           b.graphs.push_back({key, exec});
+          b.captures += 1;
           b.graphs.back().launches = nl;
           gr = &b.graphs.back();
         }

@@ -51,6 +51,7 @@ struct BatchState {
   std::vector<Graph> graphs;
   // tuned launch parameters, keyed by the batch's shape
   std::map<uint64_t, std::vector<int>> tuned;
+  int64_t captures = 0;          // launch chains captured so far
   // the last batch: STFT groups, its launch parameters, replayed from a graph
   int last_groups = 0;
   std::vector<int> last_params;

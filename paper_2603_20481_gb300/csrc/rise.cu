@@ -70,7 +70,8 @@ int ensure_hbox(rise_ctx *c, int64_t cap) {
     c->cs().hbox_dev = nullptr;
     c->cs().hbox_cap = 0;
   }
-  const int64_t want = std::max<int64_t>(cap, 4096);
+  // doubled: every move of this buffer drops the context's graphs
+  const int64_t want = std::max<int64_t>(2 * cap, 4096);
   void *h = nullptr;
   if (cudaHostAlloc(&h, (size_t)want * sizeof(rise_box), cudaHostAllocMapped) != cudaSuccess) {
     cudaGetLastError();

@@ -68,6 +68,7 @@ struct Done {
 struct Lane {
   rise_ctx *ctx = nullptr;
   std::thread th;
+  int64_t captures = 0, generations = 0;   // copied from the context after each batch
 };
 
 constexpr uint32_t kStateMagic = 0x52534531u;   // stream state blob, version 1
@@ -99,7 +100,7 @@ struct rise_server {
   bool stop = false;
   int64_t running = 0;
   int64_t st_submitted = 0, st_rejected = 0, st_completed = 0, st_batches = 0, st_max_batch = 0,
-          st_max_inflight = 0;
+          st_max_inflight = 0, st_max_batch_us = 0;
 };
 
 namespace {
@@ -119,7 +120,7 @@ void lane_main(rise_server *s, int li) {
   std::vector<Item> items;
   std::vector<rise_capture> caps;
   std::vector<int64_t> offs;
-  std::vector<rise_box> boxes(1 << 16);
+  std::vector<rise_box> boxes(1 << 18);   // grown (and the context's box buffer with it) on demand
   for (;;) {
     std::unique_lock<std::mutex> lk(s->mu);
     s->cv_work.wait(lk, [&] { return s->stop || (!s->pending.empty() && !s->free_slots.empty()); });
@@ -189,7 +190,7 @@ void lane_main(rise_server *s, int li) {
       if (rc == RISE_ETRUNC) {
         // more boxes than the buffer: grow it and run the batch again (the
         // slots still hold the inputs)
-        boxes.resize((size_t)offs.back() + offs.back() / 4 + 1024);
+        boxes.resize((size_t)2 * offs.back() + 1024);
         rc = rise_detect_batch(ctx, caps.data(), (int)caps.size(), &s->thr, boxes.data(),
                                (int64_t)boxes.size(), offs.data());
       }
@@ -227,6 +228,9 @@ void lane_main(rise_server *s, int li) {
     s->running -= (int64_t)items.size();
     s->st_completed += (int64_t)items.size();
     s->st_batches += 1;
+    s->st_max_batch_us = std::max<int64_t>(s->st_max_batch_us, (t_done - t_start) / 1000);
+    s->lanes[li].captures = ctx->batch.captures;
+    s->lanes[li].generations = (int64_t)ctx->gen;
     lk.unlock();
     s->cv_done.notify_all();
     s->cv_work.notify_all();
@@ -435,10 +439,15 @@ int rise_stream_import(rise_server *s, int stream, const void *buf, size_t bytes
 int rise_server_stats(rise_server *s, int64_t *out, int n) {
   if (!s || !out || n < 0) return RISE_EINVAL;
   std::lock_guard<std::mutex> lk(s->mu);
-  const int64_t w[8] = {s->st_submitted, s->st_rejected, s->st_completed, s->st_batches,
-                        s->st_max_batch, s->st_max_inflight, (int64_t)s->slot_dev.size(),
-                        (int64_t)s->lanes.size()};
-  for (int i = 0; i < n && i < 8; ++i) out[i] = w[i];
+  int64_t captures = 0, generations = 0;
+  for (const Lane &L : s->lanes) {
+    captures += L.captures;
+    generations += L.generations;
+  }
+  const int64_t w[11] = {s->st_submitted, s->st_rejected, s->st_completed, s->st_batches,
+                         s->st_max_batch, s->st_max_inflight, (int64_t)s->slot_dev.size(),
+                         (int64_t)s->lanes.size(), captures, generations, s->st_max_batch_us};
+  for (int i = 0; i < n && i < 11; ++i) out[i] = w[i];
   return RISE_OK;
 }
 

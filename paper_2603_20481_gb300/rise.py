@@ -514,7 +514,8 @@ def column_stats_noalloc(img, cols, stream=None) -> int:
 
 
 SERVER_STATS = ("submitted", "rejected", "completed", "batches", "largest_batch",
-                "most_in_flight", "slots", "lanes")
+                "most_in_flight", "slots", "lanes", "graph_captures", "buffer_generations",
+                "longest_batch_us")
 
 
 class Server:
@@ -626,8 +627,8 @@ class Server:
         self._seq[stream] = int(np.frombuffer(state[24:32], np.int64)[0])
 
     def stats(self) -> dict:
-        v = np.zeros(8, np.int64)
-        lib().rise_server_stats(self._h, v.ctypes.data, 8)
+        v = np.zeros(len(SERVER_STATS), np.int64)
+        lib().rise_server_stats(self._h, v.ctypes.data, len(SERVER_STATS))
         return dict(zip(SERVER_STATS, (int(x) for x in v)))
 
 
