@@ -604,7 +604,20 @@ int detect_batch(rise_ctx *c, const rise_capture *caps, int ncap, const rise_thr
     BatchState::Graph *gr = nullptr;
     for (auto &g : b.graphs)
       if (g.key == key) gr = &g;
+    // a composition is captured the second time it comes: one that comes
+    // once (a served batch of an odd size) does not pay for a capture
+    bool capture = false;
     if (!gr) {
+      auto it = std::find(b.seen.begin(), b.seen.end(), key);
+      if (it != b.seen.end()) {
+        b.seen.erase(it);
+        capture = true;
+      } else {
+        if (b.seen.size() >= 64) b.seen.erase(b.seen.begin());
+        b.seen.push_back(key);
+      }
+    }
+    if (capture) {
       cudaGraph_t graph = nullptr;
       int nl = 0;
       if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {

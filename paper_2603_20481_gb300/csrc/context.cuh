@@ -49,6 +49,7 @@ struct BatchState {
     int launches = 0;            // kernels one replay runs
   };
   std::vector<Graph> graphs;
+  std::vector<uint64_t> seen;    // compositions run once without a graph
   // tuned launch parameters, keyed by the batch's shape
   std::map<uint64_t, std::vector<int>> tuned;
   int64_t captures = 0;          // launch chains captured so far

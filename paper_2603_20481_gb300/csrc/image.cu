@@ -756,44 +756,48 @@ morph_batch_kernel(const MorphArgs *segs, const MorphItem *mi, const int *warp_b
 // mostly idle.  At least ceil(T / HIST_MAX_ROWS) bands for a single cluster.
 template <bool FP>
 int bands_for(int groups, int64_t max_T) {
+  // clusters of B blocks that fit on the device at once, from the occupancy
+  // API once per process (it does not depend on the grid); -1: B does not fit
   static std::mutex mu;
-  static std::map<int, int> cache;
+  static int fit[CH_BANDS + 1];
+  static bool known = false;
   const int need = (int)std::min<int64_t>(CH_BANDS, (max_T + HIST_MAX_ROWS - 1) / HIST_MAX_ROWS);
   {
     std::lock_guard<std::mutex> lk(mu);
-    auto it = cache.find(groups);
-    if (it != cache.end()) return std::max(it->second, need);
+    if (!known) {
+      const size_t sm = ch_smem();
+      cudaFuncSetAttribute(cluster_hist_kernel<FP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      for (int B = 1; B <= CH_BANDS; ++B) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(1u, (unsigned)B);
+        cfg.blockDim = dim3(32 * CH_WARPS);
+        cfg.dynamicSmemBytes = sm;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 1;
+        at[0].val.clusterDim.y = (unsigned)B;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, cluster_hist_kernel<FP>, &cfg) != cudaSuccess || n < 1) {
+          cudaGetLastError();
+          n = -1;
+        }
+        fit[B] = n;
+      }
+      known = true;
+    }
   }
-  const size_t sm = ch_smem();
-  cudaFuncSetAttribute(cluster_hist_kernel<FP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   int best = CH_BANDS;
   double best_cost = 1e30;
   for (int B = 1; B <= CH_BANDS; ++B) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)groups, (unsigned)B);
-    cfg.blockDim = dim3(32 * CH_WARPS);
-    cfg.dynamicSmemBytes = sm;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 1;
-    at[0].val.clusterDim.y = (unsigned)B;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, cluster_hist_kernel<FP>, &cfg) != cudaSuccess || n < 1) {
-      cudaGetLastError();
-      continue;
-    }
-    const double cost = (double)((groups + n - 1) / n) / B;
+    if (fit[B] < 1) continue;
+    const double cost = (double)((groups + fit[B] - 1) / fit[B]) / B;
     if (cost <= best_cost) {
       best_cost = cost;
       best = B;
     }
-  }
-  {
-    std::lock_guard<std::mutex> lk(mu);
-    cache[groups] = best;
   }
   return std::max(best, need);
 }

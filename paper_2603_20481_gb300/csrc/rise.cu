@@ -58,6 +58,7 @@ void new_generation(rise_ctx *c) {
   for (auto &g : c->batch.graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   c->batch.graphs.clear();
+  c->batch.seen.clear();
 }
 
 // Mapped pinned host buffer for the boxes (grown to at least `cap` entries).

@@ -96,9 +96,17 @@ def test_graph_replay_reads_fresh_inputs(det):
         n = min(x.numel(), c.iq.shape[0])
         x[:n].copy_(torch.from_numpy(c.iq[:n]))
     b2, o2 = det.detect_batch(xs, Ns, hops)
-    assert det.batch_info()[1] == 1                       # replayed from the graph
+    assert det.batch_info()[1] == 1                       # run from the captured graph
     _check(b2, o2, _plain(det, xs, Ns, hops))
     assert not (len(b1) == len(b2) and np.array_equal(b1, b2))
+    # and once more with the first contents: a replay of the same graph
+    for x, c in zip(xs, caps):
+        n = min(x.numel(), c.iq.shape[0])
+        x[:n].copy_(torch.from_numpy(c.iq[:n]))
+    b3, o3 = det.detect_batch(xs, Ns, hops)
+    assert det.batch_info()[1] == 1
+    np.testing.assert_array_equal(b3, b1)
+    np.testing.assert_array_equal(o3, o1)
 
 
 def test_switches_give_the_same_boxes(det):
