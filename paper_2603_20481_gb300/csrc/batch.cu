@@ -543,6 +543,10 @@ int check_capture(const rise_capture &k) {
 
 }  // namespace
 
+}  // namespace host
+void batch_preload() { preload_kernel(host::copy16_kernel); }
+namespace host {
+
 void destroy_batch(rise_ctx *c) {
   BatchState &b = c->batch;
   destroy_graphs(b);

@@ -714,6 +714,27 @@ cudaError_t label_common(const CclArgs &a, const RowSeg *segs, const int64_t *ro
 }
 }  // namespace
 
+void ccl_preload() {
+  preload_kernel(row_scan_kernel);
+  preload_kernel(runs_init_kernel);
+  preload_kernel(runs_row_kernel<1>);
+  preload_kernel(runs_row_kernel<2>);
+  preload_kernel(runs_row_kernel<4>);
+  preload_kernel(runs_row_kernel<8>);
+  preload_kernel(runs_row_batch_kernel<1>);
+  preload_kernel(runs_row_batch_kernel<2>);
+  preload_kernel(runs_row_batch_kernel<4>);
+  preload_kernel(runs_row_batch_kernel<8>);
+  preload_kernel(ccl_offsets_kernel);
+  preload_kernel(ccl_flatten_merge_kernel<true, true>);
+  preload_kernel(ccl_flatten_merge_kernel<true, false>);
+  preload_kernel(ccl_flatten_merge_kernel<false, true>);
+  preload_kernel(ccl_reduce_kernel);
+  preload_kernel(root_scan_kernel);
+  preload_kernel(runs_export_kernel);
+  preload_kernel(boundary_kernel);
+}
+
 cudaError_t launch_runs_export(const CclArgs &a, int4 *out, int64_t cap, int num_sms, cudaStream_t s) {
   const int g = grid_for(std::max<int64_t>(cap, 1), 256, num_sms, 8);
   runs_export_kernel<<<g, 256, 0, s>>>(a, out, cap);

@@ -132,6 +132,21 @@ namespace rise {
 
 // Kernels launched by the library (process-wide), for launch accounting.
 void count_launches(int k);
+// Kernels load lazily on their first launch (milliseconds each for the
+// large FFT instances): each translation unit's preload queries the
+// attributes of all its kernels, which loads them, so that no detection
+// call pays for a load.  Called once per process by rise_create.
+template <typename K>
+inline void preload_kernel(K k) {
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, k) != cudaSuccess) cudaGetLastError();
+}
+void stft_preload();
+void stft_sc16_preload();
+void image_preload();
+void ccl_preload();
+void batch_preload();
+void match_preload();
 long long launches_so_far();
 
 enum IqFormat { IQ_FC32 = 0, IQ_SC16 = 1 };

@@ -825,6 +825,22 @@ cudaError_t launch_clustered(K kernel, size_t sm, dim3 grid, int B, cudaStream_t
 
 }  // namespace
 
+void image_preload() {
+  preload_kernel(otsu_kernel);
+  preload_kernel(cluster_hist_kernel<true>);
+  preload_kernel(cluster_hist_kernel<false>);
+  preload_kernel(cluster_hist_batch_kernel<true>);
+  preload_kernel(cluster_hist_batch_kernel<false>);
+  preload_kernel(floor_kernel);
+  preload_kernel(floor_part_kernel);
+  preload_kernel(floor_eff_kernel);
+  preload_kernel(floor_batch_kernel);
+  preload_kernel(morph_stream_kernel<0>);
+  preload_kernel(morph_stream_kernel<1>);
+  preload_kernel(morph_batch_kernel<0>);
+  preload_kernel(morph_batch_kernel<1>);
+}
+
 // Cluster histogram (optionally quantising float power on the way).  The
 // histogram is written whole (no zeroing needed) unless T needs more than one
 // cluster of bands, in which case the caller's zeroed histogram is accumulated.

@@ -84,6 +84,11 @@ __global__ void iou_count_kernel(const ulonglong2 *gbest, int64_t ng, const ulon
 }
 
 }  // namespace
+
+void match_preload() {
+  preload_kernel(best_iou_kernel);
+  preload_kernel(iou_count_kernel);
+}
 }  // namespace rise
 
 using namespace rise;

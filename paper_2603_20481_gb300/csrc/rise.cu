@@ -4,6 +4,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
+#include <set>
 #include <map>
 #include <new>
 #include <vector>
@@ -656,6 +658,21 @@ int rise_create(rise_ctx **out, const rise_config *cfg) {
     return RISE_ECUDA;
   }
   if (cfg->device < 0 || cfg->device >= ndev) return RISE_EINVAL;
+  {
+    // every kernel loaded once per device, here rather than in a call
+    static std::mutex mu;
+    static std::set<int> loaded;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!loaded.count(cfg->device) && cudaSetDevice(cfg->device) == cudaSuccess) {
+      stft_preload();
+      stft_sc16_preload();
+      image_preload();
+      ccl_preload();
+      batch_preload();
+      match_preload();
+      loaded.insert(cfg->device);
+    }
+  }
   rise_ctx *c = new (std::nothrow) rise_ctx();
   if (!c) return RISE_ENOMEM;
   c->device = cfg->device;

@@ -321,6 +321,9 @@ int rise_server_create(rise_server **out, const rise_server_config *cfg) {
     cc.mem_budget = cfg->mem_budget ? scratch + scratch / 2 : 0;
     if ((rc = rise_create(&s->lanes[li].ctx, &cc))) break;
     rise_set_option(s->lanes[li].ctx, RISE_OPT_AUTOTUNE, 0);   // batch sizes vary: fixed shapes
+#ifdef RISE_WINDOW_NO_GRAPHS
+    if (s->window) rise_set_option(s->lanes[li].ctx, RISE_OPT_GRAPH, 0);
+#endif
   }
   if (rc) {
     cudaGetLastError();

@@ -101,6 +101,12 @@ void stft_fill_tables(int N, float2 *tw, float *win) {
   for (int m = 0; m < N; ++m) win[m] = (float)(0.5 - 0.5 * std::cos(two_pi * (double)m / (double)N));
 }
 
+void stft_preload() {
+  preload_stft_in<float2>();
+  preload_kernel(levels_kernel);
+  preload_kernel(levels_batch_kernel);
+}
+
 cudaError_t launch_stft(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s) {
   return a.fmt == IQ_SC16 ? launch_stft_sc16(a, mode, num_sms, s)
                           : launch_stft_in<float2>(a, mode, num_sms, s);

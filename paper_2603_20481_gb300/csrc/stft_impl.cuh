@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -511,6 +512,29 @@ cudaError_t launch_size(const StftArgs &a, StftMode mode, int num_sms, cudaStrea
   const bool tma = ((int64_t)a.hop * (int64_t)sizeof(IN)) % 16 == 0 &&
                    ((reinterpret_cast<uintptr_t>(a.iq) & 15) == 0);
   return tma ? launch_mode<N, true, IN>(a, mode, num_sms, s) : launch_mode<N, false, IN>(a, mode, num_sms, s);
+}
+
+template <int N, typename IN, bool TMA>
+void preload_stft_nt() {
+  preload_kernel(stft_kernel<N, STFT_MAX, TMA, IN>);
+  preload_kernel(stft_kernel<N, STFT_QUANT, TMA, IN>);
+  preload_kernel(stft_kernel<N, STFT_POWER, TMA, IN>);
+  preload_kernel(stft_kernel<N, STFT_QUANT_POWER, TMA, IN>);
+  if constexpr (std::is_same<IN, float2>::value) {
+    preload_kernel(stft_batch_kernel<N, STFT_MAX, TMA>);
+    preload_kernel(stft_batch_kernel<N, STFT_QUANT, TMA>);
+    preload_kernel(stft_batch_kernel<N, STFT_POWER, TMA>);
+    preload_kernel(stft_batch_kernel<N, STFT_QUANT_POWER, TMA>);
+  }
+}
+template <typename IN>
+void preload_stft_in() {
+  preload_stft_nt<256, IN, false>();  preload_stft_nt<256, IN, true>();
+  preload_stft_nt<512, IN, false>();  preload_stft_nt<512, IN, true>();
+  preload_stft_nt<1024, IN, false>(); preload_stft_nt<1024, IN, true>();
+  preload_stft_nt<2048, IN, false>(); preload_stft_nt<2048, IN, true>();
+  preload_stft_nt<4096, IN, false>(); preload_stft_nt<4096, IN, true>();
+  preload_stft_nt<8192, IN, false>(); preload_stft_nt<8192, IN, true>();
 }
 
 // the launch for the input type IN, by FFT size

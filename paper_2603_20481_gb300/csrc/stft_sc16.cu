@@ -8,4 +8,6 @@ cudaError_t launch_stft_sc16(const StftArgs &a, StftMode mode, int num_sms, cuda
   return launch_stft_in<short2>(a, mode, num_sms, s);
 }
 
+void stft_sc16_preload() { preload_stft_in<short2>(); }
+
 }  // namespace rise
