@@ -207,6 +207,8 @@ cudaError_t launch_levels(const uint32_t *max_bits, double hi_power, int use_fix
 // (only for T > 8 * 65535); call with needs_zero to query before launching.
 // Also writes each column's PSD S and Otsu threshold into cols (unless the
 // histogram is accumulated over several clusters: then launch_colstats runs Otsu).
+// launch_colstats is the one-image floor (it needs a.st, the call's zeroed
+// status); batches use launch_floor_batch.
 cudaError_t launch_cluster_hist(const void *src, bool from_power, int64_t T, int F,
                                 const float *edges, const float *qconst, uint8_t *img,
                                 uint32_t *hist, rise_colstat *cols, bool *needs_zero,

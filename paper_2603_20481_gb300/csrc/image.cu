@@ -433,8 +433,6 @@ __device__ __forceinline__ void floor_body(const ColArgs &a) {
   }
 }
 
-__global__ void __launch_bounds__(FLOOR_THREADS) floor_kernel(ColArgs a) { floor_body(a); }
-
 // One image, column-parallel: the same floor in two launches of F/256
 // blocks.  Keys map int64 order to reversed uint64 order, so that an
 // atomicMax over keys is a minimum over values and the zeroed word is empty.
@@ -831,7 +829,6 @@ void image_preload() {
   preload_kernel(cluster_hist_kernel<false>);
   preload_kernel(cluster_hist_batch_kernel<true>);
   preload_kernel(cluster_hist_batch_kernel<false>);
-  preload_kernel(floor_kernel);
   preload_kernel(floor_part_kernel);
   preload_kernel(floor_eff_kernel);
   preload_kernel(floor_batch_kernel);
@@ -925,6 +922,7 @@ cudaError_t launch_morph_batch(int order, const MorphArgs *segs, const MorphItem
 }
 
 cudaError_t launch_colstats(const ColArgs &a, bool need_otsu, cudaStream_t s) {
+  if (!a.st || a.m >= 64) return cudaErrorInvalidValue;
   cudaError_t e;
   if (need_otsu) {
     const int warps_per_block = 8;
@@ -933,18 +931,11 @@ cudaError_t launch_colstats(const ColArgs &a, bool need_otsu, cudaStream_t s) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  if (a.st && a.m < 64) {   // column-parallel: two launches of F/256 blocks
-    const unsigned g = (unsigned)((a.F + FP_COLS - 1) / FP_COLS);
-    floor_part_kernel<<<g, FP_COLS, 0, s>>>(a);
-    floor_eff_kernel<<<g, FP_COLS, 0, s>>>(a);
-    count_launches(2);
-    return cudaGetLastError();
-  }
-  const size_t sm = 2 * (size_t)a.F * sizeof(int64_t);
-  e = cudaFuncSetAttribute(floor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  floor_kernel<<<1, FLOOR_THREADS, sm, s>>>(a);
-  count_launches(1);
+  // column-parallel: two launches of F/256 blocks
+  const unsigned g = (unsigned)((a.F + FP_COLS - 1) / FP_COLS);
+  floor_part_kernel<<<g, FP_COLS, 0, s>>>(a);
+  floor_eff_kernel<<<g, FP_COLS, 0, s>>>(a);
+  count_launches(2);
   return cudaGetLastError();
 }
 
