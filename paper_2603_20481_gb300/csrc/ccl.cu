@@ -12,7 +12,8 @@
 //
 //   1. the morphology kernel counts the runs of each row; a single-pass
 //      exclusive scan gives row_base[t], the number of the first run of row t.
-//   2. init: every run is its own tree.
+//   2. init: every run is its own tree (done by the row-offset scan; a
+//      separate kernel when the labelling runs again with grown arrays).
 //   3. rows: one warp per row records each run's extent, area, level sum and
 //      energy, and unites it with the runs of the next row that share a
 //      column (4-connectivity), on a global lock-free union-find.
@@ -141,8 +142,9 @@ __device__ __forceinline__ void tile_scan(const In *in, int64_t n, int64_t tile,
 // Row offsets of the runs: row_base[t] = runs in rows before t, row_base[T]
 // and n_runs = all runs.
 __global__ void __launch_bounds__(SCAN_THREADS)
-row_scan_kernel(const uint32_t *cnt, int64_t T, int64_t *row_base, DeviceStatus *st, ScanState ss) {
-  __shared__ int64_t s_tile;
+row_scan_kernel(const uint32_t *cnt, int64_t T, int64_t *row_base, DeviceStatus *st, ScanState ss,
+                int32_t *run_parent, int64_t run_cap) {
+  __shared__ int64_t s_tile, s_lo, s_hi;
   if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(reinterpret_cast<unsigned long long *>(ss.ticket_rows), 1ull);
   __syncthreads();
   const int64_t tile = s_tile;
@@ -157,8 +159,15 @@ row_scan_kernel(const uint32_t *cnt, int64_t T, int64_t *row_base, DeviceStatus 
     if (k == T) {   // one past the last row: the total
       row_base[T] = ex[i];
       st->n_runs = ex[i];
+      if (ex[i] > run_cap) set_err(st, ERR_RUN_CAPACITY);
     }
   }
+  // the runs of this tile's rows start as trees of their own
+  if (threadIdx.x == 0) s_lo = ex[0];
+  if (threadIdx.x == SCAN_THREADS - 1) s_hi = ex[SCAN_ITEMS - 1] + v[SCAN_ITEMS - 1];
+  __syncthreads();
+  const int64_t hi = min(s_hi, run_cap);
+  for (int64_t g = s_lo + threadIdx.x; g < hi; g += SCAN_THREADS) run_parent[g] = (int32_t)g;
 }
 
 // ---------------------------------------------------------------------------
@@ -665,23 +674,29 @@ cudaError_t launch_ccl_count(const CclArgs &a, int num_sms, cudaStream_t s) {
   if ((size_t)(3 + tiles + scan_tiles(a.run_cap)) * sizeof(uint64_t) > a.scan_tmp_bytes)
     return cudaErrorInvalidValue;
   const ScanState ss = scan_state(a.scan_tmp, tiles);
-  cudaError_t e = cudaMemsetAsync(a.scan_tmp, 0, (size_t)(3 + tiles) * sizeof(uint64_t), s);
+  // both scans' tickets and tile words (the root scan's too: no init kernel
+  // runs between the two on this path)
+  cudaError_t e =
+      cudaMemsetAsync(a.scan_tmp, 0, (size_t)(3 + tiles + scan_tiles(a.run_cap)) * sizeof(uint64_t), s);
   if (e != cudaSuccess) return e;
-  row_scan_kernel<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(a.row_cnt, a.T, a.row_base, a.status, ss);
+  row_scan_kernel<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(a.row_cnt, a.T, a.row_base, a.status, ss,
+                                                          a.run_parent, a.run_cap);
   count_launches(1);
   return cudaGetLastError();
 }
 
 namespace {
 cudaError_t label_common(const CclArgs &a, const RowSeg *segs, const int64_t *row0, int ncap,
-                         int64_t *offs, int num_sms, cudaStream_t s) {
+                         int64_t *offs, int num_sms, cudaStream_t s, bool after_count) {
   const int g = grid_for(a.run_cap, 256, num_sms, segs ? 16 : 4);
   const int64_t root_tiles = scan_tiles(a.run_cap);
   if ((size_t)(3 + scan_tiles(a.T) + root_tiles) * sizeof(uint64_t) > a.scan_tmp_bytes)
     return cudaErrorInvalidValue;
   const ScanState ss = scan_state(a.scan_tmp, scan_tiles(a.T));
-  runs_init_kernel<<<g, 256, 0, s>>>(a, ss, root_tiles);
-  count_launches(1);
+  if (!after_count) {   // a relabel with larger run arrays: the row scan is not run again
+    runs_init_kernel<<<g, 256, 0, s>>>(a, ss, root_tiles);
+    count_launches(1);
+  }
   // widest image of the launch (a.F; for a batch, the largest F)
   const int nch = (a.F / 32 + 31) / 32;
   cudaError_t er = nch <= 1 ? launch_rows<1>(a, segs, row0, ncap, s)
@@ -750,13 +765,13 @@ cudaError_t launch_boundary(const uint32_t *mask, int64_t T, int F, uint32_t *ou
   return cudaGetLastError();
 }
 
-cudaError_t launch_ccl_label(const CclArgs &a, int num_sms, cudaStream_t s) {
-  return label_common(a, nullptr, nullptr, 0, nullptr, num_sms, s);
+cudaError_t launch_ccl_label(const CclArgs &a, int num_sms, cudaStream_t s, bool after_count) {
+  return label_common(a, nullptr, nullptr, 0, nullptr, num_sms, s, after_count);
 }
 
 cudaError_t launch_ccl_label_batch(const CclArgs &a, const RowSeg *segs, const int64_t *row0,
                                    int ncap, int64_t *offs, int num_sms, cudaStream_t s) {
-  return label_common(a, segs, row0, ncap, offs, num_sms, s);
+  return label_common(a, segs, row0, ncap, offs, num_sms, s, true);
 }
 
 }  // namespace rise

@@ -314,7 +314,9 @@ cudaError_t launch_ccl_count(const CclArgs &a, int num_sms, cudaStream_t s);
 // Run records, unions, reduction into roots and compaction (needs run_cap >=
 // n_runs, checked on the device: on shortfall it sets ERR_RUN_CAPACITY and
 // does nothing).
-cudaError_t launch_ccl_label(const CclArgs &a, int num_sms, cudaStream_t s);
+// after_count: launch_ccl_count ran just before (it initialised the run
+// parents and the scan state); false for a relabel with grown run arrays.
+cudaError_t launch_ccl_label(const CclArgs &a, int num_sms, cudaStream_t s, bool after_count = true);
 struct RowSeg {               // one capture's image in a batch
   const uint32_t *mask;       // [T][F/32]
   const uint8_t *img;         // [T][F]

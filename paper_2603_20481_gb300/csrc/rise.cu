@@ -290,7 +290,7 @@ int image_finish(rise_ctx *c, const uint8_t *img, int64_t T, int F, rise_box *ou
     c->run_cap = need;
     const CclArgs la = ccl_args(c, img, T, F, cap);
     CK(cudaMemsetAsync(&sm->status.err, 0, sizeof(uint32_t), s));
-    CK(launch_ccl_label(la, c->num_sms, s));
+    CK(launch_ccl_label(la, c->num_sms, s, false));   // the row scan is not run again
     record(c, 6);
     record(c, 7);
     CK(cudaStreamSynchronize(s));
