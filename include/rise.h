@@ -352,7 +352,8 @@ int rise_stream_import(rise_server *s, int stream, const void *buf, size_t bytes
  * [3] batches, [4] largest batch, [5] most chunks in flight, [6] slots,
  * [7] lanes, [8] launch chains captured as graphs (all lanes), [9] scratch
  * buffer generations (all lanes; each one drops the lane's graphs),
- * [10] longest batch in microseconds.  Writes min(n, 11) values. */
+ * [10] longest batch in microseconds, [11] batches run again with grown
+ * run arrays.  Writes min(n, 12) values. */
 int rise_server_stats(rise_server *s, int64_t *out, int n);
 
 /* Stops the lanes after the chunks in flight and frees everything; queued

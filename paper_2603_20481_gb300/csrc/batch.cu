@@ -230,7 +230,7 @@ int ensure_buffers(rise_ctx *c, const Plan &p, int64_t cap) {
   if ((rc = ensure(c, c->mask, px / 8))) return rc;
   if ((rc = ensure(c, c->row_cnt, (size_t)p.total_rows * sizeof(uint32_t)))) return rc;
   if ((rc = ensure(c, c->row_base, (size_t)(p.total_rows + 1) * sizeof(int64_t)))) return rc;
-  const int64_t want = std::max<int64_t>(1 << 20, (int64_t)(px / 256));
+  const int64_t want = std::max<int64_t>(1 << 20, (int64_t)(px / 64));
   if (c->run_cap < want) {
     if ((rc = ensure(c, c->run_parent, want * sizeof(int32_t)))) return rc;
     if ((rc = ensure(c, c->run_sroot, want))) return rc;
@@ -655,7 +655,9 @@ int detect_batch(rise_ctx *c, const rise_capture *caps, int ncap, const rise_thr
   DeviceStatus h = (*c->cs().st_h);
   if (h.err & ERR_RUN_CAPACITY) {
     // more runs than the run arrays hold: grow them and run the chain again
-    const int64_t need = h.n_runs + h.n_runs / 4 + 1024;
+    // doubled: each growth synchronises the device and drops the graphs
+    const int64_t need = std::max<int64_t>(2 * h.n_runs, 2 * c->run_cap);
+    c->batch.relabels += 1;
     if ((rc = ensure(c, c->run_parent, need * sizeof(int32_t)))) return rc;
     if ((rc = ensure(c, c->run_sroot, need))) return rc;
     if ((rc = ensure(c, c->rec, need * sizeof(rise_box)))) return rc;

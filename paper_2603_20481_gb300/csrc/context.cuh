@@ -53,6 +53,7 @@ struct BatchState {
   // tuned launch parameters, keyed by the batch's shape
   std::map<uint64_t, std::vector<int>> tuned;
   int64_t captures = 0;          // launch chains captured so far
+  int64_t relabels = 0;          // batches run again with grown run arrays
   // the last batch: STFT groups, its launch parameters, replayed from a graph
   int last_groups = 0;
   std::vector<int> last_params;

@@ -280,7 +280,7 @@ int image_finish(rise_ctx *c, const uint8_t *img, int64_t T, int F, rise_box *ou
   DeviceStatus h = (*c->cs().st_h);
   if (h.err & ERR_RUN_CAPACITY) {
     // the run arrays were too small for this mask: grow to fit and relabel
-    int64_t need = h.n_runs + h.n_runs / 4 + 1024;
+    int64_t need = std::max<int64_t>(2 * h.n_runs, 2 * c->run_cap);   // doubled: few growths
     if ((rc = ensure(c, c->run_parent, need * sizeof(int32_t)))) return rc;
     if ((rc = ensure(c, c->run_sroot, need))) return rc;
     if ((rc = ensure(c, c->rec, need * sizeof(rise_box)))) return rc;
@@ -549,7 +549,7 @@ int finish_call(rise_ctx *c, rise_box *out, int64_t cap, int64_t *n_boxes) {
   DeviceStatus h = *sl.st_h;
   if (h.err & ERR_RUN_CAPACITY) {
     CK(cudaStreamSynchronize(c->stream));
-    const int64_t need = h.n_runs + h.n_runs / 4 + 1024;
+    const int64_t need = std::max<int64_t>(2 * h.n_runs, 2 * c->run_cap);   // doubled: few growths
     if ((rc = ensure(c, c->run_parent, need * sizeof(int32_t)))) return rc;
     if ((rc = ensure(c, c->run_sroot, need))) return rc;
     if ((rc = ensure(c, c->rec, need * sizeof(rise_box)))) return rc;

@@ -68,7 +68,7 @@ struct Done {
 struct Lane {
   rise_ctx *ctx = nullptr;
   std::thread th;
-  int64_t captures = 0, generations = 0;   // copied from the context after each batch
+  int64_t captures = 0, generations = 0, relabels = 0;   // copied from the context after each batch
 };
 
 constexpr uint32_t kStateMagic = 0x52534531u;   // stream state blob, version 1
@@ -231,6 +231,7 @@ void lane_main(rise_server *s, int li) {
     s->st_max_batch_us = std::max<int64_t>(s->st_max_batch_us, (t_done - t_start) / 1000);
     s->lanes[li].captures = ctx->batch.captures;
     s->lanes[li].generations = (int64_t)ctx->gen;
+    s->lanes[li].relabels = ctx->batch.relabels;
     lk.unlock();
     s->cv_done.notify_all();
     s->cv_work.notify_all();
@@ -321,9 +322,10 @@ int rise_server_create(rise_server **out, const rise_server_config *cfg) {
     cc.mem_budget = cfg->mem_budget ? scratch + scratch / 2 : 0;
     if ((rc = rise_create(&s->lanes[li].ctx, &cc))) break;
     rise_set_option(s->lanes[li].ctx, RISE_OPT_AUTOTUNE, 0);   // batch sizes vary: fixed shapes
-#ifdef RISE_WINDOW_NO_GRAPHS
-    if (s->window) rise_set_option(s->lanes[li].ctx, RISE_OPT_GRAPH, 0);
+#ifndef RISE_SERVER_GRAPHS
+#define RISE_SERVER_GRAPHS 1
 #endif
+    if (!RISE_SERVER_GRAPHS || s->window) rise_set_option(s->lanes[li].ctx, RISE_OPT_GRAPH, 0);
   }
   if (rc) {
     cudaGetLastError();
@@ -442,15 +444,16 @@ int rise_stream_import(rise_server *s, int stream, const void *buf, size_t bytes
 int rise_server_stats(rise_server *s, int64_t *out, int n) {
   if (!s || !out || n < 0) return RISE_EINVAL;
   std::lock_guard<std::mutex> lk(s->mu);
-  int64_t captures = 0, generations = 0;
+  int64_t captures = 0, generations = 0, relabels = 0;
   for (const Lane &L : s->lanes) {
     captures += L.captures;
     generations += L.generations;
+    relabels += L.relabels;
   }
-  const int64_t w[11] = {s->st_submitted, s->st_rejected, s->st_completed, s->st_batches,
+  const int64_t w[12] = {s->st_submitted, s->st_rejected, s->st_completed, s->st_batches,
                          s->st_max_batch, s->st_max_inflight, (int64_t)s->slot_dev.size(),
-                         (int64_t)s->lanes.size(), captures, generations, s->st_max_batch_us};
-  for (int i = 0; i < n && i < 11; ++i) out[i] = w[i];
+                         (int64_t)s->lanes.size(), captures, generations, s->st_max_batch_us, relabels};
+  for (int i = 0; i < n && i < 12; ++i) out[i] = w[i];
   return RISE_OK;
 }
 

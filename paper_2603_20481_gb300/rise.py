@@ -515,7 +515,7 @@ def column_stats_noalloc(img, cols, stream=None) -> int:
 
 SERVER_STATS = ("submitted", "rejected", "completed", "batches", "largest_batch",
                 "most_in_flight", "slots", "lanes", "graph_captures", "buffer_generations",
-                "longest_batch_us")
+                "longest_batch_us", "relabels")
 
 
 class Server:
