@@ -52,7 +52,7 @@ HBM_FALLBACK_GBS = 6800.0
 # DRAM bytes (read + write) per launch of the dominant kernel at this workload,
 # from the ncu capture summarised in profiles/stft_power_wideband_2e26_fft4096.md
 # (set to None whenever that kernel changes).
-TRAFFIC_BYTES = {2: 541975040 + 493511680}
+TRAFFIC_BYTES = {2: 541917184 + 493364224}
 
 
 def _peaks():
