@@ -322,10 +322,9 @@ int rise_server_create(rise_server **out, const rise_server_config *cfg) {
     cc.mem_budget = cfg->mem_budget ? scratch + scratch / 2 : 0;
     if ((rc = rise_create(&s->lanes[li].ctx, &cc))) break;
     rise_set_option(s->lanes[li].ctx, RISE_OPT_AUTOTUNE, 0);   // batch sizes vary: fixed shapes
-#ifndef RISE_SERVER_GRAPHS
-#define RISE_SERVER_GRAPHS 1
-#endif
-    if (!RISE_SERVER_GRAPHS || s->window) rise_set_option(s->lanes[li].ctx, RISE_OPT_GRAPH, 0);
+    // window mode: plain launches (its batch compositions are many and a
+    // capture inside a deadline costs more than the launches it saves)
+    if (s->window) rise_set_option(s->lanes[li].ctx, RISE_OPT_GRAPH, 0);
   }
   if (rc) {
     cudaGetLastError();
