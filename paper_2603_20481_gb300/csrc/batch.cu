@@ -561,6 +561,32 @@ void destroy_batch(rise_ctx *c) {
   b = BatchState();
 }
 
+int reserve_batch(rise_ctx *c, const rise_capture *caps, int ncap, const rise_thresholds &thr,
+                  int64_t cap) {
+  if (!c || ncap < 1 || !caps || cap < 0 || c->npend) return RISE_EINVAL;
+  c->cur = 0;   // the slot whose box buffer a batch uses
+  for (int k = 0; k < ncap; ++k) {
+    int rc = check_capture(caps[k]);
+    if (rc) return rc;
+    if ((rc = check_thresholds(thr, caps[k].fft_size))) return rc;
+  }
+  CK(cudaSetDevice(c->device));
+  Plan p;
+  int rc = make_plan(caps, ncap, thr.range_mode == RISE_RANGE_FIXED, p);
+  if (rc) return rc;
+  if ((rc = upload_level_tables(c, thr.level_db))) return rc;
+  if ((rc = upload_sg(c, thr.sg_half_window))) return rc;
+  for (const auto &g : p.groups) {
+    Tables *tb;
+    if ((rc = get_tables(c, g.N, &tb))) return rc;
+  }
+  // the default launch parameters (what an untuned batch uses)
+  p.item_mult.assign(p.groups.size(), 2);
+  p.morph_wps = 16;
+  size_tables(c, caps, p);
+  return ensure_buffers(c, p, cap);
+}
+
 int detect_batch(rise_ctx *c, const rise_capture *caps, int ncap, const rise_thresholds *thr_in,
                  rise_box *out, int64_t cap, int64_t *offsets) {
   rise_thresholds thr;

@@ -161,6 +161,12 @@ int upload_sg(rise_ctx *c, int m);
 void destroy_batch(rise_ctx *c);
 int detect_batch(rise_ctx *c, const rise_capture *caps, int ncap, const rise_thresholds *thr,
                  rise_box *out, int64_t cap, int64_t *offsets);
+// Grows every buffer of the batch path to what a batch of these captures
+// (and box capacity `cap`) needs, launching nothing: a caller that knows its
+// largest batch reserves it once, so that no later batch of that size or
+// less allocates (an allocation synchronises the device and drops graphs).
+int reserve_batch(rise_ctx *c, const rise_capture *caps, int ncap, const rise_thresholds &thr,
+                  int64_t cap);
 
 }  // namespace host
 }  // namespace rise

@@ -105,6 +105,28 @@ struct rise_server {
 
 namespace {
 
+constexpr int64_t kLaneBoxes = 1 << 18;   // a lane's first box buffer (doubled on demand)
+
+// The largest batch a lane can be given: max_batch chunks, each with the
+// longest carry, split into captures as lane_main splits them.
+std::vector<rise_capture> largest_batch(const rise_server *s) {
+  std::vector<rise_capture> caps;
+  if (s->slot_dev.empty()) return caps;
+  const int nslot = (int)s->slot_dev.size();
+  for (int b = 0; b < s->max_batch; ++b) {
+    float2 *dst = s->slot_dev[b % nslot];
+    if (s->window == 0) {
+      const int64_t len = s->max_chunk + s->N - 1;   // a chunk after a carry of N - 1 samples
+      caps.push_back(rise_capture{dst, len, s->N, s->hop});
+    } else {
+      const int64_t step = s->window * s->hop;
+      const int64_t k = 1 + (s->max_chunk - 1) / step;   // plots of a chunk after the longest carry
+      for (int64_t j = 0; j < k; ++j) caps.push_back(rise_capture{dst + j * step, s->span, s->N, s->hop});
+    }
+  }
+  return caps;
+}
+
 void lane_main(rise_server *s, int li) {
   cudaSetDevice(s->device);
   rise_ctx *ctx = s->lanes[li].ctx;
@@ -120,7 +142,7 @@ void lane_main(rise_server *s, int li) {
   std::vector<Item> items;
   std::vector<rise_capture> caps;
   std::vector<int64_t> offs;
-  std::vector<rise_box> boxes(1 << 18);   // grown (and the context's box buffer with it) on demand
+  std::vector<rise_box> boxes(kLaneBoxes);   // grown (and the context's box buffer with it) on demand
   for (;;) {
     std::unique_lock<std::mutex> lk(s->mu);
     s->cv_work.wait(lk, [&] { return s->stop || (!s->pending.empty() && !s->free_slots.empty()); });
@@ -325,6 +347,16 @@ int rise_server_create(rise_server **out, const rise_server_config *cfg) {
     // window mode: plain launches (its batch compositions are many and a
     // capture inside a deadline costs more than the launches it saves)
     if (s->window) rise_set_option(s->lanes[li].ctx, RISE_OPT_GRAPH, 0);
+  }
+  if (rc == RISE_OK) {
+    // every lane's buffers sized for its largest batch now: a lane that grew
+    // while serving (a burst after a stall fills batches beyond any seen
+    // before) would synchronise the device in the middle of the stream.
+    // Best effort: a lane that cannot reserve grows on demand as before.
+    const std::vector<rise_capture> worst = largest_batch(s);
+    for (int li = 0; li < lanes && !worst.empty(); ++li)
+      if (reserve_batch(s->lanes[li].ctx, worst.data(), (int)worst.size(), s->thr, kLaneBoxes) != RISE_OK)
+        cudaGetLastError();
   }
   if (rc) {
     cudaGetLastError();

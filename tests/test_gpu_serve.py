@@ -181,3 +181,35 @@ def test_window_mode_plots_match_rise_detect(det):
                 x = full[w * W * HOP: w * W * HOP + span]
                 np.testing.assert_array_equal(b, det.detect(torch.from_numpy(x).cuda(), N, HOP),
                                               err_msg=f"stream {s} plot {w}")
+
+
+@pytest.mark.parametrize("W", [0, 40])
+def test_lanes_do_not_grow_while_serving(W):
+    """A lane's buffers are sized for its largest batch when the server is
+    made: a burst that fills whole batches (the most chunks, each after the
+    longest carry) after a batch of one allocates nothing more, so the
+    lane's buffer generation stays where the first batch left it."""
+    import torch
+    from paper_2603_20481_gb300 import rise
+    n = 2 * 40 * HOP + 512 if W else 61440 + 512          # window mode: up to 2 plots a chunk
+    pinned = [torch.from_numpy(synth.served_chunk(40 + s, 0, n=n).iq).pin_memory() for s in range(8)]
+    with rise.Server(N, HOP, max_chunk=n, max_streams=8, lanes=1, max_batch=8,
+                     window_frames=W, max_pending=4096) as srv:
+        assert srv.submit(0, pinned[0])
+        srv.drain()
+        first = srv.stats()
+        assert first["batches"] == 1
+        for k in range(12):
+            for s in range(8):
+                assert srv.submit(s, pinned[s])
+        srv.drain()
+        got = 0
+        while True:
+            res = srv.poll(timeout_ms=0)
+            if not res:
+                break
+            got += len(res)
+            assert all(d["status"] == 0 for d, _ in res)
+        st = srv.stats()
+    assert st["completed"] == 97 and st["largest_batch"] == 8
+    assert st["buffer_generations"] == first["buffer_generations"]
