@@ -245,6 +245,24 @@ def test_degenerate_inputs(det):
     assert det.detect_image(img).shape == (0, 8)
 
 
+
+def test_hand_block_image_closed_form(det):
+    """The image of hand_images.block_image through the CUDA path: noise
+    floor, offsets, power floor, per-column thresholds, final mask and box
+    against values worked out by hand, not against the oracle."""
+    import hand_images
+    rise = _rise()
+    q, want, want_boxes = hand_images.block_image(256)
+    det.set_option(rise.OPT_KEEP_MASKS, 1)
+    T, F = q.shape
+    boxes = det.detect_image(torch.from_numpy(q).cuda())
+    fl = det.debug(rise.DBG_FLOOR, T, F)
+    assert fl[:5].tolist() == [want["N0"], want["delta_psd"], want["delta_pow"], want["P_q"], want["D"]]
+    cols = det.debug(rise.DBG_COLSTATS, T, F)
+    assert np.array_equal(cols["eff"], want["eff"])
+    assert np.array_equal(rise.unpack_mask(det.debug(rise.DBG_MASK3, T, F), F), want["mask"])
+    assert np.array_equal(boxes, want_boxes)
+
 def test_truncation_and_invalid_arguments(det):
     rise = _rise()
     q = _stripes(512, 1024, 3)

@@ -3,7 +3,9 @@ of its steps, and strong planted bursts come back as boxes that overlap
 their ground truth (informational accuracy, as the paper itself reports a
 mean IoU near 63%, Sec. VI-A)."""
 import numpy as np
+import pytest
 
+import hand_images
 import oracle
 from paper_2603_20481_gb300 import synth
 
@@ -50,3 +52,22 @@ def test_strong_planted_bursts_are_found():
             hits += best >= 0.5
     assert total >= 8
     assert hits >= 0.8 * total
+
+
+
+@pytest.mark.parametrize("F", [64, 256])
+def test_hand_image_closed_form(F):
+    """The block image of hand_images.block_image, worked through by hand:
+    noise floor, offsets, power floor, per-column thresholds, final mask and
+    the one box, all exact."""
+    q, want, want_boxes = hand_images.block_image(F)
+    boxes, ex = oracle.detect_image(q, extras=True)
+    for k in ("D", "N0", "delta_psd", "delta_pow", "P_q"):
+        assert ex[k] == want[k], k
+    np.testing.assert_array_equal(ex["eff"], want["eff"])
+    np.testing.assert_array_equal(ex["mask"], want["mask"])
+    np.testing.assert_array_equal(boxes, want_boxes)
+    # the Otsu step alone on a block column: the smallest of the tied splits
+    h = np.zeros(256, np.uint32)
+    h[100], h[200] = 54, 10
+    assert oracle.otsu(h) == 100
