@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -43,3 +45,35 @@ def test_box_and_struct_layouts_match_the_oracle():
     from paper_2603_20481_gb300 import rise
     assert rise.BOX_DTYPE == oracle._BOX_DTYPE
     assert [f[0] for f in rise.Thresholds._fields_] == [f[0] for f in oracle.Params._fields_]
+
+
+def test_boxes_widen_on_the_host(built_lib):
+    """rise_boxes_widen is host code: rise_box records to int64 rows in the
+    column order t0, t1, f0, f1, anchor, area, sum_q, energy_fx."""
+    import numpy as np
+    from paper_2603_20481_gb300 import rise
+    rng = np.random.default_rng(5)
+    raw = np.zeros(37, rise.BOX_DTYPE)
+    cols = ("t0", "t1", "f0", "f1", "anchor", "area", "sum_q", "energy_fx")
+    for name in cols:
+        hi = 2 ** 31 - 1 if raw.dtype[name].itemsize == 4 else 2 ** 62
+        raw[name] = rng.integers(0, hi, size=raw.shape[0], dtype=np.int64).astype(raw.dtype[name])
+    out = rise.boxes_from_raw(raw, raw.shape[0])
+    assert out.dtype == np.int64 and out.shape == (37, 8)
+    for j, name in enumerate(cols):
+        np.testing.assert_array_equal(out[:, j], raw[name].astype(np.int64))
+    assert rise.boxes_from_raw(raw, 0).shape == (0, 8)
+
+
+def test_arguments_rejected_before_any_device_call(built_lib):
+    """Invalid arguments are refused before the library touches CUDA, so
+    these calls are safe with no GPU present."""
+    import numpy as np
+    from paper_2603_20481_gb300 import rise
+    L = rise.lib()
+    offs = np.zeros(2, np.int64)
+    assert L.rise_detect_batch(None, None, 0, None, None, 0, offs.ctypes.data) == rise.RISE_EINVAL
+    for N, hop in ((1000, 500), (128, 64), (2048, 0), (2048, 4096)):
+        with pytest.raises(rise.RiseError) as e:
+            rise.Server(N, hop, max_chunk=8192, max_streams=1)
+        assert e.value.code == rise.RISE_EINVAL
