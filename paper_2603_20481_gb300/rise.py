@@ -581,17 +581,16 @@ class Server:
         return True
 
     def poll(self, timeout_ms: int = 0, max_results: int = 1024):
-        """Finished chunks: list of (result fields dict, boxes (n, 8) int64)."""
+        """Finished chunks: list of (result fields dict, boxes (n, 8) int64).
+        A result with more boxes than the host arena comes back alone with
+        status RISE_ETRUNC and the arena's worth of boxes; the arena is then
+        doubled for later polls."""
         n = C.c_int(0)
-        while True:
-            rc = lib().rise_server_poll(self._h, self._res, min(max_results, 1024),
-                                        self._arena.ctypes.data, self._arena.shape[0],
-                                        C.byref(n), timeout_ms)
-            if rc != RISE_OK:
-                raise RiseError(rc, "rise_server_poll")
-            if n.value == 1 and self._res[0].status == RISE_ETRUNC:
-                raise RiseError(RISE_ETRUNC, "rise_server_poll (box arena)")
-            break
+        rc = lib().rise_server_poll(self._h, self._res, min(max_results, 1024),
+                                    self._arena.ctypes.data, self._arena.shape[0],
+                                    C.byref(n), timeout_ms)
+        if rc != RISE_OK:
+            raise RiseError(rc, "rise_server_poll")
         out = []
         for i in range(n.value):
             r = self._res[i]
@@ -600,6 +599,8 @@ class Server:
             out.append((d, boxes_from_raw(b, r.n_boxes)))
             if not self.window:   # window mode: results are per plot; buffers go at drain()
                 self._held.pop((r.stream, r.seq), None)
+        if n.value == 1 and self._res[0].status == RISE_ETRUNC:
+            self._arena = np.empty(2 * self._arena.shape[0], BOX_DTYPE)
         return out
 
     def drain(self, timeout_ms: int = -1):
