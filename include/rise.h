@@ -214,7 +214,9 @@ typedef struct {
  *           the total, also on RISE_ETRUNC (then `out` holds the first cap).
  * Per capture T = (n - fft_size) / hop + 1 must be in 1..RISE_BATCH_MAX_ROWS.
  * Errors: RISE_EINVAL, RISE_ENOMEM, RISE_ETRUNC, RISE_ECUDA, RISE_ETIMEOUT,
- * RISE_EINTERNAL.  rise_debug_export intermediates are not kept for batches. */
+ * RISE_EINTERNAL.  rise_debug_export gives the batch's images, float power
+ * and anchors (RISE_DBG_BATCH_*); the single-capture intermediates are not
+ * kept for batches. */
 int rise_detect_batch(rise_ctx *ctx, const rise_capture *caps, int ncap,
                       const rise_thresholds *thr, rise_box *out, int64_t cap, int64_t *offsets);
 
@@ -298,6 +300,10 @@ typedef struct {
   const rise_thresholds *thr; /* NULL: defaults; copied at create                 */
   int64_t window_frames;  /* 0: detect each chunk (its complete frames); W > 0:   *
                            * window mode, detect TF plots of W frames             */
+  int keep_images;        /* 1: keep every result's 8-bit image on the host for   *
+                           * rise_server_result_image (introspection: costs a     *
+                           * device-to-host copy per batch and T*F host bytes per *
+                           * result until taken); 0: off                          */
 } rise_server_config;
 
 typedef struct {
@@ -356,6 +362,15 @@ int rise_stream_import(rise_server *s, int stream, const void *buf, size_t bytes
  * run arrays.  Writes min(n, 12) values. */
 int rise_server_stats(rise_server *s, int64_t *out, int n);
 
+/* With keep_images set: moves the 8-bit image the result (stream, seq) was
+ * detected on (chunk mode: the chunk's frames, carried samples included;
+ * window mode: plot seq) into dst, [T][F] with F = fft_size, and drops it
+ * from the server.  *T receives its rows; dst may be NULL to ask for T
+ * only (the image is then kept).  Valid once the result is ready (polled or
+ * not).  Errors: RISE_EINVAL (no such image kept, bytes < T * F). */
+int rise_server_result_image(rise_server *s, int stream, int64_t seq, uint8_t *dst, size_t bytes,
+                             int64_t *T);
+
 /* Stops the lanes after the chunks in flight and frees everything; queued
  * chunks that never started are dropped. */
 void rise_server_destroy(rise_server *s);
@@ -383,6 +398,14 @@ void rise_server_destroy(rise_server *s);
                                 * [1] replayed from a graph (0/1), [2..2+G) frames  *
                                 * per STFT item in steps, [2+G] morphology warps    *
                                 * per SM                                            */
+/* Intermediates of the last rise_detect_batch call, kept until the next call
+ * of the context (or a buffer growth) overwrites them.  Captures follow one
+ * another in call order, capture c taking T_c * F_c entries ([T_c][F_c],
+ * row-major, layout above), with no gaps. */
+#define RISE_DBG_BATCH_IMAGES 16  /* uint8: every capture's 8-bit image           */
+#define RISE_DBG_BATCH_POWER 17   /* float: every capture's |X|^2 (AUTO range only) */
+#define RISE_DBG_BATCH_ANCHORS 18 /* float [ncap]: each capture's anchor power     *
+                                   * (its largest |X|^2; FIXED: 10^(hi_db/10))     */
 
 typedef struct {
   uint64_t S;    /* column sum of levels                                */
@@ -440,9 +463,9 @@ int rise_stage_times(rise_ctx *ctx, float *ms, int nstages);
  *
  * For the 8-bit image img_dev ([T][F] uint8 on the current device, layout
  * above, 2-byte aligned) it writes, per column f, cols_dev[f].S = sum of the
- * column's levels and cols_dev[f].otsu = its exact Otsu threshold (Eq. 4;
- * -1 when no split exists), the same values rise_detect_image reports;
- * Shat, keep, eff and pad are set to 0.  cols_dev: device rise_colstat[F],
+ * column's levels and cols_dev[f].otsu = the exact Otsu threshold, the same
+ * value rise_detect_image reports (-1 when no split exists); Shat, keep, eff
+ * and pad are set to 0.  cols_dev: device rise_colstat[F],
  * 8-byte aligned.  F a power of two in [RISE_MIN_FFT, RISE_NOALLOC_MAX_COLS],
  * 1 <= T <= RISE_MAX_ROWS.
  *
@@ -450,13 +473,17 @@ int rise_stage_times(rise_ctx *ctx, float *ms, int nstages);
  * current device and the call returns without waiting; the results are
  * valid once the stream reaches them.  The first call on a device looks up
  * the array's device address (a one-time set-up per device); make that first
- * call before any stream capture.  Every call, on any stream or thread,
- * shares the one array per device and clears the part it uses before
- * counting: calls whose work overlaps on the GPU race and give wrong
- * results, so order them (one stream, or events).
- * Errors (nothing is queued): RISE_EINVAL (NULL or misaligned pointers,
- * pointers not in the current device's memory, bad T or F), RISE_ESCRATCH
- * (F > RISE_NOALLOC_MAX_COLS), RISE_ECUDA. */
+ * call before any stream capture.  Later calls made outside a stream capture
+ * look the address up again, so a device reset between calls is safe; calls
+ * made while their stream is capturing use the address of the last call.
+ * Every call, on any stream or thread, shares the one array per device and
+ * clears the part it uses before counting: calls whose work overlaps on the
+ * GPU race and give wrong results, so order them (one stream, or events).
+ * Errors: RISE_EINVAL (NULL or misaligned pointers, pointers not in the
+ * current device's memory, bad T or F) and RISE_ESCRATCH
+ * (F > RISE_NOALLOC_MAX_COLS) queue nothing; RISE_ECUDA (a CUDA call or
+ * launch failed) may come after part of the work was queued, so cols_dev
+ * may already have been cleared on the stream. */
 #define RISE_NOALLOC_MAX_COLS 4096
 int rise_column_stats_noalloc(const uint8_t *img_dev, int64_t T, int F, rise_colstat *cols_dev,
                               void *cuda_stream);

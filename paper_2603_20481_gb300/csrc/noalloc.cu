@@ -71,11 +71,20 @@ constexpr int NA_MAX_DEVICES = 64;
 std::mutex g_setup_mu;
 uint32_t *g_scratch[NA_MAX_DEVICES];   // device address of rise_noalloc_hist, per device
 
-// Once per device, with that device current: the device address of the
-// scratch array and the shared-memory size of the histogram kernel.
-int setup_device(int dev, uint32_t **out) {
+// With device dev current: the device address of the scratch array and the
+// shared-memory size of the histogram kernel.  Looked up on the first call
+// on a device and again on every call whose stream is not capturing (a
+// device reset gives the array a new address and clears the kernel's
+// attribute); a capturing call reuses the last address, since the set-up
+// calls are not stream work.
+int setup_device(int dev, cudaStream_t s, uint32_t **out) {
   std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (!g_scratch[dev]) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    cap = cudaStreamCaptureStatusActive;   // unknown: take the capturing branch
+  }
+  if (!g_scratch[dev] || cap == cudaStreamCaptureStatusNone) {
     uint32_t *p = nullptr;
     if (cudaGetSymbolAddress(reinterpret_cast<void **>(&p), rise_noalloc_hist) != cudaSuccess || !p)
       return RISE_ECUDA;
@@ -114,10 +123,10 @@ extern "C" int rise_column_stats_noalloc(const uint8_t *img_dev, int64_t T, int 
   if (cudaGetDevice(&dev) != cudaSuccess) return RISE_ECUDA;
   if (dev < 0 || dev >= NA_MAX_DEVICES) return RISE_EINVAL;
   if (!on_device(img_dev, dev) || !on_device(cols_dev, dev)) return RISE_EINVAL;
-  uint32_t *hist = nullptr;
-  int rc = setup_device(dev, &hist);
-  if (rc != RISE_OK) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  uint32_t *hist = nullptr;
+  int rc = setup_device(dev, s, &hist);
+  if (rc != RISE_OK) return rc;
   // the array keeps the previous call's counts: clear this call's columns
   if (cudaMemsetAsync(hist, 0, (size_t)F * 256 * sizeof(uint32_t), s) != cudaSuccess) return RISE_ECUDA;
   if (cudaMemsetAsync(cols_dev, 0, (size_t)F * sizeof(rise_colstat), s) != cudaSuccess) return RISE_ECUDA;

@@ -7,8 +7,11 @@ and stall other streams).  It keeps its column histograms in one fixed device
 array shared by every call, so each test here makes two calls in a row: the
 second one only comes out right if the first call's counts were cleared.
 Both are checked against rise_detect_image (which allocates its scratch in a
-context) on the same image: S and the Otsu threshold are integers, so they
-must agree exactly.  This file is collected last on purpose.
+context) and against the FP64 oracle's column histograms and exhaustive Otsu
+search on the same image: S and the Otsu threshold are integers, so they must
+agree exactly.  One test orders two calls on two streams with an event, the
+way a caller with several streams keeps them from racing on the shared
+array.  This file is collected last on purpose.
 """
 import ctypes
 
@@ -51,11 +54,17 @@ def _via_noalloc(img, stream=None):
     return cols.cpu().numpy().view(rise.COLSTAT_DTYPE)
 
 
-def _check(got, want):
+def _check(got, want, img=None):
     np.testing.assert_array_equal(got["S"], want["S"])
     np.testing.assert_array_equal(got["otsu"], want["otsu"])
     assert not got["Shat"].any() and not got["keep"].any()
     assert not got["eff"].any() and not got["pad"].any()
+    if img is not None:
+        import oracle
+        q = img.cpu().numpy()
+        ref = oracle.column_thresholds(oracle.column_hist(q), q.shape[0])
+        np.testing.assert_array_equal(got["S"], ref["S"])
+        np.testing.assert_array_equal(got["otsu"], ref["otsu"])
 
 
 @pytest.mark.parametrize("shapes", [
@@ -66,7 +75,7 @@ def test_two_calls_in_a_row_match_the_context_path(det, shapes):
     import torch
     for k, (T, F) in enumerate(shapes):
         img = torch.from_numpy(_image(T, F, 40 + k)).cuda()
-        _check(_via_noalloc(img), _via_context(det, img))
+        _check(_via_noalloc(img), _via_context(det, img), img)
 
 
 def test_on_a_side_stream(det):
@@ -78,6 +87,28 @@ def test_on_a_side_stream(det):
         with torch.cuda.stream(s):
             got = _via_noalloc(img, s)
         _check(got, _via_context(det, img))
+
+
+def test_two_streams_ordered_by_an_event(det):
+    """The first call runs on stream a, the second on stream b after an event
+    recorded behind the first: the second call's clear of the shared array
+    waits for the first call's counts to be used, so both results are right."""
+    import torch
+    from paper_2603_20481_gb300 import rise
+    imgs = [torch.from_numpy(_image(4099, 1024, 80 + k)).cuda() for k in range(2)]
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = [torch.full((1024 * rise.COLSTAT_DTYPE.itemsize,), 0xAB, dtype=torch.uint8, device="cuda")
+            for _ in range(2)]
+    done = torch.cuda.Event()
+    assert rise.column_stats_noalloc(imgs[0], outs[0], a) == rise.RISE_OK
+    done.record(a)
+    b.wait_event(done)
+    assert rise.column_stats_noalloc(imgs[1], outs[1], b) == rise.RISE_OK
+    b.synchronize()
+    a.synchronize()
+    for img, out in zip(imgs, outs):
+        _check(out.cpu().numpy().view(rise.COLSTAT_DTYPE), _via_context(det, img), img)
 
 
 def test_rejects_what_it_cannot_hold(det):
