@@ -606,6 +606,7 @@ int detect_batch(rise_ctx *c, const rise_capture *caps, int ncap, const rise_thr
   }
   CK(cudaSetDevice(c->device));
   c->last_valid = false;
+  c->batch.last_valid = false;
   Plan p;
   int rc = make_plan(caps, ncap, thr.range_mode == RISE_RANGE_FIXED, p);
   if (rc) return rc;
@@ -698,6 +699,11 @@ int detect_batch(rise_ctx *c, const rise_capture *caps, int ncap, const rise_thr
     h = (*c->cs().st_h);
   }
   c->last_status = c->cs().st_h;
+  b.last_valid = true;   // images, power and anchors stay until the next call moves or overwrites them
+  b.last_fixed = p.fixed;
+  b.last_ncap = ncap;
+  b.last_px = p.total_px;
+  b.last_hi_db = thr.hi_db;
   if (h.err & (ERR_UNION_LIMIT | ERR_SCAN)) return RISE_ETIMEOUT;
   if (h.err) return RISE_EINTERNAL;
   std::memcpy(offsets, b.offs_h, sizeof(int64_t) * (ncap + 1));

@@ -58,6 +58,13 @@ struct BatchState {
   int last_groups = 0;
   std::vector<int> last_params;
   bool last_graph = false;
+  // what the last batch left in the context's buffers, for rise_debug_export:
+  // its captures' images (and float power) back to back, and their anchors
+  bool last_valid = false;
+  bool last_fixed = false;
+  int last_ncap = 0;
+  int64_t last_px = 0;
+  double last_hi_db = 0.0;
 };
 
 // One call in flight: where its boxes, status and stage events land, and

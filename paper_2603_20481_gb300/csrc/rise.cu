@@ -52,6 +52,7 @@ int ensure(rise_ctx *c, Buf &b, size_t bytes) {
 
 void new_generation(rise_ctx *c) {
   ++c->gen;
+  c->batch.last_valid = false;   // a moved buffer lost the last batch's intermediates
   cudaStreamSynchronize(c->stream);
   for (auto &g : c->single_graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -428,6 +429,7 @@ int submit_call(rise_ctx *c, const void *iq, int flags, int64_t n, int N, int ho
   if (rc) return rc;
   if (c->npend >= 2) return RISE_EAGAIN;
   CK(cudaSetDevice(c->device));
+  c->batch.last_valid = false;   // this call overwrites the image buffer
   c->cur = c->next_slot;
   CallSlot &sl = c->cs();
   const int F = N;
@@ -795,6 +797,7 @@ int rise_detect_image(rise_ctx *c, const uint8_t *img_dev, int64_t T, int F,
   int rc = check_thresholds(thr, F);
   if (rc) return rc;
   CK(cudaSetDevice(c->device));
+  c->batch.last_valid = false;
   if ((rc = prepare_image_buffers(c, T, F))) return rc;
   record(c, 0);
   CK(cudaMemsetAsync(&c->small->status, 0, sizeof(DeviceStatus), c->stream));
@@ -895,6 +898,33 @@ int rise_debug_export(rise_ctx *c, int what, void *dst, size_t bytes) {
     v[1] = c->batch.last_graph ? 1 : 0;
     for (size_t i = 0; i < c->batch.last_params.size() && i + 2 < 16; ++i) v[2 + i] = c->batch.last_params[i];
     std::memcpy(dst, v, sizeof v);
+    return RISE_OK;
+  }
+  if (what == RISE_DBG_BATCH_IMAGES || what == RISE_DBG_BATCH_POWER || what == RISE_DBG_BATCH_ANCHORS) {
+    const BatchState &b = c->batch;
+    if (!b.last_valid) return RISE_EINVAL;
+    CK(cudaSetDevice(c->device));
+    if (what == RISE_DBG_BATCH_ANCHORS) {
+      const size_t need = (size_t)b.last_ncap * sizeof(float);
+      if (bytes < need) return RISE_EINVAL;
+      float *o = static_cast<float *>(dst);
+      if (b.last_fixed) {
+        for (int k = 0; k < b.last_ncap; ++k) o[k] = (float)std::pow(10.0, b.last_hi_db / 10.0);
+        return RISE_OK;
+      }
+      std::vector<CapSmall> cs((size_t)b.last_ncap);
+      CK(cudaMemcpyAsync(cs.data(), b.small.p, cs.size() * sizeof(CapSmall), cudaMemcpyDeviceToHost,
+                         c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      for (int k = 0; k < b.last_ncap; ++k) std::memcpy(&o[k], &cs[k].max_bits, sizeof(float));
+      return RISE_OK;
+    }
+    if (what == RISE_DBG_BATCH_POWER && b.last_fixed) return RISE_EINVAL;
+    const size_t need = (size_t)b.last_px * (what == RISE_DBG_BATCH_POWER ? sizeof(float) : 1);
+    const void *src = what == RISE_DBG_BATCH_POWER ? c->power.p : c->img.p;
+    if (bytes < need || !src) return RISE_EINVAL;
+    CK(cudaMemcpyAsync(dst, src, need, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     return RISE_OK;
   }
   if (!c->last_valid) return RISE_EINVAL;

@@ -27,6 +27,7 @@ RANGE_AUTO_MAX, RANGE_FIXED = 0, 1
 DBG_POWER_F32, DBG_IMAGE_U8, DBG_HIST, DBG_COLSTATS, DBG_FLOOR = 1, 2, 3, 4, 5
 DBG_MASK0, DBG_MASK1, DBG_MASK2, DBG_MASK3, DBG_MAXPOW, DBG_LEVEL_EDGES = 6, 7, 8, 9, 10, 11
 DBG_LAUNCHES, DBG_BATCH_INFO, DBG_GRAPHS, DBG_CCL = 12, 13, 14, 15
+DBG_BATCH_IMAGES, DBG_BATCH_POWER, DBG_BATCH_ANCHORS = 16, 17, 18
 STAGES = ("spectrum_pass1", "spectrum_pass2", "histogram", "column_stats", "morphology",
           "labelling", "readback", "total")
 OPT_KEEP_POWER, OPT_KEEP_MASKS, OPT_TIMING, OPT_RANGE_PATH = 1, 2, 3, 4
@@ -43,7 +44,7 @@ EXPORTS = ("rise_thresholds_default", "rise_create", "rise_destroy", "rise_strer
            "rise_detect_batch", "rise_submit", "rise_collect", "rise_match_boxes", "rise_contours",
            "rise_server_create", "rise_stream_submit", "rise_server_poll",
            "rise_server_drain", "rise_stream_export", "rise_stream_import", "rise_server_stats",
-           "rise_server_destroy")
+           "rise_server_result_image", "rise_server_destroy")
 
 
 class RiseError(RuntimeError):
@@ -71,7 +72,7 @@ class ServerConfig(C.Structure):
     _fields_ = [("device", C.c_int), ("fft_size", C.c_int), ("hop", C.c_int),
                 ("max_chunk", C.c_int64), ("max_streams", C.c_int), ("lanes", C.c_int),
                 ("max_batch", C.c_int), ("max_pending", C.c_int), ("mem_budget", C.c_size_t),
-                ("thr", C.c_void_p), ("window_frames", C.c_int64)]
+                ("thr", C.c_void_p), ("window_frames", C.c_int64), ("keep_images", C.c_int)]
 
 
 class Result(C.Structure):
@@ -152,6 +153,8 @@ def lib() -> C.CDLL:
     L.rise_stream_import.restype = i32
     L.rise_server_stats.argtypes = [P, P, i32]
     L.rise_server_stats.restype = i32
+    L.rise_server_result_image.argtypes = [P, i32, i64, P, C.c_size_t, C.POINTER(i64)]
+    L.rise_server_result_image.restype = i32
     L.rise_server_destroy.argtypes = [P]
     L.rise_server_destroy.restype = None
     L.rise_column_stats_noalloc.argtypes = [P, i64, i32, P, P]
@@ -469,6 +472,27 @@ class Detector:
             raise RiseError(rc, "rise_debug_export")
         return v
 
+    def batch_debug(self, shapes, what: int = DBG_BATCH_IMAGES):
+        """Intermediates of the last detect_batch call: the captures' 8-bit
+        images (DBG_BATCH_IMAGES) or float |X|^2 (DBG_BATCH_POWER) as a list of
+        [T_c, F_c] arrays, given `shapes` = [(T_c, F_c), ...] in call order;
+        DBG_BATCH_ANCHORS gives the float32 anchor power of every capture."""
+        if what == DBG_BATCH_ANCHORS:
+            out = np.zeros(len(shapes), np.float32)
+        else:
+            dt = np.float32 if what == DBG_BATCH_POWER else np.uint8
+            out = np.zeros(sum(int(T) * int(F) for T, F in shapes), dt)
+        rc = lib().rise_debug_export(self._h, what, out.ctypes.data, out.nbytes)
+        if rc != RISE_OK:
+            raise RiseError(rc, "rise_debug_export")
+        if what == DBG_BATCH_ANCHORS:
+            return out
+        res, at = [], 0
+        for T, F in shapes:
+            res.append(out[at:at + int(T) * int(F)].reshape(int(T), int(F)))
+            at += int(T) * int(F)
+        return res
+
     # -- introspection ----------------------------------------------------------
     def debug(self, what: int, T: int, F: int) -> np.ndarray:
         shapes = {
@@ -525,13 +549,15 @@ class Server:
 
     def __init__(self, fft_size: int, hop: int, max_chunk: int, max_streams: int,
                  device: int = 0, lanes: int = 0, max_batch: int = 0, max_pending: int = 0,
-                 mem_budget: int = 0, thr: Optional[Thresholds] = None, window_frames: int = 0):
+                 mem_budget: int = 0, thr: Optional[Thresholds] = None, window_frames: int = 0,
+                 keep_images: bool = False):
         self._thr = thr
         self.window = window_frames
+        self.fft_size = fft_size
         cfg = ServerConfig(device, fft_size, hop, max_chunk, max_streams, lanes, max_batch,
                            max_pending, mem_budget,
                            C.cast(C.pointer(thr), C.c_void_p) if thr is not None else None,
-                           window_frames)
+                           window_frames, int(bool(keep_images)))
         h = C.c_void_p()
         rc = lib().rise_server_create(C.byref(h), C.byref(cfg))
         if rc != RISE_OK:
@@ -541,6 +567,19 @@ class Server:
         self._seq = [0] * max_streams
         self._arena = np.empty(1 << 16, BOX_DTYPE)
         self._res = (Result * 1024)()
+
+    def result_image(self, stream: int, seq: int) -> np.ndarray:
+        """The 8-bit image result (stream, seq) was detected on (servers made
+        with keep_images=True), [T, fft_size] uint8; taken out of the server."""
+        T = C.c_int64(0)
+        rc = lib().rise_server_result_image(self._h, stream, seq, None, 0, C.byref(T))
+        if rc != RISE_OK:
+            raise RiseError(rc, "rise_server_result_image")
+        out = np.zeros((int(T.value), self.fft_size), np.uint8)
+        rc = lib().rise_server_result_image(self._h, stream, seq, out.ctypes.data, out.nbytes, C.byref(T))
+        if rc != RISE_OK:
+            raise RiseError(rc, "rise_server_result_image")
+        return out
 
     def close(self):
         if getattr(self, "_h", None):

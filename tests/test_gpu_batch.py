@@ -1,16 +1,59 @@
-"""rise_detect_batch against one rise_detect call per capture.
+"""rise_detect_batch against the FP64 oracle and against one rise_detect call
+per capture.
 
-A batch shares launches, not results: every capture must come out exactly as
-it does alone (same 8-bit anchor, noise floor, Otsu thresholds, components),
-so the boxes are compared bit for bit, capture by capture.  The single-capture
-path is itself checked against the oracle in test_gpu_parity.py.
+A batch runs its own kernels (a persistent STFT over all captures of one FFT
+size, batch-indexed histogram, floor, morphology and labelling), so every
+capture is checked against the oracle directly, with the bars of the
+single-capture parity tests: the float |X|^2 within 1e-4 relative, the anchor
+within 1e-5, the 8-bit image equal to the oracle's quantiser applied to the
+GPU's own power and within one level of the FP64 image on at most
+ceil(1e-5 px) + 6 pixels, and the boxes bit-exact against the oracle run on
+the capture's own 8-bit image.  A batch shares launches, not results: every
+capture must also come out exactly as it does alone (same 8-bit anchor, noise
+floor, Otsu thresholds, components), so the boxes are compared bit for bit
+with rise_detect, capture by capture.
 """
+import math
+
 import numpy as np
 import pytest
 
+import oracle
 from paper_2603_20481_gb300 import synth
 
 pytestmark = pytest.mark.gpu
+
+
+def _oracle_check(det, xs, Ns, hops, boxes, offs, prm=None, power=True):
+    """Every capture of the last batch against the oracle (see the module bars)."""
+    from paper_2603_20481_gb300 import rise
+    shapes = [(oracle.num_frames(int(x.numel()), N, h), N) for x, N, h in zip(xs, Ns, hops)]
+    imgs = det.batch_debug(shapes, rise.DBG_BATCH_IMAGES)
+    anchors = det.batch_debug(shapes, rise.DBG_BATCH_ANCHORS)
+    pows = det.batch_debug(shapes, rise.DBG_BATCH_POWER) if power else [None] * len(xs)
+    fixed = prm is not None and prm.range_mode == 1
+    for c, (x, N, h, qg, Pg, Mg) in enumerate(zip(xs, Ns, hops, imgs, pows, anchors)):
+        iq = x.cpu().numpy()
+        want = oracle.detect_image(qg, prm)
+        np.testing.assert_array_equal(boxes[offs[c]:offs[c + 1]], want, err_msg=f"capture {c}")
+        boxes_r, qr, Mr = oracle.detect(iq, N, h, prm)
+        d = qg.astype(np.int16) - qr.astype(np.int16)
+        assert np.abs(d).max(initial=0) <= 1, f"capture {c}"
+        assert np.count_nonzero(d) <= math.ceil(1e-5 * qg.size) + 6, f"capture {c}"
+        if not fixed:
+            assert abs(float(Mg) - Mr) <= 1e-5 * Mr, f"capture {c}"
+        if Pg is not None:
+            assert float(Mg) == float(Pg.max())
+            T = qg.shape[0]
+            rows = sorted({0, T // 2, T - 1})
+            for t in rows:
+                Pr = oracle.stft_power(iq, N, h, t, 1)
+                floor = 1e-6 * Pr.mean(axis=1, keepdims=True)
+                assert np.all(np.abs(Pg[t:t + 1].astype(np.float64) - Pr) <= 1e-4 * Pr + floor), \
+                    f"capture {c} frame {t}"
+            q_same = oracle.quantize(Pg.astype(np.float64), oracle.hi_db_of(float(Mg)),
+                                     prm.level_db if prm is not None else 0.25)
+            assert np.array_equal(q_same, qg), f"capture {c}"
 
 
 def _batch(count, seed0, n_range=(1 << 13, 1 << 18), sizes=(256, 512, 1024, 2048)):
@@ -45,9 +88,10 @@ def test_mixed_sizes_match_single_calls(det):
     Ns = [c.fft_size for c in caps]
     hops = [c.hop for c in caps]
     boxes, offs = det.detect_batch(xs, Ns, hops)
-    _check(boxes, offs, _plain(det, xs, Ns, hops))
     info = det.batch_info()
     assert info[0] >= 2                                  # several FFT sizes -> several STFT groups
+    _oracle_check(det, xs, Ns, hops, boxes, offs)
+    _check(boxes, offs, _plain(det, xs, Ns, hops))
 
 
 def test_odd_hops_and_unaligned_starts(det):
@@ -64,6 +108,7 @@ def test_odd_hops_and_unaligned_starts(det):
         Ns.append(c.fft_size)
         hops.append(c.fft_size // 2 + (1 if i % 3 == 0 else 0))
     boxes, offs = det.detect_batch(xs, Ns, hops)
+    _oracle_check(det, xs, Ns, hops, boxes, offs)
     _check(boxes, offs, _plain(det, xs, Ns, hops))
 
 
@@ -73,10 +118,13 @@ def test_fixed_range_and_other_thresholds(det):
     xs = _to_gpu(caps)
     Ns = [c.fft_size for c in caps]
     hops = [c.hop for c in caps]
-    for thr in (rise.default_thresholds(range_mode=rise.RANGE_FIXED, hi_db=75.0),
-                rise.default_thresholds(level_db=0.5, psd_offset_db=1.0, power_offset_db=6.0,
-                                        sg_half_window=3, morph_order=1)):
+    for kw in (dict(range_mode=rise.RANGE_FIXED, hi_db=75.0),
+               dict(level_db=0.5, psd_offset_db=1.0, power_offset_db=6.0, sg_half_window=3,
+                    morph_order=1)):
+        thr = rise.default_thresholds(**kw)
         boxes, offs = det.detect_batch(xs, Ns, hops, thr)
+        _oracle_check(det, xs, Ns, hops, boxes, offs, oracle.params(**kw),
+                      power=kw.get("range_mode", 0) == 0)
         _check(boxes, offs, _plain(det, xs, Ns, hops, thr))
 
 
@@ -97,6 +145,7 @@ def test_graph_replay_reads_fresh_inputs(det):
         x[:n].copy_(torch.from_numpy(c.iq[:n]))
     b2, o2 = det.detect_batch(xs, Ns, hops)
     assert det.batch_info()[1] == 1                       # run from the captured graph
+    _oracle_check(det, xs, Ns, hops, b2, o2)
     _check(b2, o2, _plain(det, xs, Ns, hops))
     assert not (len(b1) == len(b2) and np.array_equal(b1, b2))
     # and once more with the first contents: a replay of the same graph
@@ -173,7 +222,22 @@ def test_many_uneven_captures(det):
     Ns = [c.fft_size for c in caps]
     hops = [c.hop for c in caps]
     boxes, offs = det.detect_batch(xs, Ns, hops)
+    _oracle_check(det, xs, Ns, hops, boxes, offs)
     _check(boxes, offs, _plain(det, xs, Ns, hops))
+
+
+def test_intermediates_are_dropped_by_the_next_call(det):
+    from paper_2603_20481_gb300 import rise
+    caps = _batch(3, 7700, n_range=(1 << 13, 1 << 14))
+    xs = _to_gpu(caps)
+    Ns = [c.fft_size for c in caps]
+    hops = [c.hop for c in caps]
+    det.detect_batch(xs, Ns, hops)
+    shapes = [(oracle.num_frames(int(x.numel()), N, h), N) for x, N, h in zip(xs, Ns, hops)]
+    det.batch_debug(shapes)
+    det.detect(xs[0], Ns[0], hops[0])          # overwrites the image buffer
+    with pytest.raises(rise.RiseError):
+        det.batch_debug(shapes)
 
 
 def test_replay_after_the_tables_grew():
