@@ -25,6 +25,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -97,6 +98,12 @@ struct rise_server {
   std::vector<int> free_slots;
   std::deque<Done> done;
   std::vector<Lane> lanes;
+  bool keep_images = false;
+  struct Image {
+    int64_t T = 0;
+    std::vector<uint8_t> px;
+  };
+  std::map<std::pair<int, int64_t>, Image> images;   // (stream, seq) -> kept 8-bit image
   bool stop = false;
   int64_t running = 0;
   int64_t st_submitted = 0, st_rejected = 0, st_completed = 0, st_batches = 0, st_max_batch = 0,
@@ -220,6 +227,16 @@ void lane_main(rise_server *s, int li) {
       cudaStreamSynchronize(cs);   // the carry copies of frame-less chunks
     }
     const int64_t t_done = now_ns();
+    // introspection: every capture's 8-bit image, back to back in batch order
+    std::vector<uint8_t> imgs;
+    std::vector<int64_t> img_off;
+    if (s->keep_images && rc == RISE_OK && !caps.empty()) {
+      img_off.assign(caps.size() + 1, 0);
+      for (size_t c = 0; c < caps.size(); ++c)
+        img_off[c + 1] = img_off[c] + ((caps[c].n - s->N) / s->hop + 1) * (int64_t)s->N;
+      imgs.resize((size_t)img_off.back());
+      if (rise_debug_export(ctx, RISE_DBG_BATCH_IMAGES, imgs.data(), imgs.size()) != RISE_OK) imgs.clear();
+    }
 
     lk.lock();
     for (const Item &it : items) {
@@ -240,6 +257,12 @@ void lane_main(rise_server *s, int li) {
         if (rc == RISE_OK && it.cap_index >= 0) {
           const int64_t b0 = offs[it.cap_index + j], b1 = offs[it.cap_index + j + 1];
           d.boxes.assign(boxes.begin() + b0, boxes.begin() + b1);
+          if (!imgs.empty()) {
+            const int64_t ci = it.cap_index + j;
+            rise_server::Image &im = s->images[{d.r.stream, d.r.seq}];
+            im.T = (img_off[ci + 1] - img_off[ci]) / s->N;
+            im.px.assign(imgs.begin() + img_off[ci], imgs.begin() + img_off[ci + 1]);
+          }
         }
         d.r.n_boxes = (int64_t)d.boxes.size();
         s->done.push_back(std::move(d));
@@ -325,6 +348,7 @@ int rise_server_create(rise_server **out, const rise_server_config *cfg) {
   s->max_batch = max_batch;
   s->max_pending = cfg->max_pending > 0 ? cfg->max_pending : 4096;
   s->thr = thr;
+  s->keep_images = cfg->keep_images != 0;
   int rc = RISE_OK;
   s->streams.resize(cfg->max_streams);
   for (auto &st : s->streams) {
@@ -469,6 +493,20 @@ int rise_stream_import(rise_server *s, int stream, const void *buf, size_t bytes
   st.next_frame = h.next_frame;
   st.next_window = h.next_window;
   st.has_event = false;
+  return RISE_OK;
+}
+
+int rise_server_result_image(rise_server *s, int stream, int64_t seq, uint8_t *dst, size_t bytes,
+                             int64_t *T) {
+  if (!s || !T) return RISE_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->images.find({stream, seq});
+  if (it == s->images.end()) return RISE_EINVAL;
+  *T = it->second.T;
+  if (!dst) return RISE_OK;
+  if (bytes < it->second.px.size()) return RISE_EINVAL;
+  std::memcpy(dst, it->second.px.data(), it->second.px.size());
+  s->images.erase(it);
   return RISE_OK;
 }
 
