@@ -71,6 +71,7 @@ def lib():
             "ro_label": (i32, [P, i64, i32, P]),
             "ro_component_runs": (i32, [P, i64, i32, P, i64, P]),
             "ro_boundary": (None, [P, i64, i32, P]),
+            "ro_set_threads": (i32, [i32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -94,6 +95,13 @@ def params(range_mode: int = 0, hi_db: float = 0.0, level_db: float = 0.25,
 def _check(rc: int, what: str):
     if rc not in (0, -3):
         raise RuntimeError(f"oracle {what} failed with code {rc}")
+
+
+def set_threads(n: int) -> int:
+    """Host threads of the oracle's parallel loops (n < 1: every core).
+    Returns the count in effect (1 without OpenMP).  Results do not depend
+    on it."""
+    return int(lib().ro_set_threads(int(n)))
 
 
 def fft(x: np.ndarray) -> np.ndarray:

@@ -24,12 +24,32 @@
  * with the paper's own thresholds is not.
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared (no fast-math), so
- * x86-64 and aarch64 give the same doubles.
+ * x86-64 and aarch64 give the same doubles.  With -fopenmp the independent
+ * loops run on several host threads (frames of the STFT, column groups of the
+ * histogram, columns of Otsu, rows of the mask and of each morphological
+ * operation; the flood fill stays sequential).  Each thread computes whole
+ * frames, columns or rows exactly as one thread would, and the only
+ * reduction is a maximum, so the results do not depend on the thread count.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Host threads the parallel loops use (n < 1: every core); returns the
+ * count in effect, 1 when the library was built without OpenMP. */
+int ro_set_threads(int n) {
+#ifdef _OPENMP
+  omp_set_num_threads(n >= 1 ? n : omp_get_num_procs());
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 #define RO_OK 0
 #define RO_EINVAL -1
@@ -141,15 +161,24 @@ int ro_stft_power(const float *iq, int64_t n, int N, int hop, int64_t t0, int64_
 int ro_max_power(const float *iq, int64_t n, int N, int hop, double *out_max) {
   int64_t T = ro_num_frames(n, N, hop);
   if (T < 1) return RO_EINVAL;
-  double *row = malloc(sizeof(double) * N);
-  if (!row) return RO_ENOMEM;
   double mx = 0.0;
-  for (int64_t t = 0; t < T; t++) {
-    int rc = ro_stft_power(iq, n, N, hop, t, 1, row);
-    if (rc) { free(row); return rc; }
-    for (int f = 0; f < N; f++) if (row[f] > mx) mx = row[f];
+  int err = RO_OK;
+#pragma omp parallel
+  {
+    double *row = malloc(sizeof(double) * N);
+#pragma omp for reduction(max : mx) schedule(static)
+    for (int64_t t = 0; t < T; t++) {
+      int rc = row ? ro_stft_power(iq, n, N, hop, t, 1, row) : RO_ENOMEM;
+      if (rc) {
+#pragma omp atomic write
+        err = rc;
+        continue;
+      }
+      for (int f = 0; f < N; f++) if (row[f] > mx) mx = row[f];
+    }
+    free(row);
   }
-  free(row);
+  if (err) return err;
   *out_max = mx;
   return RO_OK;
 }
@@ -162,6 +191,7 @@ int ro_max_power(const float *iq, int64_t n, int N, int hop, double *out_max) {
  * lo = hi_db - 255 * level.  P = 0 gives q = 0. */
 void ro_quantize(const double *P, int64_t npx, double hi_db, double level_db, uint8_t *q) {
   double lo = hi_db - 255.0 * level_db;
+#pragma omp parallel for schedule(static) if (npx > 65536)
   for (int64_t i = 0; i < npx; i++) {
     if (!(P[i] > 0.0)) { q[i] = 0; continue; }
     double db = 10.0 * log10(P[i]);
@@ -187,8 +217,13 @@ void ro_energy_table(double level_db, uint64_t *E) {
 /* hist[f*256 + v] = number of rows t with q[t][f] == v. */
 void ro_column_hist(const uint8_t *q, int64_t T, int F, uint32_t *hist) {
   memset(hist, 0, sizeof(uint32_t) * 256 * (size_t)F);
-  for (int64_t t = 0; t < T; t++)
-    for (int f = 0; f < F; f++) hist[(size_t)f * 256 + q[t * F + f]]++;
+  /* groups of 64 columns, each counted by one thread over every row */
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int g = 0; g < F; g += 64) {
+    const int ge = g + 64 < F ? g + 64 : F;
+    for (int64_t t = 0; t < T; t++)
+      for (int f = g; f < ge; f++) hist[(size_t)f * 256 + q[t * F + f]]++;
+  }
 }
 
 /* Quadratic Savitzky-Golay smoothing weights for a 2m+1 window, scaled to
@@ -289,6 +324,7 @@ int ro_column_thresholds(const uint32_t *hist, int64_t T, int F, const ro_params
     if (Pq < 0) Pq = 0;
     if (Pq > 256) Pq = 256;
   }
+#pragma omp parallel for schedule(static)
   for (int f = 0; f < F; f++) {
     int keep = psd_on ? (D * S[f] >= N0 + dpsd) : 1;
     int th = ro_otsu(hist + (size_t)f * 256);
@@ -314,6 +350,7 @@ int ro_column_thresholds(const uint32_t *hist, int64_t T, int F, const ro_params
 
 /* Foreground: q[t][f] >= eff[f]  (eff = 256 -> none). Masks hold 0/1 bytes. */
 void ro_threshold(const uint8_t *q, int64_t T, int F, const int32_t *eff, uint8_t *mask) {
+#pragma omp parallel for schedule(static)
   for (int64_t t = 0; t < T; t++)
     for (int f = 0; f < F; f++) mask[t * F + f] = (int32_t)q[t * F + f] >= eff[f];
 }
@@ -331,6 +368,7 @@ int ro_morph(const uint8_t *in, uint8_t *out, int64_t T, int F, int op) {
   int rt = (op == RO_DILATE3 || op == RO_ERODE3) ? 1 : 0;
   int erode = (op == RO_ERODE3 || op == RO_ERODE1x3);
   if (op < 0 || op > 3) return RO_EINVAL;
+#pragma omp parallel for schedule(static)
   for (int64_t t = 0; t < T; t++) {
     for (int f = 0; f < F; f++) {
       int v = erode ? 1 : 0;
@@ -496,15 +534,25 @@ int ro_detect(const float *iq, int64_t n, int N, int hop, const ro_params *p, ro
   if (max_out) *max_out = mx;
   hi_db = p->range_mode == 1 ? p->hi_db : 10.0 * log10(mx);
   uint8_t *q = image_out ? image_out : malloc((size_t)T * N);
-  double *row = malloc(sizeof(double) * N);
-  if (!q || !row) { if (!image_out) free(q); free(row); return RO_ENOMEM; }
-  for (int64_t t = 0; t < T; t++) {
-    ro_stft_power(iq, n, N, hop, t, 1, row);
-    ro_quantize(row, N, hi_db, p->level_db, q + t * (int64_t)N);
+  if (!q) return RO_ENOMEM;
+  int err = RO_OK;
+#pragma omp parallel
+  {
+    double *row = malloc(sizeof(double) * N);
+#pragma omp for schedule(static)
+    for (int64_t t = 0; t < T; t++) {
+      if (!row) {
+#pragma omp atomic write
+        err = RO_ENOMEM;
+        continue;
+      }
+      ro_stft_power(iq, n, N, hop, t, 1, row);
+      ro_quantize(row, N, hi_db, p->level_db, q + t * (int64_t)N);
+    }
+    free(row);
   }
-  rc = ro_detect_image(q, T, N, p, out, cap, n_out, NULL, NULL, NULL, NULL);
+  rc = err ? err : ro_detect_image(q, T, N, p, out, cap, n_out, NULL, NULL, NULL, NULL);
   if (!image_out) free(q);
-  free(row);
   return rc;
 }
 

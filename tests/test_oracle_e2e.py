@@ -71,3 +71,28 @@ def test_hand_image_closed_form(F):
     h = np.zeros(256, np.uint32)
     h[100], h[200] = 54, 10
     assert oracle.otsu(h) == 100
+
+
+def test_thread_count_does_not_change_results():
+    """The oracle's parallel loops (frames, column groups, rows) give what one
+    thread gives: the same image, anchor, histograms, masks and boxes."""
+    cap = synth.make_capture(3 * 512 * 97 + 311, 20e6, 6, 99, fft_size=512, hop=384,
+                             bw_hz=(0.5e6, 4e6), dur_s=(0.2e-3, 2e-3), snr_db=(5, 20),
+                             tone_fraction=0.3)
+    oracle.set_threads(1)
+    try:
+        one = oracle.detect(cap.iq, 512, 384)
+        q = one[1]
+        b1, ex1 = oracle.detect_image(q, extras=True)
+        for n in (0, 3):
+            oracle.set_threads(n)
+            many = oracle.detect(cap.iq, 512, 384)
+            assert many[2] == one[2]
+            np.testing.assert_array_equal(many[1], one[1])
+            np.testing.assert_array_equal(many[0], one[0])
+            bn, exn = oracle.detect_image(q, extras=True)
+            np.testing.assert_array_equal(bn, b1)
+            for k in ("hist", "eff", "mask"):
+                np.testing.assert_array_equal(exn[k], ex1[k])
+    finally:
+        oracle.set_threads(0)          # back to the default: every core
