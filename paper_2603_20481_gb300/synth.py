@@ -197,7 +197,7 @@ def gt_boxes(cap: Capture, fft_size: Optional[int] = None,
 
 
 # ---------------------------------------------------------------------------
-# Named workloads (seeded; the recipes are stated in the design doc)
+# Named workloads (seeded)
 # ---------------------------------------------------------------------------
 
 def single_capture(seed: int = 101, n: int = 1 << 20) -> Capture:

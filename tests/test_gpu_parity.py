@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
-Bars (stated in the design doc):
+Bars:
 * spectrogram: |P_gpu - P_ref| <= 1e-4 P_ref + 1e-6 * mean of the frame's P_ref;
 * 8-bit image: at most ceil(1e-5 * pixels) pixels differ, each by one level,
   and the GPU's levels equal the oracle's quantiser applied to the GPU's own
