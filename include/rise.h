@@ -438,6 +438,16 @@ int rise_debug_export(rise_ctx *ctx, int what, void *dst, size_t bytes);
 #define RISE_OPT_RUN_CAPACITY 7 /* runs the labelling arrays hold at the next call *
                                  * (>= 1024; they still grow when a mask needs    *
                                  * more)                                          */
+/* Bounds of the labelling stage's device waits.  Every wait gives up after
+ * its bound, records the fact in the call's status and lets the kernel
+ * return, so the call ends with RISE_ETIMEOUT and the context stays usable.
+ * 0 restores the default.  Changing one drops the context's captured graphs. */
+#define RISE_OPT_SCAN_WAIT_LIMIT 8 /* polls (32 ns apart) a single-pass scan tile   *
+                                    * waits for a predecessor's sum (2^20)          */
+#define RISE_OPT_UNION_LIMIT 9     /* steps of one union-find walk (2^26)           */
+#define RISE_OPT_TEST_WITHHOLD 10  /* test only: the box-slot scan's tile with this *
+                                    * index publishes no sum, so every later tile's *
+                                    * wait runs out; -1 (default): none             */
 
 /* Sets an option; errors: RISE_EINVAL. */
 int rise_set_option(rise_ctx *ctx, int option, int64_t value);

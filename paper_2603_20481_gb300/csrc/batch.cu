@@ -459,6 +459,9 @@ int enqueue(rise_ctx *c, const Plan &p, const rise_thresholds &thr, int64_t cap,
   la.box_cap = cap;
   la.status = &sm->status;
   la.status_out = nullptr;   // the offsets kernel runs after the labelling: a copy node reads the status
+  la.uf_limit = c->uf_limit;
+  la.spin_limit = c->spin_limit;
+  la.withhold_tile = c->withhold_tile;
   CK(launch_ccl_count(la, c->num_sms, s));
   CK(launch_ccl_label_batch(la, rseg, row0, p.ncap, b.offs_dev, c->num_sms, s));
   record(c, 6);

@@ -40,7 +40,7 @@ constexpr int SCAN_THREADS = 256, SCAN_ITEMS = 8, SCAN_BLOCK = SCAN_THREADS * SC
 // wait is bounded (ERR_SCAN).
 // ---------------------------------------------------------------------------
 constexpr uint64_t LB_AGG = 1ull << 62, LB_INC = 2ull << 62, LB_VAL = (1ull << 62) - 1;
-constexpr int LB_SPIN_LIMIT = 1 << 20;   // with 32 ns sleeps: about a second
+constexpr int LB_SPIN_LIMIT = 1 << 20;   // default; with 32 ns sleeps: about a second
 
 __device__ __forceinline__ uint64_t ld_acquire(const uint64_t *p) {
   uint64_t v;
@@ -53,16 +53,20 @@ __device__ __forceinline__ void st_release(uint64_t *p, uint64_t v) {
 
 // Warp 0 of tile `tile` (sum `agg`): the sum of all earlier tiles, returned
 // to every lane.  The warp reads 32 predecessors at once (lane l: tile
-// hi - l), waits until each has published, and adds the values up to and
-// including the nearest full prefix; without one in the window it moves 32
-// tiles back.  Tiles before 0 read as a full prefix of 0.
-__device__ int64_t lookback(uint64_t *stat, int64_t tile, int64_t agg, DeviceStatus *st) {
+// hi - l), waits until each has published (at most `spin_limit` polls),
+// and adds the values up to and including the nearest full prefix; without
+// one in the window it moves 32 tiles back.  Tiles before 0 read as a full
+// prefix of 0.  The tile numbered `withhold` publishes nothing (a test of
+// the bounded wait: its successors give up and report ERR_SCAN).
+__device__ int64_t lookback(uint64_t *stat, int64_t tile, int64_t agg, DeviceStatus *st, int spin_limit,
+                            int64_t withhold) {
   const int lane = threadIdx.x & 31;
+  const bool publish = tile != withhold;
   if (tile == 0) {
-    if (lane == 0) st_release(&stat[0], LB_INC | (uint64_t)agg);
+    if (lane == 0 && publish) st_release(&stat[0], LB_INC | (uint64_t)agg);
     return 0;
   }
-  if (lane == 0) st_release(&stat[tile], LB_AGG | (uint64_t)agg);
+  if (lane == 0 && publish) st_release(&stat[tile], LB_AGG | (uint64_t)agg);
   int64_t excl = 0;
   for (int64_t hi = tile - 1;; hi -= 32) {
     const int64_t k = hi - lane;
@@ -71,7 +75,7 @@ __device__ int64_t lookback(uint64_t *stat, int64_t tile, int64_t agg, DeviceSta
     if (k >= 0) {
       w = ld_acquire(&stat[k]);
       for (int spins = 0; (w >> 62) == 0; ++spins) {
-        if (spins >= LB_SPIN_LIMIT) {
+        if (spins >= spin_limit) {
           late = true;
           break;
         }
@@ -91,7 +95,7 @@ __device__ int64_t lookback(uint64_t *stat, int64_t tile, int64_t agg, DeviceSta
     excl += v;
     if (inc) break;
   }
-  if (lane == 0) st_release(&stat[tile], LB_INC | (uint64_t)(excl + agg));
+  if (lane == 0 && publish) st_release(&stat[tile], LB_INC | (uint64_t)(excl + agg));
   return excl;
 }
 
@@ -113,7 +117,7 @@ inline ScanState scan_state(void *tmp, int64_t row_tiles) {
 template <typename In>
 __device__ __forceinline__ void tile_scan(const In *in, int64_t n, int64_t tile, uint64_t *stat,
                                           DeviceStatus *st, int64_t (&v)[SCAN_ITEMS],
-                                          int64_t (&ex)[SCAN_ITEMS]) {
+                                          int64_t (&ex)[SCAN_ITEMS], int spin_limit, int64_t withhold) {
   __shared__ int64_t scratch[32];
   __shared__ int64_t s_prefix;
   const int64_t base = tile * SCAN_BLOCK + (int64_t)threadIdx.x * SCAN_ITEMS;
@@ -127,7 +131,7 @@ __device__ __forceinline__ void tile_scan(const In *in, int64_t n, int64_t tile,
   int64_t tot;
   const int64_t mine = block_exclusive_scan<int64_t>(sum, scratch, &tot);
   if (threadIdx.x < 32) {
-    const int64_t e = lookback(stat, tile, tot, st);
+    const int64_t e = lookback(stat, tile, tot, st, spin_limit, withhold);
     if (threadIdx.x == 0) s_prefix = e;
   }
   __syncthreads();
@@ -143,14 +147,14 @@ __device__ __forceinline__ void tile_scan(const In *in, int64_t n, int64_t tile,
 // and n_runs = all runs.
 __global__ void __launch_bounds__(SCAN_THREADS)
 row_scan_kernel(const uint32_t *cnt, int64_t T, int64_t *row_base, DeviceStatus *st, ScanState ss,
-                int32_t *run_parent, int64_t run_cap) {
+                int32_t *run_parent, int64_t run_cap, int spin_limit) {
   __shared__ int64_t s_tile, s_lo, s_hi;
   if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(reinterpret_cast<unsigned long long *>(ss.ticket_rows), 1ull);
   __syncthreads();
   const int64_t tile = s_tile;
   if (tile >= scan_tiles(T)) return;
   int64_t v[SCAN_ITEMS], ex[SCAN_ITEMS];
-  tile_scan<uint32_t>(cnt, T, tile, ss.rows, st, v, ex);
+  tile_scan<uint32_t>(cnt, T, tile, ss.rows, st, v, ex, spin_limit, -1);
   const int64_t base = tile * SCAN_BLOCK + (int64_t)threadIdx.x * SCAN_ITEMS;
 #pragma unroll
   for (int i = 0; i < SCAN_ITEMS; ++i) {
@@ -292,6 +296,7 @@ __device__ __forceinline__ void runs_row_body(const CclArgs &a, const unsigned l
       while (ss) {
         const int b = __ffs(ss) - 1;
         ss &= ss - 1;
+        if (!ck_index(base + id, a.run_cap, st)) break;
         rise_box *rc = &a.rec[base + id++];
         rc->t0 = (int32_t)t;
         rc->t1 = (int32_t)t;
@@ -303,6 +308,7 @@ __device__ __forceinline__ void runs_row_body(const CclArgs &a, const unsigned l
       while (ee) {
         const int b = __ffs(ee) - 1;
         ee &= ee - 1;
+        if (!ck_index(base + id, a.run_cap, st)) break;
         a.rec[base + id++].f1 = 32 * w + b;
       }
     }
@@ -315,6 +321,10 @@ __device__ __forceinline__ void runs_row_body(const CclArgs &a, const unsigned l
         os &= os - 1;
         const int ia = (int)(base + bs + __popc(sx & mask_upto(cc)) - 1);
         const int ib = (int)(base2 + by + __popc(sy & mask_upto(cc)) - 1);
+        if (kChecked && !(ck_index(ia, a.run_cap, st) && ck_index(ib, a.run_cap, st) && ia < ib)) {
+          set_err(st, ERR_INDEX);
+          continue;
+        }
         // a lower run touched by one upper run (the common case) hangs under
         // it with one CAS: ib is still a root and ia < ib, so this is a union.
         // A failed CAS means ib already hangs elsewhere (it touches a second
@@ -323,7 +333,7 @@ __device__ __forceinline__ void runs_row_body(const CclArgs &a, const unsigned l
         if (atomicCAS(&a.run_parent[ib], ib, ia) != ib) {
           const unsigned long long k = atomicAdd(reinterpret_cast<unsigned long long *>(&st->n_merge), 1ull);
           if ((int64_t)k < a.run_cap) a.merge[k] = make_int2(ia, ib);
-          else uf_union(a.run_parent, ia, ib, st);   // list full: unite now (slower)
+          else uf_union(a.run_parent, ia, ib, st, a.uf_limit);   // list full: unite now (slower)
         }
       }
     }
@@ -355,7 +365,9 @@ __device__ __forceinline__ void runs_row_body(const CclArgs &a, const unsigned l
         sq += q;
         se += Es[q];
       }
-      rise_box *rc = &a.rec[base + BS[c] + __popc(SX[c] & mask_upto(b0)) - 1];
+      const int64_t ri = base + BS[c] + __popc(SX[c] & mask_upto(b0)) - 1;
+      if (!ck_index(ri, a.run_cap, st)) break;
+      rise_box *rc = &a.rec[ri];
       if ((SX[c] >> b0) & 1u) {
         rc->area = len;
         rc->sum_q = sq;
@@ -419,6 +431,7 @@ runs_row_batch_kernel(CclArgs a, const RowSeg *segs, const int64_t *row0, int nc
     else hi = mid - 1;
   }
   const RowSeg rs = segs[lo];
+  if (!ck_index(tg - __ldg(&row0[lo]), rs.T, a.status)) return;
   runs_row_body<MAXC>(a, Es, lqs + (wib * 32 + lane) * row_lane_bytes(MAXC), tg, tg - __ldg(&row0[lo]), rs.T, rs.F,
                       rs.mask, rs.img);
 }
@@ -456,6 +469,7 @@ __global__ void ccl_offsets_kernel(CclArgs a, const int64_t *row0, int ncap, int
     offs[c] = st->n_boxes;
     return;
   }
+  if (!ck_index(row0[c], a.T + 1, a.status)) return;
   const int64_t r = a.row_base[row0[c]];   // the capture's first run
   offs[c] = r < n ? a.run_out[r] : st->n_boxes;
 }
@@ -479,7 +493,7 @@ __global__ void ccl_flatten_merge_kernel(CclArgs a) {
   if (FLATTEN) {
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
          g += (int64_t)gridDim.x * blockDim.x) {
-      const int r = uf_find(a.run_parent, (int)g, st);
+      const int r = uf_find(a.run_parent, (int)g, st, a.uf_limit);
       if (r != (int)g) *(volatile int *)&a.run_parent[g] = r;   // an ancestor: still valid
     }
   }
@@ -488,7 +502,7 @@ __global__ void ccl_flatten_merge_kernel(CclArgs a) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int2 e = a.merge[k];
-    uf_union(a.run_parent, e.x, e.y, st);
+    uf_union(a.run_parent, e.x, e.y, st, a.uf_limit);
   }
 }
 
@@ -506,7 +520,7 @@ __global__ void ccl_reduce_kernel(CclArgs a) {
   for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x; g0 < n; g0 += (int64_t)gridDim.x * blockDim.x) {
     const int64_t g = g0 + threadIdx.x;
     const bool live = g < n;
-    int r = live ? uf_find(a.run_parent, (int)g, st) : -1;
+    int r = live ? uf_find(a.run_parent, (int)g, st, a.uf_limit) : -1;
     const bool contrib = live && r != (int)g;
     if (live) a.run_sroot[g] = contrib ? 0 : 1;
     rise_box src;
@@ -561,7 +575,7 @@ __device__ __forceinline__ void root_scan_body(const CclArgs &a, const ScanState
     const int64_t tile = s_tile;
     if (tile >= tiles) return;
     int64_t v[SCAN_ITEMS], ex[SCAN_ITEMS];
-    tile_scan<uint8_t>(a.run_sroot, n, tile, ss.roots, st, v, ex);
+    tile_scan<uint8_t>(a.run_sroot, n, tile, ss.roots, st, v, ex, a.spin_limit, a.withhold_tile);
     const int64_t base = tile * SCAN_BLOCK + (int64_t)threadIdx.x * SCAN_ITEMS;
 #pragma unroll
     for (int i = 0; i < SCAN_ITEMS; ++i) {
@@ -612,7 +626,7 @@ __global__ void runs_export_kernel(CclArgs a, int4 *out, int64_t cap) {
   const int Wd = a.F / 32;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < min(n, cap);
        g += (int64_t)gridDim.x * blockDim.x) {
-    const int r = uf_find(a.run_parent, (int)g, st);
+    const int r = uf_find(a.run_parent, (int)g, st, a.uf_limit);
     const rise_box &b = a.rec[g];
     int t, f0, f1;
     if (r != (int)g) {
@@ -620,6 +634,7 @@ __global__ void runs_export_kernel(CclArgs a, int4 *out, int64_t cap) {
       f0 = b.f0;
       f1 = b.f1;
     } else {
+      if (!ck_index(b.anchor, a.T * (int64_t)a.F, st)) continue;
       t = (int)(b.anchor / a.F);
       f0 = (int)(b.anchor % a.F);
       const uint32_t *row = a.mask + (int64_t)t * Wd;
@@ -680,7 +695,7 @@ cudaError_t launch_ccl_count(const CclArgs &a, int num_sms, cudaStream_t s) {
       cudaMemsetAsync(a.scan_tmp, 0, (size_t)(3 + tiles + scan_tiles(a.run_cap)) * sizeof(uint64_t), s);
   if (e != cudaSuccess) return e;
   row_scan_kernel<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(a.row_cnt, a.T, a.row_base, a.status, ss,
-                                                          a.run_parent, a.run_cap);
+                                                          a.run_parent, a.run_cap, a.spin_limit);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -42,6 +42,28 @@ __device__ __forceinline__ void set_err(DeviceStatus *st, uint32_t bit) {
   atomicOr(&st->err, bit);
 }
 
+// ---------------------------------------------------------------------------
+// Checked build (compiled with -DRISE_CHECKED): indices that come from data
+// (run offsets, union-find parents, table entries, frame ranges) are checked
+// before use; a failed check records ERR_INDEX (the call returns
+// RISE_EINTERNAL) and the access is skipped, so no kernel traps or touches
+// memory out of range.  In the normal build every check is a constant true.
+// ---------------------------------------------------------------------------
+#ifdef RISE_CHECKED
+constexpr bool kChecked = true;
+__device__ __forceinline__ bool ck_index(int64_t i, int64_t n, uint32_t *err) {
+  if (i >= 0 && i < n) return true;
+  atomicOr(err, ERR_INDEX);
+  return false;
+}
+#else
+constexpr bool kChecked = false;
+__device__ __forceinline__ bool ck_index(int64_t, int64_t, uint32_t *) { return true; }
+#endif
+__device__ __forceinline__ bool ck_index(int64_t i, int64_t n, DeviceStatus *st) {
+  return ck_index(i, n, &st->err);
+}
+
 // bits 0..b inclusive
 __device__ __forceinline__ uint32_t mask_upto(int b) {
   return b >= 31 ? 0xffffffffu : ((2u << b) - 1u);
@@ -60,14 +82,16 @@ __device__ __forceinline__ uint32_t run_ends(uint32_t w, uint32_t next_word) {
 // ---------------------------------------------------------------------------
 // Lock-free union-find with union by smaller index (parent[x] <= x always),
 // usable on shared or global memory through generic pointers.  Each loop is
-// bounded; hitting the bound records ERR_UNION_LIMIT.
+// bounded (`limit` steps, UF_LIMIT by default); hitting the bound records
+// ERR_UNION_LIMIT and returns an ancestor, so every index stays in range.
 // ---------------------------------------------------------------------------
 constexpr int UF_LIMIT = 1 << 26;
 
-__device__ __forceinline__ int uf_find(int *parent, int x, DeviceStatus *st) {
-  for (int it = 0; it < UF_LIMIT; ++it) {
+__device__ __forceinline__ int uf_find(int *parent, int x, DeviceStatus *st, int limit = UF_LIMIT) {
+  for (int it = 0; it < limit; ++it) {
     int p = *(volatile int *)&parent[x];
     if (p == x) return x;
+    if (!ck_index(p, (int64_t)x, st)) return x;   // checked build: a parent is a smaller run
     int gp = *(volatile int *)&parent[p];
     // path halving: x is not a root and never becomes one, so any ancestor
     // (all smaller than x) is a valid parent; a plain store is enough
@@ -78,10 +102,10 @@ __device__ __forceinline__ int uf_find(int *parent, int x, DeviceStatus *st) {
   return x;
 }
 
-__device__ __forceinline__ void uf_union(int *parent, int a, int b, DeviceStatus *st) {
-  for (int it = 0; it < UF_LIMIT; ++it) {
-    a = uf_find(parent, a, st);
-    b = uf_find(parent, b, st);
+__device__ __forceinline__ void uf_union(int *parent, int a, int b, DeviceStatus *st, int limit = UF_LIMIT) {
+  for (int it = 0; it < limit; ++it) {
+    a = uf_find(parent, a, st, limit);
+    b = uf_find(parent, b, st, limit);
     if (a == b) return;
     if (a > b) { int t = a; a = b; b = t; }
     // link the larger root under the smaller one if it is still a root
@@ -307,6 +331,9 @@ struct CclArgs {
   int64_t box_cap;
   DeviceStatus *status;
   DeviceStatus *status_out;   // mapped host copy written by the last kernel, or NULL
+  int uf_limit;               // steps before a union-find walk gives up (ERR_UNION_LIMIT)
+  int spin_limit;             // polls before a look-back wait gives up (ERR_SCAN)
+  int64_t withhold_tile;      // test only: this root-scan tile publishes no sum (-1: none)
 };
 size_t ccl_scan_tmp_bytes(int64_t max_items);
 // Scan of the per-row run counts: fills row_base and status->n_runs.

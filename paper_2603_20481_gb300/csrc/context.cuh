@@ -102,6 +102,10 @@ struct rise_ctx {
   // options
   int keep_power = 0, keep_masks = 0, timing = 0, range_path = 0;
   int graphs = 1, autotune = 1;
+  // bounds of the device waits (defaults of the kernels) and the test-only
+  // withheld root-scan tile (-1: none)
+  int spin_limit = 1 << 20, uf_limit = 1 << 26;
+  int64_t withhold_tile = -1;
   bool capturing = false;         // enqueueing into a graph capture
   // scratch
   rise::host::Buf power, img, hist, cols, effm1, mask, dbg[3], row_cnt, row_base, run_parent,

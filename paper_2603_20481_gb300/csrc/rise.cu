@@ -198,6 +198,9 @@ CclArgs ccl_args(rise_ctx *c, const uint8_t *img, int64_t T, int F, int64_t cap)
   la.run_out = reinterpret_cast<int64_t *>(c->run_out.p);
   la.scan_tmp = c->scan_tmp.p;
   la.scan_tmp_bytes = c->scan_tmp.bytes;
+  la.uf_limit = c->uf_limit;
+  la.spin_limit = c->spin_limit;
+  la.withhold_tile = c->withhold_tile;
   return la;
 }
 
@@ -858,6 +861,25 @@ int rise_set_option(rise_ctx *c, int option, int64_t value) {
     case RISE_OPT_RANGE_PATH:
       if (value < 0 || value > 2) return RISE_EINVAL;
       c->range_path = (int)value;
+      return RISE_OK;
+    // the limits are kernel arguments inside captured graphs: a change drops them
+    case RISE_OPT_SCAN_WAIT_LIMIT:
+      if (value < 0 || value > INT32_MAX) return RISE_EINVAL;
+      CK(cudaSetDevice(c->device));
+      c->spin_limit = value ? (int)value : (1 << 20);
+      new_generation(c);
+      return RISE_OK;
+    case RISE_OPT_UNION_LIMIT:
+      if (value < 0 || value > INT32_MAX) return RISE_EINVAL;
+      CK(cudaSetDevice(c->device));
+      c->uf_limit = value ? (int)value : (1 << 26);
+      new_generation(c);
+      return RISE_OK;
+    case RISE_OPT_TEST_WITHHOLD:
+      if (value < -1) return RISE_EINVAL;
+      CK(cudaSetDevice(c->device));
+      c->withhold_tile = value;
+      new_generation(c);
       return RISE_OK;
   }
   return RISE_EINVAL;

@@ -18,7 +18,9 @@ from typing import Optional
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_lib", "librise.so")
+# RISE_CHECKED=1 selects the checked build (device index checks; see build.py)
+LIB_PATH = (os.path.join(HERE, "_lib_checked", "librise_checked.so") if os.environ.get("RISE_CHECKED") == "1"
+            else os.path.join(HERE, "_lib", "librise.so"))
 
 RISE_OK, RISE_EINVAL, RISE_ENOMEM, RISE_ETRUNC = 0, -1, -2, -3
 RISE_ECUDA, RISE_ETIMEOUT, RISE_EINTERNAL, RISE_ESCRATCH, RISE_EAGAIN = -4, -5, -6, -7, -8
@@ -32,6 +34,7 @@ STAGES = ("spectrum_pass1", "spectrum_pass2", "histogram", "column_stats", "morp
           "labelling", "readback", "total")
 OPT_KEEP_POWER, OPT_KEEP_MASKS, OPT_TIMING, OPT_RANGE_PATH = 1, 2, 3, 4
 OPT_GRAPH, OPT_AUTOTUNE, OPT_RUN_CAPACITY = 5, 6, 7
+OPT_SCAN_WAIT_LIMIT, OPT_UNION_LIMIT, OPT_TEST_WITHHOLD = 8, 9, 10
 IQ_HOST, IQ_SC16 = 1, 2
 OPT_BATCH_GRAPH = OPT_GRAPH
 BATCH_MAX_ROWS = 524280
