@@ -2,6 +2,11 @@
 
 Each translation unit is compiled in parallel with nvcc, then linked into
 paper_2603_20481_gb300/_lib/librise.so with a static CUDA runtime.
+
+`--checked` builds the checked variant instead (-DRISE_CHECKED, into
+_lib_checked/librise_checked.so): every data-dependent index is checked on
+the device, a failed check is reported as RISE_EINTERNAL, and nothing is
+accessed out of range.  The binding loads it when RISE_CHECKED=1 is set.
 """
 from __future__ import annotations
 
@@ -14,6 +19,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "librise.so")
+CHECKED_DIR = os.path.join(HERE, "_lib_checked")
+CHECKED_LIB = os.path.join(CHECKED_DIR, "librise_checked.so")
 SOURCES = ["stft.cu", "stft_sc16.cu", "image.cu", "ccl.cu", "rise.cu", "batch.cu", "server.cu",
            "match.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -37,13 +44,16 @@ def _stale(obj: str, src: str) -> bool:
     return any(os.path.getmtime(d) > os.path.getmtime(obj) for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), checked: bool = False) -> str:
+    out_dir, lib = (CHECKED_DIR, CHECKED_LIB) if checked else (OUT_DIR, LIB)
+    if checked:
+        extra = (*extra, "-DRISE_CHECKED")
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
+        o = os.path.join(out_dir, src.replace(".cu", ".o"))
         if force or _stale(o, s):
             jobs.append([nvcc, *ARCH, *FLAGS, *extra, "-c", s, "-o", o])
 
@@ -57,14 +67,15 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         list(ex.map(run, jobs))
-    objs = [os.path.join(OUT_DIR, s.replace(".cu", ".o")) for s in SOURCES]
-    if jobs or not os.path.exists(LIB):
-        tmp = LIB + f".tmp{os.getpid()}"
+    objs = [os.path.join(out_dir, s.replace(".cu", ".o")) for s in SOURCES]
+    if jobs or not os.path.exists(lib):
+        tmp = lib + f".tmp{os.getpid()}"
         run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     extra = ["-Xptxas", "-v"] if "-v" in sys.argv else []
-    print(build(force="--force" in sys.argv, verbose=bool(extra), extra=extra))
+    print(build(force="--force" in sys.argv, verbose=bool(extra), extra=extra,
+                checked="--checked" in sys.argv))

@@ -326,6 +326,7 @@ cluster_hist_batch_kernel(const HistArgs *segs, const HistItem *items) {
   const HistItem it = items[blockIdx.x];
   if (threadIdx.x == 0) sa = segs[it.seg];
   __syncthreads();
+  if (kChecked && (it.cg < 0 || it.cg >= sa.F / 64)) return;   // checked build: a column group of the capture
   cluster_hist_body<FROM_POWER>(sa, it.cg, blockIdx.y);
 }
 
@@ -746,6 +747,7 @@ morph_batch_kernel(const MorphArgs *segs, const MorphItem *mi, const int *warp_b
   if (lane == 0) sa[wib] = segs[lo];
   __syncwarp();
   const MorphItem it = mi[lo];
+  if (kChecked && gwarp - __ldg(&warp_base[lo]) >= __ldg(&warp_base[lo + 1]) - __ldg(&warp_base[lo])) return;
   morph_body<ORDER>(sa[wib], it.nx, it.rows, gwarp - __ldg(&warp_base[lo]));
 }
 // Bands per cluster.  Grid: (column groups) x (bands); the clusters that fit

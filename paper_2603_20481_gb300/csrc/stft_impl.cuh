@@ -276,6 +276,10 @@ __device__ __forceinline__ bool stft_frames(const StftArgs &a, int64_t f_begin, 
   auto issue = [&](int64_t st) {
     const int64_t t0 = f_begin + st * FPB;
     const uint32_t bytes = step_bytes(st);
+    if (kChecked && (t0 < 0 || t0 * (int64_t)a.hop * (int64_t)sizeof(IN) + bytes > a.n * (int64_t)sizeof(IN))) {
+      atomicOr(a.err, ERR_INDEX);   // checked build: a frame beyond the capture
+      return;
+    }
     mbar_expect_tx(bar, bytes);
     bulk_g2s(stage, iq + t0 * (int64_t)a.hop, bytes, bar);
   };
@@ -320,10 +324,11 @@ __device__ __forceinline__ bool stft_frames(const StftArgs &a, int64_t f_begin, 
         v[i] = make_float2(s.x * win[i], s.y * win[i]);
       }
     } else {
-      const IN *x = iq + (valid ? t * (int64_t)a.hop : 0) + tau;
+      const bool ok = !kChecked || !valid || ck_index(t * (int64_t)a.hop + N - 1, a.n, a.err);
+      const IN *x = iq + (valid && ok ? t * (int64_t)a.hop : 0) + tau;
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
-        const float2 s = valid ? to_f2(__ldg(x + i * (N / 16))) : make_float2(0.f, 0.f);
+        const float2 s = valid && ok ? to_f2(__ldg(x + i * (N / 16))) : make_float2(0.f, 0.f);
         v[i] = make_float2(s.x * win[i], s.y * win[i]);
       }
     }
@@ -361,7 +366,7 @@ __device__ __forceinline__ bool stft_frames(const StftArgs &a, int64_t f_begin, 
         }
       }
     }
-    if (valid) {
+    if (valid && ck_index(t, a.T, a.err)) {
       constexpr int R = PL::radix(NPASS - 1);
       uint8_t *qrow = DO_Q ? a.img + t * (int64_t)N : nullptr;
       float *prow = DO_P ? a.power + t * (int64_t)N : nullptr;
@@ -427,6 +432,11 @@ stft_batch_kernel(const StftArgs *segs, const StftItem *items, int n_items, int 
     const int it = s_item;
     if (it >= n_items) return;
     const StftItem item = items[it];
+    if (kChecked && (item.f0 < 0 || item.f1 > sa.T || item.f0 > item.f1)) {
+      if (threadIdx.x == 0) atomicOr(sa.err, ERR_INDEX);   // checked build: frames of the capture
+      __syncthreads();
+      continue;
+    }
     const bool ok = stft_frames<N, MODE, TMA, float2>(sa, item.f0, item.f1, smem, red, &bar);
     if (!ok) return;   // uniform over the block
     __syncthreads();   // every wait on the barrier and every read of sa is done

@@ -18,7 +18,7 @@ import pytest  # noqa: E402
 def built_lib():
     """Path of the CUDA library, building it in-tree when missing."""
     from paper_2603_20481_gb300 import build
-    return build.build()
+    return build.build(checked=os.environ.get("RISE_CHECKED") == "1")
 
 
 @pytest.fixture(scope="session")
