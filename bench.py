@@ -1,20 +1,29 @@
 #!/usr/bin/env python
 """Throughput of the RISE IQ -> boxes path on one GB300 (or N replicas).
 
-Workload (default): wideband single stream -- 2^26 complex64 samples
-(notional 100 MS/s), Hann window, FFT 4096, hop 2048 (T = 32767 frames),
-128 planted emitters, seed 102; synthetic, generated by
-paper_2603_20481_gb300.synth.  One step = one rise_detect call: the whole
+Workload (default, "headline"): the stress capture -- 2^28 complex64 samples
+(notional 100 MS/s), Hann window, FFT 8192, hop 2048 (T = 131069 frames,
+75% overlap), 1024 planted emitters at SNR -5..10 dB, half of them
+fragmented, 16 narrowband emitters over the whole capture, seed 105;
+synthetic, generated by paper_2603_20481_gb300.synth.  It is the largest
+configuration that fits one GPU.  One step = one rise_detect call: the whole
 path (spectrum, 8-bit image, histogram, column statistics, morphology,
-labelling, boxes back in host memory).  The 512 MiB capture is larger than
-L2, so no flush is needed between steps.
+labelling, boxes back in host memory).  The 2 GiB capture is larger than
+L2, so no flush is needed between steps.  The same run measures, as
+sub-objects of the line, the wideband capture (2^26 samples, FFT 4096, hop
+2048), the batched workload (256 uneven captures in one rise_detect_batch
+call against one rise_detect call per capture) and the served workload
+(32 radios, p50/p99 chunk latency at 0.5 and 0.75 x saturation, continuous
+batching against one chunk per launch chain).
 
 Printed: one JSON line (rank 0).  `value` is samples of all ranks / the
 slowest rank's CUDA-event time over the K timed steps, inputs resident in
 HBM; `e2e` is the same metric through rise_detect_host from pinned host
-memory (copy in the timed region); `roofline` is the dominant kernel's
-algorithmic bytes / its event-timed duration against the measured HBM copy
-bandwidth; `cpu_baseline` is the FP64 oracle on a bounded sample.
+memory (copy in the timed region); `roofline` is the dominant kernel (the
+STFT) against the roofline that bounds it (the FP32 pipe or HBM, from its
+algorithmic flops and bytes) with its CUDA-event duration, and the whole
+step's algorithmic bytes against HBM; `cpu_baseline` is the FP64 oracle on
+a bounded sample, on every host core and on one.
 
 Multi-GPU: replicas only (independent captures per rank, weak scaling), no
 collective on the data path.  `--impl reference` times the oracle instead.
@@ -49,10 +58,13 @@ STRESS_WORKLOAD = ("stress: 2^28 complex64 IQ samples, FFT 8192, hop 2048 (75% o
 SINGLE = {"wideband": ("wideband_capture", 102, 4096, 2048, 1 << 26, WORKLOAD),
           "stress": ("stress_capture", 105, 8192, 2048, 1 << 28, STRESS_WORKLOAD)}
 HBM_FALLBACK_GBS = 6800.0
-# DRAM bytes (read + write) per launch of the dominant kernel at this workload,
-# from the ncu capture summarised in profiles/stft_power_wideband_2e26_fft4096.md
-# (set to None whenever that kernel changes).
-TRAFFIC_BYTES = {2: 541917184 + 493364224}
+# DRAM bytes (read + write) per launch of the dominant kernel (the STFT), from
+# one ncu capture per workload, with the SHA-256 of the kernel's sources when
+# the counters were taken: a changed kernel reports no traffic until it is
+# captured again.
+STFT_SOURCES = ("paper_2603_20481_gb300/csrc/stft_impl.cuh", "paper_2603_20481_gb300/csrc/stft.cu",
+                "paper_2603_20481_gb300/csrc/common.cuh")
+TRAFFIC = {}
 
 
 def _peaks():
@@ -165,27 +177,114 @@ def _barrier(world: int):
         dist.barrier()
 
 
-def cpu_oracle_rate(iq, n_sample: int, N: int, hop: int):
-    """FP64 oracle (single-threaded C) on the first n_sample samples."""
+def cpu_oracle_rate(iq, n_sample: int, N: int, hop: int, threads: int):
+    """FP64 oracle on the first n_sample samples with `threads` host threads
+    (0: every core).  Returns (MS/s, seconds, boxes, threads used)."""
     import oracle
-    x = iq[:n_sample]
-    t0 = time.perf_counter()
-    boxes, _, _ = oracle.detect(x, N, hop)
-    dt = time.perf_counter() - t0
-    return n_sample / dt / 1e6, dt, len(boxes)
+    used = oracle.set_threads(threads)
+    try:
+        x = iq[:n_sample]
+        t0 = time.perf_counter()
+        boxes, _, _ = oracle.detect(x, N, hop)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(0)
+    return n_sample / dt / 1e6, dt, len(boxes), used
 
 
-def run_ours(args):
+# bounded samples of each workload for the oracle: (all cores, one core), about
+# 5-15 s of host time each on a 16-core host
+CPU_SAMPLES = {"stress": (1 << 25, 1 << 23), "wideband": (1 << 25, 1 << 23)}
+
+
+def cpu_baseline(iq, N: int, hop: int, name: str):
+    """The FP64 oracle as it stands, on the host cores: all of them (the
+    baseline) and one (beside it), each on a prefix of the same capture."""
+    m_all, m_one = CPU_SAMPLES[name]
+    m_all, m_one = min(m_all, iq.shape[0]), min(m_one, iq.shape[0])
+    r_all, dt_all, _, used = cpu_oracle_rate(iq, m_all, N, hop, 0)
+    r_one, dt_one, _, _ = cpu_oracle_rate(iq, m_one, N, hop, 1)
+    return {"value": round(r_all, 3), "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"first {m_all} samples of the same capture ({(m_all - N) // hop + 1} frames), "
+                      f"one pass on {used} threads, {dt_all:.1f} s",
+            "nproc": os.cpu_count(),
+            "single_core": {"value": round(r_one, 3), "unit": UNIT, "cores": 1,
+                            "sample": f"first {m_one} samples ({(m_one - N) // hop + 1} frames), "
+                                      f"one pass, {dt_one:.1f} s"}}
+
+
+def _sha256(paths):
+    import hashlib
+    h = hashlib.sha256()
+    for rel in paths:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def _traffic(workload: str, n: int):
+    """DRAM bytes per launch of the dominant kernel from the ncu capture kept
+    for this workload, or None: a capture is only valid while the kernel's
+    sources hash as they did when its counters were taken, and only for the
+    full-size capture it was scaled to."""
+    t = TRAFFIC.get(workload)
+    if t is None or n != t["n_samples"] or _sha256(STFT_SOURCES) != t["sha256"]:
+        return None
+    return t["bytes"]
+
+
+def _fp32_peak(sms: int, mhz: float) -> float:
+    """FP32 peak in TFLOP/s: SMs x 128 FP32 lanes x 2 flop (FMA) x SM clock."""
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def _spectrum_roofline(name, stage_ms, n, T, N_FFT, sms, mhz, peak, peak_kind, step_s, path, traffic):
+    """Roofline of the STFT stage (the dominant kernel of every single-capture
+    workload) and of the whole step.  Algorithmic bytes per unit are those of
+    the survey's measurement plan: per sample, the IQ read (twice with the
+    range anchored on the capture maximum, once per FFT pass), and per pixel
+    the 8-bit image write and read; the kernel's own share is its IQ read.
+    Its flops follow the 5 N log2 N per frame convention.  The bound is the
+    roofline (HBM or FP32 pipe) that gives the longer time."""
+    px = T * N_FFT
+    flops = T * 5 * N_FFT * int(math.log2(N_FFT))
+    kernel_bytes = 8 * n
+    fp32_peak = _fp32_peak(sms, mhz)
+    t = stage_ms / 1e3
+    t_hbm = kernel_bytes / (peak * 1e9)
+    t_fp32 = flops / (fp32_peak * 1e12)
+    hbm = {"achieved": round(kernel_bytes / t / 1e9, 1), "peak": peak, "unit": "GB/s",
+           "frac": round(kernel_bytes / t / 1e9 / peak, 4), "alg_bytes_per_launch": kernel_bytes,
+           "peak_source": peak_kind}
+    fp32 = {"achieved": round(flops / t / 1e12, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
+            "frac": round(flops / t / 1e12 / fp32_peak, 4), "flops_per_launch": flops,
+            "convention": "5 N log2 N per frame",
+            "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz"}
+    alg_path = 16 * n + 2 * px
+    path_gbs = alg_path / step_s / 1e9
+    main = fp32 if t_fp32 >= t_hbm else hbm
+    roof = {"bound": "alu" if t_fp32 >= t_hbm else "hbm", "kernel": name, **main,
+            "traffic": traffic, "ms_per_launch": round(stage_ms, 4),
+            "hbm": hbm, "fp32": fp32,
+            "path": {"alg_bytes_per_step": alg_path, "achieved": round(path_gbs, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(path_gbs / peak, 4),
+                     "bytes": "16 B/sample (IQ read twice) + 2 B/px (8-bit image written and read)"}}
+    return roof
+
+
+def measure_single(args, name: str):
+    """One single-capture workload (stress or wideband): the device-resident
+    rate with its stage times and roofline, and the end-to-end rate from
+    pinned host memory.  Returns the result dict (rank 0) or None."""
     import numpy as np
     import torch
 
     from paper_2603_20481_gb300 import rise, synth
 
     world, rank, local = _dist()
-    torch.cuda.set_device(local)
-    _init_dist(local, world)
-    gen, seed, N_FFT, HOP, n_default, workload = SINGLE[args.workload]
-    cap = getattr(synth, gen)(seed=seed + rank, n=args.samples or n_default)
+    gen, seed, N_FFT, HOP, n_default, workload = SINGLE[name]
+    n_req = args.samples if (args.samples and args.workload == name) else n_default
+    cap = getattr(synth, gen)(seed=seed + rank, n=n_req)
     n = cap.iq.shape[0]
     x = torch.from_numpy(cap.iq).cuda()
     host = torch.from_numpy(cap.iq).pin_memory()
@@ -254,10 +353,10 @@ def run_ours(args):
                "h2d_bytes_per_step": n * 8,
                "d2h_bytes_per_step": len(bh) * 48 + 40}
         # the same capture as 16-bit I/Q (a radio's sc16 wire format): half the copy
-        peak = float(max(np.abs(cap.iq.real).max(), np.abs(cap.iq.imag).max()))
+        peak_amp = float(max(np.abs(cap.iq.real).max(), np.abs(cap.iq.imag).max()))
         q16 = np.empty((n, 2), np.int16)
-        q16[:, 0] = np.round(cap.iq.real * (0.7 * 32767.0 / peak))
-        q16[:, 1] = np.round(cap.iq.imag * (0.7 * 32767.0 / peak))
+        q16[:, 0] = np.round(cap.iq.real * (0.7 * 32767.0 / peak_amp))
+        q16[:, 1] = np.round(cap.iq.imag * (0.7 * 32767.0 / peak_amp))
         h16 = torch.from_numpy(q16).pin_memory()
         for _ in range(max(1, args.warmup)):
             det.submit(h16, N_FFT, HOP)
@@ -274,30 +373,21 @@ def run_ours(args):
         e2e["sc16"] = {"value": round(world * args.steps * n / t16 / 1e6, 1), "unit": UNIT,
                        "h2d_bytes_per_step": n * 4, "d2h_bytes_per_step": len(b16) * 48 + 40,
                        "note": "same samples quantised to 16-bit I/Q, copied from pinned memory"}
+        del h16
 
-    # roofline of the dominant kernel (per-stage CUDA events on the launch stream)
     T = (n - N_FFT) // HOP + 1
-    px = T * N_FFT
-    path = args.range_path or 2   # the library's auto choice without a memory budget
-    if path == 1:   # FFT twice: anchor max, then quantise; histogram from the image
-        stage_bytes = {
-            "spectrum_pass1": n * 8,                 # IQ read (max pass)
-            "spectrum_pass2": n * 8 + px,            # IQ read + 8-bit image write
-            "histogram": px,                          # image read
-            "morphology": px + px // 8,               # image read + final mask write
-        }
-    else:           # FFT once keeping float power, then quantise + histogram
-        stage_bytes = {
-            "spectrum_pass1": n * 8 + 4 * px,        # IQ read + float power write
-            "spectrum_pass2": 4 * px + px,           # float power read + image write
-            "morphology": px + px // 8,
-        }
     names = rise.STAGES
-    dom = max(stage_bytes, key=lambda k: stage[names.index(k)])
-    dom_ms = stage[names.index(dom)]
+    path = args.range_path or 2   # the library's auto choice without a memory budget
     peak, peak_kind = _peaks()
-    achieved = stage_bytes[dom] / (dom_ms / 1e3) / 1e9
-    alg_path = 16 * n + 2 * px                      # IQ twice + image write + image read
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = float((clocks or {}).get("sm_max_mhz") or 2070.0)
+    dom = max(names[:-1], key=lambda k: stage[names.index(k)])
+    kname = {2: f"stft_kernel<{N_FFT}, power>", 1: f"stft_kernel<{N_FFT}, max>"}[path]
+    roof = _spectrum_roofline(kname, float(stage[names.index("spectrum_pass1")]), n, T, N_FFT,
+                              sms, mhz, peak, peak_kind, t_max / args.steps, path,
+                              _traffic(name, n))
+    if dom != "spectrum_pass1":
+        roof["note"] = f"the longest stage this run was {dom}"
     result = {
         "metric": METRIC, "value": round(rate / 1e6, 1), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -305,47 +395,86 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload, "n_samples": n, "fft_size": N_FFT, "hop": HOP,
                    "frames": T, "boxes": n_boxes, "range_path": path,
-                   "l2": "inputs larger than L2 (512 MiB capture per step)",
+                   "l2": f"inputs larger than L2 ({8 * n >> 20} MiB capture per step)",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
-                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": (TRAFFIC_BYTES.get(path) if dom == "spectrum_pass1" and n == N_SAMPLES
-                                 and args.workload == "wideband"
-                                 else None),
-                     "peak_source": peak_kind,
-                     "alg_bytes_per_launch": stage_bytes[dom], "ms_per_launch": round(dom_ms, 4),
-                     "path_frac": round(alg_path / (t_max / args.steps) / 1e9 / peak, 4)},
+        "roofline": roof,
         "stage_ms": {k: round(float(v), 4) for k, v in zip(names, stage)},
         "gpu_launches": int(launches),
         "clocks": clocks,
         "e2e": e2e,
     }
-    if dom == "spectrum_pass1":
-        # the same kernel against the FP32 pipe: FFT flops by the 5 N log2 N
-        # convention over the peak of 128 FP32 lanes x 2 flops per SM clock
-        sms = torch.cuda.get_device_properties(local).multi_processor_count
-        mhz = float((clocks or {}).get("sm_max_mhz") or 2070.0)
-        fp32_peak = sms * 128 * 2 * mhz * 1e6 / 1e12
-        flops = T * 5 * N_FFT * int(math.log2(N_FFT))
-        fp32_ach = flops / (dom_ms / 1e3) / 1e12
-        result["roofline"]["fp32"] = {
-            "achieved": round(fp32_ach, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
-            "frac": round(fp32_ach / fp32_peak, 4), "flops_per_launch": flops,
-            "convention": "5 N log2 N per frame",
-            "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz"}
     if rank == 0 and not args.no_cpu_baseline:
-        m = min(args.cpu_sample, n)
-        rate, dt, nb = cpu_oracle_rate(cap.iq, m, N_FFT, HOP)
-        result["cpu_baseline"] = {
-            "value": round(rate, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {m} samples of the same capture "
-                      f"({(m - N_FFT) // HOP + 1} frames), one pass, {dt:.1f} s"}
-    if rank == 0:
-        print(json.dumps(result), flush=True)
+        result["cpu_baseline"] = cpu_baseline(cap.iq, N_FFT, HOP, name)
     det.close()
+    del x, host
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return result if rank == 0 else None
+
+
+def run_ours(args):
+    """One single-capture workload as the JSON line."""
+    world, rank, local = _dist()
+    import torch
+    torch.cuda.set_device(local)
+    _init_dist(local, world)
+    res = measure_single(args, args.workload)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_headline(args):
+    """The default line: the stress capture (the largest configuration that
+    fits one GPU), with the wideband capture, batched vs plain and the
+    served latencies measured in the same run as sub-objects."""
+    world, rank, local = _dist()
+    import torch
+    torch.cuda.set_device(local)
+    _init_dist(local, world)
+    res = measure_single(args, "stress")
+    if world == 1:
+        sub = argparse.Namespace(**vars(args))
+        sub.no_cpu_baseline = True
+        res["wideband"] = _sub_line(measure_single(sub, "wideband"))
+        res["batched"] = _sub_line(measure_batched(sub))
+        res["served"] = _served_summary(measure_served(sub, loads=(0.5, 0.75)))
+    else:
+        res["sub_workloads"] = "wideband, batched and served are measured at one GPU only"
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def _served_summary(r):
+    """Saturation and the latency at each load, served and plain."""
+    if r is None:
+        return None
+
+    def one(m):
+        return {"saturation_chunks_per_s": m["saturation_chunks_per_s"],
+                "saturation_ms_s": m["saturation_ms_s"],
+                "by_load": [{k: x[k] for k in ("rho", "offered_chunks_per_s", "completed", "rejected",
+                                                "p50_ms", "p99_ms", "max_ms", "deadline_miss_frac")}
+                            for x in m["by_load"]]}
+    return {"workload": r["config"]["workload"], "lanes": r["config"]["lanes"],
+            "max_batch": r["config"]["max_batch"], "value": r["value"], "unit": UNIT,
+            "chunk_period_ms": SERVE_PERIOD_MS, "served": one(r["served"]), "plain": one(r["plain"]),
+            "served_over_plain": round(r["served"]["saturation_chunks_per_s"]
+                                       / r["plain"]["saturation_chunks_per_s"], 3),
+            "failed_results": r["failed_results"], "stats": r["served"]["stats"], "e2e": r["e2e"]}
+
+
+def _sub_line(r):
+    """A workload's result without the keys the main line already carries."""
+    if r is None:
+        return None
+    return {k: v for k, v in r.items() if k not in ("metric", "n_gpus", "higher_is_better", "scaling",
+                                                     "vs_baseline", "data", "clocks", "warmup")}
 
 
 BATCH_WORKLOAD = ("batched: 256 captures of log-uniform length 2^16..2^22 complex64 samples, "
@@ -360,19 +489,32 @@ def _gen_batch(i):
 
 
 def run_batched(args):
+    """Batched captures as the JSON line."""
+    world, rank, local = _dist()
+    import torch
+    torch.cuda.set_device(local)
+    _init_dist(local, world)
+    res = measure_batched(args)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def measure_batched(args):
     """Batched captures: rise_detect_batch vs a per-capture rise_detect loop."""
     import multiprocessing as mp
 
     import numpy as np
-    # the synthetic captures are built in a spawn pool before any CUDA call
+    # the synthetic captures are built in a spawn pool (a fresh interpreter
+    # per worker: safe before and after the first CUDA call)
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
         caps = pool.map(_gen_batch, range(args.batch))
     import torch
 
     from paper_2603_20481_gb300 import rise
     world, rank, local = _dist()
-    torch.cuda.set_device(local)
-    _init_dist(local, world)
     xs = [torch.from_numpy(c.iq).cuda() for c in caps]
     hosts = [torch.from_numpy(c.iq).pin_memory() for c in caps]
     Ns = [c.fft_size for c in caps]
@@ -446,7 +588,25 @@ def run_batched(args):
                "h2d_bytes_per_step": 8 * n_total, "d2h_bytes_per_step": 48 * int(oh[-1]) + 8 * len(oh)}
     peak, peak_kind = _peaks()
     stft_ms = float(st_batch[0])
-    alg = 8 * n_total + 4 * px_total          # IQ read + float power write, all STFT launches
+    # the STFT launches of the batch (one per FFT size) against both rooflines,
+    # with the survey's algorithmic units: IQ read per sample, 5 N log2 N flops
+    # per frame; the whole step with IQ twice + the 8-bit image written and read
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak = _fp32_peak(sms, 2070.0)
+    flops = sum(((int(x.numel()) - N) // h + 1) * 5 * N * int(math.log2(N)) for x, N, h in zip(xs, Ns, hops))
+    kb = 8 * n_total
+    t_s = stft_ms / 1e3
+    alu = flops / (fp32_peak * 1e12) >= kb / (peak * 1e9)
+    roof_main = ({"achieved": round(flops / t_s / 1e12, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
+                  "frac": round(flops / t_s / 1e12 / fp32_peak, 4), "flops_per_launch": flops,
+                  "convention": "5 N log2 N per frame",
+                  "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+                 if alu else
+                 {"achieved": round(kb / t_s / 1e9, 1), "peak": peak, "unit": "GB/s",
+                  "frac": round(kb / t_s / 1e9 / peak, 4), "alg_bytes_per_launch": kb,
+                  "peak_source": peak_kind})
+    alg_path = 16 * n_total + 2 * px_total
+    step_s = t_batch / args.steps
     result = {
         "metric": METRIC, "value": round(world * args.steps * n_total / t_batch / 1e6, 1), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -465,21 +625,23 @@ def run_batched(args):
         "boxes_identical": bool(same), "boxes": int(offs[-1]),
         "runs": int(ccl[0]) if ccl is not None else None,
         "deferred_unions": int(ccl[1]) if ccl is not None else None,
-        "roofline": {"bound": "hbm", "kernel": "spectrum (all STFT launches of the batch)",
-                     "achieved": round(alg / (stft_ms / 1e3) / 1e9, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(alg / (stft_ms / 1e3) / 1e9 / peak, 4), "traffic": None,
-                     "peak_source": peak_kind, "alg_bytes_per_launch": alg,
-                     "ms_per_launch": round(stft_ms, 4)},
+        "roofline": {"bound": "alu" if alu else "hbm",
+                     "kernel": "stft_batch_kernel (all STFT launches of the batch)", **roof_main,
+                     "traffic": None, "ms_per_launch": round(stft_ms, 4),
+                     "hbm": {"achieved": round(kb / t_s / 1e9, 1), "peak": peak, "unit": "GB/s",
+                             "frac": round(kb / t_s / 1e9 / peak, 4), "alg_bytes_per_launch": kb},
+                     "path": {"alg_bytes_per_step": alg_path, "unit": "GB/s", "peak": peak,
+                              "achieved": round(alg_path / step_s / 1e9, 1),
+                              "frac": round(alg_path / step_s / 1e9 / peak, 4)}},
         "stage_ms": {k: round(float(v), 4) for k, v in zip(rise.STAGES, st_batch)},
         "gpu_launches": int(l_batch),
         "e2e": e2e,
     }
-    if rank == 0:
-        print(json.dumps(result), flush=True)
     det.close()
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    del xs, hosts
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return result if rank == 0 else None
 
 
 SERVE_WORKLOAD = ("served: 32 radios sending 10 ms chunks of 614,400 complex64 samples "
@@ -540,7 +702,18 @@ _serve_run.failed = 0   # results whose status was not RISE_OK (must stay 0)
 
 
 def run_served(args):
-    """Served chunks: continuous batching vs one chunk per launch chain."""
+    """Served chunks as the JSON line."""
+    world, rank, local = _dist()
+    import torch
+    torch.cuda.set_device(local)
+    res = measure_served(args)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
+def measure_served(args, loads=(0.5, 0.75, 1.0, 1.25, 1.5)):
+    """Served chunks: continuous batching vs one chunk per launch chain, at
+    Poisson loads of `loads` x the measured saturation rate."""
     import multiprocessing as mp
 
     import numpy as np
@@ -551,7 +724,6 @@ def run_served(args):
 
     from paper_2603_20481_gb300 import rise
     world, rank, local = _dist()
-    torch.cuda.set_device(local)
     pinned = [[torch.from_numpy(data[s * per + k]).pin_memory() for k in range(per)]
               for s in range(SERVE_RADIOS)]
     rng = np.random.default_rng(4242)
@@ -583,7 +755,7 @@ def run_served(args):
                "saturation_ms_per_step": round(1e3 / sat, 4),
                "saturation_ms_s": round(sat * SERVE_CHUNK / 1e6, 1),
                "boxes_per_chunk": round(box_per_chunk, 2), "by_load": []}
-        for rho in (0.5, 0.75, 1.0, 1.25, 1.5):
+        for rho in loads:
             lam = rho * sat
             count = max(50, int(lam * args.serve_seconds))
             gaps = rng.exponential(1.0 / lam, size=count)
@@ -607,7 +779,7 @@ def run_served(args):
 
     served = measure(args.lanes, args.max_batch)
     plain = measure(1, 1)
-    at1 = next(x for x in served["by_load"] if x["rho"] == 1.0)
+    at1 = next((x for x in served["by_load"] if x["rho"] == 1.0), {"p99_ms": None})
     result = {
         "metric": METRIC, "value": served["saturation_ms_s"], "unit": UNIT, "n_gpus": world,
         "steps": int(served["stats"]["completed"]), "warmup": 3,
@@ -624,8 +796,7 @@ def run_served(args):
                 "d2h_bytes_per_step": int(round(served["boxes_per_chunk"] * 48)) + 80,
                 "note": "the served numbers are end to end: pinned host chunks in, boxes on the host out"},
     }
-    if rank == 0:
-        print(json.dumps(result), flush=True)
+    return result if rank == 0 else None
 
 
 WINDOW_WORKLOAD = ("streaming TF plots (Sec. IV-D configuration): radios at 100 MS/s sending "
@@ -745,30 +916,35 @@ def run_windows(args):
 
 
 def run_reference(args):
+    """The FP64 oracle as it stands on the host cores (all of them), on the
+    default workload's capture: each step one pass over a bounded prefix."""
     world, rank, local = _dist()
     if rank != 0:
         return
     from paper_2603_20481_gb300 import synth
     import oracle
-    cap = synth.wideband_capture(seed=102, n=args.samples or N_SAMPLES)
+    name = "stress" if args.workload in ("headline", "stress") else "wideband"
+    gen, seed, N, hop, n_default, workload = SINGLE[name]
+    cap = getattr(synth, gen)(seed=seed, n=n_default)
     m = min(args.ref_sample, cap.iq.shape[0])
     x = cap.iq[:m]
+    used = oracle.set_threads(0)
     for _ in range(args.warmup):
-        oracle.detect(x, N_FFT, HOP)
+        oracle.detect(x, N, hop)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.detect(x, N_FFT, HOP)
+        oracle.detect(x, N, hop)
     dt = time.perf_counter() - t0
     value = round(args.steps * m / dt / 1e6, 3)
-    sample = (f"first {m} samples of the wideband capture ({(m - N_FFT) // HOP + 1} frames) "
-              f"per step, FP64 C oracle, single thread")
+    sample = (f"first {m} samples of the {name} capture ({(m - N) // hop + 1} frames) per step, "
+              f"FP64 C oracle on {used} host threads (nproc {os.cpu_count()})")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt / args.steps * 1e3, 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_samples": m, "fft_size": N_FFT, "hop": HOP},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "config": {"workload": workload, "n_samples": m, "fft_size": N, "hop": hop},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -910,14 +1086,17 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--samples", type=int, default=0, help="capture length (0: the workload's)")
     ap.add_argument("--range-path", type=int, default=0, choices=(0, 1, 2))
-    ap.add_argument("--cpu-sample", type=int, default=1 << 26)
-    ap.add_argument("--ref-sample", type=int, default=1 << 22)
+    ap.add_argument("--ref-sample", type=int, default=1 << 23,
+                    help="reference arm: samples per step (a prefix of the capture)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--clock-window", type=float, default=1.0,
                     help="seconds of steady load the clock samples span (0: the timed steps only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=("wideband", "stress", "batched", "served", "windows", "quality"),
-                    default="wideband")
+    ap.add_argument("--workload", choices=("headline", "wideband", "stress", "batched", "served", "windows",
+                                           "quality"),
+                    default="headline",
+                    help="headline (default): the stress capture, with wideband, batched and served "
+                         "measured in the same run as sub-objects")
     ap.add_argument("--radios", type=int, default=32, help="windows: streams at 100 MS/s")
     ap.add_argument("--lanes", type=int, default=3, help="served: batches in flight")
     ap.add_argument("--max-batch", type=int, default=32, help="served: chunks per batch")
@@ -936,9 +1115,8 @@ def main():
         run_windows(args)
     elif args.workload == "quality":
         run_quality(args)
-    elif args.workload == "stress" and args.cpu_sample == 1 << 26:
-        args.cpu_sample = 1 << 24      # about 20 s of oracle time at FFT 8192, hop 2048
-        run_ours(args)
+    elif args.workload == "headline":
+        run_headline(args)
     else:
         run_ours(args)
 
