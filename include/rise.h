@@ -394,10 +394,12 @@ void rise_server_destroy(rise_server *s);
                               * graphs kept, [3] 0                                */
 #define RISE_DBG_CCL 15      /* int64 [4] of the last call's labelling: runs,      *
                               * deferred unions, components, run capacity         */
-#define RISE_DBG_BATCH_INFO 13 /* int64 [16] of the last batch: [0] STFT groups G,   *
+#define RISE_DBG_BATCH_INFO 13 /* int64 [64] of the last batch: [0] STFT groups G,   *
                                 * [1] replayed from a graph (0/1), [2..2+G) frames  *
                                 * per STFT item in steps, [2+G] morphology warps    *
-                                * per SM                                            */
+                                * per SM, [3+G..3+2G) radix schedule per group,     *
+                                * [3+2G..3+3G) FFT size per group, [63] tuned       *
+                                * compositions read from the tune cache so far      */
 /* Intermediates of the last rise_detect_batch call, kept until the next call
  * of the context (or a buffer growth) overwrites them.  Captures follow one
  * another in call order, capture c taking T_c * F_c entries ([T_c][F_c],
@@ -433,8 +435,9 @@ int rise_debug_export(rise_ctx *ctx, int what, void *dst, size_t bytes);
 #define RISE_OPT_GRAPH 5       /* 1 (default): a call repeating the previous     *
                                 * call's arguments (a batch: its composition)     *
                                 * replays the launches captured as a CUDA graph   */
-#define RISE_OPT_AUTOTUNE 6    /* 1 (default): tune batch launch shapes once per   *
-                                * composition; 0: fixed defaults                   */
+#define RISE_OPT_AUTOTUNE 6    /* 1 (default): tune batch launch shapes and radix  *
+                                * schedules once per composition (or read them    *
+                                * from the tune cache); 0: fixed defaults          */
 #define RISE_OPT_RUN_CAPACITY 7 /* runs the labelling arrays hold at the next call *
                                  * (>= 1024; they still grow when a mask needs    *
                                  * more)                                          */
@@ -448,6 +451,23 @@ int rise_debug_export(rise_ctx *ctx, int what, void *dst, size_t bytes);
 #define RISE_OPT_TEST_WITHHOLD 10  /* test only: the box-slot scan's tile with this *
                                     * index publishes no sum, so every later tile's *
                                     * wait runs out; -1 (default): none             */
+/* Radix schedule of the FFT of single captures.  An N-point transform with
+ * N = 16^a * r (r = 2, 4 or 8) runs its radix-r pass last (schedule 0) or
+ * first (schedule 1, the default); for N a power of 16 both are the same.
+ * -1: the schedule this context's batch tuner (or the tune cache) picked
+ * for N, else 1.  The two schedules round differently, so the 8-bit image
+ * can differ in a few pixels (both stay within the tolerance of the FP64
+ * reference).  The batch tuner times both per FFT size of a new composition
+ * and keeps the faster; an untuned batch runs schedule 1.  A batch capture's
+ * results equal those of rise_detect run with the batch's schedule. */
+#define RISE_OPT_FFT_SCHEDULE 11
+
+/* Tune cache: when the environment variable RISE_TUNE_CACHE names a file,
+ * every composition the batch tuner tunes is appended to it as one text
+ * line ("rise-tune 1 <device name:SMs> <composition key> <G> <G frames-per-
+ * item multipliers> <G radix schedules> <morphology warps per SM>"), and a
+ * composition found there for the same device is run without tuning (also
+ * in another process). */
 
 /* Sets an option; errors: RISE_EINVAL. */
 int rise_set_option(rise_ctx *ctx, int option, int64_t value);

@@ -10,7 +10,11 @@
 // matter (frames per STFT work item, morphology warps per SM) are picked by
 // timing candidates on the first batch of each composition.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <string>
 
 #include "context.cuh"
 
@@ -59,8 +63,9 @@ struct Plan {
   };
   std::vector<Group> groups;
   std::vector<int> group_of;                      // capture -> group
-  // tuned launch parameters: item multiplier per group, morphology warps per SM
-  std::vector<int> item_mult;
+  // tuned launch parameters: item multiplier and radix schedule per group,
+  // morphology warps per SM
+  std::vector<int> item_mult, sched;
   int morph_wps = 16;
   // blob layout
   size_t o_stft, o_items, o_hseg, o_hitem, o_col, o_mseg, o_mitem, o_wbase, o_rseg, o_row0, bytes;
@@ -284,7 +289,7 @@ int fill_tables(rise_ctx *c, const rise_capture *caps, const Plan &p, const rise
     const int F = cp.fft_size;
     const int64_t T = p.T[k];
     Tables *tb;
-    int rc = get_tables(c, F, &tb);
+    int rc = get_tables(c, F, p.sched[p.group_of[k]], &tb);
     if (rc) return rc;
     StftArgs &a = stft[k];
     a.iq = cp.iq_dev;
@@ -301,6 +306,7 @@ int fill_tables(rise_ctx *c, const rise_capture *caps, const Plan &p, const rise
     a.tw = tb->tw;
     a.win = tb->win;
     a.err = &c->small->status.err;
+    a.sched = tb->sched;
     const int g = p.group_of[k];
     const int frames = p.item_mult[g] * stft_frames_per_step(F);
     for (int64_t f0 = 0; f0 < T; f0 += frames) {
@@ -421,7 +427,7 @@ int enqueue(rise_ctx *c, const Plan &p, const rise_thresholds &thr, int64_t cap,
   mark();
   for (size_t g = 0; g < p.groups.size(); ++g) {
     const auto &G = p.groups[g];
-    CK(launch_stft_batch(G.N, G.tma, p.fixed ? STFT_QUANT : STFT_POWER, stft, items + G.item0,
+    CK(launch_stft_batch(G.N, p.sched[g], G.tma, p.fixed ? STFT_QUANT : STFT_POWER, stft, items + G.item0,
                          G.n_items, counters + g, c->num_sms, s));
     mark();
   }
@@ -481,12 +487,113 @@ uint64_t graph_key(const Plan &p, const rise_thresholds &thr, int64_t cap, uint6
   h = fnv(h, &gen, sizeof(gen));
   h = fnv(h, &timing, sizeof(timing));
   h = fnv(h, p.item_mult.data(), p.item_mult.size() * sizeof(int));
+  h = fnv(h, p.sched.data(), p.sched.size() * sizeof(int));
   h = fnv(h, &p.morph_wps, sizeof(p.morph_wps));
   return h;
 }
 
+// Radix schedule of an untuned batch group: 1 (the small radix first, the
+// faster one where it differs), the same as 0 for powers of 16.
+int default_sched(int N) { return stft_sched_distinct(N, 1) ? 1 : 0; }
+
+// Tuned parameters of a composition: item multiplier per STFT group, radix
+// schedule per group, morphology warps per SM.
+struct Tuned {
+  std::vector<int> item_mult, sched;
+  int morph_wps = 16;
+};
+
+std::vector<int> pack(const Tuned &t) {
+  std::vector<int> v(t.item_mult);
+  v.insert(v.end(), t.sched.begin(), t.sched.end());
+  v.push_back(t.morph_wps);
+  return v;
+}
+
+bool unpack(const std::vector<int> &v, size_t ng, Tuned *t) {
+  if (v.size() != 2 * ng + 1) return false;
+  t->item_mult.assign(v.begin(), v.begin() + ng);
+  t->sched.assign(v.begin() + ng, v.begin() + 2 * ng);
+  t->morph_wps = v.back();
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Tune cache: a text file named by $RISE_TUNE_CACHE, one line per tuned
+// composition, "rise-tune 1 <device> <composition key, 16 hex digits> <G>
+// <G item multipliers> <G schedules> <morphology warps per SM>", where
+// <device> is the device name (spaces as '_') and its SM count joined by
+// ':'.  A line is appended whenever a composition is tuned; on reading, the
+// last line for a device and key wins.  A process that finds its
+// composition there runs it without tuning.
+// ---------------------------------------------------------------------------
+std::string device_tag(const rise_ctx *c) {
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) {
+    cudaGetLastError();
+    return "unknown";
+  }
+  std::string n(prop.name);
+  for (char &ch : n)
+    if (ch == ' ' || ch == '\t' || ch == '\n') ch = '_';
+  return n + ":" + std::to_string(prop.multiProcessorCount);
+}
+
+bool cache_lookup(const rise_ctx *c, uint64_t key, size_t ng, Tuned *out) {
+  const char *path = std::getenv("RISE_TUNE_CACHE");
+  if (!path || !*path) return false;
+  FILE *f = std::fopen(path, "r");
+  if (!f) return false;
+  const std::string dev = device_tag(c);
+  char line[4096];
+  bool found = false;
+  while (std::fgets(line, sizeof line, f)) {
+    char tag[16], dname[512];
+    int ver = 0, g = 0, off = 0;
+    unsigned long long k = 0;
+    if (std::sscanf(line, "%15s %d %511s %llx %d%n", tag, &ver, dname, &k, &g, &off) != 5) continue;
+    if (std::strcmp(tag, "rise-tune") != 0 || ver != 1 || dev != dname || k != key || g != (int)ng) continue;
+    std::vector<int> v;
+    const char *q = line + off;
+    for (size_t i = 0; i < 2 * ng + 1; ++i) {
+      int x = 0, used = 0;
+      if (std::sscanf(q, "%d%n", &x, &used) != 1) break;
+      v.push_back(x);
+      q += used;
+    }
+    Tuned t;
+    if (!unpack(v, ng, &t)) continue;
+    bool ok = t.morph_wps >= 1 && t.morph_wps <= 64;
+    for (size_t i = 0; i < ng; ++i)
+      ok = ok && t.item_mult[i] >= 1 && t.item_mult[i] <= 64 && (t.sched[i] == 0 || t.sched[i] == 1);
+    if (ok) {
+      *out = t;
+      found = true;
+    }
+  }
+  std::fclose(f);
+  return found;
+}
+
+void cache_store(const rise_ctx *c, uint64_t key, const Tuned &t) {
+  const char *path = std::getenv("RISE_TUNE_CACHE");
+  if (!path || !*path) return;
+  std::string line = "rise-tune 1 " + device_tag(c);
+  char hex[32];
+  std::snprintf(hex, sizeof hex, " %016llx %d", (unsigned long long)key, (int)t.item_mult.size());
+  line += hex;
+  for (int v : pack(t)) line += " " + std::to_string(v);
+  line += "\n";
+  FILE *f = std::fopen(path, "a");   // one short append per tuned composition
+  if (!f) return;
+  std::fputs(line.c_str(), f);
+  std::fclose(f);
+}
+
 // Runs the chain once per candidate launch shape and keeps, per STFT group,
-// the fastest item size and, for the morphology, the fastest warps per SM.
+// the fastest item size and, for the morphology, the fastest warps per SM;
+// then, for groups whose FFT size has a second radix schedule, runs the chain
+// with that schedule and keeps it where it is faster.
 int autotune(rise_ctx *c, const rise_capture *caps, Plan &p, const rise_thresholds &thr,
              int64_t cap) {
   const size_t ng = p.groups.size();
@@ -501,33 +608,59 @@ int autotune(rise_ctx *c, const rise_capture *caps, Plan &p, const rise_threshol
       return RISE_ECUDA;
     }
   int rc = RISE_OK;
+  auto run_timed = [&](std::vector<float> *group_ms, float *morph_ms) -> int {
+    size_tables(c, caps, p);
+    int r2;
+    if ((r2 = ensure_buffers(c, p, cap))) return r2;
+    if ((r2 = fill_tables(c, caps, p, thr))) return r2;
+    for (int rep = 0; rep < 2; ++rep) {   // the first run warms up
+      ev.n = 0;
+      if ((r2 = enqueue(c, p, thr, cap, &ev, nullptr, false))) return r2;
+      if (cudaStreamSynchronize(c->stream) != cudaSuccess) return RISE_ECUDA;
+    }
+    for (size_t g = 0; g < ng; ++g) cudaEventElapsedTime(&(*group_ms)[g], ev.e[g], ev.e[g + 1]);
+    cudaEventElapsedTime(morph_ms, ev.e[ng + 1], ev.e[ng + 2]);
+    return RISE_OK;
+  };
+  std::vector<float> ms(ng);
+  float mm = 0.f;
+  p.sched.assign(ng, 0);
   for (int r = 0; r < kNumCands && rc == RISE_OK; ++r) {
     p.item_mult.assign(ng, kItemCands[r]);
     p.morph_wps = kMorphCands[r % 3];
-    size_tables(c, caps, p);
-    if ((rc = ensure_buffers(c, p, cap))) break;
-    if ((rc = fill_tables(c, caps, p, thr))) break;
-    for (int rep = 0; rep < 2 && rc == RISE_OK; ++rep) {   // the first run warms up
-      ev.n = 0;
-      if ((rc = enqueue(c, p, thr, cap, &ev, nullptr, false))) break;
-      if (cudaStreamSynchronize(c->stream) != cudaSuccess) { rc = RISE_ECUDA; break; }
-      if (rep == 0) continue;
+    if ((rc = run_timed(&ms, &mm))) break;
+    for (size_t g = 0; g < ng; ++g)
+      if (ms[g] < best_g[g]) { best_g[g] = ms[g]; pick_g[g] = kItemCands[r]; }
+    if (mm < best_m) { best_m = mm; pick_m = kMorphCands[r % 3]; }
+  }
+  // the radix schedule, one per FFT size (a size's groups differ only in
+  // their input staging): the faster total over the size's groups
+  std::vector<int> pick_s(ng, 0);
+  bool any = false;
+  for (size_t g = 0; g < ng; ++g) any = any || stft_sched_distinct(p.groups[g].N, 1);
+  if (rc == RISE_OK && any) {
+    p.item_mult = pick_g;
+    p.morph_wps = pick_m;
+    for (size_t g = 0; g < ng; ++g) p.sched[g] = stft_sched_distinct(p.groups[g].N, 1) ? 1 : 0;
+    if ((rc = run_timed(&ms, &mm)) == RISE_OK) {
+      std::map<int, float> t0, t1;
       for (size_t g = 0; g < ng; ++g) {
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, ev.e[g], ev.e[g + 1]);
-        if (ms < best_g[g]) { best_g[g] = ms; pick_g[g] = kItemCands[r]; }
+        t0[p.groups[g].N] += best_g[g];
+        t1[p.groups[g].N] += ms[g];
       }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, ev.e[ng + 1], ev.e[ng + 2]);
-      if (ms < best_m) { best_m = ms; pick_m = kMorphCands[r % 3]; }
+      for (size_t g = 0; g < ng; ++g)
+        if (p.sched[g] == 1 && t1[p.groups[g].N] < t0[p.groups[g].N]) pick_s[g] = 1;
     }
   }
   for (auto &e : ev.e)
     if (e) cudaEventDestroy(e);
   if (rc) return rc;
-  std::vector<int> t(pick_g);
-  t.push_back(pick_m);
-  c->batch.tuned[p.shape_key] = t;
+  Tuned t;
+  t.item_mult = pick_g;
+  t.sched = pick_s;
+  t.morph_wps = pick_m;
+  c->batch.tuned[p.shape_key] = pack(t);
+  cache_store(c, p.shape_key, t);
   return RISE_OK;
 }
 
@@ -581,10 +714,12 @@ int reserve_batch(rise_ctx *c, const rise_capture *caps, int ncap, const rise_th
   if ((rc = upload_sg(c, thr.sg_half_window))) return rc;
   for (const auto &g : p.groups) {
     Tables *tb;
-    if ((rc = get_tables(c, g.N, &tb))) return rc;
+    if ((rc = get_tables(c, g.N, default_sched(g.N), &tb))) return rc;
   }
   // the default launch parameters (what an untuned batch uses)
   p.item_mult.assign(p.groups.size(), 2);
+  p.sched.assign(p.groups.size(), 0);
+  for (size_t g = 0; g < p.groups.size(); ++g) p.sched[g] = default_sched(p.groups[g].N);
   p.morph_wps = 16;
   size_tables(c, caps, p);
   return ensure_buffers(c, p, cap);
@@ -615,19 +750,31 @@ int detect_batch(rise_ctx *c, const rise_capture *caps, int ncap, const rise_thr
   if (rc) return rc;
   if ((rc = upload_level_tables(c, thr.level_db))) return rc;
   if ((rc = upload_sg(c, thr.sg_half_window))) return rc;
-  // launch parameters: tuned once per composition, else the defaults
+  // launch parameters: tuned once per composition (or read from the tune
+  // cache), else the defaults
+  const size_t ng = p.groups.size();
   auto it = c->batch.tuned.find(p.shape_key);
   if (it == c->batch.tuned.end() && c->autotune) {
-    if ((rc = autotune(c, caps, p, thr, cap))) return rc;
+    Tuned t;
+    if (cache_lookup(c, p.shape_key, ng, &t)) {
+      c->batch.tuned[p.shape_key] = pack(t);
+      c->batch.cache_hits += 1;
+    } else if ((rc = autotune(c, caps, p, thr, cap))) {
+      return rc;
+    }
     it = c->batch.tuned.find(p.shape_key);
   }
-  if (it != c->batch.tuned.end()) {
-    p.item_mult.assign(it->second.begin(), it->second.end() - 1);
-    p.morph_wps = it->second.back();
-  } else {
-    p.item_mult.assign(p.groups.size(), 2);
-    p.morph_wps = 16;
+  Tuned use;
+  if (it == c->batch.tuned.end() || !unpack(it->second, ng, &use)) {
+    use.item_mult.assign(ng, 2);
+    use.sched.assign(ng, 0);
+    for (size_t g = 0; g < ng; ++g) use.sched[g] = default_sched(p.groups[g].N);
+    use.morph_wps = 16;
   }
+  p.item_mult = use.item_mult;
+  p.sched = use.sched;
+  p.morph_wps = use.morph_wps;
+  for (size_t g = 0; g < ng; ++g) c->sched_pick[p.groups[g].N] = p.sched[g];
   size_tables(c, caps, p);
   if ((rc = ensure_buffers(c, p, cap))) return rc;
   if ((rc = fill_tables(c, caps, p, thr))) return rc;
@@ -720,6 +867,8 @@ int detect_batch(rise_ctx *c, const rise_capture *caps, int ncap, const rise_thr
   b.last_groups = (int)p.groups.size();
   b.last_params.assign(p.item_mult.begin(), p.item_mult.end());
   b.last_params.push_back(p.morph_wps);
+  b.last_params.insert(b.last_params.end(), p.sched.begin(), p.sched.end());
+  for (const auto &g : p.groups) b.last_params.push_back(g.N);
   b.last_graph = launched;
   return total > cap ? RISE_ETRUNC : RISE_OK;
 }

@@ -166,6 +166,7 @@ inline void preload_kernel(K k) {
   if (cudaFuncGetAttributes(&a, k) != cudaSuccess) cudaGetLastError();
 }
 void stft_preload();
+void stft_s1_preload();
 void stft_sc16_preload();
 void image_preload();
 void ccl_preload();
@@ -190,10 +191,15 @@ struct StftArgs {
   const float *win;       // per-N Hann window (device)
   uint32_t *err;          // device error word (ERR_* bits)
   int fmt;                // IqFormat
+  int sched;              // radix schedule of the tables tw (0: radix 16 first, 1: the small radix first)
 };
 
 enum StftMode { STFT_MAX = 0, STFT_QUANT = 1, STFT_POWER = 2, STFT_QUANT_POWER = 3 };
 cudaError_t launch_stft_sc16(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s);
+// Schedule 1 of complex64 input (its own translation unit).
+cudaError_t launch_stft_s1(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s);
+// True when schedule S of size N is not schedule 0 (N is not a power of 16).
+bool stft_sched_distinct(int N, int S);
 
 // ---------------------------------------------------------------------------
 // Batches: one launch per stage covers many captures; each block or warp
@@ -210,16 +216,19 @@ struct StftItem {             // frames [f0, f1) of capture `seg`
   int32_t seg, pad;
   int64_t f0, f1;
 };
-cudaError_t launch_stft_batch(int N, bool tma, StftMode mode, const StftArgs *segs,
+cudaError_t launch_stft_batch(int N, int sched, bool tma, StftMode mode, const StftArgs *segs,
                               const StftItem *items, int n_items, int *counter, int num_sms,
                               cudaStream_t s);
+cudaError_t launch_stft_batch_s1(int N, bool tma, StftMode mode, const StftArgs *segs, const StftItem *items,
+                                 int n_items, int *counter, int num_sms, cudaStream_t s);
 int stft_frames_per_step(int N);
 cudaError_t launch_levels_batch(CapSmall *cs, int ncap, double hi_power, int use_fixed,
                                 const double *ratio, double level_db, cudaStream_t s);
 
-// Twiddle and window tables for FFT size N (host-computed, FP64 -> float).
-size_t stft_table_floats(int N);
-void stft_fill_tables(int N, float2 *tw_host, float *win_host);
+// Twiddle and window tables for FFT size N, radix schedule S (host-computed,
+// FP64 -> float).
+size_t stft_table_floats(int N, int S);
+void stft_fill_tables(int N, int S, float2 *tw_host, float *win_host);
 cudaError_t launch_stft(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s);
 // Level edges from the anchor (AUTO: read from max_bits; FIXED: hi_power).
 cudaError_t launch_levels(const uint32_t *max_bits, double hi_power, int use_fixed,

@@ -16,10 +16,11 @@ struct Buf {
   size_t bytes = 0;
 };
 
-// Per-FFT-size tables (twiddles + Hann window), built once.
+// Per-FFT-size and radix-schedule tables (twiddles + Hann window), built once.
 struct Tables {
   float2 *tw = nullptr;
   float *win = nullptr;
+  int sched = 0;
 };
 
 struct Small {              // one device block of small per-call data
@@ -53,6 +54,7 @@ struct BatchState {
   // tuned launch parameters, keyed by the batch's shape
   std::map<uint64_t, std::vector<int>> tuned;
   int64_t captures = 0;          // launch chains captured so far
+  int64_t cache_hits = 0;        // compositions whose launch parameters came from the tune cache
   int64_t relabels = 0;          // batches run again with grown run arrays
   // the last batch: STFT groups, its launch parameters, replayed from a graph
   int last_groups = 0;
@@ -84,7 +86,7 @@ struct CallSlot {
   // the queued call, kept to run it again if its run arrays overflow
   const void *src = nullptr;
   int64_t n = 0, T = 0, cap = 0;
-  int N = 0, hop = 0, path = 0, fmt = 0;
+  int N = 0, hop = 0, path = 0, fmt = 0, sched = 0;
   bool want_power = false;
   rise_thresholds thr{};
 };
@@ -106,6 +108,10 @@ struct rise_ctx {
   // withheld root-scan tile (-1: none)
   int spin_limit = 1 << 20, uf_limit = 1 << 26;
   int64_t withhold_tile = -1;
+  // radix schedule of single captures: 0 or 1 (default), or -1: the one the
+  // batch tuner (or the tune cache) picked for the FFT size, else 1
+  int fft_sched = 1;
+  std::map<int, int> sched_pick;   // FFT size -> schedule picked by the batch tuner
   bool capturing = false;         // enqueueing into a graph capture
   // scratch
   rise::host::Buf power, img, hist, cols, effm1, mask, dbg[3], row_cnt, row_base, run_parent,
@@ -122,7 +128,7 @@ struct rise_ctx {
   cudaStream_t copy_stream = nullptr;
   rise::host::CallSlot &cs() { return slot[cur]; }
   const rise::DeviceStatus *last_status = nullptr;   // status of the last finished call
-  std::map<int, rise::host::Tables> tables;
+  std::map<int, rise::host::Tables> tables;   // key: FFT size * 2 + schedule
   double energy_level_db = NAN;
   int sg_m = -1;
   // last call
@@ -160,8 +166,11 @@ void new_generation(rise_ctx *c);
 int ensure(rise_ctx *c, Buf &b, size_t bytes);
 // Mapped pinned host buffer for the current slot's boxes (at least `cap`).
 int ensure_hbox(rise_ctx *c, int64_t cap);
-// Twiddle and window tables of FFT size N (built once per context).
-int get_tables(rise_ctx *c, int N, Tables **out);
+// Twiddle and window tables of FFT size N and radix schedule S (built once
+// per context).
+int get_tables(rise_ctx *c, int N, int S, Tables **out);
+// The radix schedule a single capture of FFT size N runs.
+int single_sched(const rise_ctx *c, int N);
 bool pow2(int64_t v);
 int check_thresholds(const rise_thresholds &t, int F);
 void record(rise_ctx *c, int i);

@@ -94,16 +94,18 @@ int ensure_hbox(rise_ctx *c, int64_t cap) {
   return RISE_OK;
 }
 
-int get_tables(rise_ctx *c, int N, Tables **out) {
-  auto it = c->tables.find(N);
+int get_tables(rise_ctx *c, int N, int S, Tables **out) {
+  if (!stft_sched_distinct(N, S)) S = 0;
+  const int key = N * 2 + S;
+  auto it = c->tables.find(key);
   if (it != c->tables.end()) {
     *out = &it->second;
     return RISE_OK;
   }
-  const size_t nf = stft_table_floats(N);
+  const size_t nf = stft_table_floats(N, S);
   std::vector<float> host(nf);
   const size_t ntw = (nf - N) / 2;
-  stft_fill_tables(N, reinterpret_cast<float2 *>(host.data()), host.data() + 2 * ntw);
+  stft_fill_tables(N, S, reinterpret_cast<float2 *>(host.data()), host.data() + 2 * ntw);
   void *d = nullptr;
   if (cudaMalloc(&d, nf * sizeof(float)) != cudaSuccess) {
     cudaGetLastError();
@@ -113,9 +115,19 @@ int get_tables(rise_ctx *c, int N, Tables **out) {
   Tables t;
   t.tw = reinterpret_cast<float2 *>(d);
   t.win = reinterpret_cast<float *>(d) + 2 * ntw;
-  c->tables[N] = t;
-  *out = &c->tables[N];
+  t.sched = S;
+  c->tables[key] = t;
+  *out = &c->tables[key];
   return RISE_OK;
+}
+
+int single_sched(const rise_ctx *c, int N) {
+  int S = c->fft_sched;
+  if (S < 0) {
+    auto it = c->sched_pick.find(N);
+    S = it == c->sched_pick.end() ? 1 : it->second;
+  }
+  return stft_sched_distinct(N, S) ? S : 0;
 }
 
 bool pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
@@ -383,6 +395,7 @@ int enqueue_detect(rise_ctx *c, const void *iq, int fmt, int64_t n, int N, int h
   a.tw = tb->tw;
   a.win = tb->win;
   a.err = &sm->status.err;
+  a.sched = tb->sched;
   bool hist_ready = false;
   if (thr.range_mode == RISE_RANGE_FIXED) {
     const double hp = std::pow(10.0, thr.hi_db / 10.0);
@@ -450,7 +463,8 @@ int submit_call(rise_ctx *c, const void *iq, int flags, int64_t n, int N, int ho
   const bool want_power = c->keep_power || (path == 2 && thr.range_mode == RISE_RANGE_AUTO_MAX);
   if (want_power && (rc = ensure(c, c->power, px * sizeof(float)))) return rc;
   Tables *tb;
-  if ((rc = get_tables(c, N, &tb))) return rc;
+  const int sched = single_sched(c, N);
+  if ((rc = get_tables(c, N, sched, &tb))) return rc;
   if ((rc = image_prepare(c, thr, cap))) return rc;
   const void *src = iq;
   if (on_host) {
@@ -466,10 +480,10 @@ int submit_call(rise_ctx *c, const void *iq, int flags, int64_t n, int N, int ho
   bool launched = false;
   if (c->graphs) {
     uint64_t key = 1469598103934665603ull;
-    const int64_t kv[14] = {(int64_t)reinterpret_cast<uintptr_t>(src), n, N, hop, cap, path,
+    const int64_t kv[15] = {(int64_t)reinterpret_cast<uintptr_t>(src), n, N, hop, cap, path,
                             c->keep_power, c->keep_masks, c->timing, (int64_t)c->gen,
                             thr.range_mode, (int64_t)thr.sg_half_window * 2 + thr.morph_order,
-                            c->cur, fmt};
+                            c->cur, fmt, sched};
     const double dv[4] = {thr.hi_db, thr.level_db, thr.psd_offset_db, thr.power_offset_db};
     key = fnv_mix(key, kv, sizeof(kv));
     key = fnv_mix(key, dv, sizeof(dv));
@@ -523,6 +537,7 @@ int submit_call(rise_ctx *c, const void *iq, int flags, int64_t n, int N, int ho
   sl.N = N;
   sl.hop = hop;
   sl.path = path;
+  sl.sched = sched;
   sl.want_power = want_power;
   sl.thr = thr;
   c->pend[c->npend++] = c->cur;
@@ -563,7 +578,7 @@ int finish_call(rise_ctx *c, rise_box *out, int64_t cap, int64_t *n_boxes) {
     if ((rc = ensure(c, c->scan_tmp, ccl_scan_tmp_bytes(std::max<int64_t>(need, sl.T + 1))))) return rc;
     c->run_cap = need;
     Tables *tb;
-    if ((rc = get_tables(c, sl.N, &tb))) return rc;
+    if ((rc = get_tables(c, sl.N, sl.sched, &tb))) return rc;
     if ((rc = enqueue_detect(c, sl.src, sl.fmt, sl.n, sl.N, sl.hop, sl.T, sl.thr, sl.path,
                              sl.want_power, tb, sl.cap)))
       return rc;
@@ -576,7 +591,7 @@ int finish_call(rise_ctx *c, rise_box *out, int64_t cap, int64_t *n_boxes) {
       c->cur = c->pend[0];
       CallSlot &nx = c->cs();
       Tables *tb2;
-      if ((rc = get_tables(c, nx.N, &tb2))) return rc;
+      if ((rc = get_tables(c, nx.N, nx.sched, &tb2))) return rc;
       rc = enqueue_detect(c, nx.src, nx.fmt, nx.n, nx.N, nx.hop, nx.T, nx.thr, nx.path, nx.want_power,
                           tb2, nx.cap);
       c->cur = me;
@@ -670,6 +685,7 @@ int rise_create(rise_ctx **out, const rise_config *cfg) {
     std::lock_guard<std::mutex> lk(mu);
     if (!loaded.count(cfg->device) && cudaSetDevice(cfg->device) == cudaSuccess) {
       stft_preload();
+      stft_s1_preload();
       stft_sc16_preload();
       image_preload();
       ccl_preload();
@@ -881,6 +897,10 @@ int rise_set_option(rise_ctx *c, int option, int64_t value) {
       c->withhold_tile = value;
       new_generation(c);
       return RISE_OK;
+    case RISE_OPT_FFT_SCHEDULE:
+      if (value < -1 || value > 1) return RISE_EINVAL;
+      c->fft_sched = (int)value;
+      return RISE_OK;
   }
   return RISE_EINVAL;
 }
@@ -914,11 +934,12 @@ int rise_debug_export(rise_ctx *c, int what, void *dst, size_t bytes) {
     return RISE_OK;
   }
   if (what == RISE_DBG_BATCH_INFO) {
-    if (bytes < 16 * sizeof(int64_t) || c->batch.last_groups == 0) return RISE_EINVAL;
-    int64_t v[16] = {};
+    if (bytes < 64 * sizeof(int64_t) || c->batch.last_groups == 0) return RISE_EINVAL;
+    int64_t v[64] = {};
     v[0] = c->batch.last_groups;
     v[1] = c->batch.last_graph ? 1 : 0;
-    for (size_t i = 0; i < c->batch.last_params.size() && i + 2 < 16; ++i) v[2 + i] = c->batch.last_params[i];
+    for (size_t i = 0; i < c->batch.last_params.size() && i + 2 < 63; ++i) v[2 + i] = c->batch.last_params[i];
+    v[63] = c->batch.cache_hits;
     std::memcpy(dst, v, sizeof v);
     return RISE_OK;
   }

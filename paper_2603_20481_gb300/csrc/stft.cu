@@ -4,8 +4,10 @@
 // One frame of N complex samples is transformed by N/16 threads, each
 // holding 16 values in registers.  N = 16^a * r (r in {1,2,4,8}): a radix-16
 // passes in registers (each thread one 16-point DFT) plus one pass of radix
-// r (each thread 16/r DFTs).  Between passes the data cross shared memory
-// once, in a layout padded by one slot per 16 so that every 16-lane group
+// r (each thread 16/r DFTs), the radix-r pass last (schedule 0) or first
+// (schedule 1, compiled in stft_s1.cu; the batch tuner times both).  Between
+// passes the data cross shared memory once, in a layout padded by one slot
+// per 16 so that every 16-lane group
 // hits 16 distinct 8-byte bank pairs.  The decomposition is the
 // decimation-in-frequency four-step recursion: pass i splits the current
 // sub-transform of length M into R interleaved pieces, DFTs over the slow
@@ -15,6 +17,8 @@
 // Epilogues: MAX (running max of |X|^2 for the anchor), QUANT (8-bit level
 // per bin, stored with DC in column N/2), POWER (float |X|^2 stored plus the
 // running max) and QUANT_POWER (both).
+#include <vector>
+
 #include "stft_impl.cuh"
 
 namespace rise {
@@ -57,22 +61,25 @@ __global__ void levels_batch_kernel(CapSmall *cs, double hi_power, int use_fixed
 
 }  // namespace
 
-// Host plan mirror (runtime) for table construction.
-static void host_plan(int N, int &np16, int &rlast, int &npass) {
+// Host mirror of Plan<N, S> (runtime) for table construction: the radix of
+// every pass.
+static std::vector<int> host_radices(int N, int S) {
   int l = 0;
   while ((1 << l) < N) ++l;
-  np16 = l / 4;
-  rlast = 1 << (l % 4);
-  npass = np16 + (rlast > 1 ? 1 : 0);
+  const int np16 = l / 4, rs = 1 << (l % 4);
+  std::vector<int> r;
+  if (rs > 1 && S == 1) r.push_back(rs);
+  for (int i = 0; i < np16; ++i) r.push_back(16);
+  if (rs > 1 && S != 1) r.push_back(rs);
+  return r;
 }
 
-size_t stft_table_floats(int N) {
-  int np16, rl, np;
-  host_plan(N, np16, rl, np);
+size_t stft_table_floats(int N, int S) {
+  const std::vector<int> rad = host_radices(N, S);
   size_t tw = 0;
   int L = 1;
-  for (int i = 0; i < np - 1; ++i) {
-    int R = i < np16 ? 16 : rl;
+  for (size_t i = 0; i + 1 < rad.size(); ++i) {
+    const int R = rad[i];
     int Mi = N / L, Mp = Mi / R;
     tw += 15 * (size_t)Mp;
     L *= R;
@@ -80,14 +87,13 @@ size_t stft_table_floats(int N) {
   return 2 * tw + N;  // complex twiddles + window
 }
 
-void stft_fill_tables(int N, float2 *tw, float *win) {
-  int np16, rl, np;
-  host_plan(N, np16, rl, np);
+void stft_fill_tables(int N, int S, float2 *tw, float *win) {
+  const std::vector<int> rad = host_radices(N, S);
   const double two_pi = 6.283185307179586476925286766559;
   size_t off = 0;
   int L = 1;
-  for (int i = 0; i < np - 1; ++i) {
-    int R = i < np16 ? 16 : rl;
+  for (size_t i = 0; i + 1 < rad.size(); ++i) {
+    const int R = rad[i];
     int Mi = N / L, Mp = Mi / R;
     for (int p = 1; p < 16; ++p)
       for (int j = 0; j < Mp; ++j) {
@@ -102,28 +108,31 @@ void stft_fill_tables(int N, float2 *tw, float *win) {
 }
 
 void stft_preload() {
-  preload_stft_in<float2>();
+  preload_stft_in<float2, 0>();
   preload_kernel(levels_kernel);
   preload_kernel(levels_batch_kernel);
 }
 
-cudaError_t launch_stft(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s) {
-  return a.fmt == IQ_SC16 ? launch_stft_sc16(a, mode, num_sms, s)
-                          : launch_stft_in<float2>(a, mode, num_sms, s);
+bool stft_sched_distinct(int N, int S) {
+  int l = 0;
+  while ((1 << l) < N) ++l;
+  return S == 1 && l % 4 != 0;
 }
 
-cudaError_t launch_stft_batch(int N, bool tma, StftMode mode, const StftArgs *segs,
+// The kernels of schedule 1 (where it differs from schedule 0) live in
+// stft_s1.cu, the 16-bit input's in stft_sc16.cu.
+cudaError_t launch_stft(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s) {
+  if (a.fmt == IQ_SC16) return launch_stft_sc16(a, mode, num_sms, s);
+  if (stft_sched_distinct(a.N, a.sched)) return launch_stft_s1(a, mode, num_sms, s);
+  return launch_stft_in<float2, 0>(a, mode, num_sms, s);
+}
+
+cudaError_t launch_stft_batch(int N, int sched, bool tma, StftMode mode, const StftArgs *segs,
                               const StftItem *items, int n_items, int *counter, int num_sms,
                               cudaStream_t s) {
-  switch (N) {
-    case 256: return batch_size<256>(tma, mode, segs, items, n_items, counter, num_sms, s);
-    case 512: return batch_size<512>(tma, mode, segs, items, n_items, counter, num_sms, s);
-    case 1024: return batch_size<1024>(tma, mode, segs, items, n_items, counter, num_sms, s);
-    case 2048: return batch_size<2048>(tma, mode, segs, items, n_items, counter, num_sms, s);
-    case 4096: return batch_size<4096>(tma, mode, segs, items, n_items, counter, num_sms, s);
-    case 8192: return batch_size<8192>(tma, mode, segs, items, n_items, counter, num_sms, s);
-  }
-  return cudaErrorInvalidValue;
+  if (stft_sched_distinct(N, sched))
+    return launch_stft_batch_s1(N, tma, mode, segs, items, n_items, counter, num_sms, s);
+  return launch_stft_batch_s<0>(N, tma, mode, segs, items, n_items, counter, num_sms, s);
 }
 
 int stft_frames_per_step(int N) {

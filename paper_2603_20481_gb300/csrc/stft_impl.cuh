@@ -13,24 +13,34 @@ namespace {
 
 constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
 
-template <int N>
+// Radix schedule S of an N-point transform, N = 16^a * r (r in {1,2,4,8}):
+// S = 0 runs the a radix-16 passes first and the radix-r pass last; S = 1
+// runs the radix-r pass first (the same schedule as S = 0 when r = 1).
+constexpr bool sched_distinct(int N, int S) { return S == 1 && (ilog2c(N) % 4) != 0; }
+
+template <int N, int S = 0>
 struct Plan {
   static constexpr int LOG2N = ilog2c(N);
   static constexpr int NP16 = LOG2N / 4;
-  static constexpr int RLAST = 1 << (LOG2N % 4);
-  static constexpr int NPASS = NP16 + (RLAST > 1 ? 1 : 0);
+  static constexpr int RSMALL = 1 << (LOG2N % 4);
+  static constexpr bool SMALL_FIRST = sched_distinct(N, S);
+  static constexpr int NPASS = NP16 + (RSMALL > 1 ? 1 : 0);
   static constexpr int TPF = N / 16;                       // threads per frame
   static constexpr int FPB = TPF >= 256 ? 1 : 256 / TPF;   // frames per block step
   static constexpr int THREADS = TPF * FPB;
   static constexpr int SLOT = N + N / 16;                  // padded complex per frame
-  static constexpr int radix(int i) { return i < NP16 ? 16 : RLAST; }
+  static constexpr int radix(int i) {
+    return SMALL_FIRST ? (i == 0 ? RSMALL : 16) : (i < NP16 ? 16 : RSMALL);
+  }
   static constexpr int lprev(int i) { return i == 0 ? 1 : lprev(i - 1) * radix(i - 1); }
   static constexpr int mi(int i) { return N / lprev(i); }
   static constexpr int mp(int i) { return mi(i) / radix(i); }
-  // twiddle tables: pass 0 [15][N/16] kept in registers, passes 1..NPASS-2 in smem
+  // twiddle tables [15][mp(i)] of passes 0..NPASS-2; pass 0's share of a
+  // thread ((16 / r0) (r0 - 1) values) is kept in registers, the rest in smem
   static constexpr int tw_off(int i) { return i == 0 ? 0 : tw_off(i - 1) + 15 * mp(i - 1); }
   static constexpr int TW_TOTAL = tw_off(NPASS - 1);
-  static constexpr int TW_REST = TW_TOTAL - 15 * (N / 16);
+  static constexpr int TW_REST = TW_TOTAL - tw_off(1);
+  static constexpr int TW0 = 16 - 16 / radix(0);
 };
 
 __device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
@@ -185,13 +195,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
   return false;
 }
 
-template <int N, int I, bool FIRST>
+// Pass I of the transform.  Butterfly d = tau + (N/16) s (s < 16/R) of
+// sub-problem P = d / MP takes the R values P MI + a MP + j (j = d % MP).
+// The first pass takes its values from registers loaded in sample order
+// (v[i] = x[tau + (N/16) i]), so a radix-r first pass first regroups them
+// per butterfly (v[s r + a] = x[d + a N/r]).
+template <int N, int S, int I, bool FIRST>
 __device__ __forceinline__ void fft_pass(float2 (&v)[16], const float2 *src, float2 *dst, int tau,
                                          const float2 (&tw0)[15], const float2 *twr) {
-  using PL = Plan<N>;
+  using PL = Plan<N, S>;
   constexpr int R = PL::radix(I);
   constexpr int MI = PL::mi(I), MP = PL::mp(I);
   constexpr bool LAST = (I == PL::NPASS - 1);
+  static_assert(R == 16 || I == 0 || LAST, "a radix below 16 runs first or last");
   if constexpr (!FIRST) {
 #pragma unroll
     for (int s = 0; s < 16 / R; ++s) {
@@ -200,35 +216,57 @@ __device__ __forceinline__ void fft_pass(float2 (&v)[16], const float2 *src, flo
 #pragma unroll
       for (int a = 0; a < R; ++a) v[s * R + a] = src[padi(P * MI + a * MP + j)];
     }
+  } else if constexpr (R < 16) {
+    float2 t[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) t[i] = v[i];
+#pragma unroll
+    for (int s = 0; s < 16 / R; ++s)
+#pragma unroll
+      for (int a = 0; a < R; ++a) v[s * R + a] = t[s + (16 / R) * a];
   }
 #pragma unroll
   for (int s = 0; s < 16 / R; ++s) dft_r<R>(&v[s * R]);
   if constexpr (!LAST) {
-    static_assert(R == 16, "only the last pass may have a radix below 16");
     if constexpr (I == 0) {
+      // W_N^(d p) of butterfly s, output p >= 1
 #pragma unroll
-      for (int p = 1; p < 16; ++p) v[p] = cmul(v[p], tw0[p - 1]);
+      for (int s = 0; s < 16 / R; ++s)
+#pragma unroll
+        for (int p = 1; p < R; ++p) v[s * R + p] = cmul(v[s * R + p], tw0[s * (R - 1) + p - 1]);
     } else {
       const int j = tau % MP;
-      const float2 *t = twr + (PL::tw_off(I) - 15 * (N / 16));
+      const float2 *t = twr + (PL::tw_off(I) - PL::tw_off(1));
 #pragma unroll
       for (int p = 1; p < 16; ++p) v[p] = cmul(v[p], t[(p - 1) * MP + j]);
     }
   }
 }
 
-template <int N, int I>
+// Stores pass I's outputs: output p of sub-problem P becomes element P MP + j
+// of sub-problem P + lprev(I) p.  With radix 16 that is slot tau + (N/16) p
+// for v[p]; a radix-r first pass stores v[s r + p] at p N/r + tau + (N/16) s.
+template <int N, int S, int I>
 __device__ __forceinline__ void store_pass(const float2 (&v)[16], float2 *dst, int tau) {
-  constexpr int NR = N / 16;
+  using PL = Plan<N, S>;
+  constexpr int NR = N / 16, R = PL::radix(I);
+  if constexpr (R == 16) {
 #pragma unroll
-  for (int p = 0; p < 16; ++p) dst[padi(tau + p * NR)] = v[p];
+    for (int p = 0; p < 16; ++p) dst[padi(tau + p * NR)] = v[p];
+  } else {
+    static_assert(I == 0, "a radix below 16 stores only as the first pass");
+#pragma unroll
+    for (int s = 0; s < 16 / R; ++s)
+#pragma unroll
+      for (int p = 0; p < R; ++p) dst[padi(p * (N / R) + tau + NR * s)] = v[s * R + p];
+  }
 }
 
 // Exchange buffers: two (ping-pong, one barrier per pass) unless they would
 // not fit next to the input stages, then one (two barriers per pass).
-template <int N, bool TMA>
+template <int N, int S, bool TMA>
 struct Smem {
-  using PL = Plan<N>;
+  using PL = Plan<N, S>;
   static constexpr size_t STAGE = TMA ? (size_t)PL::FPB * N : 0;   // complex in the input stage
   static constexpr size_t XB = (size_t)PL::FPB * PL::SLOT;         // complex per exchange buffer
   static constexpr size_t FIXED = (size_t)PL::TW_REST * 8 + 260 * 4;
@@ -246,12 +284,12 @@ __device__ __forceinline__ float2 to_f2(short2 s) {
   return make_float2((float)s.x * 3.0517578125e-05f, (float)s.y * 3.0517578125e-05f);
 }
 
-template <int N, int MODE, bool TMA, typename IN>
+template <int N, int S, int MODE, bool TMA, typename IN>
 __device__ __forceinline__ bool stft_frames(const StftArgs &a, int64_t f_begin, int64_t f_end,
                                             float2 *smem, float *red, uint64_t *bar) {
   const IN *iq = static_cast<const IN *>(a.iq);
-  using PL = Plan<N>;
-  using SM = Smem<N, TMA>;
+  using PL = Plan<N, S>;
+  using SM = Smem<N, S, TMA>;
   constexpr int TPF = PL::TPF, FPB = PL::FPB, SLOT = PL::SLOT, NPASS = PL::NPASS, NXB = SM::NXB;
   constexpr bool DO_MAX = (MODE == STFT_MAX || MODE == STFT_POWER);
   constexpr bool DO_Q = (MODE == STFT_QUANT || MODE == STFT_QUANT_POWER);
@@ -296,9 +334,18 @@ __device__ __forceinline__ bool stft_frames(const StftArgs &a, int64_t f_begin, 
   float2 tw0[15];
 #pragma unroll
   for (int i = 0; i < 16; ++i) win[i] = __ldg(&a.win[i * (N / 16) + tau]);
+  {
+    // pass 0: W_N^(d p) of butterfly d = tau + (N/16) s, table [15][N / r0]
+    constexpr int R0 = PL::radix(0), MP0 = PL::mp(0);
 #pragma unroll
-  for (int p = 1; p < 16; ++p) tw0[p - 1] = __ldg(&a.tw[(p - 1) * (N / 16) + tau]);
-  for (int i = tid; i < PL::TW_REST; i += PL::THREADS) twr[i] = a.tw[15 * (N / 16) + i];
+    for (int s = 0; s < 16 / R0; ++s)
+#pragma unroll
+      for (int p = 1; p < R0; ++p)
+        tw0[s * (R0 - 1) + p - 1] = __ldg(&a.tw[(p - 1) * MP0 + tau + (N / 16) * s]);
+#pragma unroll
+    for (int i = PL::TW0; i < 15; ++i) tw0[i] = make_float2(0.f, 0.f);
+  }
+  for (int i = tid; i < PL::TW_REST; i += PL::THREADS) twr[i] = a.tw[PL::tw_off(1) + i];
   float inv_anchor = 0.f, c1 = 0.f;
   if constexpr (DO_Q) {
     for (int i = tid; i < 257; i += PL::THREADS) edges[i] = a.edges[i];
@@ -335,8 +382,8 @@ __device__ __forceinline__ bool stft_frames(const StftArgs &a, int64_t f_begin, 
     float2 *b0 = (parity ? xb1 : xb0) + slot * SLOT;
     float2 *b1 = (parity ? xb0 : xb1) + slot * SLOT;
     if constexpr (NXB == 1) __syncthreads();   // previous frame's last reads done
-    fft_pass<N, 0, true>(v, nullptr, b0, tau, tw0, twr);
-    store_pass<N, 0>(v, b0, tau);
+    fft_pass<N, S, 0, true>(v, nullptr, b0, tau, tw0, twr);
+    store_pass<N, S, 0>(v, b0, tau);
     if (__syncthreads_or(failed)) {
       // a staged copy never arrived: record it, let copies in flight land, leave
       if (tid == 0) {
@@ -352,17 +399,17 @@ __device__ __forceinline__ bool stft_frames(const StftArgs &a, int64_t f_begin, 
       }
     }
     if constexpr (NPASS >= 2) {
-      fft_pass<N, 1, false>(v, b0, b1, tau, tw0, twr);
+      fft_pass<N, S, 1, false>(v, b0, b1, tau, tw0, twr);
       if constexpr (NPASS >= 3) {
         if constexpr (NXB == 1) __syncthreads();
-        store_pass<N, 1>(v, b1, tau);
+        store_pass<N, S, 1>(v, b1, tau);
         __syncthreads();
-        fft_pass<N, 2, false>(v, b1, b0, tau, tw0, twr);
+        fft_pass<N, S, 2, false>(v, b1, b0, tau, tw0, twr);
         if constexpr (NPASS >= 4) {
           if constexpr (NXB == 1) __syncthreads();
-          store_pass<N, 2>(v, b0, tau);
+          store_pass<N, S, 2>(v, b0, tau);
           __syncthreads();
-          fft_pass<N, 3, false>(v, b0, b1, tau, tw0, twr);
+          fft_pass<N, S, 3, false>(v, b0, b1, tau, tw0, twr);
         }
       }
     }
@@ -399,23 +446,23 @@ __device__ __forceinline__ bool stft_frames(const StftArgs &a, int64_t f_begin, 
   return true;
 }
 
-template <int N, int MODE, bool TMA, typename IN>
-__global__ void __launch_bounds__(Plan<N>::THREADS, (Smem<N, TMA>::BLOCKS))
+template <int N, int S, int MODE, bool TMA, typename IN>
+__global__ void __launch_bounds__(Plan<N, S>::THREADS, (Smem<N, S, TMA>::BLOCKS))
 stft_kernel(StftArgs a, int64_t frames_per_block) {
   extern __shared__ __align__(128) float2 smem[];
   __shared__ float red[32];
   __shared__ __align__(8) uint64_t bar;
   const int64_t f_begin = (int64_t)blockIdx.x * frames_per_block;
   const int64_t f_end = min(a.T, f_begin + frames_per_block);
-  stft_frames<N, MODE, TMA, IN>(a, f_begin, f_end, smem, red, &bar);
+  stft_frames<N, S, MODE, TMA, IN>(a, f_begin, f_end, smem, red, &bar);
 }
 
 // Many captures of one FFT size in one launch: a persistent grid whose
 // blocks take (capture, frame range) items from a shared counter until none
 // are left, so uneven captures balance across the SMs.  Items come sorted by
 // size, largest first.
-template <int N, int MODE, bool TMA>
-__global__ void __launch_bounds__(Plan<N>::THREADS, (Smem<N, TMA>::BLOCKS))
+template <int N, int S, int MODE, bool TMA>
+__global__ void __launch_bounds__(Plan<N, S>::THREADS, (Smem<N, S, TMA>::BLOCKS))
 stft_batch_kernel(const StftArgs *segs, const StftItem *items, int n_items, int *counter) {
   extern __shared__ __align__(128) float2 smem[];
   __shared__ float red[32];
@@ -437,18 +484,18 @@ stft_batch_kernel(const StftArgs *segs, const StftItem *items, int n_items, int 
       __syncthreads();
       continue;
     }
-    const bool ok = stft_frames<N, MODE, TMA, float2>(sa, item.f0, item.f1, smem, red, &bar);
+    const bool ok = stft_frames<N, S, MODE, TMA, float2>(sa, item.f0, item.f1, smem, red, &bar);
     if (!ok) return;   // uniform over the block
     __syncthreads();   // every wait on the barrier and every read of sa is done
     if (TMA && threadIdx.x == 0) mbar_inval(&bar);
   }
 }
 
-template <int N, int MODE, bool TMA, typename IN>
+template <int N, int S, int MODE, bool TMA, typename IN>
 cudaError_t launch_n(const StftArgs &a, int num_sms, cudaStream_t s) {
-  using PL = Plan<N>;
-  auto kern = stft_kernel<N, MODE, TMA, IN>;
-  const size_t sm = Smem<N, TMA>::BYTES;
+  using PL = Plan<N, S>;
+  auto kern = stft_kernel<N, S, MODE, TMA, IN>;
+  const size_t sm = Smem<N, S, TMA>::BYTES;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int occ = 0;
@@ -465,23 +512,23 @@ cudaError_t launch_n(const StftArgs &a, int num_sms, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int N, bool TMA, typename IN>
+template <int N, int S, bool TMA, typename IN>
 cudaError_t launch_mode(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s) {
   switch (mode) {
-    case STFT_MAX: return launch_n<N, STFT_MAX, TMA, IN>(a, num_sms, s);
-    case STFT_QUANT: return launch_n<N, STFT_QUANT, TMA, IN>(a, num_sms, s);
-    case STFT_POWER: return launch_n<N, STFT_POWER, TMA, IN>(a, num_sms, s);
-    case STFT_QUANT_POWER: return launch_n<N, STFT_QUANT_POWER, TMA, IN>(a, num_sms, s);
+    case STFT_MAX: return launch_n<N, S, STFT_MAX, TMA, IN>(a, num_sms, s);
+    case STFT_QUANT: return launch_n<N, S, STFT_QUANT, TMA, IN>(a, num_sms, s);
+    case STFT_POWER: return launch_n<N, S, STFT_POWER, TMA, IN>(a, num_sms, s);
+    case STFT_QUANT_POWER: return launch_n<N, S, STFT_QUANT_POWER, TMA, IN>(a, num_sms, s);
   }
   return cudaErrorInvalidValue;
 }
 
-template <int N, int MODE, bool TMA>
+template <int N, int S, int MODE, bool TMA>
 cudaError_t launch_batch_n(const StftArgs *segs, const StftItem *items, int n_items, int *counter,
                            int num_sms, cudaStream_t s) {
-  using PL = Plan<N>;
-  auto kern = stft_batch_kernel<N, MODE, TMA>;
-  const size_t sm = Smem<N, TMA>::BYTES;
+  using PL = Plan<N, S>;
+  auto kern = stft_batch_kernel<N, S, MODE, TMA>;
+  const size_t sm = Smem<N, S, TMA>::BYTES;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int occ = 0;
@@ -495,68 +542,102 @@ cudaError_t launch_batch_n(const StftArgs *segs, const StftItem *items, int n_it
   return cudaGetLastError();
 }
 
-template <int N, bool TMA>
+template <int N, int S, bool TMA>
 cudaError_t batch_mode(StftMode mode, const StftArgs *segs, const StftItem *items, int n_items,
                        int *counter, int num_sms, cudaStream_t s) {
   switch (mode) {
-    case STFT_MAX: return launch_batch_n<N, STFT_MAX, TMA>(segs, items, n_items, counter, num_sms, s);
-    case STFT_QUANT: return launch_batch_n<N, STFT_QUANT, TMA>(segs, items, n_items, counter, num_sms, s);
-    case STFT_POWER: return launch_batch_n<N, STFT_POWER, TMA>(segs, items, n_items, counter, num_sms, s);
+    case STFT_MAX: return launch_batch_n<N, S, STFT_MAX, TMA>(segs, items, n_items, counter, num_sms, s);
+    case STFT_QUANT: return launch_batch_n<N, S, STFT_QUANT, TMA>(segs, items, n_items, counter, num_sms, s);
+    case STFT_POWER: return launch_batch_n<N, S, STFT_POWER, TMA>(segs, items, n_items, counter, num_sms, s);
     case STFT_QUANT_POWER:
-      return launch_batch_n<N, STFT_QUANT_POWER, TMA>(segs, items, n_items, counter, num_sms, s);
+      return launch_batch_n<N, S, STFT_QUANT_POWER, TMA>(segs, items, n_items, counter, num_sms, s);
   }
   return cudaErrorInvalidValue;
 }
 
-template <int N>
+template <int N, int S>
 cudaError_t batch_size(bool tma, StftMode mode, const StftArgs *segs, const StftItem *items,
                        int n_items, int *counter, int num_sms, cudaStream_t s) {
-  return tma ? batch_mode<N, true>(mode, segs, items, n_items, counter, num_sms, s)
-             : batch_mode<N, false>(mode, segs, items, n_items, counter, num_sms, s);
+  return tma ? batch_mode<N, S, true>(mode, segs, items, n_items, counter, num_sms, s)
+             : batch_mode<N, S, false>(mode, segs, items, n_items, counter, num_sms, s);
 }
 
-template <int N, typename IN>
+template <int N, int S, typename IN>
 cudaError_t launch_size(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s) {
   // staged input needs every copy 16-byte aligned: hop * sample size a
   // multiple of 16 bytes and a 16-byte aligned base
   const bool tma = ((int64_t)a.hop * (int64_t)sizeof(IN)) % 16 == 0 &&
                    ((reinterpret_cast<uintptr_t>(a.iq) & 15) == 0);
-  return tma ? launch_mode<N, true, IN>(a, mode, num_sms, s) : launch_mode<N, false, IN>(a, mode, num_sms, s);
+  return tma ? launch_mode<N, S, true, IN>(a, mode, num_sms, s) : launch_mode<N, S, false, IN>(a, mode, num_sms, s);
 }
 
-template <int N, typename IN, bool TMA>
+template <int N, int S, typename IN, bool TMA>
 void preload_stft_nt() {
-  preload_kernel(stft_kernel<N, STFT_MAX, TMA, IN>);
-  preload_kernel(stft_kernel<N, STFT_QUANT, TMA, IN>);
-  preload_kernel(stft_kernel<N, STFT_POWER, TMA, IN>);
-  preload_kernel(stft_kernel<N, STFT_QUANT_POWER, TMA, IN>);
+  preload_kernel(stft_kernel<N, S, STFT_MAX, TMA, IN>);
+  preload_kernel(stft_kernel<N, S, STFT_QUANT, TMA, IN>);
+  preload_kernel(stft_kernel<N, S, STFT_POWER, TMA, IN>);
+  preload_kernel(stft_kernel<N, S, STFT_QUANT_POWER, TMA, IN>);
   if constexpr (std::is_same<IN, float2>::value) {
-    preload_kernel(stft_batch_kernel<N, STFT_MAX, TMA>);
-    preload_kernel(stft_batch_kernel<N, STFT_QUANT, TMA>);
-    preload_kernel(stft_batch_kernel<N, STFT_POWER, TMA>);
-    preload_kernel(stft_batch_kernel<N, STFT_QUANT_POWER, TMA>);
+    preload_kernel(stft_batch_kernel<N, S, STFT_MAX, TMA>);
+    preload_kernel(stft_batch_kernel<N, S, STFT_QUANT, TMA>);
+    preload_kernel(stft_batch_kernel<N, S, STFT_POWER, TMA>);
+    preload_kernel(stft_batch_kernel<N, S, STFT_QUANT_POWER, TMA>);
   }
 }
-template <typename IN>
+template <int N, int S, typename IN>
+void preload_stft_n() {
+  if constexpr (S == 0 || sched_distinct(N, S)) {
+    preload_stft_nt<N, S, IN, false>();
+    preload_stft_nt<N, S, IN, true>();
+  }
+}
+template <typename IN, int S>
 void preload_stft_in() {
-  preload_stft_nt<256, IN, false>();  preload_stft_nt<256, IN, true>();
-  preload_stft_nt<512, IN, false>();  preload_stft_nt<512, IN, true>();
-  preload_stft_nt<1024, IN, false>(); preload_stft_nt<1024, IN, true>();
-  preload_stft_nt<2048, IN, false>(); preload_stft_nt<2048, IN, true>();
-  preload_stft_nt<4096, IN, false>(); preload_stft_nt<4096, IN, true>();
-  preload_stft_nt<8192, IN, false>(); preload_stft_nt<8192, IN, true>();
+  preload_stft_n<256, S, IN>();
+  preload_stft_n<512, S, IN>();
+  preload_stft_n<1024, S, IN>();
+  preload_stft_n<2048, S, IN>();
+  preload_stft_n<4096, S, IN>();
+  preload_stft_n<8192, S, IN>();
 }
 
-// the launch for the input type IN, by FFT size
-template <typename IN>
+// The launch for the input type IN and schedule S, by FFT size; a size
+// whose schedule S equals schedule 0 runs schedule 0's kernels.
+template <int N, int S, typename IN>
+cudaError_t launch_sized(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s) {
+  if constexpr (S == 0 || sched_distinct(N, S)) return launch_size<N, S, IN>(a, mode, num_sms, s);
+  else return cudaErrorInvalidValue;
+}
+template <typename IN, int S>
 cudaError_t launch_stft_in(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s) {
   switch (a.N) {
-    case 256: return launch_size<256, IN>(a, mode, num_sms, s);
-    case 512: return launch_size<512, IN>(a, mode, num_sms, s);
-    case 1024: return launch_size<1024, IN>(a, mode, num_sms, s);
-    case 2048: return launch_size<2048, IN>(a, mode, num_sms, s);
-    case 4096: return launch_size<4096, IN>(a, mode, num_sms, s);
-    case 8192: return launch_size<8192, IN>(a, mode, num_sms, s);
+    case 256: return launch_sized<256, S, IN>(a, mode, num_sms, s);
+    case 512: return launch_sized<512, S, IN>(a, mode, num_sms, s);
+    case 1024: return launch_sized<1024, S, IN>(a, mode, num_sms, s);
+    case 2048: return launch_sized<2048, S, IN>(a, mode, num_sms, s);
+    case 4096: return launch_sized<4096, S, IN>(a, mode, num_sms, s);
+    case 8192: return launch_sized<8192, S, IN>(a, mode, num_sms, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// The batch launch of schedule S, by FFT size.
+template <int N, int S>
+cudaError_t batch_sized(bool tma, StftMode mode, const StftArgs *segs, const StftItem *items, int n_items,
+                        int *counter, int num_sms, cudaStream_t s) {
+  if constexpr (S == 0 || sched_distinct(N, S)) return batch_size<N, S>(tma, mode, segs, items, n_items, counter, num_sms, s);
+  else return cudaErrorInvalidValue;
+}
+template <int S>
+cudaError_t launch_stft_batch_s(int N, bool tma, StftMode mode, const StftArgs *segs, const StftItem *items,
+                                int n_items, int *counter, int num_sms, cudaStream_t s) {
+  switch (N) {
+    case 256: return batch_sized<256, S>(tma, mode, segs, items, n_items, counter, num_sms, s);
+    case 512: return batch_sized<512, S>(tma, mode, segs, items, n_items, counter, num_sms, s);
+    case 1024: return batch_sized<1024, S>(tma, mode, segs, items, n_items, counter, num_sms, s);
+    case 2048: return batch_sized<2048, S>(tma, mode, segs, items, n_items, counter, num_sms, s);
+    case 4096: return batch_sized<4096, S>(tma, mode, segs, items, n_items, counter, num_sms, s);
+    case 8192: return batch_sized<8192, S>(tma, mode, segs, items, n_items, counter, num_sms, s);
   }
   return cudaErrorInvalidValue;
 }

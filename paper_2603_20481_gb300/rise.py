@@ -34,7 +34,7 @@ STAGES = ("spectrum_pass1", "spectrum_pass2", "histogram", "column_stats", "morp
           "labelling", "readback", "total")
 OPT_KEEP_POWER, OPT_KEEP_MASKS, OPT_TIMING, OPT_RANGE_PATH = 1, 2, 3, 4
 OPT_GRAPH, OPT_AUTOTUNE, OPT_RUN_CAPACITY = 5, 6, 7
-OPT_SCAN_WAIT_LIMIT, OPT_UNION_LIMIT, OPT_TEST_WITHHOLD = 8, 9, 10
+OPT_SCAN_WAIT_LIMIT, OPT_UNION_LIMIT, OPT_TEST_WITHHOLD, OPT_FFT_SCHEDULE = 8, 9, 10, 11
 IQ_HOST, IQ_SC16 = 1, 2
 OPT_BATCH_GRAPH = OPT_GRAPH
 BATCH_MAX_ROWS = 524280
@@ -469,7 +469,8 @@ class Detector:
         return v
 
     def batch_info(self) -> np.ndarray:
-        v = np.zeros(16, np.int64)
+        """The last batch's launch parameters (RISE_DBG_BATCH_INFO, int64[64])."""
+        v = np.zeros(64, np.int64)
         rc = lib().rise_debug_export(self._h, DBG_BATCH_INFO, v.ctypes.data, v.nbytes)
         if rc != RISE_OK:
             raise RiseError(rc, "rise_debug_export")

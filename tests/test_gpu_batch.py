@@ -61,7 +61,14 @@ def _batch(count, seed0, n_range=(1 << 13, 1 << 18), sizes=(256, 512, 1024, 2048
 
 
 def _plain(det, xs, Ns, hops, thr=None):
-    return [det.detect(x, N, h, thr) for x, N, h in zip(xs, Ns, hops)]
+    """One rise_detect per capture, each with the radix schedule the context's
+    last batch ran for its FFT size (the two schedules round differently)."""
+    from paper_2603_20481_gb300 import rise
+    det.set_option(rise.OPT_FFT_SCHEDULE, -1)
+    try:
+        return [det.detect(x, N, h, thr) for x, N, h in zip(xs, Ns, hops)]
+    finally:
+        det.set_option(rise.OPT_FFT_SCHEDULE, 1)
 
 
 def _check(boxes, offs, want):
@@ -165,14 +172,21 @@ def test_switches_give_the_same_boxes(det):
     Ns = [c.fft_size for c in caps]
     hops = [c.hop for c in caps]
     ref, ro = det.detect_batch(xs, Ns, hops)
+    ref_sched = det.batch_info()
+    G = int(ref_sched[0])
+    ref_sched = list(ref_sched[3 + G:3 + 3 * G])
     for graph, tune in ((0, 0), (0, 1), (1, 0)):
         with rise.Detector(0) as d2:
             d2.set_option(rise.OPT_BATCH_GRAPH, graph)
             d2.set_option(rise.OPT_AUTOTUNE, tune)
             for _ in range(2):
                 b, o = d2.detect_batch(xs, Ns, hops)
-                np.testing.assert_array_equal(o, ro)
-                np.testing.assert_array_equal(b, ref)
+                info = d2.batch_info()
+                if list(info[3 + G:3 + 3 * G]) == ref_sched:   # same radix schedules: same bits
+                    np.testing.assert_array_equal(o, ro)
+                    np.testing.assert_array_equal(b, ref)
+                else:
+                    _oracle_check(d2, xs, Ns, hops, b, o)
             assert d2.batch_info()[1] == graph
 
 
@@ -224,6 +238,41 @@ def test_many_uneven_captures(det):
     boxes, offs = det.detect_batch(xs, Ns, hops)
     _oracle_check(det, xs, Ns, hops, boxes, offs)
     _check(boxes, offs, _plain(det, xs, Ns, hops))
+
+
+def test_tune_cache_is_read_by_a_new_context(tmp_path, monkeypatch):
+    """With RISE_TUNE_CACHE set, the first context tunes the composition and
+    appends one line; a second context runs it from the file without tuning;
+    a cached line asking for radix schedule 1 in every group is run as
+    written and still matches the oracle."""
+    from paper_2603_20481_gb300 import rise
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("RISE_TUNE_CACHE", str(path))
+    caps = _batch(10, 7800, n_range=(1 << 14, 1 << 17), sizes=(512, 1024, 2048))
+    xs = _to_gpu(caps)
+    Ns = [c.fft_size for c in caps]
+    hops = [c.hop for c in caps]
+    with rise.Detector(0) as d1:
+        b1, o1 = d1.detect_batch(xs, Ns, hops)
+        assert d1.batch_info()[63] == 0
+    lines = path.read_text().splitlines()
+    assert len(lines) == 1 and lines[0].startswith("rise-tune 1 ")
+    with rise.Detector(0) as d2:
+        b2, o2 = d2.detect_batch(xs, Ns, hops)
+        assert d2.batch_info()[63] == 1                  # from the file, no tuning
+    assert path.read_text().splitlines() == lines
+    np.testing.assert_array_equal(b2, b1)
+    np.testing.assert_array_equal(o2, o1)
+    f = lines[0].split()
+    G = int(f[4])
+    f[5 + G:5 + 2 * G] = ["1"] * G
+    path.write_text(" ".join(f) + "\n")
+    with rise.Detector(0) as d3:
+        b3, o3 = d3.detect_batch(xs, Ns, hops)
+        info = d3.batch_info()
+        assert int(info[0]) == G and all(info[3 + G:3 + 2 * G] == 1)
+        assert sorted(set(int(v) for v in info[3 + 2 * G:3 + 3 * G])) == [512, 1024, 2048]
+        _oracle_check(d3, xs, Ns, hops, b3, o3)
 
 
 def test_intermediates_are_dropped_by_the_next_call(det):

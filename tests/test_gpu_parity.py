@@ -101,6 +101,31 @@ def test_spectrogram_and_image_parity(det, N, hop, n, fs, seed):
         assert np.array_equal(boxes_g, boxes_r)
 
 
+@pytest.mark.parametrize("N,hop,n,fs,seed", [c for c in STFT_CASES if c[0] in (512, 1024, 2048, 8192)])
+def test_radix_schedule_0_matches_the_oracle(det, N, hop, n, fs, seed):
+    """The other radix schedule (the radix-r pass last) under the same bars."""
+    rise = _rise()
+    cap = synth.make_capture(n, fs, 6, 500 + seed, fft_size=N, hop=hop,
+                             bw_hz=(fs / 200, fs / 20), dur_s=(n / fs / 20, n / fs / 3),
+                             snr_db=(5, 25), tone_fraction=0.3)
+    T = oracle.num_frames(n, N, hop)
+    det.set_option(rise.OPT_FFT_SCHEDULE, 0)
+    try:
+        boxes_g = _gpu_detect(det, cap.iq, N, hop)
+        Pg = det.debug(rise.DBG_POWER_F32, T, N)
+        qg = det.debug(rise.DBG_IMAGE_U8, T, N)
+        Mg = float(det.debug(rise.DBG_MAXPOW, T, N)[0])
+    finally:
+        det.set_option(rise.OPT_FFT_SCHEDULE, 1)   # the default
+    _check_power(Pg, oracle.stft_power(cap.iq, N, hop))
+    q_same = oracle.quantize(Pg.astype(np.float64), oracle.hi_db_of(Mg))
+    assert np.array_equal(q_same, qg)
+    _, qr, Mr = oracle.detect(cap.iq, N, hop)
+    assert abs(Mg - Mr) <= 1e-5 * Mr
+    _check_image(qg, qr)
+    assert np.array_equal(boxes_g, oracle.detect_image(qg))
+
+
 def test_image_level_mismatch_rate(det):
     """At most 1e-5 of pixels may differ by one 8-bit level from the FP64
     oracle (the fp32 FFT's rounding puts a few pixels on the other side of a

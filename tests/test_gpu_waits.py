@@ -94,11 +94,13 @@ def test_waits_run_out_on_the_capture_and_batch_paths():
     Ns = [c.fft_size for c in caps]
     hops = [c.hop for c in caps]
     with rise.Detector(0) as ref:
+        ref.set_option(rise.OPT_AUTOTUNE, 0)         # fixed launch shapes and schedules in both
         want = ref.detect(x, 1024, 512)
         want_b, want_o = ref.detect_batch(xs, Ns, hops)
         runs = int(ref.debug(rise.DBG_CCL, 0, 0)[0])
     assert runs > 2048                                 # the batch's scan has a second tile
     with rise.Detector(0) as d:
+        d.set_option(rise.OPT_AUTOTUNE, 0)
         d.detect(x, 1024, 512)
         d.set_option(rise.OPT_SCAN_WAIT_LIMIT, 64)
         d.set_option(rise.OPT_TEST_WITHHOLD, 0)
