@@ -291,6 +291,8 @@ def measure_single(args, name: str):
     det = rise.Detector(local)
     if args.range_path:
         det.set_option(rise.OPT_RANGE_PATH, args.range_path)
+    if args.fft_schedule >= 0:
+        det.set_option(rise.OPT_FFT_SCHEDULE, args.fft_schedule)
     det.set_option(rise.OPT_TIMING, 1)
     stream = det.stream          # the stream the library launches on
     for _ in range(args.warmup):
@@ -395,6 +397,7 @@ def measure_single(args, name: str):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload, "n_samples": n, "fft_size": N_FFT, "hop": HOP,
                    "frames": T, "boxes": n_boxes, "range_path": path,
+                   "fft_schedule": args.fft_schedule if args.fft_schedule >= 0 else "library default (1)",
                    "l2": f"inputs larger than L2 ({8 * n >> 20} MiB capture per step)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roof,
@@ -459,7 +462,8 @@ def _served_summary(r):
         return {"saturation_chunks_per_s": m["saturation_chunks_per_s"],
                 "saturation_ms_s": m["saturation_ms_s"],
                 "by_load": [{k: x[k] for k in ("rho", "offered_chunks_per_s", "completed", "rejected",
-                                                "p50_ms", "p99_ms", "max_ms", "deadline_miss_frac")}
+                                                "p50_ms", "p99_ms", "max_ms", "deadline_miss_frac",
+                                                "p99_from_arrival_ms", "submit_lag_p99_ms")}
                             for x in m["by_load"]]}
     return {"workload": r["config"]["workload"], "lanes": r["config"]["lanes"],
             "max_batch": r["config"]["max_batch"], "value": r["value"], "unit": UNIT,
@@ -615,6 +619,8 @@ def measure_batched(args):
         "config": {"workload": BATCH_WORKLOAD, "captures": len(xs), "n_samples": n_total,
                    "pixels": px_total, "stft_groups": int(info[0]),
                    "tuned": [int(v) for v in info[2:3 + int(info[0])]],
+                   "stft_groups_fft_size": [int(v) for v in info[3 + 2 * int(info[0]):3 + 3 * int(info[0])]],
+                   "stft_groups_radix_schedule": [int(v) for v in info[3 + int(info[0]):3 + 2 * int(info[0])]],
                    "graph_replay": bool(info[1]),
                    "l2": f"inputs larger than L2 ({8 * n_total >> 20} MiB per step)",
                    "parallelism": f"replicas x{world}"},
@@ -659,42 +665,61 @@ def _gen_chunk(args):
 
 def _serve_run(srv, pinned, arrivals, limit_s):
     """Submits chunk i at arrivals[i] (seconds from start; None: as fast as the
-    queue takes them) and collects results.  Returns latency samples (ms),
-    completed count, rejected count, elapsed seconds."""
+    queue takes them) and collects results.  Returns latency samples (ms,
+    done - submitted), completed count, rejected count, elapsed seconds; the
+    latencies from each chunk's scheduled arrival and the submitter's lag
+    behind the schedule (ms) go to _serve_run.from_arrival / .lag.  Python's
+    garbage collector is paused meanwhile, so that the load generator's own
+    pauses do not turn the Poisson arrivals into bursts."""
+    import gc
+
     import numpy as np
     lat, done, rejected, nbox = [], 0, 0, 0
+    from_arr, lag = [], []
     radios = len(pinned)
     per = len(pinned[0])
     nxt = [0] * radios
-    t0 = time.perf_counter()
-    i, n = 0, len(arrivals)
-    outstanding = 0
-    while True:
-        now = time.perf_counter() - t0
-        while i < n and (arrivals[i][0] is None or arrivals[i][0] <= now):
-            r = arrivals[i][1]
-            if arrivals[i][0] is None and outstanding >= 4 * 32 * 3:
-                break                      # closed loop: keep a bounded backlog
-            ok = srv.submit(r, pinned[r][nxt[r] % per], tag=i)
-            if ok:
-                nxt[r] += 1
-                outstanding += 1
-            else:
-                rejected += 1
-            i += 1
-        for d, bx in srv.poll(timeout_ms=0):
-            lat.append((d["t_done_ns"] - d["t_submit_ns"]) / 1e6)
-            nbox += len(bx)
-            done += 1
-            outstanding -= 1
-            if d["status"] != 0:
-                _serve_run.failed += 1
-        if i >= n and outstanding == 0:
-            break
-        if time.perf_counter() - t0 > limit_s:
-            break
-        time.sleep(0.0002)
+    gc.collect()
+    gc.disable()
+    try:
+        t0 = time.perf_counter()
+        i, n = 0, len(arrivals)
+        outstanding = 0
+        while True:
+            now = time.perf_counter() - t0
+            while i < n and (arrivals[i][0] is None or arrivals[i][0] <= now):
+                r = arrivals[i][1]
+                if arrivals[i][0] is None and outstanding >= 4 * 32 * 3:
+                    break                      # closed loop: keep a bounded backlog
+                ok = srv.submit(r, pinned[r][nxt[r] % per], tag=i)
+                if ok:
+                    nxt[r] += 1
+                    outstanding += 1
+                    if arrivals[i][0] is not None:
+                        lag.append((time.perf_counter() - t0 - arrivals[i][0]) * 1e3)
+                else:
+                    rejected += 1
+                i += 1
+            for d, bx in srv.poll(timeout_ms=0):
+                lat.append((d["t_done_ns"] - d["t_submit_ns"]) / 1e6)
+                a = arrivals[d["tag"]][0]
+                if a is not None:   # steady clock and perf_counter share CLOCK_MONOTONIC
+                    from_arr.append((d["t_done_ns"] / 1e9 - (t0 + a)) * 1e3)
+                nbox += len(bx)
+                done += 1
+                outstanding -= 1
+                if d["status"] != 0:
+                    _serve_run.failed += 1
+            if i >= n and outstanding == 0:
+                break
+            if time.perf_counter() - t0 > limit_s:
+                break
+            time.sleep(0.0002)
+    finally:
+        gc.enable()
     _serve_run.boxes = nbox
+    _serve_run.from_arrival = np.array(from_arr)
+    _serve_run.lag = np.array(lag)
     return np.array(lat), done, rejected, time.perf_counter() - t0
 
 
@@ -763,6 +788,7 @@ def measure_served(args, loads=(0.5, 0.75, 1.0, 1.25, 1.5)):
             radios = rng.integers(0, SERVE_RADIOS, size=count)
             arr = [(float(t), int(r)) for t, r in zip(times, radios)]
             lat, done, rej, dt = _serve_run(srv, pinned, arr, times[-1] + 10.0)
+            fa, lg = _serve_run.from_arrival, _serve_run.lag
             srv.drain(timeout_ms=30000)
             srv.poll(timeout_ms=0)
             out["by_load"].append({
@@ -772,7 +798,9 @@ def measure_served(args, loads=(0.5, 0.75, 1.0, 1.25, 1.5)):
                 "p50_ms": round(float(np.percentile(lat, 50)), 3) if len(lat) else None,
                 "p99_ms": round(float(np.percentile(lat, 99)), 3) if len(lat) else None,
                 "max_ms": round(float(lat.max()), 3) if len(lat) else None,
-                "deadline_miss_frac": round(float((lat > SERVE_PERIOD_MS).mean()), 4) if len(lat) else None})
+                "deadline_miss_frac": round(float((lat > SERVE_PERIOD_MS).mean()), 4) if len(lat) else None,
+                "p99_from_arrival_ms": round(float(np.percentile(fa, 99)), 3) if len(fa) else None,
+                "submit_lag_p99_ms": round(float(np.percentile(lg, 99)), 3) if len(lg) else None})
         out["stats"] = srv.stats()
         srv.close()
         return out
@@ -1086,6 +1114,8 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--samples", type=int, default=0, help="capture length (0: the workload's)")
     ap.add_argument("--range-path", type=int, default=0, choices=(0, 1, 2))
+    ap.add_argument("--fft-schedule", type=int, default=-1, choices=(-1, 0, 1),
+                    help="radix schedule of single captures (-1: the library's choice)")
     ap.add_argument("--ref-sample", type=int, default=1 << 23,
                     help="reference arm: samples per step (a prefix of the capture)")
     ap.add_argument("--no-e2e", action="store_true")
