@@ -25,11 +25,12 @@
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared (no fast-math), so
  * x86-64 and aarch64 give the same doubles.  With -fopenmp the independent
- * loops run on several host threads (frames of the STFT, column groups of the
- * histogram, columns of Otsu, rows of the mask and of each morphological
- * operation; the flood fill stays sequential).  Each thread computes whole
- * frames, columns or rows exactly as one thread would, and the only
- * reduction is a maximum, so the results do not depend on the thread count.
+ * loops run on several host threads (frames of the STFT, column groups of
+ * the histogram, columns of Otsu, rows of the mask and of each morphological
+ * operation; the flood fill stays sequential), small images on one thread.
+ * Each thread computes whole frames, columns or rows exactly as one thread
+ * would, and the only reduction is a maximum, so the results do not depend
+ * on the thread count.
  */
 #include <math.h>
 #include <stdint.h>
@@ -163,7 +164,7 @@ int ro_max_power(const float *iq, int64_t n, int N, int hop, double *out_max) {
   if (T < 1) return RO_EINVAL;
   double mx = 0.0;
   int err = RO_OK;
-#pragma omp parallel
+#pragma omp parallel if (T * (int64_t)N > 65536)
   {
     double *row = malloc(sizeof(double) * N);
 #pragma omp for reduction(max : mx) schedule(static)
@@ -218,7 +219,7 @@ void ro_energy_table(double level_db, uint64_t *E) {
 void ro_column_hist(const uint8_t *q, int64_t T, int F, uint32_t *hist) {
   memset(hist, 0, sizeof(uint32_t) * 256 * (size_t)F);
   /* groups of 64 columns, each counted by one thread over every row */
-#pragma omp parallel for schedule(dynamic, 1)
+#pragma omp parallel for schedule(dynamic, 1) if (T * (int64_t)F > 65536)
   for (int g = 0; g < F; g += 64) {
     const int ge = g + 64 < F ? g + 64 : F;
     for (int64_t t = 0; t < T; t++)
@@ -324,7 +325,7 @@ int ro_column_thresholds(const uint32_t *hist, int64_t T, int F, const ro_params
     if (Pq < 0) Pq = 0;
     if (Pq > 256) Pq = 256;
   }
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (F > 256)
   for (int f = 0; f < F; f++) {
     int keep = psd_on ? (D * S[f] >= N0 + dpsd) : 1;
     int th = ro_otsu(hist + (size_t)f * 256);
@@ -350,7 +351,7 @@ int ro_column_thresholds(const uint32_t *hist, int64_t T, int F, const ro_params
 
 /* Foreground: q[t][f] >= eff[f]  (eff = 256 -> none). Masks hold 0/1 bytes. */
 void ro_threshold(const uint8_t *q, int64_t T, int F, const int32_t *eff, uint8_t *mask) {
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (T * (int64_t)F > 65536)
   for (int64_t t = 0; t < T; t++)
     for (int f = 0; f < F; f++) mask[t * F + f] = (int32_t)q[t * F + f] >= eff[f];
 }
@@ -368,7 +369,7 @@ int ro_morph(const uint8_t *in, uint8_t *out, int64_t T, int F, int op) {
   int rt = (op == RO_DILATE3 || op == RO_ERODE3) ? 1 : 0;
   int erode = (op == RO_ERODE3 || op == RO_ERODE1x3);
   if (op < 0 || op > 3) return RO_EINVAL;
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (T * (int64_t)F > 65536)
   for (int64_t t = 0; t < T; t++) {
     for (int f = 0; f < F; f++) {
       int v = erode ? 1 : 0;
@@ -536,7 +537,7 @@ int ro_detect(const float *iq, int64_t n, int N, int hop, const ro_params *p, ro
   uint8_t *q = image_out ? image_out : malloc((size_t)T * N);
   if (!q) return RO_ENOMEM;
   int err = RO_OK;
-#pragma omp parallel
+#pragma omp parallel if (T * (int64_t)N > 65536)
   {
     double *row = malloc(sizeof(double) * N);
 #pragma omp for schedule(static)
