@@ -1114,7 +1114,7 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--samples", type=int, default=0, help="capture length (0: the workload's)")
     ap.add_argument("--range-path", type=int, default=0, choices=(0, 1, 2))
-    ap.add_argument("--fft-schedule", type=int, default=-1, choices=(-1, 0, 1),
+    ap.add_argument("--fft-schedule", type=int, default=-1, choices=(-1, 0, 1, 2),
                     help="radix schedule of single captures (-1: the library's choice)")
     ap.add_argument("--ref-sample", type=int, default=1 << 23,
                     help="reference arm: samples per step (a prefix of the capture)")

@@ -21,7 +21,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "librise.so")
 CHECKED_DIR = os.path.join(HERE, "_lib_checked")
 CHECKED_LIB = os.path.join(CHECKED_DIR, "librise_checked.so")
-SOURCES = ["stft.cu", "stft_s1.cu", "stft_sc16.cu", "image.cu", "ccl.cu", "rise.cu", "batch.cu",
+SOURCES = ["stft.cu", "stft_s1.cu", "stft_s2.cu", "stft_sc16.cu", "image.cu", "ccl.cu", "rise.cu", "batch.cu",
            "server.cu", "match.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -565,7 +565,7 @@ bool cache_lookup(const rise_ctx *c, uint64_t key, size_t ng, Tuned *out) {
     if (!unpack(v, ng, &t)) continue;
     bool ok = t.morph_wps >= 1 && t.morph_wps <= 64;
     for (size_t i = 0; i < ng; ++i)
-      ok = ok && t.item_mult[i] >= 1 && t.item_mult[i] <= 64 && (t.sched[i] == 0 || t.sched[i] == 1);
+      ok = ok && t.item_mult[i] >= 1 && t.item_mult[i] <= 64 && t.sched[i] >= 0 && t.sched[i] <= 2;
     if (ok) {
       *out = t;
       found = true;
@@ -634,22 +634,30 @@ int autotune(rise_ctx *c, const rise_capture *caps, Plan &p, const rise_threshol
     if (mm < best_m) { best_m = mm; pick_m = kMorphCands[r % 3]; }
   }
   // the radix schedule, one per FFT size (a size's groups differ only in
-  // their input staging): the faster total over the size's groups
+  // their input staging): each other schedule a size has is timed in one
+  // more run, and the size keeps the one with the smallest total over its
+  // groups
   std::vector<int> pick_s(ng, 0);
-  bool any = false;
-  for (size_t g = 0; g < ng; ++g) any = any || stft_sched_distinct(p.groups[g].N, 1);
-  if (rc == RISE_OK && any) {
+  std::map<int, float> best_n;   // FFT size -> total of its groups under its picked schedule
+  for (size_t g = 0; g < ng; ++g) best_n[p.groups[g].N] += best_g[g];
+  for (int alt = 1; alt <= 2 && rc == RISE_OK; ++alt) {
+    bool any = false;
+    for (size_t g = 0; g < ng; ++g) any = any || stft_sched_distinct(p.groups[g].N, alt);
+    if (!any) continue;
     p.item_mult = pick_g;
     p.morph_wps = pick_m;
-    for (size_t g = 0; g < ng; ++g) p.sched[g] = stft_sched_distinct(p.groups[g].N, 1) ? 1 : 0;
-    if ((rc = run_timed(&ms, &mm)) == RISE_OK) {
-      std::map<int, float> t0, t1;
-      for (size_t g = 0; g < ng; ++g) {
-        t0[p.groups[g].N] += best_g[g];
-        t1[p.groups[g].N] += ms[g];
+    for (size_t g = 0; g < ng; ++g) p.sched[g] = stft_sched_distinct(p.groups[g].N, alt) ? alt : pick_s[g];
+    if ((rc = run_timed(&ms, &mm)) != RISE_OK) break;
+    std::map<int, float> tot;
+    for (size_t g = 0; g < ng; ++g) tot[p.groups[g].N] += ms[g];
+    for (auto &kv : tot) {
+      bool has = false;
+      for (size_t g = 0; g < ng; ++g) has = has || (p.groups[g].N == kv.first && p.sched[g] == alt);
+      if (has && kv.second < best_n[kv.first]) {
+        best_n[kv.first] = kv.second;
+        for (size_t g = 0; g < ng; ++g)
+          if (p.groups[g].N == kv.first) pick_s[g] = alt;
       }
-      for (size_t g = 0; g < ng; ++g)
-        if (p.sched[g] == 1 && t1[p.groups[g].N] < t0[p.groups[g].N]) pick_s[g] = 1;
     }
   }
   for (auto &e : ev.e)

@@ -40,7 +40,6 @@ constexpr int SCAN_THREADS = 256, SCAN_ITEMS = 8, SCAN_BLOCK = SCAN_THREADS * SC
 // wait is bounded (ERR_SCAN).
 // ---------------------------------------------------------------------------
 constexpr uint64_t LB_AGG = 1ull << 62, LB_INC = 2ull << 62, LB_VAL = (1ull << 62) - 1;
-constexpr int LB_SPIN_LIMIT = 1 << 20;   // default; with 32 ns sleeps: about a second
 
 __device__ __forceinline__ uint64_t ld_acquire(const uint64_t *p) {
   uint64_t v;

@@ -86,6 +86,9 @@ __device__ __forceinline__ uint32_t run_ends(uint32_t w, uint32_t next_word) {
 // ERR_UNION_LIMIT and returns an ancestor, so every index stays in range.
 // ---------------------------------------------------------------------------
 constexpr int UF_LIMIT = 1 << 26;
+// Default bound of a single-pass scan's wait for a predecessor tile: polls
+// 32 ns apart, about a second in all.
+constexpr int SCAN_SPIN_LIMIT = 1 << 20;
 
 __device__ __forceinline__ int uf_find(int *parent, int x, DeviceStatus *st, int limit = UF_LIMIT) {
   for (int it = 0; it < limit; ++it) {
@@ -167,6 +170,7 @@ inline void preload_kernel(K k) {
 }
 void stft_preload();
 void stft_s1_preload();
+void stft_s2_preload();
 void stft_sc16_preload();
 void image_preload();
 void ccl_preload();
@@ -191,14 +195,17 @@ struct StftArgs {
   const float *win;       // per-N Hann window (device)
   uint32_t *err;          // device error word (ERR_* bits)
   int fmt;                // IqFormat
-  int sched;              // radix schedule of the tables tw (0: radix 16 first, 1: the small radix first)
+  int sched;              // radix schedule of the tables tw (0: radix-16 passes first, 1: the small radix
+                          // first, 2: the frame split into two half-size transforms)
 };
 
 enum StftMode { STFT_MAX = 0, STFT_QUANT = 1, STFT_POWER = 2, STFT_QUANT_POWER = 3 };
 cudaError_t launch_stft_sc16(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s);
-// Schedule 1 of complex64 input (its own translation unit).
+// Schedules 1 and 2 of complex64 input (their own translation units).
 cudaError_t launch_stft_s1(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s);
-// True when schedule S of size N is not schedule 0 (N is not a power of 16).
+cudaError_t launch_stft_s2(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s);
+// True when schedule S of size N exists apart from schedule 0: S = 1 for N
+// not a power of 16, S = 2 for N twice a power of 16.
 bool stft_sched_distinct(int N, int S);
 
 // ---------------------------------------------------------------------------
@@ -220,6 +227,8 @@ cudaError_t launch_stft_batch(int N, int sched, bool tma, StftMode mode, const S
                               const StftItem *items, int n_items, int *counter, int num_sms,
                               cudaStream_t s);
 cudaError_t launch_stft_batch_s1(int N, bool tma, StftMode mode, const StftArgs *segs, const StftItem *items,
+                                 int n_items, int *counter, int num_sms, cudaStream_t s);
+cudaError_t launch_stft_batch_s2(int N, bool tma, StftMode mode, const StftArgs *segs, const StftItem *items,
                                  int n_items, int *counter, int num_sms, cudaStream_t s);
 int stft_frames_per_step(int N);
 cudaError_t launch_levels_batch(CapSmall *cs, int ncap, double hi_power, int use_fixed,

@@ -106,7 +106,7 @@ struct rise_ctx {
   int graphs = 1, autotune = 1;
   // bounds of the device waits (defaults of the kernels) and the test-only
   // withheld root-scan tile (-1: none)
-  int spin_limit = 1 << 20, uf_limit = 1 << 26;
+  int spin_limit = rise::SCAN_SPIN_LIMIT, uf_limit = rise::UF_LIMIT;
   int64_t withhold_tile = -1;
   // radix schedule of single captures: 0 or 1 (default), or -1: the one the
   // batch tuner (or the tune cache) picked for the FFT size, else 1
@@ -128,7 +128,7 @@ struct rise_ctx {
   cudaStream_t copy_stream = nullptr;
   rise::host::CallSlot &cs() { return slot[cur]; }
   const rise::DeviceStatus *last_status = nullptr;   // status of the last finished call
-  std::map<int, rise::host::Tables> tables;   // key: FFT size * 2 + schedule
+  std::map<int, rise::host::Tables> tables;   // key: FFT size * 4 + schedule
   double energy_level_db = NAN;
   int sg_m = -1;
   // last call

@@ -96,7 +96,7 @@ int ensure_hbox(rise_ctx *c, int64_t cap) {
 
 int get_tables(rise_ctx *c, int N, int S, Tables **out) {
   if (!stft_sched_distinct(N, S)) S = 0;
-  const int key = N * 2 + S;
+  const int key = N * 4 + S;
   auto it = c->tables.find(key);
   if (it != c->tables.end()) {
     *out = &it->second;
@@ -686,6 +686,7 @@ int rise_create(rise_ctx **out, const rise_config *cfg) {
     if (!loaded.count(cfg->device) && cudaSetDevice(cfg->device) == cudaSuccess) {
       stft_preload();
       stft_s1_preload();
+      stft_s2_preload();
       stft_sc16_preload();
       image_preload();
       ccl_preload();
@@ -882,13 +883,13 @@ int rise_set_option(rise_ctx *c, int option, int64_t value) {
     case RISE_OPT_SCAN_WAIT_LIMIT:
       if (value < 0 || value > INT32_MAX) return RISE_EINVAL;
       CK(cudaSetDevice(c->device));
-      c->spin_limit = value ? (int)value : (1 << 20);
+      c->spin_limit = value ? (int)value : SCAN_SPIN_LIMIT;
       new_generation(c);
       return RISE_OK;
     case RISE_OPT_UNION_LIMIT:
       if (value < 0 || value > INT32_MAX) return RISE_EINVAL;
       CK(cudaSetDevice(c->device));
-      c->uf_limit = value ? (int)value : (1 << 26);
+      c->uf_limit = value ? (int)value : UF_LIMIT;
       new_generation(c);
       return RISE_OK;
     case RISE_OPT_TEST_WITHHOLD:
@@ -898,7 +899,7 @@ int rise_set_option(rise_ctx *c, int option, int64_t value) {
       new_generation(c);
       return RISE_OK;
     case RISE_OPT_FFT_SCHEDULE:
-      if (value < -1 || value > 1) return RISE_EINVAL;
+      if (value < -1 || value > 2) return RISE_EINVAL;
       c->fft_sched = (int)value;
       return RISE_OK;
   }

@@ -5,7 +5,9 @@
 // holding 16 values in registers.  N = 16^a * r (r in {1,2,4,8}): a radix-16
 // passes in registers (each thread one 16-point DFT) plus one pass of radix
 // r (each thread 16/r DFTs), the radix-r pass last (schedule 0) or first
-// (schedule 1, compiled in stft_s1.cu; the batch tuner times both).  Between
+// (schedule 1, compiled in stft_s1.cu); for r = 2, schedule 2 (stft_s2.cu)
+// splits the frame into two N/2-point transforms instead (see
+// stft_frames_split).  The batch tuner times them.  Between
 // passes the data cross shared memory once, in a layout padded by one slot
 // per 16 so that every 16-lane group
 // hits 16 distinct 8-byte bank pairs.  The decomposition is the
@@ -74,7 +76,29 @@ static std::vector<int> host_radices(int N, int S) {
   return r;
 }
 
+// Schedule 2 (N = 2M, M a power of 16): the tables of schedule 0 of size M,
+// then W_N^j for j < M/16, then the window of size N.
+static bool host_split(int N, int S) {
+  int l = 0;
+  while ((1 << l) < N) ++l;
+  return S == 2 && l % 4 == 1;
+}
+
+static size_t twiddle_complex(int N, int S) {
+  const std::vector<int> rad = host_radices(N, S);
+  size_t tw = 0;
+  int L = 1;
+  for (size_t i = 0; i + 1 < rad.size(); ++i) {
+    const int R = rad[i];
+    int Mi = N / L, Mp = Mi / R;
+    tw += 15 * (size_t)Mp;
+    L *= R;
+  }
+  return tw;
+}
+
 size_t stft_table_floats(int N, int S) {
+  if (host_split(N, S)) return 2 * (twiddle_complex(N / 2, 0) + (size_t)N / 32) + N;
   const std::vector<int> rad = host_radices(N, S);
   size_t tw = 0;
   int L = 1;
@@ -88,8 +112,20 @@ size_t stft_table_floats(int N, int S) {
 }
 
 void stft_fill_tables(int N, int S, float2 *tw, float *win) {
-  const std::vector<int> rad = host_radices(N, S);
   const double two_pi = 6.283185307179586476925286766559;
+  if (host_split(N, S)) {
+    const int M = N / 2;
+    std::vector<float> half(stft_table_floats(M, 0));
+    const size_t ntw = twiddle_complex(M, 0);
+    stft_fill_tables(M, 0, tw, half.data() + 2 * ntw);   // M's twiddles; its window is not used
+    for (int j = 0; j < M / 16; ++j) {
+      const double ang = two_pi * (double)j / (double)N;   // W_N^j
+      tw[ntw + j] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+    }
+    for (int m = 0; m < N; ++m) win[m] = (float)(0.5 - 0.5 * std::cos(two_pi * (double)m / (double)N));
+    return;
+  }
+  const std::vector<int> rad = host_radices(N, S);
   size_t off = 0;
   int L = 1;
   for (size_t i = 0; i + 1 < rad.size(); ++i) {
@@ -116,22 +152,27 @@ void stft_preload() {
 bool stft_sched_distinct(int N, int S) {
   int l = 0;
   while ((1 << l) < N) ++l;
-  return S == 1 && l % 4 != 0;
+  return (S == 1 && l % 4 != 0) || (S == 2 && l % 4 == 1);
 }
 
-// The kernels of schedule 1 (where it differs from schedule 0) live in
-// stft_s1.cu, the 16-bit input's in stft_sc16.cu.
+// The kernels of schedules 1 and 2 (where they differ from schedule 0) live
+// in stft_s1.cu and stft_s2.cu, the 16-bit input's in stft_sc16.cu.
 cudaError_t launch_stft(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s) {
   if (a.fmt == IQ_SC16) return launch_stft_sc16(a, mode, num_sms, s);
-  if (stft_sched_distinct(a.N, a.sched)) return launch_stft_s1(a, mode, num_sms, s);
+  if (stft_sched_distinct(a.N, a.sched)) {
+    if (a.sched == 1) return launch_stft_s1(a, mode, num_sms, s);
+    return launch_stft_s2(a, mode, num_sms, s);
+  }
   return launch_stft_in<float2, 0>(a, mode, num_sms, s);
 }
 
 cudaError_t launch_stft_batch(int N, int sched, bool tma, StftMode mode, const StftArgs *segs,
                               const StftItem *items, int n_items, int *counter, int num_sms,
                               cudaStream_t s) {
-  if (stft_sched_distinct(N, sched))
-    return launch_stft_batch_s1(N, tma, mode, segs, items, n_items, counter, num_sms, s);
+  if (stft_sched_distinct(N, sched)) {
+    if (sched == 1) return launch_stft_batch_s1(N, tma, mode, segs, items, n_items, counter, num_sms, s);
+    return launch_stft_batch_s2(N, tma, mode, segs, items, n_items, counter, num_sms, s);
+  }
   return launch_stft_batch_s<0>(N, tma, mode, segs, items, n_items, counter, num_sms, s);
 }
 

@@ -15,15 +15,20 @@ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
 
 // Radix schedule S of an N-point transform, N = 16^a * r (r in {1,2,4,8}):
 // S = 0 runs the a radix-16 passes first and the radix-r pass last; S = 1
-// runs the radix-r pass first (the same schedule as S = 0 when r = 1).
-constexpr bool sched_distinct(int N, int S) { return S == 1 && (ilog2c(N) % 4) != 0; }
+// runs the radix-r pass first (the same schedule as S = 0 when r = 1);
+// S = 2 (r = 2 only) splits the frame into two N/2-point transforms that
+// the two halves of the threads run side by side (see stft_frames_split).
+constexpr bool sched_split(int N, int S) { return S == 2 && (ilog2c(N) % 4) == 1; }
+constexpr bool sched_distinct(int N, int S) {
+  return (S == 1 && (ilog2c(N) % 4) != 0) || sched_split(N, S);
+}
 
 template <int N, int S = 0>
 struct Plan {
   static constexpr int LOG2N = ilog2c(N);
   static constexpr int NP16 = LOG2N / 4;
   static constexpr int RSMALL = 1 << (LOG2N % 4);
-  static constexpr bool SMALL_FIRST = sched_distinct(N, S);
+  static constexpr bool SMALL_FIRST = S == 1 && sched_distinct(N, S);
   static constexpr int NPASS = NP16 + (RSMALL > 1 ? 1 : 0);
   static constexpr int TPF = N / 16;                       // threads per frame
   static constexpr int FPB = TPF >= 256 ? 1 : 256 / TPF;   // frames per block step
@@ -264,13 +269,27 @@ __device__ __forceinline__ void store_pass(const float2 (&v)[16], float2 *dst, i
 
 // Exchange buffers: two (ping-pong, one barrier per pass) unless they would
 // not fit next to the input stages, then one (two barriers per pass).
+// Twiddles of the passes after the first, kept in shared memory: those of
+// Plan<N, S>, or for the split schedule those of Plan<N/2, 0>.
+template <int N, int S>
+constexpr int tw_rest() {
+  if constexpr (sched_split(N, S)) return Plan<N / 2, 0>::TW_REST;
+  else return Plan<N, S>::TW_REST;
+}
+
+// Exchange buffers: two (ping-pong, one barrier per pass) unless they would
+// not fit next to the input stages, then one (two barriers per pass).  The
+// split schedule's blocks of more than 256 threads run alone on an SM and
+// may use up to the 227 KB a block can have.
 template <int N, int S, bool TMA>
 struct Smem {
   using PL = Plan<N, S>;
   static constexpr size_t STAGE = TMA ? (size_t)PL::FPB * N : 0;   // complex in the input stage
   static constexpr size_t XB = (size_t)PL::FPB * PL::SLOT;         // complex per exchange buffer
-  static constexpr size_t FIXED = (size_t)PL::TW_REST * 8 + 260 * 4;
-  static constexpr int NXB = (STAGE * 8 + 2 * XB * 8 + FIXED <= 113 * 1024) ? 2 : 1;
+  static constexpr int TWR = tw_rest<N, S>();
+  static constexpr size_t FIXED = (size_t)TWR * 8 + 260 * 4;
+  static constexpr size_t LIMIT = (sched_split(N, S) && PL::THREADS > 256) ? 226 * 1024 : 113 * 1024;
+  static constexpr int NXB = (STAGE * 8 + 2 * XB * 8 + FIXED <= LIMIT) ? 2 : 1;
   static constexpr size_t BYTES = STAGE * 8 + NXB * XB * 8 + FIXED;
   static constexpr int BLOCKS = (BYTES <= 113 * 1024 && PL::THREADS <= 256) ? 2 : 1;  // per SM
 };
@@ -285,8 +304,8 @@ __device__ __forceinline__ float2 to_f2(short2 s) {
 }
 
 template <int N, int S, int MODE, bool TMA, typename IN>
-__device__ __forceinline__ bool stft_frames(const StftArgs &a, int64_t f_begin, int64_t f_end,
-                                            float2 *smem, float *red, uint64_t *bar) {
+__device__ __forceinline__ bool stft_frames_plain(const StftArgs &a, int64_t f_begin, int64_t f_end,
+                                                  float2 *smem, float *red, uint64_t *bar) {
   const IN *iq = static_cast<const IN *>(a.iq);
   using PL = Plan<N, S>;
   using SM = Smem<N, S, TMA>;
@@ -298,7 +317,7 @@ __device__ __forceinline__ bool stft_frames(const StftArgs &a, int64_t f_begin, 
   float2 *xb0 = smem + SM::STAGE;
   float2 *xb1 = xb0 + (NXB == 2 ? SM::XB : 0);
   float2 *twr = xb0 + NXB * SM::XB;
-  float *edges = reinterpret_cast<float *>(twr + PL::TW_REST);
+  float *edges = reinterpret_cast<float *>(twr + SM::TWR);
 
   const int tid = threadIdx.x;
   const int slot = tid / TPF, tau = tid % TPF;
@@ -444,6 +463,219 @@ __device__ __forceinline__ bool stft_frames(const StftArgs &a, int64_t f_begin, 
     }
   }
   return true;
+}
+
+// W_32^a = exp(-2 pi i a / 32), a = 0..15
+__device__ __forceinline__ float2 mul_w32(float2 v, int a) {
+  constexpr float c1 = 0.98078528040323044913f, s1 = 0.19509032201612826785f;   // pi/16
+  constexpr float c3 = 0.83146961230254523708f, s3 = 0.55557023301960222474f;   // 3 pi/16
+  switch (a) {
+    case 0: return v;
+    case 1: return cmul(v, make_float2(c1, -s1));
+    case 2: return cmul(v, make_float2(kC, -kS));
+    case 3: return cmul(v, make_float2(c3, -s3));
+    case 4: return mul_w8_1(v);
+    case 5: return cmul(v, make_float2(s3, -c3));
+    case 6: return cmul(v, make_float2(kS, -kC));
+    case 7: return cmul(v, make_float2(s1, -c1));
+    case 8: return mul_negi(v);
+    case 9: return cmul(v, make_float2(-s1, -c1));
+    case 10: return cmul(v, make_float2(-kS, -kC));
+    case 11: return cmul(v, make_float2(-s3, -c3));
+    case 12: return mul_w8_3(v);
+    case 13: return cmul(v, make_float2(-c3, -s3));
+    case 14: return cmul(v, make_float2(-kC, -kS));
+    default: return cmul(v, make_float2(-c1, -s1));
+  }
+}
+
+// Schedule 2 of N = 2M (M a power of 16).  The first decimation-in-frequency
+// radix-2 step turns the windowed frame into two M-point transforms,
+//   y0[m] = x[m] w[m] + x[m+M] w[m+M]            (bins X[2k]),
+//   y1[m] = (x[m] w[m] - x[m+M] w[m+M]) W_N^m    (bins X[2k+1]),
+// and the periodic Hann window has w[m+M] = 1 - w[m], so y0 = x2 + w (x1 - x2)
+// and y1 = (w (x1 + x2) - x2) W_N^m with x1 = x[m], x2 = x[m+M], w = w[m].
+// Threads [0, M/16) of a frame run the passes of Plan<M, 0> on y0, threads
+// [M/16, N/16) on y1, each group in its own half of the exchange buffer.
+// The radix-2 step is folded into the first pass, which reads the 32
+// samples it combines from the stage (every sample is read by the two
+// groups), so the frame crosses shared memory one time fewer than a
+// radix-2 pass of its own would make it.  With M/16 a multiple of 32 the
+// groups are whole warps and synchronise after the second pass on named
+// barriers of their own.  W_N^m = W_N^j W_32^a for m = j + (M/16) a.
+template <int N, int MODE, bool TMA, typename IN>
+__device__ __forceinline__ bool stft_frames_split(const StftArgs &a, int64_t f_begin, int64_t f_end,
+                                                  float2 *smem, float *red, uint64_t *bar) {
+  constexpr int M = N / 2;
+  using PM = Plan<M, 0>;
+  using PL = Plan<N, 2>;
+  using SM = Smem<N, 2, TMA>;
+  constexpr int TPF = PL::TPF, FPB = PL::FPB, SLOT = PL::SLOT, NXB = SM::NXB;
+  constexpr int HALF = M / 16, SLOTM = M + M / 16, NPM = PM::NPASS;
+  constexpr bool WARP_GROUPS = HALF % 32 == 0;
+  static_assert(PM::RSMALL == 1 && NPM >= 2 && NPM <= 3, "M is 256 or 4096");
+  static_assert(SLOT == 2 * SLOTM, "two padded halves per frame");
+  constexpr bool DO_MAX = (MODE == STFT_MAX || MODE == STFT_POWER);
+  constexpr bool DO_Q = (MODE == STFT_QUANT || MODE == STFT_QUANT_POWER);
+  constexpr bool DO_P = (MODE == STFT_POWER || MODE == STFT_QUANT_POWER);
+  const IN *iq = static_cast<const IN *>(a.iq);
+  float2 *stage = smem;
+  float2 *xb0 = smem + SM::STAGE;
+  float2 *xb1 = xb0 + (NXB == 2 ? SM::XB : 0);
+  float2 *twr = xb0 + NXB * SM::XB;
+  float *edges = reinterpret_cast<float *>(twr + SM::TWR);
+
+  const int tid = threadIdx.x;
+  const int slot = tid / TPF, tau = tid % TPF;
+  const int P = tau / HALF, j = tau % HALF;            // parity group and its thread
+  const int64_t nsteps = (f_end - f_begin + FPB - 1) / FPB;
+
+  auto step_bytes = [&](int64_t st) -> uint32_t {
+    const int64_t t0 = f_begin + st * FPB;
+    const int64_t nfr = (f_end - t0 < FPB) ? (f_end - t0) : (int64_t)FPB;
+    return (uint32_t)(((nfr - 1) * a.hop + N) * sizeof(IN));
+  };
+  auto issue = [&](int64_t st) {
+    const int64_t t0 = f_begin + st * FPB;
+    const uint32_t bytes = step_bytes(st);
+    if (kChecked && (t0 < 0 || t0 * (int64_t)a.hop * (int64_t)sizeof(IN) + bytes > a.n * (int64_t)sizeof(IN))) {
+      atomicOr(a.err, ERR_INDEX);   // checked build: a frame beyond the capture
+      return;
+    }
+    mbar_expect_tx(bar, bytes);
+    bulk_g2s(stage, iq + t0 * (int64_t)a.hop, bytes, bar);
+  };
+  if constexpr (TMA) {
+    if (tid == 0) {
+      mbar_init(bar, 1);
+      mbar_fence_init();
+      fence_proxy_async();
+      if (nsteps > 0) issue(0);
+    }
+  }
+  // tables: Plan<M, 0>'s twiddles (first pass [15][HALF] in registers, the
+  // rest in shared memory), then W_N^j for j < HALF; the window of size N
+  float win[16];
+  float2 tw0[15];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) win[i] = __ldg(&a.win[j + HALF * i]);
+#pragma unroll
+  for (int p = 1; p < 16; ++p) tw0[p - 1] = __ldg(&a.tw[(p - 1) * HALF + j]);
+  const float2 wN = P ? __ldg(&a.tw[PM::TW_TOTAL + j]) : make_float2(1.f, 0.f);
+  for (int i = tid; i < PM::TW_REST; i += PL::THREADS) twr[i] = a.tw[PM::tw_off(1) + i];
+  float inv_anchor = 0.f, c1 = 0.f;
+  if constexpr (DO_Q) {
+    for (int i = tid; i < 257; i += PL::THREADS) edges[i] = a.edges[i];
+    inv_anchor = a.qconst[0];
+    c1 = a.qconst[1];
+  }
+  __syncthreads();
+  auto group_sync = [&]() {
+    if constexpr (WARP_GROUPS)
+      asm volatile("bar.sync %0, %1;" ::"r"(1 + 2 * slot + P), "r"(HALF) : "memory");
+    else
+      __syncthreads();
+  };
+
+  float run_max = 0.0f;
+  int parity = 0;
+  bool failed = false;
+  // with two passes per half and two buffers, frames alternate buffers
+  for (int64_t st = 0; st < nsteps; ++st, parity ^= (NXB == 2 && (NPM & 1) == 0)) {
+    const int64_t t0 = f_begin + st * FPB;
+    const int64_t t = t0 + slot;
+    const bool valid = t < f_end;
+    float2 v[16];
+    {
+      const IN *x;
+      bool ok = valid;
+      if constexpr (TMA) {
+        if (!mbar_wait(bar, (uint32_t)(st & 1))) failed = true;
+        x = reinterpret_cast<const IN *>(stage) + (valid ? slot * a.hop : 0) + j;
+      } else {
+        ok = valid && (!kChecked || ck_index(t * (int64_t)a.hop + N - 1, a.n, a.err));
+        x = iq + (ok ? t * (int64_t)a.hop : 0) + j;
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        float2 x1 = make_float2(0.f, 0.f), x2 = x1;
+        if (ok) {
+          if constexpr (TMA) {
+            x1 = to_f2(x[HALF * i]);
+            x2 = to_f2(x[HALF * i + M]);
+          } else {
+            x1 = to_f2(__ldg(x + HALF * i));
+            x2 = to_f2(__ldg(x + HALF * i + M));
+          }
+        }
+        const float w = win[i];
+        if (P == 0) {
+          v[i] = make_float2(fmaf(w, x1.x - x2.x, x2.x), fmaf(w, x1.y - x2.y, x2.y));
+        } else {
+          const float2 y = make_float2(fmaf(w, x1.x + x2.x, -x2.x), fmaf(w, x1.y + x2.y, -x2.y));
+          v[i] = mul_w32(cmul(y, wN), i);
+        }
+      }
+    }
+    float2 *b0 = (parity ? xb1 : xb0) + slot * SLOT + P * SLOTM;
+    float2 *b1 = (parity ? xb0 : xb1) + slot * SLOT + P * SLOTM;
+    if constexpr (NXB == 1) __syncthreads();   // the previous frame's last reads are done
+    fft_pass<M, 0, 0, true>(v, nullptr, b0, j, tw0, twr);    // the values are already loaded
+    store_pass<M, 0, 0>(v, b0, j);
+    if (__syncthreads_or(failed)) {
+      if (tid == 0) {
+        atomicOr(a.err, ERR_INDEX);
+        if constexpr (TMA) mbar_wait(bar, (uint32_t)(st & 1));
+      }
+      return false;
+    }
+    if constexpr (TMA) {
+      if (tid == 0 && st + 1 < nsteps) {
+        fence_proxy_async();
+        issue(st + 1);
+      }
+    }
+    fft_pass<M, 0, 1, false>(v, b0, b1, j, tw0, twr);
+    if constexpr (NPM >= 3) {
+      if constexpr (NXB == 1) group_sync();
+      store_pass<M, 0, 1>(v, b1, j);
+      group_sync();
+      fft_pass<M, 0, 2, false>(v, b1, b0, j, tw0, twr);
+    }
+    if (valid && ck_index(t, a.T, a.err)) {
+      uint8_t *qrow = DO_Q ? a.img + t * (int64_t)N : nullptr;
+      float *prow = DO_P ? a.power + t * (int64_t)N : nullptr;
+#pragma unroll
+      for (int p = 0; p < 16; ++p) {
+        const int k = 2 * (j + HALF * p) + P;   // bin j + (M/16) p of the half, bin 2k' + P of the frame
+        const int f = (k + N / 2) & (N - 1);
+        const float2 z = v[p];
+        const float Pw = fmaf(z.x, z.x, z.y * z.y);
+        if constexpr (DO_MAX) run_max = fmaxf(run_max, Pw);
+        if constexpr (DO_P) prow[f] = Pw;
+        if constexpr (DO_Q) qrow[f] = (uint8_t)level_of(Pw, inv_anchor, c1, edges);
+      }
+    }
+  }
+  if constexpr (DO_MAX) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) run_max = fmaxf(run_max, __shfl_xor_sync(0xffffffffu, run_max, o));
+    if ((tid & 31) == 0) red[tid >> 5] = run_max;
+    __syncthreads();
+    if (tid == 0) {
+      float m = 0.f;
+      for (int w = 0; w < PL::THREADS / 32; ++w) m = fmaxf(m, red[w]);
+      atomicMax(a.max_bits, __float_as_uint(m));
+    }
+  }
+  return true;
+}
+
+template <int N, int S, int MODE, bool TMA, typename IN>
+__device__ __forceinline__ bool stft_frames(const StftArgs &a, int64_t f_begin, int64_t f_end,
+                                            float2 *smem, float *red, uint64_t *bar) {
+  if constexpr (sched_split(N, S)) return stft_frames_split<N, MODE, TMA, IN>(a, f_begin, f_end, smem, red, bar);
+  else return stft_frames_plain<N, S, MODE, TMA, IN>(a, f_begin, f_end, smem, red, bar);
 }
 
 template <int N, int S, int MODE, bool TMA, typename IN>

@@ -101,15 +101,20 @@ def test_spectrogram_and_image_parity(det, N, hop, n, fs, seed):
         assert np.array_equal(boxes_g, boxes_r)
 
 
-@pytest.mark.parametrize("N,hop,n,fs,seed", [c for c in STFT_CASES if c[0] in (512, 1024, 2048, 8192)])
-def test_radix_schedule_0_matches_the_oracle(det, N, hop, n, fs, seed):
-    """The other radix schedule (the radix-r pass last) under the same bars."""
+@pytest.mark.parametrize("sched", [0, 2])
+@pytest.mark.parametrize("N,hop,n,fs,seed", [c for c in STFT_CASES if c[0] in (512, 1024, 2048, 8192)]
+                         + [(8192, 2047, 8192 * 9 + 5, 100e6, 10),   # odd hop: the unstaged loads
+                            (512, 255, 512 * 200 + 7, 20e6, 11)])
+def test_other_radix_schedules_match_the_oracle(det, N, hop, n, fs, seed, sched):
+    """The other radix schedules under the same bars: 0 (the radix-r pass
+    last) and 2 (the frame split into two half-size transforms, N = 512 and
+    8192; other sizes run schedule 0 for it)."""
     rise = _rise()
     cap = synth.make_capture(n, fs, 6, 500 + seed, fft_size=N, hop=hop,
                              bw_hz=(fs / 200, fs / 20), dur_s=(n / fs / 20, n / fs / 3),
                              snr_db=(5, 25), tone_fraction=0.3)
     T = oracle.num_frames(n, N, hop)
-    det.set_option(rise.OPT_FFT_SCHEDULE, 0)
+    det.set_option(rise.OPT_FFT_SCHEDULE, sched)
     try:
         boxes_g = _gpu_detect(det, cap.iq, N, hop)
         Pg = det.debug(rise.DBG_POWER_F32, T, N)

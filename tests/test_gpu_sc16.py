@@ -36,18 +36,25 @@ def _run(det, iq, N, hop):
     return b, det.debug(rise.DBG_POWER_F32, T, N), det.debug(rise.DBG_IMAGE_U8, T, N)
 
 
-@pytest.mark.parametrize("N,hop,n", [(1024, 512, 1 << 20), (4096, 2048, 1 << 21),
-                                     (256, 129, 50000), (2048, 1000, 300001)])
-def test_sc16_equals_complex64_on_the_same_samples(det, N, hop, n):
+@pytest.mark.parametrize("N,hop,n,sched", [(1024, 512, 1 << 20, 1), (4096, 2048, 1 << 21, 1),
+                                           (256, 129, 50000, 1), (2048, 1000, 300001, 1),
+                                           (2048, 1000, 300001, 0), (8192, 2048, 1 << 19, 1),
+                                           (8192, 2048, 1 << 19, 2), (512, 257, 70001, 2)])
+def test_sc16_equals_complex64_on_the_same_samples(det, N, hop, n, sched):
+    from paper_2603_20481_gb300 import rise
     cap = synth.make_capture(n, 50e6, 12, 300 + N, fft_size=N, hop=hop,
                              bw_hz=(0.5e6, 5e6), dur_s=(n / 50e6 / 20, n / 50e6 / 4),
                              snr_db=(5, 25))
     q, f = _sc16(cap.iq)
-    want = _run(det, torch.from_numpy(f).cuda(), N, hop)
-    for src in (torch.from_numpy(q).cuda(), torch.from_numpy(q).pin_memory(), q):
-        got = _run(det, src, N, hop)
-        for g, w in zip(got, want):
-            np.testing.assert_array_equal(g, w)
+    det.set_option(rise.OPT_FFT_SCHEDULE, sched)   # the same radix schedule for both inputs
+    try:
+        want = _run(det, torch.from_numpy(f).cuda(), N, hop)
+        for src in (torch.from_numpy(q).cuda(), torch.from_numpy(q).pin_memory(), q):
+            got = _run(det, src, N, hop)
+            for g, w in zip(got, want):
+                np.testing.assert_array_equal(g, w)
+    finally:
+        det.set_option(rise.OPT_FFT_SCHEDULE, 1)
     assert len(want[0]) > 0
 
 
