@@ -49,6 +49,10 @@ struct Plan {
 };
 
 __device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
+// padi(b + c) = padi(b) + padc(c) for a constant offset c that is a multiple
+// of 16, or when b % 16 + c stays below 16 plus the multiple of 16 in c (the
+// callers' cases): the offsets then fold into the load and store instructions
+constexpr int padc(int c) { return c + (c >> 4); }
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -214,12 +218,22 @@ __device__ __forceinline__ void fft_pass(float2 (&v)[16], const float2 *src, flo
   constexpr bool LAST = (I == PL::NPASS - 1);
   static_assert(R == 16 || I == 0 || LAST, "a radix below 16 runs first or last");
   if constexpr (!FIRST) {
+    // the R values of a butterfly sit MP apart from b = P MI + j: when MP or
+    // MI is a multiple of 16 (then j < MP divides 16), padi(b + a MP) =
+    // padi(b) + padc(a MP)
+    constexpr bool LIN = (MP % 16 == 0) || (MI % 16 == 0 && 16 % MP == 0);
 #pragma unroll
     for (int s = 0; s < 16 / R; ++s) {
       const int d = tau + (N / 16) * s;
       const int P = d / MP, j = d % MP;
+      if constexpr (LIN) {
+        const float2 *sb = src + padi(P * MI + j);
 #pragma unroll
-      for (int a = 0; a < R; ++a) v[s * R + a] = src[padi(P * MI + a * MP + j)];
+        for (int a = 0; a < R; ++a) v[s * R + a] = sb[padc(a * MP)];
+      } else {
+#pragma unroll
+        for (int a = 0; a < R; ++a) v[s * R + a] = src[padi(P * MI + a * MP + j)];
+      }
     }
   } else if constexpr (R < 16) {
     float2 t[16];
@@ -255,15 +269,17 @@ template <int N, int S, int I>
 __device__ __forceinline__ void store_pass(const float2 (&v)[16], float2 *dst, int tau) {
   using PL = Plan<N, S>;
   constexpr int NR = N / 16, R = PL::radix(I);
+  static_assert(NR % 16 == 0, "slot offsets are multiples of 16");
+  float2 *db = dst + padi(tau);   // every other offset is a multiple of 16
   if constexpr (R == 16) {
 #pragma unroll
-    for (int p = 0; p < 16; ++p) dst[padi(tau + p * NR)] = v[p];
+    for (int p = 0; p < 16; ++p) db[padc(p * NR)] = v[p];
   } else {
     static_assert(I == 0, "a radix below 16 stores only as the first pass");
 #pragma unroll
     for (int s = 0; s < 16 / R; ++s)
 #pragma unroll
-      for (int p = 0; p < R; ++p) dst[padi(p * (N / R) + tau + NR * s)] = v[s * R + p];
+      for (int p = 0; p < R; ++p) db[padc(p * (N / R) + NR * s)] = v[s * R + p];
   }
 }
 
@@ -436,17 +452,20 @@ __device__ __forceinline__ bool stft_frames_plain(const StftArgs &a, int64_t f_b
       constexpr int R = PL::radix(NPASS - 1);
       uint8_t *qrow = DO_Q ? a.img + t * (int64_t)N : nullptr;
       float *prow = DO_P ? a.power + t * (int64_t)N : nullptr;
+      // bin k = tau + C, C = (N/16) s + (N/R) p a multiple of N/16 > tau, so
+      // its column (k + N/2) mod N is tau + (C + N/2) mod N
+      if constexpr (DO_Q) qrow += tau;
+      if constexpr (DO_P) prow += tau;
 #pragma unroll
       for (int s = 0; s < 16 / R; ++s) {
 #pragma unroll
         for (int p = 0; p < R; ++p) {
-          const int k = tau + (N / 16) * s + (N / R) * p;
-          const int f = (k + N / 2) & (N - 1);
+          const int fc = ((N / 16) * s + (N / R) * p + N / 2) & (N - 1);
           const float2 z = v[s * R + p];
           const float P = fmaf(z.x, z.x, z.y * z.y);
           if constexpr (DO_MAX) run_max = fmaxf(run_max, P);
-          if constexpr (DO_P) prow[f] = P;
-          if constexpr (DO_Q) qrow[f] = (uint8_t)level_of(P, inv_anchor, c1, edges);
+          if constexpr (DO_P) prow[fc] = P;
+          if constexpr (DO_Q) qrow[fc] = (uint8_t)level_of(P, inv_anchor, c1, edges);
         }
       }
     }
@@ -645,10 +664,13 @@ __device__ __forceinline__ bool stft_frames_split(const StftArgs &a, int64_t f_b
     if (valid && ck_index(t, a.T, a.err)) {
       uint8_t *qrow = DO_Q ? a.img + t * (int64_t)N : nullptr;
       float *prow = DO_P ? a.power + t * (int64_t)N : nullptr;
+      // bin 2 (j + (M/16) p) + P of the frame (bin j + (M/16) p of the half):
+      // column 2j + P + (2 (M/16) p + N/2) mod N, since 2j + P < 2 (M/16)
+      if constexpr (DO_Q) qrow += 2 * j + P;
+      if constexpr (DO_P) prow += 2 * j + P;
 #pragma unroll
       for (int p = 0; p < 16; ++p) {
-        const int k = 2 * (j + HALF * p) + P;   // bin j + (M/16) p of the half, bin 2k' + P of the frame
-        const int f = (k + N / 2) & (N - 1);
+        const int f = (2 * HALF * p + N / 2) & (N - 1);
         const float2 z = v[p];
         const float Pw = fmaf(z.x, z.x, z.y * z.y);
         if constexpr (DO_MAX) run_max = fmaxf(run_max, Pw);
