@@ -63,8 +63,15 @@ HBM_FALLBACK_GBS = 6800.0
 # the counters were taken: a changed kernel reports no traffic until it is
 # captured again.
 STFT_SOURCES = ("paper_2603_20481_gb300/csrc/stft_impl.cuh", "paper_2603_20481_gb300/csrc/stft.cu",
+                "paper_2603_20481_gb300/csrc/stft_s1.cu", "paper_2603_20481_gb300/csrc/stft_s2.cu",
                 "paper_2603_20481_gb300/csrc/common.cuh")
-TRAFFIC = {}
+TRAFFIC = {
+    # stft_kernel<8192, 2, POWER>: one capture of the stress generator cut to
+    # 2^25 samples (16381 frames), 278,758,400 B read + 480,090,880 B written,
+    # scaled by frames to the 131069 frames of the full capture
+    "stress": {"sha256": "ea9bfad22a823574819f365d54abca2ab5bc9f4480820c85ca1d48475fc88210",
+               "n_samples": 1 << 28, "sched": 2, "bytes": 6071767064},
+}
 
 
 def _peaks():
@@ -222,13 +229,26 @@ def _sha256(paths):
     return h.hexdigest()
 
 
-def _traffic(workload: str, n: int):
+def _sched_of(N: int, requested: int) -> int:
+    """The radix schedule a single capture of size N runs: the requested one
+    where the size has it, else the library's (2 at N = 8192, 1 at sizes
+    that are not powers of 16, 0 at powers of 16)."""
+    log2n = N.bit_length() - 1
+    has = {0: True, 1: log2n % 4 != 0, 2: log2n % 4 == 1}
+    if requested in (0, 1, 2):
+        return requested if has[requested] else 0
+    return 2 if N == 8192 else (1 if has[1] else 0)
+
+
+def _traffic(workload: str, n: int, sched: int):
     """DRAM bytes per launch of the dominant kernel from the ncu capture kept
-    for this workload, or None: a capture is only valid while the kernel's
-    sources hash as they did when its counters were taken, and only for the
-    full-size capture it was scaled to."""
+    for this workload, or None: a capture is only valid for the radix
+    schedule it measured, while the kernel's sources hash as they did when
+    its counters were taken, and only for the full-size capture it was
+    scaled to."""
     t = TRAFFIC.get(workload)
-    if t is None or n != t["n_samples"] or _sha256(STFT_SOURCES) != t["sha256"]:
+    if (t is None or n != t["n_samples"] or sched != t["sched"]
+            or _sha256(STFT_SOURCES) != t["sha256"]):
         return None
     return t["bytes"]
 
@@ -384,10 +404,11 @@ def measure_single(args, name: str):
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     mhz = float((clocks or {}).get("sm_max_mhz") or 2070.0)
     dom = max(names[:-1], key=lambda k: stage[names.index(k)])
-    kname = {2: f"stft_kernel<{N_FFT}, power>", 1: f"stft_kernel<{N_FFT}, max>"}[path]
+    sch = _sched_of(N_FFT, args.fft_schedule)
+    kname = {2: f"stft_kernel<{N_FFT}, schedule {sch}, power>", 1: f"stft_kernel<{N_FFT}, schedule {sch}, max>"}[path]
     roof = _spectrum_roofline(kname, float(stage[names.index("spectrum_pass1")]), n, T, N_FFT,
                               sms, mhz, peak, peak_kind, t_max / args.steps, path,
-                              _traffic(name, n))
+                              _traffic(name, n, _sched_of(N_FFT, args.fft_schedule)) if path == 2 else None)
     if dom != "spectrum_pass1":
         roof["note"] = f"the longest stage this run was {dom}"
     result = {
@@ -397,7 +418,8 @@ def measure_single(args, name: str):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload, "n_samples": n, "fft_size": N_FFT, "hop": HOP,
                    "frames": T, "boxes": n_boxes, "range_path": path,
-                   "fft_schedule": args.fft_schedule if args.fft_schedule >= 0 else "library default (1)",
+                   "fft_schedule": (args.fft_schedule if args.fft_schedule in (0, 1, 2)
+                                    else f"library default ({_sched_of(N_FFT, 3)})"),
                    "l2": f"inputs larger than L2 ({8 * n >> 20} MiB capture per step)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roof,
@@ -675,7 +697,7 @@ def _serve_run(srv, pinned, arrivals, limit_s):
 
     import numpy as np
     lat, done, rejected, nbox = [], 0, 0, 0
-    from_arr, lag = [], []
+    from_arr, lag, service = [], [], []
     radios = len(pinned)
     per = len(pinned[0])
     nxt = [0] * radios
@@ -702,6 +724,7 @@ def _serve_run(srv, pinned, arrivals, limit_s):
                 i += 1
             for d, bx in srv.poll(timeout_ms=0):
                 lat.append((d["t_done_ns"] - d["t_submit_ns"]) / 1e6)
+                service.append((d["t_done_ns"] - d["t_start_ns"]) / 1e6)
                 a = arrivals[d["tag"]][0]
                 if a is not None:   # steady clock and perf_counter share CLOCK_MONOTONIC
                     from_arr.append((d["t_done_ns"] / 1e9 - (t0 + a)) * 1e3)
@@ -720,10 +743,16 @@ def _serve_run(srv, pinned, arrivals, limit_s):
     _serve_run.boxes = nbox
     _serve_run.from_arrival = np.array(from_arr)
     _serve_run.lag = np.array(lag)
+    _serve_run.service = np.array(service)
     return np.array(lat), done, rejected, time.perf_counter() - t0
 
 
 _serve_run.failed = 0   # results whose status was not RISE_OK (must stay 0)
+
+
+def _stat_delta(now, before, key):
+    """How much a server counter moved during one load phase."""
+    return int(now.get(key, 0)) - int(before.get(key, 0))
 
 
 def run_served(args):
@@ -752,6 +781,7 @@ def measure_served(args, loads=(0.5, 0.75, 1.0, 1.25, 1.5)):
     pinned = [[torch.from_numpy(data[s * per + k]).pin_memory() for k in range(per)]
               for s in range(SERVE_RADIOS)]
     rng = np.random.default_rng(4242)
+    uuid = str(torch.cuda.get_device_properties(local).uuid)
 
     def measure(lanes, max_batch):
         srv = rise.Server(SERVE_N, SERVE_HOP, max_chunk=SERVE_CHUNK, max_streams=SERVE_RADIOS,
@@ -787,8 +817,13 @@ def measure_served(args, loads=(0.5, 0.75, 1.0, 1.25, 1.5)):
             times = np.cumsum(gaps)
             radios = rng.integers(0, SERVE_RADIOS, size=count)
             arr = [(float(t), int(r)) for t, r in zip(times, radios)]
+            st0 = srv.stats()
+            sampler = ClockSampler(uuid if uuid.startswith("GPU-") else f"GPU-{uuid}")
+            sampler.start()
+            w0 = time.time()
             lat, done, rej, dt = _serve_run(srv, pinned, arr, times[-1] + 10.0)
-            fa, lg = _serve_run.from_arrival, _serve_run.lag
+            clocks = sampler.stop(w0, time.time())
+            fa, lg, sv = _serve_run.from_arrival, _serve_run.lag, _serve_run.service
             srv.drain(timeout_ms=30000)
             srv.poll(timeout_ms=0)
             out["by_load"].append({
@@ -800,7 +835,13 @@ def measure_served(args, loads=(0.5, 0.75, 1.0, 1.25, 1.5)):
                 "max_ms": round(float(lat.max()), 3) if len(lat) else None,
                 "deadline_miss_frac": round(float((lat > SERVE_PERIOD_MS).mean()), 4) if len(lat) else None,
                 "p99_from_arrival_ms": round(float(np.percentile(fa, 99)), 3) if len(fa) else None,
-                "submit_lag_p99_ms": round(float(np.percentile(lg, 99)), 3) if len(lg) else None})
+                "submit_lag_p99_ms": round(float(np.percentile(lg, 99)), 3) if len(lg) else None,
+                # from the batch's start to the result (the rest of the latency is queueing)
+                "service_p99_ms": round(float(np.percentile(sv, 99)), 3) if len(sv) else None,
+                "service_max_ms": round(float(sv.max()), 3) if len(sv) else None,
+                "graph_captures": _stat_delta(srv.stats(), st0, "graph_captures"),
+                "buffer_generations": _stat_delta(srv.stats(), st0, "buffer_generations"),
+                "clocks": clocks})
         out["stats"] = srv.stats()
         srv.close()
         return out
@@ -1114,7 +1155,7 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--samples", type=int, default=0, help="capture length (0: the workload's)")
     ap.add_argument("--range-path", type=int, default=0, choices=(0, 1, 2))
-    ap.add_argument("--fft-schedule", type=int, default=-1, choices=(-1, 0, 1, 2),
+    ap.add_argument("--fft-schedule", type=int, default=-1, choices=(-1, 0, 1, 2, 3),
                     help="radix schedule of single captures (-1: the library's choice)")
     ap.add_argument("--ref-sample", type=int, default=1 << 23,
                     help="reference arm: samples per step (a prefix of the capture)")

@@ -453,16 +453,19 @@ int rise_debug_export(rise_ctx *ctx, int what, void *dst, size_t bytes);
                                     * wait runs out; -1 (default): none             */
 /* Radix schedule of the FFT of single captures.  An N-point transform with
  * N = 16^a * r (r = 2, 4 or 8) runs its radix-r pass last (schedule 0) or
- * first (schedule 1, the default); for r = 2 (N = 512, 8192) schedule 2
- * splits the frame into two N/2-point transforms run side by side.  A
- * schedule a size does not have runs schedule 0 (N a power of 16: all are
- * the same).  -1: the schedule this context's batch tuner (or the tune
- * cache) picked for N, else 1.  The schedules round differently, so the
- * 8-bit image can differ in a few pixels (all stay within the tolerance of
- * the FP64 reference).  The batch tuner times every schedule an FFT size of
- * a new composition has and keeps the fastest; an untuned batch runs
- * schedule 1.  A batch capture's results equal those of rise_detect run
- * with the batch's schedule. */
+ * first (schedule 1); for r = 2 (N = 512, 8192) schedule 2 splits the
+ * frame into two N/2-point transforms run side by side (at N = 8192 by the
+ * two halves of the block, which never wait for each other inside the
+ * frame loop).  A schedule a size does not have runs schedule 0 (N a power
+ * of 16: all are the same).  3 (the default): the library's schedule for
+ * N, 2 at N = 8192 and 1 at the other sizes.  -1: the schedule this
+ * context's batch tuner (or the tune cache) picked for N, else the
+ * library's.  The schedules round differently, so the 8-bit image can
+ * differ in a few pixels (all stay within the tolerance of the FP64
+ * reference).  The batch tuner times every schedule an FFT size of a new
+ * composition has and keeps the fastest; an untuned batch runs the
+ * library's schedule.  A batch capture's results equal those of
+ * rise_detect run with the batch's schedule. */
 #define RISE_OPT_FFT_SCHEDULE 11
 
 /* Tune cache: when the environment variable RISE_TUNE_CACHE names a file,

@@ -494,7 +494,7 @@ uint64_t graph_key(const Plan &p, const rise_thresholds &thr, int64_t cap, uint6
 
 // Radix schedule of an untuned batch group: 1 (the small radix first, the
 // faster one where it differs), the same as 0 for powers of 16.
-int default_sched(int N) { return stft_sched_distinct(N, 1) ? 1 : 0; }
+int default_sched(int N) { return stft_default_sched(N); }
 
 // Tuned parameters of a composition: item multiplier per STFT group, radix
 // schedule per group, morphology warps per SM.

@@ -207,6 +207,9 @@ cudaError_t launch_stft_s2(const StftArgs &a, StftMode mode, int num_sms, cudaSt
 // True when schedule S of size N exists apart from schedule 0: S = 1 for N
 // not a power of 16, S = 2 for N twice a power of 16.
 bool stft_sched_distinct(int N, int S);
+// The library's schedule for size N: 2 at N = 8192 (its two halves run
+// decoupled), else 1 where it exists, else 0.
+int stft_default_sched(int N);
 
 // ---------------------------------------------------------------------------
 // Batches: one launch per stage covers many captures; each block or warp

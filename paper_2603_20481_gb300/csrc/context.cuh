@@ -110,7 +110,7 @@ struct rise_ctx {
   int64_t withhold_tile = -1;
   // radix schedule of single captures: 0 or 1 (default), or -1: the one the
   // batch tuner (or the tune cache) picked for the FFT size, else 1
-  int fft_sched = 1;
+  int fft_sched = 3;   // RISE_OPT_FFT_SCHEDULE: the library's schedule per size
   std::map<int, int> sched_pick;   // FFT size -> schedule picked by the batch tuner
   bool capturing = false;         // enqueueing into a graph capture
   // scratch

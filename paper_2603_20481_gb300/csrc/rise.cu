@@ -125,8 +125,9 @@ int single_sched(const rise_ctx *c, int N) {
   int S = c->fft_sched;
   if (S < 0) {
     auto it = c->sched_pick.find(N);
-    S = it == c->sched_pick.end() ? 1 : it->second;
+    S = it == c->sched_pick.end() ? 3 : it->second;
   }
+  if (S == 3) S = stft_default_sched(N);
   return stft_sched_distinct(N, S) ? S : 0;
 }
 
@@ -899,7 +900,7 @@ int rise_set_option(rise_ctx *c, int option, int64_t value) {
       new_generation(c);
       return RISE_OK;
     case RISE_OPT_FFT_SCHEDULE:
-      if (value < -1 || value > 2) return RISE_EINVAL;
+      if (value < -1 || value > 3) return RISE_EINVAL;
       c->fft_sched = (int)value;
       return RISE_OK;
   }

@@ -149,6 +149,11 @@ void stft_preload() {
   preload_kernel(levels_batch_kernel);
 }
 
+int stft_default_sched(int N) {
+  if (N == 8192) return 2;
+  return stft_sched_distinct(N, 1) ? 1 : 0;
+}
+
 bool stft_sched_distinct(int N, int S) {
   int l = 0;
   while ((1 << l) < N) ++l;

@@ -693,10 +693,215 @@ __device__ __forceinline__ bool stft_frames_split(const StftArgs &a, int64_t f_b
   return true;
 }
 
+// Named barrier over `count` threads that also ORs a predicate across them.
+__device__ __forceinline__ bool bar_or(int id, int count, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.or.pred p, %2, %3, q;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(id), "r"(count)
+      : "memory");
+  return r != 0;
+}
+
+// Schedule 2 with the two halves of the block decoupled (one frame per block
+// step, each half whole warps: N = 8192).  The halves run the same steps as
+// in stft_frames_split but share nothing except the input stage, and never
+// meet at a block barrier inside the frame loop: after its first pass each
+// half counts itself out of the stage (thread 0 of the half, on a shared
+// counter), and the half that counts out second issues the copy of the next
+// frame.  A half can then run up to most of a frame ahead of the other, so
+// the butterflies of one half overlap the exchanges of the other.  The two
+// roles (even bins; odd bins with the extra twist by W_N^m) swap halves
+// every frame, so both halves carry the same work over two frames.
+template <int N, int MODE, bool TMA, typename IN>
+__device__ __forceinline__ bool stft_frames_split_async(const StftArgs &a, int64_t f_begin, int64_t f_end,
+                                                        float2 *smem, float *red, uint64_t *bar) {
+  constexpr int M = N / 2;
+  using PM = Plan<M, 0>;
+  using PL = Plan<N, 2>;
+  using SM = Smem<N, 2, TMA>;
+  constexpr int HALF = M / 16, SLOTM = M + M / 16, NPM = PM::NPASS;
+  static_assert(PL::FPB == 1 && HALF % 32 == 0 && NPM == 3 && SM::NXB == 2 && PL::SLOT == 2 * SLOTM,
+                "one frame per step, whole-warp halves, three passes per half, two exchange buffers");
+  constexpr bool DO_MAX = (MODE == STFT_MAX || MODE == STFT_POWER);
+  constexpr bool DO_Q = (MODE == STFT_QUANT || MODE == STFT_QUANT_POWER);
+  constexpr bool DO_P = (MODE == STFT_POWER || MODE == STFT_QUANT_POWER);
+  __shared__ int s_out, s_issued, s_fail;
+  const IN *iq = static_cast<const IN *>(a.iq);
+  float2 *stage = smem;
+  float2 *xb0 = smem + SM::STAGE;
+  float2 *xb1 = xb0 + SM::XB;
+  float2 *twr = xb0 + 2 * SM::XB;
+  float *edges = reinterpret_cast<float *>(twr + SM::TWR);
+
+  const int tid = threadIdx.x;
+  const int h = tid / HALF, j = tid % HALF;             // half of the block and its thread
+  const int64_t nsteps = f_end - f_begin;
+  auto issue = [&](int64_t st) {
+    const int64_t t = f_begin + st;
+    constexpr uint32_t bytes = (uint32_t)(N * sizeof(IN));
+    if (kChecked && (t < 0 || t * (int64_t)a.hop * (int64_t)sizeof(IN) + bytes > a.n * (int64_t)sizeof(IN))) {
+      atomicOr(a.err, ERR_INDEX);   // checked build: a frame beyond the capture
+      return;
+    }
+    mbar_expect_tx(bar, bytes);
+    bulk_g2s(stage, iq + t * (int64_t)a.hop, bytes, bar);
+  };
+  if (tid == 0) {
+    s_out = 0;
+    s_issued = 0;
+    s_fail = 0;
+    if constexpr (TMA) {
+      mbar_init(bar, 1);
+      mbar_fence_init();
+      fence_proxy_async();
+      if (nsteps > 0) {
+        issue(0);
+        s_issued = 1;
+      }
+    }
+  }
+  float win[16];
+  float2 tw0[15];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) win[i] = __ldg(&a.win[j + HALF * i]);
+#pragma unroll
+  for (int p = 1; p < 16; ++p) tw0[p - 1] = __ldg(&a.tw[(p - 1) * HALF + j]);
+  const float2 wN = __ldg(&a.tw[PM::TW_TOTAL + j]);
+  for (int i = tid; i < PM::TW_REST; i += PL::THREADS) twr[i] = a.tw[PM::tw_off(1) + i];
+  float inv_anchor = 0.f, c1 = 0.f;
+  if constexpr (DO_Q) {
+    for (int i = tid; i < 257; i += PL::THREADS) edges[i] = a.edges[i];
+    inv_anchor = a.qconst[0];
+    c1 = a.qconst[1];
+  }
+  __syncthreads();
+  const int bar_id = 1 + h;
+  float2 *b0 = xb0 + h * SLOTM;
+  float2 *b1 = xb1 + h * SLOTM;
+
+  float run_max = 0.0f;
+  for (int64_t st = 0; st < nsteps; ++st) {
+    const int64_t t = f_begin + st;
+    const int P = h ^ (int)(st & 1);                     // this frame's role: even or odd bins
+    bool failed = false;
+    float2 v[16];
+    {
+      const IN *x;
+      bool ok = true;
+      if constexpr (TMA) {
+        if (!mbar_wait(bar, (uint32_t)(st & 1))) failed = true;
+        x = reinterpret_cast<const IN *>(stage) + j;
+      } else {
+        ok = !kChecked || ck_index(t * (int64_t)a.hop + N - 1, a.n, a.err);
+        x = iq + (ok ? t * (int64_t)a.hop : 0) + j;
+      }
+      if (P == 0) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          float2 x1 = make_float2(0.f, 0.f), x2 = x1;
+          if (ok) {
+            if constexpr (TMA) {
+              x1 = to_f2(x[HALF * i]);
+              x2 = to_f2(x[HALF * i + M]);
+            } else {
+              x1 = to_f2(__ldg(x + HALF * i));
+              x2 = to_f2(__ldg(x + HALF * i + M));
+            }
+          }
+          const float w = win[i];
+          v[i] = make_float2(fmaf(w, x1.x - x2.x, x2.x), fmaf(w, x1.y - x2.y, x2.y));
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          float2 x1 = make_float2(0.f, 0.f), x2 = x1;
+          if (ok) {
+            if constexpr (TMA) {
+              x1 = to_f2(x[HALF * i]);
+              x2 = to_f2(x[HALF * i + M]);
+            } else {
+              x1 = to_f2(__ldg(x + HALF * i));
+              x2 = to_f2(__ldg(x + HALF * i + M));
+            }
+          }
+          const float w = win[i];
+          const float2 y = make_float2(fmaf(w, x1.x + x2.x, -x2.x), fmaf(w, x1.y + x2.y, -x2.y));
+          v[i] = mul_w32(cmul(y, wN), i);
+        }
+      }
+    }
+    fft_pass<M, 0, 0, true>(v, nullptr, b0, j, tw0, twr);   // the values are already loaded
+    store_pass<M, 0, 0>(v, b0, j);
+    // the half's stage reads and first-pass stores are done; a wait that ran
+    // out in any thread of the half ends the half's loop
+    if (bar_or(bar_id, HALF, failed)) {
+      if (j == 0) {
+        s_fail = 1;
+        atomicOr(a.err, ERR_INDEX);
+      }
+      break;
+    }
+    if constexpr (TMA) {
+      if (j == 0) {
+        __threadfence_block();
+        const int before = atomicAdd(&s_out, 1);
+        __threadfence_block();
+        if (before == 2 * (int)st + 1 && st + 1 < nsteps) {   // both halves are out of the stage
+          fence_proxy_async();
+          issue(st + 1);
+          s_issued = (int)st + 2;
+        }
+      }
+    }
+    fft_pass<M, 0, 1, false>(v, b0, b1, j, tw0, twr);
+    store_pass<M, 0, 1>(v, b1, j);
+    asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(HALF) : "memory");
+    fft_pass<M, 0, 2, false>(v, b1, b0, j, tw0, twr);
+    if (ck_index(t, a.T, a.err)) {
+      uint8_t *qrow = DO_Q ? a.img + t * (int64_t)N : nullptr;
+      float *prow = DO_P ? a.power + t * (int64_t)N : nullptr;
+      // bin 2 (j + (M/16) p) + P of the frame: column 2j + P + (2 (M/16) p + N/2) mod N
+      if constexpr (DO_Q) qrow += 2 * j + P;
+      if constexpr (DO_P) prow += 2 * j + P;
+#pragma unroll
+      for (int p = 0; p < 16; ++p) {
+        const int f = (2 * HALF * p + N / 2) & (N - 1);
+        const float2 z = v[p];
+        const float Pw = fmaf(z.x, z.x, z.y * z.y);
+        if constexpr (DO_MAX) run_max = fmaxf(run_max, Pw);
+        if constexpr (DO_P) prow[f] = Pw;
+        if constexpr (DO_Q) qrow[f] = (uint8_t)level_of(Pw, inv_anchor, c1, edges);
+      }
+    }
+  }
+  __syncthreads();
+  const bool failed = s_fail != 0;
+  // after a wait ran out, the last copy issued may still be in flight: wait
+  // (bounded) for it before the block lets go of its shared memory
+  if (TMA && failed && tid == 0 && s_issued > 0) mbar_wait(bar, (uint32_t)((s_issued - 1) & 1));
+  if constexpr (DO_MAX) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) run_max = fmaxf(run_max, __shfl_xor_sync(0xffffffffu, run_max, o));
+    if ((tid & 31) == 0) red[tid >> 5] = run_max;
+    __syncthreads();
+    if (tid == 0) {
+      float m = 0.f;
+      for (int w = 0; w < PL::THREADS / 32; ++w) m = fmaxf(m, red[w]);
+      atomicMax(a.max_bits, __float_as_uint(m));
+    }
+  }
+  return !failed;
+}
+
 template <int N, int S, int MODE, bool TMA, typename IN>
 __device__ __forceinline__ bool stft_frames(const StftArgs &a, int64_t f_begin, int64_t f_end,
                                             float2 *smem, float *red, uint64_t *bar) {
-  if constexpr (sched_split(N, S)) return stft_frames_split<N, MODE, TMA, IN>(a, f_begin, f_end, smem, red, bar);
+  if constexpr (sched_split(N, S) && N / 32 >= 256)
+    return stft_frames_split_async<N, MODE, TMA, IN>(a, f_begin, f_end, smem, red, bar);
+  else if constexpr (sched_split(N, S)) return stft_frames_split<N, MODE, TMA, IN>(a, f_begin, f_end, smem, red, bar);
   else return stft_frames_plain<N, S, MODE, TMA, IN>(a, f_begin, f_end, smem, red, bar);
 }
 

@@ -68,7 +68,7 @@ def _plain(det, xs, Ns, hops, thr=None):
     try:
         return [det.detect(x, N, h, thr) for x, N, h in zip(xs, Ns, hops)]
     finally:
-        det.set_option(rise.OPT_FFT_SCHEDULE, 1)
+        det.set_option(rise.OPT_FFT_SCHEDULE, 3)
 
 
 def _check(boxes, offs, want):

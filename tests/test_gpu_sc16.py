@@ -54,7 +54,7 @@ def test_sc16_equals_complex64_on_the_same_samples(det, N, hop, n, sched):
             for g, w in zip(got, want):
                 np.testing.assert_array_equal(g, w)
     finally:
-        det.set_option(rise.OPT_FFT_SCHEDULE, 1)
+        det.set_option(rise.OPT_FFT_SCHEDULE, 3)
     assert len(want[0]) > 0
 
 
