@@ -1052,27 +1052,35 @@ def run_quality(args):
     world, rank, local = _dist()
     torch.cuda.set_device(local)
     det = rise.Detector(local)
-    sweep = []
-    for i, snr in enumerate(QUALITY_SNR):
-        nt = np.zeros(len(QUALITY_THETAS), np.int64)
-        nf = np.zeros(len(QUALITY_THETAS), np.int64)
-        ng = nd = 0
-        iou_sum = 0.0
-        for k in range(per):
-            iq, gt = data[i * per + k]
-            boxes = det.detect(torch.from_numpy(iq).cuda(), 1024, 512)
-            g = np.array(gt, dtype=np.int64).reshape(-1, 4)
-            r = det.match(g, boxes, QUALITY_THETAS)
-            nt += r["n_t"]
-            nf += r["n_f"]
-            ng += g.shape[0]
-            nd += boxes.shape[0]
-            b = r["gt_best"]
-            iou_sum += float((b[:, 0] / np.maximum(b[:, 1], 1)).sum())
-        sweep.append({"snr_db": snr, "gt_boxes": int(ng), "detections": int(nd),
-                      "mean_best_iou": round(iou_sum / max(ng, 1), 4),
-                      "p_d": [round(float(x) / max(ng, 1), 4) for x in nt],
-                      "p_fa": [round(float(x) / max(nd, 1), 4) for x in nf]})
+
+    def run_sweep(thr):
+        out = []
+        for i, snr in enumerate(QUALITY_SNR):
+            nt = np.zeros(len(QUALITY_THETAS), np.int64)
+            nf = np.zeros(len(QUALITY_THETAS), np.int64)
+            ng = nd = 0
+            iou_sum = 0.0
+            for k in range(per):
+                iq, gt = data[i * per + k]
+                boxes = det.detect(torch.from_numpy(iq).cuda(), 1024, 512, thr=thr)
+                g = np.array(gt, dtype=np.int64).reshape(-1, 4)
+                r = det.match(g, boxes, QUALITY_THETAS)
+                nt += r["n_t"]
+                nf += r["n_f"]
+                ng += g.shape[0]
+                nd += boxes.shape[0]
+                b = r["gt_best"]
+                iou_sum += float((b[:, 0] / np.maximum(b[:, 1], 1)).sum())
+            out.append({"snr_db": snr, "gt_boxes": int(ng), "detections": int(nd),
+                        "mean_best_iou": round(iou_sum / max(ng, 1), 4),
+                        "p_d": [round(float(x) / max(ng, 1), 4) for x in nt],
+                        "p_fa": [round(float(x) / max(nd, 1), 4) for x in nf]})
+        return out
+    # the library's default offsets (0.5 dB over the PSD floor, 10 dB over the
+    # power floor, chosen on the wideband generator), and the 1 dB / 3 dB
+    # offsets a first reading of the method suggested: the paper gives no value
+    sweep = run_sweep(None)
+    sweep_alt = run_sweep(rise.default_thresholds(psd_offset_db=1.0, power_offset_db=3.0))
     # the IoU harness on large random sets, through the C ABI call
     rng = np.random.default_rng(7)
     n_box = 1 << 16
@@ -1140,6 +1148,10 @@ def run_quality(args):
         "config": {"workload": QUALITY_WORKLOAD, "thetas": list(QUALITY_THETAS),
                    "parallelism": "replicas x1"},
         "p_d_at_iou_0.5": {str(e["snr_db"]): e["p_d"][at] for e in sweep},
+        "p_fa_at_iou_0.5": {str(e["snr_db"]): e["p_fa"][at] for e in sweep},
+        "offsets_1db_3db": {"p_d_at_iou_0.5": {str(e["snr_db"]): e["p_d"][at] for e in sweep_alt},
+                            "p_fa_at_iou_0.5": {str(e["snr_db"]): e["p_fa"][at] for e in sweep_alt},
+                            "detections": {str(e["snr_db"]): e["detections"] for e in sweep_alt}},
         "sweep": sweep, "harness": harness, "shapes": shapes,
     }
     det.close()

@@ -451,6 +451,20 @@ int rise_debug_export(rise_ctx *ctx, int what, void *dst, size_t bytes);
 #define RISE_OPT_TEST_WITHHOLD 10  /* test only: the box-slot scan's tile with this *
                                     * index publishes no sum, so every later tile's *
                                     * wait runs out; -1 (default): none             */
+/* The STFT stages each frame group into shared memory with a bulk copy and
+ * waits for it on a shared-memory barrier.  That wait gives up after
+ * RISE_OPT_COPY_WAIT_LIMIT polls (each suspends the thread for a
+ * hardware-defined interval; 0 restores the default 2^22).  Values below
+ * 2^12 are rejected: 2^12 polls already last far longer than an issued
+ * copy takes to land, and a shorter bound could give up on one on its way.
+ * The block then waits, with the same bound, for any copy it still has in
+ * flight, records the fact and leaves, and the call returns RISE_ETIMEOUT.
+ * Changing either option drops the context's captured graphs. */
+#define RISE_OPT_COPY_WAIT_LIMIT 12
+#define RISE_OPT_TEST_WITHHOLD_COPY 13  /* test only: block 0 of every STFT launch   *
+                                         * issues no copy for its frame group with   *
+                                         * this index, so its wait runs out; -1      *
+                                         * (default): none                           */
 /* Radix schedule of the FFT of single captures.  An N-point transform with
  * N = 16^a * r (r = 2, 4 or 8) runs its radix-r pass last (schedule 0) or
  * first (schedule 1); for r = 2 (N = 512, 8192) schedule 2 splits the

@@ -307,6 +307,8 @@ int fill_tables(rise_ctx *c, const rise_capture *caps, const Plan &p, const rise
     a.win = tb->win;
     a.err = &c->small->status.err;
     a.sched = tb->sched;
+    a.wait_limit = c->copy_wait_limit;
+    a.withhold_step = c->withhold_copy;
     const int g = p.group_of[k];
     const int frames = p.item_mult[g] * stft_frames_per_step(F);
     for (int64_t f0 = 0; f0 < T; f0 += frames) {
@@ -862,7 +864,7 @@ int detect_batch(rise_ctx *c, const rise_capture *caps, int ncap, const rise_thr
   b.last_ncap = ncap;
   b.last_px = p.total_px;
   b.last_hi_db = thr.hi_db;
-  if (h.err & (ERR_UNION_LIMIT | ERR_SCAN)) return RISE_ETIMEOUT;
+  if (h.err & (ERR_UNION_LIMIT | ERR_SCAN | ERR_COPY_WAIT)) return RISE_ETIMEOUT;
   if (h.err) return RISE_EINTERNAL;
   std::memcpy(offsets, b.offs_h, sizeof(int64_t) * (ncap + 1));
   const int64_t total = h.n_boxes;

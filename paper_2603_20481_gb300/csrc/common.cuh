@@ -19,6 +19,7 @@ enum : uint32_t {
   ERR_ROW_RUNS = 1u << 2,       // a row holds more runs than the morphology allows
   ERR_INDEX = 1u << 3,          // an index check failed
   ERR_SCAN = 1u << 4,           // a single-pass scan waited too long for a predecessor tile
+  ERR_COPY_WAIT = 1u << 5,      // the STFT waited too long for a staged input copy
 };
 
 struct DeviceStatus {
@@ -197,7 +198,12 @@ struct StftArgs {
   int fmt;                // IqFormat
   int sched;              // radix schedule of the tables tw (0: radix-16 passes first, 1: the small radix
                           // first, 2: the frame split into two half-size transforms)
+  int wait_limit;         // try_wait calls before a staged copy is given up (STFT_WAIT_LIMIT)
+  int64_t withhold_step;  // test only: block 0 issues no copy for this step (-1: none)
 };
+// Default bound of the STFT's wait for a staged input copy, in try_wait calls
+// (each suspends the thread for a hardware-defined interval).
+constexpr int STFT_WAIT_LIMIT = 1 << 22;
 
 enum StftMode { STFT_MAX = 0, STFT_QUANT = 1, STFT_POWER = 2, STFT_QUANT_POWER = 3 };
 cudaError_t launch_stft_sc16(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s);

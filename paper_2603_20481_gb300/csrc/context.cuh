@@ -108,6 +108,8 @@ struct rise_ctx {
   // withheld root-scan tile (-1: none)
   int spin_limit = rise::SCAN_SPIN_LIMIT, uf_limit = rise::UF_LIMIT;
   int64_t withhold_tile = -1;
+  int copy_wait_limit = rise::STFT_WAIT_LIMIT;   // RISE_OPT_COPY_WAIT_LIMIT
+  int64_t withhold_copy = -1;                    // RISE_OPT_TEST_WITHHOLD_COPY
   // radix schedule of single captures: 0 or 1 (default), or -1: the one the
   // batch tuner (or the tune cache) picked for the FFT size, else 1
   int fft_sched = 3;   // RISE_OPT_FFT_SCHEDULE: the library's schedule per size

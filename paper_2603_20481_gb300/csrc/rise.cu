@@ -314,7 +314,7 @@ int image_finish(rise_ctx *c, const uint8_t *img, int64_t T, int F, rise_box *ou
     h = (*c->cs().st_h);
   }
   c->last_status = c->cs().st_h;
-  if (h.err & (ERR_UNION_LIMIT | ERR_SCAN)) return RISE_ETIMEOUT;
+  if (h.err & (ERR_UNION_LIMIT | ERR_SCAN | ERR_COPY_WAIT)) return RISE_ETIMEOUT;
   if (h.err) return RISE_EINTERNAL;
   *n_boxes = h.n_boxes;
   const int64_t ncopy = std::min<int64_t>(h.n_boxes, cap);
@@ -397,6 +397,8 @@ int enqueue_detect(rise_ctx *c, const void *iq, int fmt, int64_t n, int N, int h
   a.win = tb->win;
   a.err = &sm->status.err;
   a.sched = tb->sched;
+  a.wait_limit = c->copy_wait_limit;
+  a.withhold_step = c->withhold_copy;
   bool hist_ready = false;
   if (thr.range_mode == RISE_RANGE_FIXED) {
     const double hp = std::pow(10.0, thr.hi_db / 10.0);
@@ -613,7 +615,7 @@ int finish_call(rise_ctx *c, rise_box *out, int64_t cap, int64_t *n_boxes) {
     std::memcpy(&mf, &h.max_bits, 4);
     c->last_anchor = mf;
   }
-  if (h.err & (ERR_UNION_LIMIT | ERR_SCAN)) return RISE_ETIMEOUT;
+  if (h.err & (ERR_UNION_LIMIT | ERR_SCAN | ERR_COPY_WAIT)) return RISE_ETIMEOUT;
   if (h.err) return RISE_EINTERNAL;
   *n_boxes = h.n_boxes;
   const int64_t lim = std::min(cap, sl.cap);
@@ -902,6 +904,20 @@ int rise_set_option(rise_ctx *c, int option, int64_t value) {
     case RISE_OPT_FFT_SCHEDULE:
       if (value < -1 || value > 3) return RISE_EINVAL;
       c->fft_sched = (int)value;
+      return RISE_OK;
+    case RISE_OPT_COPY_WAIT_LIMIT:
+      // at least 2^12 polls, far longer than an issued copy takes to land,
+      // so that a block does not give up on a copy that is on its way
+      if ((value != 0 && value < 4096) || value > INT32_MAX) return RISE_EINVAL;
+      CK(cudaSetDevice(c->device));
+      c->copy_wait_limit = value ? (int)value : STFT_WAIT_LIMIT;
+      new_generation(c);
+      return RISE_OK;
+    case RISE_OPT_TEST_WITHHOLD_COPY:
+      if (value < -1) return RISE_EINVAL;
+      CK(cudaSetDevice(c->device));
+      c->withhold_copy = value;
+      new_generation(c);
       return RISE_OK;
   }
   return RISE_EINVAL;

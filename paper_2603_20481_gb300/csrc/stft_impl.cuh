@@ -196,10 +196,10 @@ __device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait: try_wait suspends for a hardware-defined interval per call
-constexpr int kWaitLimit = 1 << 22;
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
-  for (int i = 0; i < kWaitLimit; ++i)
+// bounded wait: try_wait suspends for a hardware-defined interval per call,
+// and gives up after `limit` calls (STFT_WAIT_LIMIT unless an option lowers it)
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, int limit) {
+  for (int i = 0; i < limit; ++i)
     if (mbar_test(b, parity)) return true;
   return false;
 }
@@ -353,6 +353,7 @@ __device__ __forceinline__ bool stft_frames_plain(const StftArgs &a, int64_t f_b
       atomicOr(a.err, ERR_INDEX);   // checked build: a frame beyond the capture
       return;
     }
+    if (blockIdx.x == 0 && st == a.withhold_step) return;   // test only: this copy never comes
     mbar_expect_tx(bar, bytes);
     bulk_g2s(stage, iq + t0 * (int64_t)a.hop, bytes, bar);
   };
@@ -398,7 +399,7 @@ __device__ __forceinline__ bool stft_frames_plain(const StftArgs &a, int64_t f_b
     const bool valid = t < f_end;
     float2 v[16];
     if constexpr (TMA) {
-      if (!mbar_wait(bar, (uint32_t)(st & 1))) failed = true;
+      if (!mbar_wait(bar, (uint32_t)(st & 1), a.wait_limit)) failed = true;
       const IN *x = reinterpret_cast<const IN *>(stage) + (valid ? slot * a.hop : 0) + tau;
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
@@ -422,8 +423,8 @@ __device__ __forceinline__ bool stft_frames_plain(const StftArgs &a, int64_t f_b
     if (__syncthreads_or(failed)) {
       // a staged copy never arrived: record it, let copies in flight land, leave
       if (tid == 0) {
-        atomicOr(a.err, ERR_INDEX);
-        if constexpr (TMA) mbar_wait(bar, (uint32_t)(st & 1));
+        atomicOr(a.err, ERR_COPY_WAIT);
+        if constexpr (TMA) mbar_wait(bar, (uint32_t)(st & 1), a.wait_limit);
       }
       return false;
     }
@@ -561,6 +562,7 @@ __device__ __forceinline__ bool stft_frames_split(const StftArgs &a, int64_t f_b
       atomicOr(a.err, ERR_INDEX);   // checked build: a frame beyond the capture
       return;
     }
+    if (blockIdx.x == 0 && st == a.withhold_step) return;   // test only: this copy never comes
     mbar_expect_tx(bar, bytes);
     bulk_g2s(stage, iq + t0 * (int64_t)a.hop, bytes, bar);
   };
@@ -609,7 +611,7 @@ __device__ __forceinline__ bool stft_frames_split(const StftArgs &a, int64_t f_b
       const IN *x;
       bool ok = valid;
       if constexpr (TMA) {
-        if (!mbar_wait(bar, (uint32_t)(st & 1))) failed = true;
+        if (!mbar_wait(bar, (uint32_t)(st & 1), a.wait_limit)) failed = true;
         x = reinterpret_cast<const IN *>(stage) + (valid ? slot * a.hop : 0) + j;
       } else {
         ok = valid && (!kChecked || ck_index(t * (int64_t)a.hop + N - 1, a.n, a.err));
@@ -643,8 +645,8 @@ __device__ __forceinline__ bool stft_frames_split(const StftArgs &a, int64_t f_b
     store_pass<M, 0, 0>(v, b0, j);
     if (__syncthreads_or(failed)) {
       if (tid == 0) {
-        atomicOr(a.err, ERR_INDEX);
-        if constexpr (TMA) mbar_wait(bar, (uint32_t)(st & 1));
+        atomicOr(a.err, ERR_COPY_WAIT);
+        if constexpr (TMA) mbar_wait(bar, (uint32_t)(st & 1), a.wait_limit);
       }
       return false;
     }
@@ -739,15 +741,17 @@ __device__ __forceinline__ bool stft_frames_split_async(const StftArgs &a, int64
   const int tid = threadIdx.x;
   const int h = tid / HALF, j = tid % HALF;             // half of the block and its thread
   const int64_t nsteps = f_end - f_begin;
-  auto issue = [&](int64_t st) {
+  auto issue = [&](int64_t st) -> bool {   // true when the copy is in flight
     const int64_t t = f_begin + st;
     constexpr uint32_t bytes = (uint32_t)(N * sizeof(IN));
     if (kChecked && (t < 0 || t * (int64_t)a.hop * (int64_t)sizeof(IN) + bytes > a.n * (int64_t)sizeof(IN))) {
       atomicOr(a.err, ERR_INDEX);   // checked build: a frame beyond the capture
-      return;
+      return false;
     }
+    if (blockIdx.x == 0 && st == a.withhold_step) return false;   // test only: this copy never comes
     mbar_expect_tx(bar, bytes);
     bulk_g2s(stage, iq + t * (int64_t)a.hop, bytes, bar);
+    return true;
   };
   if (tid == 0) {
     s_out = 0;
@@ -757,10 +761,7 @@ __device__ __forceinline__ bool stft_frames_split_async(const StftArgs &a, int64
       mbar_init(bar, 1);
       mbar_fence_init();
       fence_proxy_async();
-      if (nsteps > 0) {
-        issue(0);
-        s_issued = 1;
-      }
+      if (nsteps > 0 && issue(0)) s_issued = 1;
     }
   }
   float win[16];
@@ -792,7 +793,7 @@ __device__ __forceinline__ bool stft_frames_split_async(const StftArgs &a, int64
       const IN *x;
       bool ok = true;
       if constexpr (TMA) {
-        if (!mbar_wait(bar, (uint32_t)(st & 1))) failed = true;
+        if (!mbar_wait(bar, (uint32_t)(st & 1), a.wait_limit)) failed = true;
         x = reinterpret_cast<const IN *>(stage) + j;
       } else {
         ok = !kChecked || ck_index(t * (int64_t)a.hop + N - 1, a.n, a.err);
@@ -840,7 +841,7 @@ __device__ __forceinline__ bool stft_frames_split_async(const StftArgs &a, int64
     if (bar_or(bar_id, HALF, failed)) {
       if (j == 0) {
         s_fail = 1;
-        atomicOr(a.err, ERR_INDEX);
+        atomicOr(a.err, ERR_COPY_WAIT);
       }
       break;
     }
@@ -851,8 +852,7 @@ __device__ __forceinline__ bool stft_frames_split_async(const StftArgs &a, int64
         __threadfence_block();
         if (before == 2 * (int)st + 1 && st + 1 < nsteps) {   // both halves are out of the stage
           fence_proxy_async();
-          issue(st + 1);
-          s_issued = (int)st + 2;
+          if (issue(st + 1)) s_issued = (int)st + 2;
         }
       }
     }
@@ -881,7 +881,7 @@ __device__ __forceinline__ bool stft_frames_split_async(const StftArgs &a, int64
   const bool failed = s_fail != 0;
   // after a wait ran out, the last copy issued may still be in flight: wait
   // (bounded) for it before the block lets go of its shared memory
-  if (TMA && failed && tid == 0 && s_issued > 0) mbar_wait(bar, (uint32_t)((s_issued - 1) & 1));
+  if (TMA && failed && tid == 0 && s_issued > 0) mbar_wait(bar, (uint32_t)((s_issued - 1) & 1), a.wait_limit);
   if constexpr (DO_MAX) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) run_max = fmaxf(run_max, __shfl_xor_sync(0xffffffffu, run_max, o));

@@ -35,6 +35,7 @@ STAGES = ("spectrum_pass1", "spectrum_pass2", "histogram", "column_stats", "morp
 OPT_KEEP_POWER, OPT_KEEP_MASKS, OPT_TIMING, OPT_RANGE_PATH = 1, 2, 3, 4
 OPT_GRAPH, OPT_AUTOTUNE, OPT_RUN_CAPACITY = 5, 6, 7
 OPT_SCAN_WAIT_LIMIT, OPT_UNION_LIMIT, OPT_TEST_WITHHOLD, OPT_FFT_SCHEDULE = 8, 9, 10, 11
+OPT_COPY_WAIT_LIMIT, OPT_TEST_WITHHOLD_COPY = 12, 13
 IQ_HOST, IQ_SC16 = 1, 2
 OPT_BATCH_GRAPH = OPT_GRAPH
 BATCH_MAX_ROWS = 524280

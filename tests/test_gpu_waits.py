@@ -123,10 +123,53 @@ def test_waits_run_out_on_the_capture_and_batch_paths():
             np.testing.assert_array_equal(b, want_b)
 
 
+@pytest.mark.parametrize("N,hop,sched", [(1024, 512, 1), (4096, 2048, 1), (8192, 2048, 1), (8192, 2048, 2)])
+def test_staged_copy_wait_runs_out_and_the_context_recovers(N, hop, sched):
+    """The STFT's wait for a staged input copy: with RISE_OPT_TEST_WITHHOLD_COPY
+    block 0 never issues the copy of one frame group, so its barrier wait runs
+    out after RISE_OPT_COPY_WAIT_LIMIT polls; the block leaves (the halves of a
+    schedule-2 block both leave, since no copy is issued without both), the
+    call ends with RISE_ETIMEOUT on the single-capture and batch paths, and the
+    next calls give the boxes of an untouched context.  No copy is in flight
+    when a block leaves: the withheld one was never issued."""
+    from paper_2603_20481_gb300 import rise
+    cap = synth.make_capture(N * 64, 100e6, 12, 71 + N, fft_size=N, hop=hop,
+                             bw_hz=(0.2e6, 20e6), dur_s=(0.05e-3, 0.3e-3), snr_db=(5, 20))
+    x = torch.from_numpy(cap.iq).cuda()
+    caps = synth.batched_captures(4, 8200 + N, n_range=(1 << 15, 1 << 17))
+    xs = [torch.from_numpy(c.iq).cuda() for c in caps]
+    Ns = [c.fft_size for c in caps]
+    hops = [c.hop for c in caps]
+    with rise.Detector(0) as d:
+        d.set_option(rise.OPT_AUTOTUNE, 0)
+        d.set_option(rise.OPT_FFT_SCHEDULE, sched)
+        want = d.detect(x, N, hop)
+        want_b, want_o = d.detect_batch(xs, Ns, hops)
+        d.set_option(rise.OPT_COPY_WAIT_LIMIT, 1 << 14)
+        d.set_option(rise.OPT_TEST_WITHHOLD_COPY, 0)   # the first copy of block 0
+        for _ in range(2):
+            with pytest.raises(rise.RiseError) as e:
+                d.detect(x, N, hop)
+            assert e.value.code == rise.RISE_ETIMEOUT
+        with pytest.raises(rise.RiseError) as e:
+            d.detect_batch(xs, Ns, hops)
+        assert e.value.code == rise.RISE_ETIMEOUT
+        d.set_option(rise.OPT_TEST_WITHHOLD_COPY, -1)
+        d.set_option(rise.OPT_COPY_WAIT_LIMIT, 0)
+        for _ in range(2):
+            np.testing.assert_array_equal(d.detect(x, N, hop), want)
+            b, o = d.detect_batch(xs, Ns, hops)
+            np.testing.assert_array_equal(o, want_o)
+            np.testing.assert_array_equal(b, want_b)
+
+
 def test_limit_options_are_checked():
     from paper_2603_20481_gb300 import rise
     with rise.Detector(0) as d:
         for opt, bad in ((rise.OPT_SCAN_WAIT_LIMIT, -1), (rise.OPT_UNION_LIMIT, -5),
-                         (rise.OPT_TEST_WITHHOLD, -2), (rise.OPT_UNION_LIMIT, 1 << 40)):
+                         (rise.OPT_TEST_WITHHOLD, -2), (rise.OPT_UNION_LIMIT, 1 << 40),
+                         (rise.OPT_COPY_WAIT_LIMIT, -1), (rise.OPT_COPY_WAIT_LIMIT, 1 << 40),
+                         (rise.OPT_COPY_WAIT_LIMIT, 4095),
+                         (rise.OPT_TEST_WITHHOLD_COPY, -2)):
             with pytest.raises(rise.RiseError):
                 d.set_option(opt, bad)
