@@ -67,10 +67,14 @@ STFT_SOURCES = ("paper_2603_20481_gb300/csrc/stft_impl.cuh", "paper_2603_20481_g
                 "paper_2603_20481_gb300/csrc/common.cuh")
 TRAFFIC = {
     # stft_kernel<8192, 2, POWER>: one capture of the stress generator cut to
-    # 2^25 samples (16381 frames), 278,758,400 B read + 480,090,880 B written,
+    # 2^25 samples (16381 frames), 278,363,904 B read + 479,712,256 B written,
     # scaled by frames to the 131069 frames of the full capture
-    "stress": {"sha256": "ea9bfad22a823574819f365d54abca2ab5bc9f4480820c85ca1d48475fc88210",
-               "n_samples": 1 << 28, "sched": 2, "bytes": 6071767064},
+    "stress": {"sha256": "dfa90f1288657640ccb3465989eb5e985fceb853bc28557a04b0aa07da6f09f1",
+               "n_samples": 1 << 28, "sched": 2, "bytes": 6065581113},
+    # stft_kernel<4096, 0, POWER>: the full wideband capture, one launch
+    # (542,057,728 B read + 493,294,848 B written)
+    "wideband": {"sha256": "2be35a2dfa8d3704d5eda7e4bfec14075a21c3ebc6b0f138d186dbb727a27b8e",
+                 "n_samples": 1 << 26, "sched": 0, "bytes": 1035352576},
 }
 
 
@@ -359,8 +363,16 @@ def measure_single(args, name: str):
     # end to end through the host entry point (pinned memory -> HBM -> boxes)
     e2e = None
     if not args.no_e2e:
-        for _ in range(max(1, args.warmup)):
-            det.detect_host(host, N_FFT, HOP)
+        def pipelined(src, k):
+            det.submit(src, N_FFT, HOP)  # the next capture's copy overlaps this one's detection
+            for i in range(k):
+                if i + 1 < k:
+                    det.submit(src, N_FFT, HOP)
+                out = det.collect()
+            return out
+        # warm-up in the same pattern as the timed loop: both call slots get
+        # their device copy of the input and their captured graph before timing
+        pipelined(host, max(3, args.warmup))
         torch.cuda.synchronize()
         _barrier(world)
         t0 = time.perf_counter()
@@ -380,9 +392,7 @@ def measure_single(args, name: str):
         q16[:, 0] = np.round(cap.iq.real * (0.7 * 32767.0 / peak_amp))
         q16[:, 1] = np.round(cap.iq.imag * (0.7 * 32767.0 / peak_amp))
         h16 = torch.from_numpy(q16).pin_memory()
-        for _ in range(max(1, args.warmup)):
-            det.submit(h16, N_FFT, HOP)
-            det.collect()
+        pipelined(h16, max(3, args.warmup))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         det.submit(h16, N_FFT, HOP)

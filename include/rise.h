@@ -459,7 +459,10 @@ int rise_debug_export(rise_ctx *ctx, int what, void *dst, size_t bytes);
  * copy takes to land, and a shorter bound could give up on one on its way.
  * The block then waits, with the same bound, for any copy it still has in
  * flight, records the fact and leaves, and the call returns RISE_ETIMEOUT.
- * Changing either option drops the context's captured graphs. */
+ * Both options act on the float-power STFT (range path 2, the default, and
+ * batches without a fixed range), which runs a separate kernel instance
+ * while either is away from its default; the other STFT kernels always wait
+ * 2^22 polls.  Changing either option drops the context's captured graphs. */
 #define RISE_OPT_COPY_WAIT_LIMIT 12
 #define RISE_OPT_TEST_WITHHOLD_COPY 13  /* test only: block 0 of every STFT launch   *
                                          * issues no copy for its frame group with   *

@@ -429,7 +429,8 @@ int enqueue(rise_ctx *c, const Plan &p, const rise_thresholds &thr, int64_t cap,
   mark();
   for (size_t g = 0; g < p.groups.size(); ++g) {
     const auto &G = p.groups[g];
-    CK(launch_stft_batch(G.N, p.sched[g], G.tma, p.fixed ? STFT_QUANT : STFT_POWER, stft, items + G.item0,
+    CK(launch_stft_batch(G.N, p.sched[g], G.tma,
+                         p.fixed ? STFT_QUANT : (stft_hooks_on(c) ? STFT_POWER_HOOKED : STFT_POWER), stft, items + G.item0,
                          G.n_items, counters + g, c->num_sms, s));
     mark();
   }

@@ -205,7 +205,11 @@ struct StftArgs {
 // (each suspends the thread for a hardware-defined interval).
 constexpr int STFT_WAIT_LIMIT = 1 << 22;
 
-enum StftMode { STFT_MAX = 0, STFT_QUANT = 1, STFT_POWER = 2, STFT_QUANT_POWER = 3 };
+// STFT_POWER_HOOKED is STFT_POWER in a separate kernel instance that also
+// honours the copy-wait bound and the withheld copy of StftArgs (the test
+// hooks); the other instances wait with the fixed bound STFT_WAIT_LIMIT and
+// never withhold, so the hooks cost the default path nothing.
+enum StftMode { STFT_MAX = 0, STFT_QUANT = 1, STFT_POWER = 2, STFT_QUANT_POWER = 3, STFT_POWER_HOOKED = 4 };
 cudaError_t launch_stft_sc16(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s);
 // Schedules 1 and 2 of complex64 input (their own translation units).
 cudaError_t launch_stft_s1(const StftArgs &a, StftMode mode, int num_sms, cudaStream_t s);

@@ -173,6 +173,12 @@ int ensure_hbox(rise_ctx *c, int64_t cap);
 int get_tables(rise_ctx *c, int N, int S, Tables **out);
 // The radix schedule a single capture of FFT size N runs.
 int single_sched(const rise_ctx *c, int N);
+// True when an STFT test hook is set (RISE_OPT_COPY_WAIT_LIMIT not at its
+// default, or RISE_OPT_TEST_WITHHOLD_COPY >= 0): the float-power STFT then
+// runs its hooked instance (StftMode STFT_POWER_HOOKED).
+inline bool stft_hooks_on(const rise_ctx *c) {
+  return c->copy_wait_limit != rise::STFT_WAIT_LIMIT || c->withhold_copy >= 0;
+}
 bool pow2(int64_t v);
 int check_thresholds(const rise_thresholds &t, int F);
 void record(rise_ctx *c, int i);

@@ -406,7 +406,7 @@ int enqueue_detect(rise_ctx *c, const void *iq, int fmt, int64_t n, int N, int h
     CK(launch_levels(a.max_bits, hp, 1, sm->ratio, thr.level_db, sm->edges, sm->qconst, s));
     CK(launch_stft(a, c->keep_power ? STFT_QUANT_POWER : STFT_QUANT, c->num_sms, s));
   } else if (path == 2) {
-    CK(launch_stft(a, STFT_POWER, c->num_sms, s));
+    CK(launch_stft(a, stft_hooks_on(c) ? STFT_POWER_HOOKED : STFT_POWER, c->num_sms, s));
     record(c, 1);
     if (cluster_hist_accumulates(T))
       CK(cudaMemsetAsync(c->hist.p, 0, (size_t)F * 256 * sizeof(uint32_t), s));

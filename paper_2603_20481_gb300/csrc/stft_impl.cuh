@@ -326,9 +326,12 @@ __device__ __forceinline__ bool stft_frames_plain(const StftArgs &a, int64_t f_b
   using PL = Plan<N, S>;
   using SM = Smem<N, S, TMA>;
   constexpr int TPF = PL::TPF, FPB = PL::FPB, SLOT = PL::SLOT, NPASS = PL::NPASS, NXB = SM::NXB;
-  constexpr bool DO_MAX = (MODE == STFT_MAX || MODE == STFT_POWER);
-  constexpr bool DO_Q = (MODE == STFT_QUANT || MODE == STFT_QUANT_POWER);
-  constexpr bool DO_P = (MODE == STFT_POWER || MODE == STFT_QUANT_POWER);
+  constexpr bool HOOK = MODE == STFT_POWER_HOOKED;                // test hooks (see StftMode)
+  constexpr int EM = HOOK ? STFT_POWER : MODE;                     // the mode's work
+  constexpr bool DO_MAX = (EM == STFT_MAX || EM == STFT_POWER);
+  constexpr bool DO_Q = (EM == STFT_QUANT || EM == STFT_QUANT_POWER);
+  constexpr bool DO_P = (EM == STFT_POWER || EM == STFT_QUANT_POWER);
+  const int wait_limit = HOOK ? a.wait_limit : STFT_WAIT_LIMIT;
   float2 *stage = smem;                                   // [STAGE] (TMA only)
   float2 *xb0 = smem + SM::STAGE;
   float2 *xb1 = xb0 + (NXB == 2 ? SM::XB : 0);
@@ -353,7 +356,7 @@ __device__ __forceinline__ bool stft_frames_plain(const StftArgs &a, int64_t f_b
       atomicOr(a.err, ERR_INDEX);   // checked build: a frame beyond the capture
       return;
     }
-    if (blockIdx.x == 0 && st == a.withhold_step) return;   // test only: this copy never comes
+    if (HOOK && blockIdx.x == 0 && st == a.withhold_step) return;   // test only: this copy never comes
     mbar_expect_tx(bar, bytes);
     bulk_g2s(stage, iq + t0 * (int64_t)a.hop, bytes, bar);
   };
@@ -399,7 +402,7 @@ __device__ __forceinline__ bool stft_frames_plain(const StftArgs &a, int64_t f_b
     const bool valid = t < f_end;
     float2 v[16];
     if constexpr (TMA) {
-      if (!mbar_wait(bar, (uint32_t)(st & 1), a.wait_limit)) failed = true;
+      if (!mbar_wait(bar, (uint32_t)(st & 1), wait_limit)) failed = true;
       const IN *x = reinterpret_cast<const IN *>(stage) + (valid ? slot * a.hop : 0) + tau;
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
@@ -424,7 +427,7 @@ __device__ __forceinline__ bool stft_frames_plain(const StftArgs &a, int64_t f_b
       // a staged copy never arrived: record it, let copies in flight land, leave
       if (tid == 0) {
         atomicOr(a.err, ERR_COPY_WAIT);
-        if constexpr (TMA) mbar_wait(bar, (uint32_t)(st & 1), a.wait_limit);
+        if constexpr (TMA) mbar_wait(bar, (uint32_t)(st & 1), wait_limit);
       }
       return false;
     }
@@ -535,9 +538,12 @@ __device__ __forceinline__ bool stft_frames_split(const StftArgs &a, int64_t f_b
   constexpr bool WARP_GROUPS = HALF % 32 == 0;
   static_assert(PM::RSMALL == 1 && NPM >= 2 && NPM <= 3, "M is 256 or 4096");
   static_assert(SLOT == 2 * SLOTM, "two padded halves per frame");
-  constexpr bool DO_MAX = (MODE == STFT_MAX || MODE == STFT_POWER);
-  constexpr bool DO_Q = (MODE == STFT_QUANT || MODE == STFT_QUANT_POWER);
-  constexpr bool DO_P = (MODE == STFT_POWER || MODE == STFT_QUANT_POWER);
+  constexpr bool HOOK = MODE == STFT_POWER_HOOKED;                // test hooks (see StftMode)
+  constexpr int EM = HOOK ? STFT_POWER : MODE;                     // the mode's work
+  constexpr bool DO_MAX = (EM == STFT_MAX || EM == STFT_POWER);
+  constexpr bool DO_Q = (EM == STFT_QUANT || EM == STFT_QUANT_POWER);
+  constexpr bool DO_P = (EM == STFT_POWER || EM == STFT_QUANT_POWER);
+  const int wait_limit = HOOK ? a.wait_limit : STFT_WAIT_LIMIT;
   const IN *iq = static_cast<const IN *>(a.iq);
   float2 *stage = smem;
   float2 *xb0 = smem + SM::STAGE;
@@ -562,7 +568,7 @@ __device__ __forceinline__ bool stft_frames_split(const StftArgs &a, int64_t f_b
       atomicOr(a.err, ERR_INDEX);   // checked build: a frame beyond the capture
       return;
     }
-    if (blockIdx.x == 0 && st == a.withhold_step) return;   // test only: this copy never comes
+    if (HOOK && blockIdx.x == 0 && st == a.withhold_step) return;   // test only: this copy never comes
     mbar_expect_tx(bar, bytes);
     bulk_g2s(stage, iq + t0 * (int64_t)a.hop, bytes, bar);
   };
@@ -611,7 +617,7 @@ __device__ __forceinline__ bool stft_frames_split(const StftArgs &a, int64_t f_b
       const IN *x;
       bool ok = valid;
       if constexpr (TMA) {
-        if (!mbar_wait(bar, (uint32_t)(st & 1), a.wait_limit)) failed = true;
+        if (!mbar_wait(bar, (uint32_t)(st & 1), wait_limit)) failed = true;
         x = reinterpret_cast<const IN *>(stage) + (valid ? slot * a.hop : 0) + j;
       } else {
         ok = valid && (!kChecked || ck_index(t * (int64_t)a.hop + N - 1, a.n, a.err));
@@ -646,7 +652,7 @@ __device__ __forceinline__ bool stft_frames_split(const StftArgs &a, int64_t f_b
     if (__syncthreads_or(failed)) {
       if (tid == 0) {
         atomicOr(a.err, ERR_COPY_WAIT);
-        if constexpr (TMA) mbar_wait(bar, (uint32_t)(st & 1), a.wait_limit);
+        if constexpr (TMA) mbar_wait(bar, (uint32_t)(st & 1), wait_limit);
       }
       return false;
     }
@@ -727,9 +733,12 @@ __device__ __forceinline__ bool stft_frames_split_async(const StftArgs &a, int64
   constexpr int HALF = M / 16, SLOTM = M + M / 16, NPM = PM::NPASS;
   static_assert(PL::FPB == 1 && HALF % 32 == 0 && NPM == 3 && SM::NXB == 2 && PL::SLOT == 2 * SLOTM,
                 "one frame per step, whole-warp halves, three passes per half, two exchange buffers");
-  constexpr bool DO_MAX = (MODE == STFT_MAX || MODE == STFT_POWER);
-  constexpr bool DO_Q = (MODE == STFT_QUANT || MODE == STFT_QUANT_POWER);
-  constexpr bool DO_P = (MODE == STFT_POWER || MODE == STFT_QUANT_POWER);
+  constexpr bool HOOK = MODE == STFT_POWER_HOOKED;                // test hooks (see StftMode)
+  constexpr int EM = HOOK ? STFT_POWER : MODE;                     // the mode's work
+  constexpr bool DO_MAX = (EM == STFT_MAX || EM == STFT_POWER);
+  constexpr bool DO_Q = (EM == STFT_QUANT || EM == STFT_QUANT_POWER);
+  constexpr bool DO_P = (EM == STFT_POWER || EM == STFT_QUANT_POWER);
+  const int wait_limit = HOOK ? a.wait_limit : STFT_WAIT_LIMIT;
   __shared__ int s_out, s_issued, s_fail;
   const IN *iq = static_cast<const IN *>(a.iq);
   float2 *stage = smem;
@@ -748,7 +757,7 @@ __device__ __forceinline__ bool stft_frames_split_async(const StftArgs &a, int64
       atomicOr(a.err, ERR_INDEX);   // checked build: a frame beyond the capture
       return false;
     }
-    if (blockIdx.x == 0 && st == a.withhold_step) return false;   // test only: this copy never comes
+    if (HOOK && blockIdx.x == 0 && st == a.withhold_step) return false;   // test only: this copy never comes
     mbar_expect_tx(bar, bytes);
     bulk_g2s(stage, iq + t * (int64_t)a.hop, bytes, bar);
     return true;
@@ -793,7 +802,7 @@ __device__ __forceinline__ bool stft_frames_split_async(const StftArgs &a, int64
       const IN *x;
       bool ok = true;
       if constexpr (TMA) {
-        if (!mbar_wait(bar, (uint32_t)(st & 1), a.wait_limit)) failed = true;
+        if (!mbar_wait(bar, (uint32_t)(st & 1), wait_limit)) failed = true;
         x = reinterpret_cast<const IN *>(stage) + j;
       } else {
         ok = !kChecked || ck_index(t * (int64_t)a.hop + N - 1, a.n, a.err);
@@ -881,7 +890,7 @@ __device__ __forceinline__ bool stft_frames_split_async(const StftArgs &a, int64
   const bool failed = s_fail != 0;
   // after a wait ran out, the last copy issued may still be in flight: wait
   // (bounded) for it before the block lets go of its shared memory
-  if (TMA && failed && tid == 0 && s_issued > 0) mbar_wait(bar, (uint32_t)((s_issued - 1) & 1), a.wait_limit);
+  if (TMA && failed && tid == 0 && s_issued > 0) mbar_wait(bar, (uint32_t)((s_issued - 1) & 1), wait_limit);
   if constexpr (DO_MAX) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) run_max = fmaxf(run_max, __shfl_xor_sync(0xffffffffu, run_max, o));
@@ -978,6 +987,7 @@ cudaError_t launch_mode(const StftArgs &a, StftMode mode, int num_sms, cudaStrea
     case STFT_QUANT: return launch_n<N, S, STFT_QUANT, TMA, IN>(a, num_sms, s);
     case STFT_POWER: return launch_n<N, S, STFT_POWER, TMA, IN>(a, num_sms, s);
     case STFT_QUANT_POWER: return launch_n<N, S, STFT_QUANT_POWER, TMA, IN>(a, num_sms, s);
+    case STFT_POWER_HOOKED: return launch_n<N, S, STFT_POWER_HOOKED, TMA, IN>(a, num_sms, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -1010,6 +1020,8 @@ cudaError_t batch_mode(StftMode mode, const StftArgs *segs, const StftItem *item
     case STFT_POWER: return launch_batch_n<N, S, STFT_POWER, TMA>(segs, items, n_items, counter, num_sms, s);
     case STFT_QUANT_POWER:
       return launch_batch_n<N, S, STFT_QUANT_POWER, TMA>(segs, items, n_items, counter, num_sms, s);
+    case STFT_POWER_HOOKED:
+      return launch_batch_n<N, S, STFT_POWER_HOOKED, TMA>(segs, items, n_items, counter, num_sms, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -1036,11 +1048,13 @@ void preload_stft_nt() {
   preload_kernel(stft_kernel<N, S, STFT_QUANT, TMA, IN>);
   preload_kernel(stft_kernel<N, S, STFT_POWER, TMA, IN>);
   preload_kernel(stft_kernel<N, S, STFT_QUANT_POWER, TMA, IN>);
+  preload_kernel(stft_kernel<N, S, STFT_POWER_HOOKED, TMA, IN>);
   if constexpr (std::is_same<IN, float2>::value) {
     preload_kernel(stft_batch_kernel<N, S, STFT_MAX, TMA>);
     preload_kernel(stft_batch_kernel<N, S, STFT_QUANT, TMA>);
     preload_kernel(stft_batch_kernel<N, S, STFT_POWER, TMA>);
     preload_kernel(stft_batch_kernel<N, S, STFT_QUANT_POWER, TMA>);
+    preload_kernel(stft_batch_kernel<N, S, STFT_POWER_HOOKED, TMA>);
   }
 }
 template <int N, int S, typename IN>
