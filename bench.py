@@ -72,9 +72,9 @@ TRAFFIC = {
     "stress": {"sha256": "dfa90f1288657640ccb3465989eb5e985fceb853bc28557a04b0aa07da6f09f1",
                "n_samples": 1 << 28, "sched": 2, "bytes": 6065581113},
     # stft_kernel<4096, 0, POWER>: the full wideband capture, one launch
-    # (542,057,728 B read + 493,294,848 B written)
-    "wideband": {"sha256": "2be35a2dfa8d3704d5eda7e4bfec14075a21c3ebc6b0f138d186dbb727a27b8e",
-                 "n_samples": 1 << 26, "sched": 0, "bytes": 1035352576},
+    # (541,914,368 B read + 493,135,616 B written)
+    "wideband": {"sha256": "dfa90f1288657640ccb3465989eb5e985fceb853bc28557a04b0aa07da6f09f1",
+                 "n_samples": 1 << 26, "sched": 0, "bytes": 1035049984},
 }
 
 
