@@ -795,7 +795,8 @@ def measure_served(args, loads=(0.5, 0.75, 1.0, 1.25, 1.5)):
 
     def measure(lanes, max_batch):
         srv = rise.Server(SERVE_N, SERVE_HOP, max_chunk=SERVE_CHUNK, max_streams=SERVE_RADIOS,
-                          device=local, lanes=lanes, max_batch=max_batch, max_pending=1 << 14)
+                          device=local, lanes=lanes, max_batch=max_batch, max_pending=1 << 14,
+                          spin_wait=args.lane_wait == "spin")
         # warm-up: every batch size the lanes will meet (largest first, so the
         # tables' staging is sized once), each a few times so that every lane
         # has captured its launch chain; then a closed loop
@@ -864,7 +865,7 @@ def measure_served(args, loads=(0.5, 0.75, 1.0, 1.25, 1.5)):
         "steps": int(served["stats"]["completed"]), "warmup": 3,
         "ms_per_step": served["saturation_ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": SERVE_WORKLOAD, "lanes": args.lanes, "max_batch": args.max_batch,
+        "config": {"workload": SERVE_WORKLOAD, "lanes": args.lanes, "max_batch": args.max_batch, "lane_wait": args.lane_wait,
                    "radios": SERVE_RADIOS, "chunk_samples": SERVE_CHUNK,
                    "step": "one chunk (steps = chunks completed; ms_per_step = 1 / saturation rate)",
                    "parallelism": "replicas x1"},
@@ -911,7 +912,7 @@ def run_windows(args):
     deadline_ms = WIN_T * WIN_N / WIN_FS * 1e3       # 20.48 ms
     srv = rise.Server(WIN_N, WIN_N, max_chunk=WIN_CHUNK, max_streams=radios, device=local,
                       lanes=args.lanes, max_batch=args.max_batch, max_pending=1 << 14,
-                      window_frames=WIN_T)
+                      window_frames=WIN_T, spin_wait=args.lane_wait == "spin")
 
     worst = []
     failed = [0]   # plots whose status was not RISE_OK (must stay 0)
@@ -970,7 +971,7 @@ def run_windows(args):
         "steps": int(plots), "warmup": 1, "ms_per_step": round(dt / max(plots, 1) * 1e3, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WINDOW_WORKLOAD, "radios": radios, "lanes": args.lanes,
+        "config": {"workload": WINDOW_WORKLOAD, "radios": radios, "lanes": args.lanes, "lane_wait": args.lane_wait,
                    "max_batch": args.max_batch, "window_frames": WIN_T,
                    "step": "one TF plot (2000 x 1024)", "parallelism": "replicas x1"},
         "saturation": {"ms_s": round(sat_ms_s, 1), "plots_per_s": round(plots / dt, 1),
@@ -1192,6 +1193,8 @@ def main():
                          "measured in the same run as sub-objects")
     ap.add_argument("--radios", type=int, default=32, help="windows: streams at 100 MS/s")
     ap.add_argument("--lanes", type=int, default=3, help="served: batches in flight")
+    ap.add_argument("--lane-wait", choices=("block", "spin"), default="block",
+                    help="served: lanes sleep (the server's default) or spin while a batch runs")
     ap.add_argument("--max-batch", type=int, default=32, help="served: chunks per batch")
     ap.add_argument("--serve-seconds", type=float, default=1.5, help="served: seconds per load level")
     ap.add_argument("--batch", type=int, default=256, help="captures of the batched workload")

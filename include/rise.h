@@ -304,6 +304,9 @@ typedef struct {
                            * rise_server_result_image (introspection: costs a     *
                            * device-to-host copy per batch and T*F host bytes per *
                            * result until taken); 0: off                          */
+  int spin_wait;          /* 1: lanes spin while their batch runs; 0 (default):   *
+                           * they sleep (RISE_OPT_BLOCKING_WAIT), leaving host    *
+                           * cores to the caller and the other lanes              */
 } rise_server_config;
 
 typedef struct {
@@ -464,6 +467,12 @@ int rise_debug_export(rise_ctx *ctx, int what, void *dst, size_t bytes);
  * while either is away from its default; the other STFT kernels always wait
  * 2^22 polls.  Changing either option drops the context's captured graphs. */
 #define RISE_OPT_COPY_WAIT_LIMIT 12
+/* How rise_detect_batch waits for its launches: 0 (default) lets the CUDA
+ * runtime decide (it spins while the process has few contexts), 1 sleeps on
+ * a blocking-sync event, which frees the calling thread's core at the cost of
+ * a wake-up delay.  Server lanes use it unless their server was made with
+ * spin_wait set. */
+#define RISE_OPT_BLOCKING_WAIT 14
 #define RISE_OPT_TEST_WITHHOLD_COPY 13  /* test only: block 0 of every STFT launch   *
                                          * issues no copy for its frame group with   *
                                          * this index, so its wait runs out; -1      *

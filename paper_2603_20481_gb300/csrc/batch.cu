@@ -839,7 +839,7 @@ int detect_batch(rise_ctx *c, const rise_capture *caps, int ncap, const rise_thr
     }
   }
   if (!launched && (rc = enqueue(c, p, thr, cap, nullptr, nullptr, false))) return rc;
-  CK(cudaStreamSynchronize(c->stream));
+  CK(wait_stream(c));
   DeviceStatus h = (*c->cs().st_h);
   if (h.err & ERR_RUN_CAPACITY) {
     // more runs than the run arrays hold: grow them and run the chain again
@@ -856,7 +856,7 @@ int detect_batch(rise_ctx *c, const rise_capture *caps, int ncap, const rise_thr
     c->run_cap = need;
     if ((rc = fill_tables(c, caps, p, thr))) return rc;
     if ((rc = enqueue(c, p, thr, cap, nullptr, nullptr, false))) return rc;
-    CK(cudaStreamSynchronize(c->stream));
+    CK(wait_stream(c));
     h = (*c->cs().st_h);
   }
   c->last_status = c->cs().st_h;

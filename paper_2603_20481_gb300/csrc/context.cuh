@@ -110,6 +110,8 @@ struct rise_ctx {
   int64_t withhold_tile = -1;
   int copy_wait_limit = rise::STFT_WAIT_LIMIT;   // RISE_OPT_COPY_WAIT_LIMIT
   int64_t withhold_copy = -1;                    // RISE_OPT_TEST_WITHHOLD_COPY
+  bool blocking_wait = false;                    // RISE_OPT_BLOCKING_WAIT
+  cudaEvent_t wait_ev = nullptr;                 // blocking-sync event for it
   // radix schedule of single captures: 0 or 1 (default), or -1: the one the
   // batch tuner (or the tune cache) picked for the FFT size, else 1
   int fft_sched = 3;   // RISE_OPT_FFT_SCHEDULE: the library's schedule per size
@@ -173,6 +175,9 @@ int ensure_hbox(rise_ctx *c, int64_t cap);
 int get_tables(rise_ctx *c, int N, int S, Tables **out);
 // The radix schedule a single capture of FFT size N runs.
 int single_sched(const rise_ctx *c, int N);
+// Waits for the context's stream: spinning (the runtime's default for one
+// context) or, with RISE_OPT_BLOCKING_WAIT, asleep on a blocking-sync event.
+cudaError_t wait_stream(rise_ctx *c);
 // True when an STFT test hook is set (RISE_OPT_COPY_WAIT_LIMIT not at its
 // default, or RISE_OPT_TEST_WITHHOLD_COPY >= 0): the float-power STFT then
 // runs its hooked instance (StftMode STFT_POWER_HOOKED).

@@ -121,6 +121,16 @@ int get_tables(rise_ctx *c, int N, int S, Tables **out) {
   return RISE_OK;
 }
 
+cudaError_t wait_stream(rise_ctx *c) {
+  if (!c->blocking_wait) return cudaStreamSynchronize(c->stream);
+  if (!c->wait_ev) {
+    const cudaError_t e = cudaEventCreateWithFlags(&c->wait_ev, cudaEventBlockingSync | cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  const cudaError_t e = cudaEventRecord(c->wait_ev, c->stream);
+  return e != cudaSuccess ? e : cudaEventSynchronize(c->wait_ev);
+}
+
 int single_sched(const rise_ctx *c, int N) {
   int S = c->fft_sched;
   if (S < 0) {
@@ -762,6 +772,7 @@ void rise_destroy(rise_ctx *c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->wait_ev) cudaEventDestroy(c->wait_ev);
   Buf *bufs[] = {&c->power, &c->img, &c->hist, &c->cols, &c->effm1, &c->mask,
                  &c->dbg[0], &c->dbg[1], &c->dbg[2], &c->row_cnt, &c->row_base,
                  &c->run_parent, &c->run_sroot, &c->rec, &c->run_out, &c->scan_tmp, &c->boxes, &c->merge,
@@ -918,6 +929,10 @@ int rise_set_option(rise_ctx *c, int option, int64_t value) {
       CK(cudaSetDevice(c->device));
       c->withhold_copy = value;
       new_generation(c);
+      return RISE_OK;
+    case RISE_OPT_BLOCKING_WAIT:
+      if (value < 0 || value > 1) return RISE_EINVAL;
+      c->blocking_wait = value != 0;
       return RISE_OK;
   }
   return RISE_EINVAL;

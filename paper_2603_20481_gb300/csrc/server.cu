@@ -224,7 +224,7 @@ void lane_main(rise_server *s, int li) {
                                (int64_t)boxes.size(), offs.data());
       }
     } else {
-      cudaStreamSynchronize(cs);   // the carry copies of frame-less chunks
+      rise::host::wait_stream(ctx);   // the carry copies of frame-less chunks
     }
     const int64_t t_done = now_ns();
     // introspection: every capture's 8-bit image, back to back in batch order
@@ -368,6 +368,7 @@ int rise_server_create(rise_server **out, const rise_server_config *cfg) {
     cc.mem_budget = cfg->mem_budget ? scratch + scratch / 2 : 0;
     if ((rc = rise_create(&s->lanes[li].ctx, &cc))) break;
     rise_set_option(s->lanes[li].ctx, RISE_OPT_AUTOTUNE, 0);   // batch sizes vary: fixed shapes
+    rise_set_option(s->lanes[li].ctx, RISE_OPT_BLOCKING_WAIT, cfg->spin_wait ? 0 : 1);
     // window mode: plain launches (its batch compositions are many and a
     // capture inside a deadline costs more than the launches it saves)
     if (s->window) rise_set_option(s->lanes[li].ctx, RISE_OPT_GRAPH, 0);

@@ -35,7 +35,7 @@ STAGES = ("spectrum_pass1", "spectrum_pass2", "histogram", "column_stats", "morp
 OPT_KEEP_POWER, OPT_KEEP_MASKS, OPT_TIMING, OPT_RANGE_PATH = 1, 2, 3, 4
 OPT_GRAPH, OPT_AUTOTUNE, OPT_RUN_CAPACITY = 5, 6, 7
 OPT_SCAN_WAIT_LIMIT, OPT_UNION_LIMIT, OPT_TEST_WITHHOLD, OPT_FFT_SCHEDULE = 8, 9, 10, 11
-OPT_COPY_WAIT_LIMIT, OPT_TEST_WITHHOLD_COPY = 12, 13
+OPT_COPY_WAIT_LIMIT, OPT_TEST_WITHHOLD_COPY, OPT_BLOCKING_WAIT = 12, 13, 14
 IQ_HOST, IQ_SC16 = 1, 2
 OPT_BATCH_GRAPH = OPT_GRAPH
 BATCH_MAX_ROWS = 524280
@@ -76,7 +76,8 @@ class ServerConfig(C.Structure):
     _fields_ = [("device", C.c_int), ("fft_size", C.c_int), ("hop", C.c_int),
                 ("max_chunk", C.c_int64), ("max_streams", C.c_int), ("lanes", C.c_int),
                 ("max_batch", C.c_int), ("max_pending", C.c_int), ("mem_budget", C.c_size_t),
-                ("thr", C.c_void_p), ("window_frames", C.c_int64), ("keep_images", C.c_int)]
+                ("thr", C.c_void_p), ("window_frames", C.c_int64), ("keep_images", C.c_int),
+                ("spin_wait", C.c_int)]
 
 
 class Result(C.Structure):
@@ -555,14 +556,14 @@ class Server:
     def __init__(self, fft_size: int, hop: int, max_chunk: int, max_streams: int,
                  device: int = 0, lanes: int = 0, max_batch: int = 0, max_pending: int = 0,
                  mem_budget: int = 0, thr: Optional[Thresholds] = None, window_frames: int = 0,
-                 keep_images: bool = False):
+                 keep_images: bool = False, spin_wait: bool = False):
         self._thr = thr
         self.window = window_frames
         self.fft_size = fft_size
         cfg = ServerConfig(device, fft_size, hop, max_chunk, max_streams, lanes, max_batch,
                            max_pending, mem_budget,
                            C.cast(C.pointer(thr), C.c_void_p) if thr is not None else None,
-                           window_frames, int(bool(keep_images)))
+                           window_frames, int(bool(keep_images)), int(bool(spin_wait)))
         h = C.c_void_p()
         rc = lib().rise_server_create(C.byref(h), C.byref(cfg))
         if rc != RISE_OK:

@@ -175,10 +175,12 @@ def test_switches_give_the_same_boxes(det):
     ref_sched = det.batch_info()
     G = int(ref_sched[0])
     ref_sched = list(ref_sched[3 + G:3 + 3 * G])
-    for graph, tune in ((0, 0), (0, 1), (1, 0)):
+    # (graphs, tuner, blocking wait): the host's way of waiting changes nothing
+    for graph, tune, block in ((0, 0, 0), (0, 1, 0), (1, 0, 0), (1, 0, 1), (0, 0, 1)):
         with rise.Detector(0) as d2:
             d2.set_option(rise.OPT_BATCH_GRAPH, graph)
             d2.set_option(rise.OPT_AUTOTUNE, tune)
+            d2.set_option(rise.OPT_BLOCKING_WAIT, block)
             for _ in range(2):
                 b, o = d2.detect_batch(xs, Ns, hops)
                 info = d2.batch_info()

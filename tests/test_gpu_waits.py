@@ -170,6 +170,7 @@ def test_limit_options_are_checked():
                          (rise.OPT_TEST_WITHHOLD, -2), (rise.OPT_UNION_LIMIT, 1 << 40),
                          (rise.OPT_COPY_WAIT_LIMIT, -1), (rise.OPT_COPY_WAIT_LIMIT, 1 << 40),
                          (rise.OPT_COPY_WAIT_LIMIT, 4095),
-                         (rise.OPT_TEST_WITHHOLD_COPY, -2)):
+                         (rise.OPT_TEST_WITHHOLD_COPY, -2), (rise.OPT_BLOCKING_WAIT, 2),
+                         (rise.OPT_BLOCKING_WAIT, -1)):
             with pytest.raises(rise.RiseError):
                 d.set_option(opt, bad)
