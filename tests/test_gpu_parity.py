@@ -264,6 +264,48 @@ def test_range_paths_and_fixed_anchor_agree(det):
     assert np.array_equal(bg, oracle.detect_image(qg, thr_r))
 
 
+@pytest.mark.parametrize("N,hop,sched", [(8192, 2048, 2), (8192, 2048, 1), (8192, 2048, 0),
+                                         (512, 256, 2), (512, 256, 1), (1024, 512, 0), (4096, 1024, 0)])
+def test_every_epilogue_under_every_schedule(det, N, hop, sched):
+    """The four STFT epilogues under each radix schedule: range path 1 (the
+    anchor from a store-free MAX pass, then the QUANT pass writing the 8-bit
+    image) against path 2 (POWER, then the quantising histogram), bit for
+    bit; a fixed range with the float power kept (QUANT_POWER) against the
+    oracle: power within the float bar, image within one level, boxes equal
+    to the oracle on the GPU image."""
+    rise = _rise()
+    n = N * 40 + hop // 3
+    cap = synth.make_capture(n, 50e6, 8, 900 + N + sched, fft_size=N, hop=hop,
+                             bw_hz=(0.5e6, 8e6), dur_s=(n / 50e6 / 20, n / 50e6 / 4), snr_db=(5, 25),
+                             tone_fraction=0.3)
+    x = torch.from_numpy(cap.iq).cuda()
+    T = oracle.num_frames(n, N, hop)
+    det.set_option(rise.OPT_FFT_SCHEDULE, sched)
+    try:
+        out = {}
+        for path in (1, 2):
+            det.set_option(rise.OPT_RANGE_PATH, path)
+            out[path] = (det.detect(x, N, hop), det.debug(rise.DBG_IMAGE_U8, T, N).copy(),
+                         float(det.debug(rise.DBG_MAXPOW, T, N)[0]))
+        det.set_option(rise.OPT_RANGE_PATH, 0)
+        for a, b in zip(out[1], out[2]):
+            assert np.array_equal(a, b)
+        hi = oracle.hi_db_of(out[2][2]) - 2.0
+        thr_g, thr_r = _thr_pair(range_mode=1, hi_db=hi)
+        det.set_option(rise.OPT_KEEP_POWER, 1)
+        bg = det.detect(x, N, hop, thr_g)
+        Pg = det.debug(rise.DBG_POWER_F32, T, N)
+        qg = det.debug(rise.DBG_IMAGE_U8, T, N)
+    finally:
+        det.set_option(rise.OPT_KEEP_POWER, 0)
+        det.set_option(rise.OPT_RANGE_PATH, 0)
+        det.set_option(rise.OPT_FFT_SCHEDULE, 3)
+    _check_power(Pg, oracle.stft_power(cap.iq, N, hop))
+    _, qr, _ = oracle.detect(cap.iq, N, hop, thr_r)
+    _check_image(qg, qr)
+    assert np.array_equal(bg, oracle.detect_image(qg, thr_r))
+
+
 def test_degenerate_inputs(det):
     rise = _rise()
     # all-zero capture: every level 0, no boxes
