@@ -1088,8 +1088,9 @@ def run_quality(args):
                         "p_fa": [round(float(x) / max(nd, 1), 4) for x in nf]})
         return out
     # the library's default offsets (0.5 dB over the PSD floor, 10 dB over the
-    # power floor, chosen on the wideband generator), and the 1 dB / 3 dB
-    # offsets a first reading of the method suggested: the paper gives no value
+    # power floor, chosen by a sweep on synthetic captures), and the 1 dB /
+    # 3 dB offsets a first reading of the method suggested: the paper gives no
+    # value
     sweep = run_sweep(None)
     sweep_alt = run_sweep(rise.default_thresholds(psd_offset_db=1.0, power_offset_db=3.0))
     # the IoU harness on large random sets, through the C ABI call
