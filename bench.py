@@ -469,10 +469,10 @@ def run_headline(args):
     import torch
     torch.cuda.set_device(local)
     _init_dist(local, world)
+    sub = argparse.Namespace(**vars(args))
+    sub.no_cpu_baseline = True
     res = measure_single(args, "stress")
     if world == 1:
-        sub = argparse.Namespace(**vars(args))
-        sub.no_cpu_baseline = True
         res["wideband"] = _sub_line(measure_single(sub, "wideband"))
         res["batched"] = _sub_line(measure_batched(sub))
         res["served"] = _served_summary(measure_served(sub, loads=(0.5, 0.75)))
@@ -495,7 +495,9 @@ def _served_summary(r):
                 "saturation_ms_s": m["saturation_ms_s"],
                 "by_load": [{k: x[k] for k in ("rho", "offered_chunks_per_s", "completed", "rejected",
                                                 "p50_ms", "p99_ms", "max_ms", "deadline_miss_frac",
-                                                "p99_from_arrival_ms", "submit_lag_p99_ms")}
+                                                "p99_from_arrival_ms", "submit_lag_p99_ms",
+                                                "service_p99_ms", "service_max_ms", "graph_captures",
+                                                "buffer_generations", "clocks")}
                             for x in m["by_load"]]}
     return {"workload": r["config"]["workload"], "lanes": r["config"]["lanes"],
             "max_batch": r["config"]["max_batch"], "value": r["value"], "unit": UNIT,
